@@ -1,0 +1,119 @@
+"""Pins of the oracle's two-sided Lanczos approximation (Sec. 2) and error estimate (Sec. 4):
+biorthogonality and the projection identity, exact termination on free-field plane waves
+(closed form), exactness at k = n with re-biorthogonalisation, and convergence of the
+derivative through Eq. (2.6) to the Frechet derivative."""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle import dirac as od
+from oracle import free_field as ff
+from oracle import sign as osg
+from oracle import tsl as ot
+from tests.helpers import oracle_ops, relerr
+
+
+def _free(dims):
+    lat = od.Lattice(dims)
+    return lat, np.tile(np.eye(3, dtype=complex), (4, lat.V, 1, 1))
+
+
+def _plane_wave(lat, seed, nmodes=1):
+    """sum of nmodes plane waves exp(i p.x) chi_p (antiperiodic p_t), random spinors chi."""
+    rng = np.random.default_rng(seed)
+    t, z, y, x = np.meshgrid(np.arange(lat.nt), np.arange(lat.nz), np.arange(lat.ny), np.arange(lat.nx), indexing="ij")
+    psi = np.zeros((lat.nt, lat.nz, lat.ny, lat.nx, 4, 3), complex)
+    for _ in range(nmodes):
+        n = [rng.integers(0, e) for e in (lat.nx, lat.ny, lat.nz, lat.nt)]
+        ph = 2 * np.pi * (n[0] * x / lat.nx + n[1] * y / lat.ny + n[2] * z / lat.nz + (n[3] + 0.5) * t / lat.nt)
+        chi = rng.standard_normal((4, 3)) + 1j * rng.standard_normal((4, 3))
+        psi += np.exp(1j * ph)[..., None, None] * chi
+    return lat.flat(psi).ravel()
+
+
+def test_biorthogonality_and_projection():
+    dims, mu, k = (4, 2, 2, 2), 0.3, 12
+    U = syn.gauge_field(dims, 0.4, 3)
+    lat, A, Ah, E, Eh = oracle_ops(dims, U, mu)
+    x = syn.gaussian_source(dims, 5).ravel()
+    r = ot.tsl(A, Ah, x / np.linalg.norm(x), x / np.linalg.norm(x), k)
+    V, W, T = r["V"], r["W"], r["T"]
+    assert np.abs(W.conj() @ V.T - np.eye(k)).max() < 1e-12
+    AV = np.array([A(v) for v in V])
+    assert np.abs(W.conj() @ AV.T - T).max() < 1e-12
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_plane_wave_sign_is_exact_at_k2(mu):
+    """H(p) on a plane wave acts on a 4-spinor with two eigenvalues +-sqrt(z(p)):
+    the Krylov space has dimension 2, so k = 2 reproduces the closed form."""
+    lat, U = _free((4, 4, 2, 2))
+    A = lambda v: od.apply_H(lat, U, v, mu).ravel()      # noqa: E731
+    Ah = lambda v: od.apply_Hdag(lat, U, v, mu).ravel()  # noqa: E731
+    x = _plane_wave(lat, 3)
+    y, r = ot.tsl_sign(A, Ah, x, 2)
+    assert relerr(y, ff.free_sign(lat, x, mu).ravel()) < 1e-13
+
+
+@pytest.mark.parametrize("mu", [0.3, 0.6])
+def test_plane_wave_derivative_is_exact_at_k4(mu):
+    """On a plane wave B = [[H, dH/dmu], [0, H]] has two 2x2 Jordan blocks (Eq. (3.2)):
+    k = 4 reproduces the closed-form mu derivative through Eq. (2.6)."""
+    lat, U = _free((4, 4, 2, 2))
+    A = lambda v: od.apply_H(lat, U, v, mu).ravel()                # noqa: E731
+    Ah = lambda v: od.apply_Hdag(lat, U, v, mu).ravel()            # noqa: E731
+    E = lambda v: od.apply_dH_dmu(lat, U, v, mu).ravel()           # noqa: E731
+    Eh = lambda v: od.apply_dH_dmu_dag(lat, U, v, mu).ravel()      # noqa: E731
+    x = _plane_wave(lat, 4)
+    yd, ys, r = ot.tsl_sign_derivative(A, Ah, E, Eh, x, 4)
+    assert relerr(ys, ff.free_sign(lat, x, mu).ravel()) < 1e-12
+    assert relerr(yd, ff.free_sign_dmu(lat, x, mu).ravel()) < 1e-11
+
+
+def test_two_plane_waves_need_k4():
+    lat, U = _free((4, 4, 2, 2))
+    mu = 0.3
+    A = lambda v: od.apply_H(lat, U, v, mu).ravel()      # noqa: E731
+    Ah = lambda v: od.apply_Hdag(lat, U, v, mu).ravel()  # noqa: E731
+    x = _plane_wave(lat, 8, nmodes=2)
+    ref = ff.free_sign(lat, x, mu).ravel()
+    y2, _ = ot.tsl_sign(A, Ah, x, 2)
+    y4, _ = ot.tsl_sign(A, Ah, x, 4)
+    assert relerr(y2, ref) > 1e-3
+    assert relerr(y4, ref) < 1e-12
+
+
+def test_exact_at_full_dimension_with_rebiorthogonalisation():
+    dims, mu = (2, 2, 2, 2), 0.3
+    U = syn.gauge_field(dims, 0.4, 3)
+    lat, A, Ah, E, Eh = oracle_ops(dims, U, mu)
+    x = syn.gaussian_source(dims, 5).ravel()
+    y, r = ot.tsl_sign(A, Ah, x, lat.n, rebiorth=True)
+    assert relerr(y, osg.sign_schur(od.dense_H(lat, U, mu)) @ x) < 1e-10
+
+
+def test_derivative_converges_to_frechet():
+    dims, mu = (4, 2, 2, 2), 0.3
+    U = syn.gauge_field(dims, 0.2, 3)
+    lat, A, Ah, E, Eh = oracle_ops(dims, U, mu)
+    x = syn.gaussian_source(dims, 5).ravel()
+    H = od.dense_H(lat, U, mu)
+    L = osg.frechet_sylvester(H, od.dense_dH_dmu(lat, U, mu))
+    errs = []
+    for k in (80, 200):
+        yd, ys, r = ot.tsl_sign_derivative(A, Ah, E, Eh, x, k)
+        errs.append(relerr(yd, L @ x))
+    assert errs[1] < 0.01 * errs[0]
+    assert errs[1] < 1e-3
+
+
+def test_error_estimate_small_on_exact_case():
+    lat, U = _free((4, 4, 2, 2))
+    mu = 0.3
+    A = lambda v: od.apply_H(lat, U, v, mu).ravel()      # noqa: E731
+    Ah = lambda v: od.apply_Hdag(lat, U, v, mu).ravel()  # noqa: E731
+    x = _plane_wave(lat, 9)
+    assert ot.error_estimate(A, Ah, x, 2) < 1e-13
+    E = lambda v: od.apply_dH_dmu(lat, U, v, mu).ravel()           # noqa: E731
+    Eh = lambda v: od.apply_dH_dmu_dag(lat, U, v, mu).ravel()      # noqa: E731
+    assert ot.error_estimate_derivative(A, Ah, E, Eh, x, 4) < 1e-11
