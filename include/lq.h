@@ -1,0 +1,190 @@
+/*
+ * lq.h -- C ABI of the GB300 library for two-sided-Lanczos approximations of the
+ * matrix sign function sgn(H(mu)) x and of its derivative d_t sgn(H(mu)) x, where
+ * H(mu) = gamma5 Dw(mu) is the finite-density Wilson kernel of the overlap operator
+ * (Puhr & Buividovich, Lattice 2016: Sec. 1, Eq. (1.1); the derivative through
+ * Mathias' block identity, Sec. 2, Eqs. (2.5)-(2.6)).
+ *
+ * Conventions shared by every entry point
+ * ---------------------------------------
+ *  Lattice  dims (nt, nx, ny, nz); V = nt*nx*ny*nz; site s = x + nx*(y + ny*(z + nz*t)).
+ *  Spinor   colour-spinor field of n = 12 V complex numbers, index 12*s + 3*spin + colour,
+ *           stored as interleaved complex128 (re, im) doubles: double[V][4][3][2].
+ *           A batch of nsrc fields is double[nsrc][V][4][3][2].  The boundary always
+ *           carries FP64 values; the internal precision is set by lq_lattice_desc.precision.
+ *  Gauge    U_nu(s) in SU(3) (nu = 0..3 = x, y, z, t; link s -> s + nu-hat), row-major,
+ *           interleaved complex128: double[4][V][3][3][2].
+ *  Operator (Dw psi)(s) = (4r + m_w) psi(s) - 1/2 sum_nu [ f+ (r - g_nu) U_nu(s) psi(s+nu)
+ *           + f- (r + g_nu) U_nu(s-nu)^dag psi(s-nu) ],  f+- = exp(+-mu) on time hops, 1
+ *           otherwise; a hop across the time boundary carries -1 when t_antiperiodic;
+ *           chiral gamma basis, gamma5 = diag(1, 1, -1, -1); H = gamma5 Dw; H^dag = H(-mu).
+ *  Memory   every pointer argument may point to host memory (pageable or pinned) or to
+ *           device memory of the context's GPU; the library detects which and stages host
+ *           data through buffers reserved by lq_reserve.  The caller owns every buffer it
+ *           passes; the library owns the context, its device copy of the gauge field, the
+ *           direction field, the Krylov workspace and the deflation space.
+ *  Streams  `stream` is a cudaStream_t (0 = legacy default stream).  Entry points that
+ *           return a report (lq_report) synchronise the stream before returning; the others
+ *           are asynchronous on the stream.
+ *  Errors   every int-returning function returns LQ_OK (0) or a negative LQ_ERR_* code;
+ *           lq_last_error() gives a one-line description.  Soft, per-source failures
+ *           (Lanczos breakdown, Newton not converged) are reported in lq_report.status and do
+ *           not fail the call.
+ *  Threads  a context is not thread safe; use one context per host thread.
+ */
+#ifndef LQ_H
+#define LQ_H
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return / status codes ---------------------------------------------------------- */
+#define LQ_OK               0
+#define LQ_ERR_ARG         -1   /* invalid argument (null pointer, bad size, r != 1, ...)   */
+#define LQ_ERR_LAYOUT      -2   /* pointer in an unsupported memory space / misaligned       */
+#define LQ_ERR_OOM         -3   /* device allocation failed in lq_reserve / uploads          */
+#define LQ_ERR_CUDA        -4   /* a CUDA runtime call failed                                */
+#define LQ_ERR_BREAKDOWN   -5   /* (status) serious Lanczos breakdown: k_eff < k             */
+#define LQ_ERR_NEWTON      -6   /* (status) Newton sign iteration did not converge           */
+#define LQ_ERR_TIMEOUT     -7   /* a bounded device-side wait gave up                        */
+#define LQ_ERR_NOT_READY   -8   /* gauge / workspace / direction / deflation not set         */
+#define LQ_ERR_NONFINITE   -9   /* (status) NaN or Inf met in a reduction                    */
+
+/* ---- internal precision ------------------------------------------------------------- */
+#define LQ_FP64   0   /* stencil, vectors, dots, scalars and Newton all in FP64                */
+#define LQ_MIXED  1   /* FP32 links, spinors and stencil (FP32 accumulation); FP64 compensated
+                         dots, FP64 Lanczos coefficients, FP64 Newton, FP64 recombination      */
+
+/* ---- derivative directions (d_t of Eq. (2.5)) --------------------------------------- */
+#define LQ_DIR_MU   0   /* d/dmu: field unused                                               */
+#define LQ_DIR_SU3  1   /* U_nu(x) -> exp(i t Omega_nu(x)) U_nu(x), Omega = sum_a w^a lambda_a/2;
+                           field = double[4][V][8] coefficients w^a_nu(x)                      */
+#define LQ_DIR_U1   2   /* U_nu(x) -> exp(i t theta_nu(x)) U_nu(x) (the external U(1) field of
+                           Sec. 4); field = double[4][V]                                       */
+
+typedef struct lq_ctx lq_ctx;
+
+typedef struct {
+    int nt, nx, ny, nz;    /* lattice extents, each >= 1                                     */
+    double m_w;            /* Wilson mass (the paper's workloads: -2.0)                       */
+    double r;              /* Wilson parameter; only r = 1 is supported (spin projectors)     */
+    double mu;             /* chemical potential                                              */
+    int t_antiperiodic;    /* 1: antiperiodic in time (default), 0: periodic                  */
+    int precision;         /* LQ_FP64 or LQ_MIXED                                             */
+} lq_lattice_desc;
+
+typedef struct {
+    int kmax;              /* Krylov depth k = number of applications of the operator, and the
+                              dimension of the projected tridiagonal T_k; 1 <= k <= reserved  */
+    double breakdown_tol;  /* serious breakdown if |<w^,v^>| < tol |w^| |v^| (default 1e-14)   */
+    int newton_max_iter;   /* cap on Newton iterations for sgn(T_k) (default 50)              */
+    double newton_tol;     /* stop when ||X_{i+1}-X_i||_F <= tol ||X_{i+1}||_F (default 1e-13) */
+    int deflate;           /* reserved (must be 0 in this version)                            */
+} lq_opts;
+
+typedef struct {
+    int k_eff;             /* dimension of T actually built (< kmax after a breakdown)        */
+    int newton_iters;      /* Newton iterations taken on sgn(T_k)                             */
+    int status;            /* LQ_OK, LQ_ERR_BREAKDOWN, LQ_ERR_NEWTON or LQ_ERR_NONFINITE      */
+    int reserved;
+    double newton_change;  /* last relative Frobenius change of the Newton iterate            */
+    double x_norm;         /* |x| of the source                                               */
+} lq_report;
+
+typedef struct {
+    int kind;              /* LQ_DIR_MU, LQ_DIR_SU3 or LQ_DIR_U1                              */
+    const double* field;   /* see the LQ_DIR_* descriptions; host or device memory           */
+} lq_direction;
+
+/* Fill *opts with the defaults named above (kmax = 0 must still be set by the caller). */
+void lq_default_opts(lq_opts* opts);
+
+/* Create a context on the current CUDA device for the lattice and Wilson parameters of
+ * Sec. 1 (Eq. (1.1)).  Allocates nothing on the device.  Returns LQ_ERR_ARG for extents
+ * < 1, r != 1 or an unknown precision. */
+int  lq_create(const lq_lattice_desc* desc, lq_ctx** out);
+void lq_destroy(lq_ctx* ctx);
+const char* lq_last_error(const lq_ctx* ctx);
+
+/* Upload the SU(3) gauge field (layout above, host or device).  Allocates the device copy
+ * in the internal layout and precision on first use.  Asynchronous on `stream`. */
+int  lq_upload_gauge(lq_ctx* ctx, const double* U, void* stream);
+
+/* Change mu (Eq. (1.1)) without re-uploading the gauge field. */
+int  lq_set_mu(lq_ctx* ctx, double mu);
+
+/* Reserve all workspace for Krylov depth <= kmax and <= nsrc sources per call; `block` = 1
+ * reserves for the derivative path (2n-dimensional block vectors of Eq. (2.6)), 0 for the
+ * sign path only.  No later call allocates device memory.  LQ_ERR_OOM on failure. */
+int  lq_reserve(lq_ctx* ctx, int kmax, int nsrc, int block);
+
+/* y = H(mu) x (dagger = 0) or y = H(mu)^dag x = H(-mu) x (dagger = 1) for nsrc fields
+ * (Eq. (1.1)); the single stencil application.  Needs the gauge field and lq_reserve(nsrc). */
+int  lq_apply_H(lq_ctx* ctx, const double* x, double* y, int nsrc, int dagger, void* stream);
+
+/* Set the derivative direction d_t (Eq. (2.5)): for LQ_DIR_SU3 / LQ_DIR_U1 the library
+ * builds dU/dt = i Omega U on the device.  Must follow lq_upload_gauge. */
+int  lq_set_direction(lq_ctx* ctx, const lq_direction* dir, void* stream);
+
+/* Apply the block operator B = [[A, dA], [0, A]] of Eq. (2.5) with A = H(mu) and dA the
+ * derivative of H along the current direction (dagger = 0), or B^dag (dagger = 1), to
+ * nsrc stacked vectors (top, bottom), each half in the spinor layout. */
+int  lq_apply_block(lq_ctx* ctx, const double* x_top, const double* x_bot,
+                    double* y_top, double* y_bot, int nsrc, int dagger, void* stream);
+
+/* y ~ sgn(H(mu)) x by the two-sided Lanczos method of Sec. 2: k steps from
+ * v_1 = w_1 = x/|x|, then y = |x| V_k sgn(T_k) e_1 with sgn(T_k) from a scaled FP64 Newton
+ * iteration on the device.  x, y: nsrc fields.  report: host array of nsrc entries (may be
+ * NULL).  Synchronises `stream`. */
+int  lq_sign_apply(lq_ctx* ctx, const double* x, double* y, int nsrc,
+                   const lq_opts* opts, lq_report* report, void* stream);
+
+/* Eq. (2.6): sgn(B)(0, x) = (d_t sgn(H) x, sgn(H) x) by the two-sided Lanczos method on the
+ * 2n x 2n block operator B of Eq. (2.5), with v_1 = (0, x)/|x| and w_1 = (x, x)/|x|, along
+ * `dir` (which replaces the current direction).  y_sign, y_deriv: nsrc fields each.
+ * Needs lq_reserve(..., block = 1).  Synchronises `stream`. */
+int  lq_sign_derivative_apply(lq_ctx* ctx, const lq_direction* dir, const double* x,
+                              double* y_sign, double* y_deriv, int nsrc,
+                              const lq_opts* opts, lq_report* report, void* stream);
+
+/* Opt-in timing of the library's own kernels with CUDA events recorded on the launch
+ * stream (no effect on results).  Enabling resets the totals.  Times are accumulated when a
+ * reporting call synchronises its stream.  launches counts every kernel the library has
+ * launched since the last reset, whether or not timing is enabled. */
+typedef struct {
+    int enabled;
+    int reserved;
+    long long launches;        /* kernel launches since the last reset                      */
+    double hop_ms;             /* stencil kernel (H, H^dag, block operator; Eq. (1.1)/(2.5)) */
+    long long hop_launches;
+    double update_ms;          /* Lanczos three-term update + omega dot                      */
+    long long update_launches;
+    double newton_ms;          /* projected sign sgn(T_k), all Newton kernels               */
+    long long newton_iterations;
+    double other_ms;           /* start vectors, recombination, layout conversion            */
+    long long other_launches;
+} lq_profile;
+
+int  lq_profile_enable(lq_ctx* ctx, int enable);
+int  lq_profile_read(lq_ctx* ctx, lq_profile* out);
+
+/* Copy the projected tridiagonal T_k of source `src` from the last lq_sign_apply /
+ * lq_sign_derivative_apply (Sec. 2): alpha[j] = T[j][j], beta[j] = T[j][j+1],
+ * delta[j] = T[j+1][j] (real, > 0).  alpha, beta: host double[k][2] (complex); delta:
+ * host double[k].  Entries beyond the source's k_eff are zero.  Synchronous. */
+int  lq_tsl_coefficients(lq_ctx* ctx, int src, int k, double* alpha, double* beta, double* delta);
+
+/* Batched dense FP64 sign of nb complex k x k matrices by the scaled Newton iteration
+ * X <- (m X + (m X)^{-1})/2, m = sqrt(||X^{-1}||_F / ||X||_F) (Higham 2008, ch. 5; the
+ * projected step of the Lanczos approximation, Sec. 2).  X, S: double[nb][k][k][2]
+ * row-major, device memory only.  Uses workspace reserved by lq_reserve(ctx, kmax >= k,
+ * nsrc >= nb, ...).  iters (host, nb entries, may be NULL) receives the iteration counts.
+ * Synchronises `stream`. */
+int  lq_newton_sign(lq_ctx* ctx, const double* X, double* S, int k, int nb,
+                    int max_iter, double tol, int* iters, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LQ_H */

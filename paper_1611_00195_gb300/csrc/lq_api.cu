@@ -1,0 +1,627 @@
+// Host implementation of the C ABI declared in include/lq.h.
+#include <cuda_runtime.h>
+
+#include <cmath>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "lq_internal.cuh"
+#include "lq_launch.h"
+
+using namespace lq;
+
+namespace {
+
+int set_err(lq_ctx* c, int code, const std::string& msg) {
+    if (c) c->err = msg;
+    return code;
+}
+
+#define LQ_CUDA(ctx, call)                                                                  \
+    do {                                                                                    \
+        cudaError_t e_ = (call);                                                            \
+        if (e_ != cudaSuccess)                                                              \
+            return set_err(ctx, LQ_ERR_CUDA, std::string(#call) + ": " + cudaGetErrorString(e_)); \
+    } while (0)
+
+// ---- opt-in kernel timing ---------------------------------------------------------------
+enum { PC_HOP = 0, PC_UPDATE = 1, PC_NEWTON = 2, PC_OTHER = 3 };
+
+cudaEvent_t prof_event(lq_ctx* c) {
+    if (c->ev_used == c->ev_pool.size()) {
+        cudaEvent_t e;
+        if (cudaEventCreate(&e) != cudaSuccess) { cudaGetLastError(); return nullptr; }
+        c->ev_pool.push_back(e);
+    }
+    return c->ev_pool[c->ev_used++];
+}
+
+// Mark the start of a timed region of class `cls`; returns the start event (or null).
+cudaEvent_t prof_begin(lq_ctx* c, cudaStream_t st) {
+    if (!c->prof_on) return nullptr;
+    cudaEvent_t a = prof_event(c);
+    if (a) cudaEventRecord(a, st);
+    return a;
+}
+void prof_end(lq_ctx* c, int cls, cudaEvent_t a, cudaStream_t st, long long count = 1) {
+    c->prof_n[cls] += count;
+    if (!c->prof_on || !a) return;
+    cudaEvent_t b = prof_event(c);
+    if (!b) return;
+    cudaEventRecord(b, st);
+    c->pending.push_back({cls, a, b});
+}
+// After a stream synchronisation: fold the recorded pairs into the totals.
+void prof_collect(lq_ctx* c) {
+    for (auto& p : c->pending) {
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, p.a, p.b) == cudaSuccess) c->prof_ms[p.cls] += ms;
+        else cudaGetLastError();
+    }
+    c->pending.clear();
+    c->ev_used = 0;
+}
+
+// 1 = device (or managed) memory of this process, 0 = host memory, -1 = unusable.
+int is_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    cudaError_t e = cudaPointerGetAttributes(&at, p);
+    if (e != cudaSuccess) { cudaGetLastError(); return 0; }
+    if (at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged) return 1;
+    return 0;
+}
+
+template <typename T>
+int dalloc(lq_ctx* c, T** p, size_t count) {
+    if (*p) { cudaFree(*p); *p = nullptr; }
+    if (count == 0) count = 1;
+    cudaError_t e = cudaMalloc((void**)p, count * sizeof(T));
+    if (e != cudaSuccess) {
+        cudaGetLastError();
+        *p = nullptr;
+        return set_err(c, LQ_ERR_OOM, "cudaMalloc of " + std::to_string(count * sizeof(T)) + " bytes failed: " + cudaGetErrorString(e));
+    }
+    return LQ_OK;
+}
+
+void dfree(void* p) { if (p) cudaFree(p); }
+
+size_t fe(const lq_ctx* c) {  // Chunk elements of one field
+    return c->prec == LQ_FP64 ? field_elems<double>(c->V) : field_elems<float>(c->V);
+}
+size_t fb(const lq_ctx* c) {  // bytes of one field
+    return c->prec == LQ_FP64 ? field_bytes<double>(c->V) : field_bytes<float>(c->V);
+}
+size_t chunk_bytes(const lq_ctx* c) { return c->prec == LQ_FP64 ? sizeof(double2) : sizeof(float4); }
+
+
+// Copy n doubles from a caller buffer (host or device) into device memory.
+int stage_in(lq_ctx* c, double* dst, const double* src, size_t n, cudaStream_t st) {
+    LQ_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double), is_device_ptr(src) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    return LQ_OK;
+}
+int stage_out(lq_ctx* c, double* dst, const double* src, size_t n, cudaStream_t st) {
+    LQ_CUDA(c, cudaMemcpyAsync(dst, src, n * sizeof(double), is_device_ptr(dst) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    return LQ_OK;
+}
+
+// Hop factors (-1/2 of Dw included).  dagger = 0: H(mu); 1: H(mu)^dag = H(-mu).
+void op_factors(double mu, int dagger, double (&f)[4], double (&b)[4]) {
+    for (int nu = 0; nu < 3; ++nu) { f[nu] = -0.5; b[nu] = -0.5; }
+    const double m = dagger ? -mu : mu;
+    f[3] = -0.5 * std::exp(m);
+    b[3] = -0.5 * std::exp(-m);
+}
+// Derivative factors.  emode 1 (d/dmu): E = dH/dmu has f+ = e^mu, f- = -e^-mu on time hops;
+// E^dag = gamma5 W(conj f-, conj f+).  emode 2 (links Y): same factors as the operator.
+void der_factors(double mu, int emode, int dagger, double (&f)[4], double (&b)[4]) {
+    for (int nu = 0; nu < 4; ++nu) { f[nu] = 0.0; b[nu] = 0.0; }
+    if (emode == 1) {
+        if (!dagger) { f[3] = -0.5 * std::exp(mu); b[3] = 0.5 * std::exp(-mu); }
+        else { f[3] = 0.5 * std::exp(-mu); b[3] = -0.5 * std::exp(mu); }
+    } else if (emode == 2) {
+        op_factors(mu, dagger, f, b);
+    }
+}
+
+HopArgs base_hop(const lq_ctx* c) {
+    HopArgs a;
+    std::memset(&a, 0, sizeof(a));
+    for (int i = 0; i < 4; ++i) a.dims[i] = c->dims[i];
+    a.strides[0] = 1;
+    a.strides[1] = (size_t)c->dims[0];
+    a.strides[2] = (size_t)c->dims[0] * c->dims[1];
+    a.strides[3] = (size_t)c->dims[0] * c->dims[1] * c->dims[2];
+    a.V = c->V;
+    a.apbc = c->desc.t_antiperiodic ? 1 : 0;
+    a.diag = 4.0 * c->desc.r + c->desc.m_w;
+    a.U = c->U;
+    a.Y = c->Y;
+    return a;
+}
+
+void set_side(HopArgs& a, int side, const lq_ctx* c, int dagger, int emode) {
+    op_factors(c->desc.mu, dagger, a.a_fwd[side], a.a_bwd[side]);
+    der_factors(c->desc.mu, emode, dagger, a.e_fwd[side], a.e_bwd[side]);
+}
+
+int check_ready(lq_ctx* c, int nsrc, int need_block) {
+    if (!c) return LQ_ERR_ARG;
+    if (!c->gauge_ready) return set_err(c, LQ_ERR_NOT_READY, "gauge field not uploaded");
+    if (!c->basis) return set_err(c, LQ_ERR_NOT_READY, "workspace not reserved (lq_reserve)");
+    if (nsrc < 1 || nsrc > c->nsrc) return set_err(c, LQ_ERR_ARG, "nsrc must be in [1, reserved nsrc]");
+    if (need_block && !c->block) return set_err(c, LQ_ERR_NOT_READY, "workspace reserved without block = 1");
+    return LQ_OK;
+}
+
+int emode_of(const lq_ctx* c) {
+    if (c->dir_kind == LQ_DIR_MU) return 1;
+    if (c->dir_kind == LQ_DIR_SU3 || c->dir_kind == LQ_DIR_U1) return 2;
+    return 0;
+}
+
+// Run the Newton iteration to convergence on the batch in `a` (already initialised).
+int run_newton(lq_ctx* c, const NewtonArgs& a, cudaStream_t st, std::vector<double>& scal) {
+    scal.assign((size_t)a.nb * 16, 0.0);
+    for (int it = 0; it < a.max_iter; ++it) {
+        cudaEvent_t e = prof_begin(c, st);
+        LQ_CUDA(c, newton_iteration(a, st));
+        prof_end(c, PC_NEWTON, e, st);
+        c->launches += a.k + 3;
+        LQ_CUDA(c, cudaMemcpyAsync(scal.data(), a.scal, scal.size() * sizeof(double), cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(c, cudaStreamSynchronize(st));
+        bool all = true;
+        for (int b = 0; b < a.nb; ++b) all = all && scal[(size_t)b * 16 + NS_DONE] != 0.0;
+        if (all) break;
+    }
+    return LQ_OK;
+}
+
+NewtonArgs newton_args(lq_ctx* c, int k, int nb, int max_iter, double tol) {
+    NewtonArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.k = k;
+    a.nb = nb;
+    a.ld = c->kmax;
+    a.X = c->nx_X;
+    a.Y = c->nx_Y;
+    a.F = c->nx_F;
+    a.perm = c->nx_perm;
+    a.scal = c->nx_scal;
+    a.partials = c->nx_partials;
+    a.partial_stride = c->nx_partial_blocks;
+    a.counters = c->nx_counters;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    a.state = c->state;
+    a.alpha = c->alpha;
+    a.beta = c->beta;
+    a.delta = c->delta;
+    a.kmax = c->kmax;
+    return a;
+}
+
+void free_workspace(lq_ctx* c) {
+    void** ps[] = {&c->basis, &c->left, &c->rout, &c->lout, (void**)&c->io, (void**)&c->partials, (void**)&c->counters,
+                   (void**)&c->state, (void**)&c->alpha, (void**)&c->beta, (void**)&c->delta, (void**)&c->scale,
+                   (void**)&c->nx_X, (void**)&c->nx_Y, (void**)&c->nx_F, (void**)&c->nx_perm, (void**)&c->nx_scal,
+                   (void**)&c->nx_partials, (void**)&c->nx_counters};
+    for (void** p : ps) { dfree(*p); *p = nullptr; }
+    c->kmax = c->nsrc = c->block = 0;
+}
+
+// The Lanczos driver shared by lq_sign_apply (nf = 1) and lq_sign_derivative_apply (nf = 2).
+// The source is already staged in c->io (region 0, boundary layout); results go to the device
+// boundary-layout buffers y0 (field 0: sign, or top = derivative) and y1 (field 1: bottom = sign).
+int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report* rep,
+            double* y0, double* y1, cudaStream_t st) {
+    const int k = o->kmax;
+    const size_t F = fe(c);
+    const size_t vstride = (size_t)nf * F;        // Chunk elements per Krylov vector
+    const size_t sb = (size_t)c->kmax * vstride;  // per source: basis
+    const size_t sl = 3 * vstride;                // per source: left ring
+    const size_t sio = vstride;                   // per source: operator outputs
+    const size_t cb = chunk_bytes(c);
+    char* basis = reinterpret_cast<char*>(c->basis);
+    char* left = reinterpret_cast<char*>(c->left);
+    auto bvec = [&](int j) -> void* { return basis + (size_t)j * vstride * cb; };
+    auto lvec = [&](int j) -> void* { return left + (size_t)(j % 3) * vstride * cb; };
+
+    InitArgs ia;
+    std::memset(&ia, 0, sizeof(ia));
+    ia.V = c->V; ia.nsrc = nsrc; ia.x = c->io; ia.v1 = bvec(0); ia.w1 = lvec(0);
+    ia.src_stride_basis = sb; ia.src_stride_left = sl; ia.state = c->state;
+    ia.partials = c->partials; ia.partial_stride = c->partial_blocks; ia.counters = c->counters;
+    ia.breakdown_tol = o->breakdown_tol;
+    cudaEvent_t e0 = prof_begin(c, st);
+    LQ_CUDA(c, launch_tsl_init(c->prec, nf, ia, st));
+    prof_end(c, PC_OTHER, e0, st);
+    c->launches += 1;
+
+    HopArgs h = base_hop(c);
+    h.nsrc = nsrc; h.nsides = 2; h.side0 = 0;
+    set_side(h, 0, c, 0, emode);
+    set_side(h, 1, c, 1, emode);
+    h.state = c->state; h.partials = c->partials; h.partial_stride = c->partial_blocks; h.counters = c->counters;
+    h.alpha = c->alpha; h.scale = c->scale; h.kmax = c->kmax; h.kmax_run = k;
+    h.src_stride_in[0] = sb; h.src_stride_in[1] = sl;
+    h.src_stride_out[0] = sio; h.src_stride_out[1] = sio;
+    h.out[0] = c->rout; h.out[1] = c->lout;
+
+    UpdArgs u;
+    std::memset(&u, 0, sizeof(u));
+    u.nelem = vstride; u.nsrc = nsrc; u.rout = c->rout; u.lout = c->lout;
+    u.src_stride_io = sio; u.src_stride_basis = sb; u.src_stride_left = sl;
+    u.state = c->state; u.partials = c->partials; u.partial_stride = c->partial_blocks; u.counters = c->counters;
+    u.beta = c->beta; u.delta = c->delta; u.kmax = c->kmax;
+
+    for (int j = 0; j < k; ++j) {
+        h.j = j;
+        h.in[0] = bvec(j);
+        h.in[1] = lvec(j);
+        cudaEvent_t eh = prof_begin(c, st);
+        LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));
+        prof_end(c, PC_HOP, eh, st);
+        c->launches += 1;
+        if (j < k - 1) {
+            u.j = j;
+            u.v_cur = bvec(j); u.v_prev = bvec(j > 0 ? j - 1 : j); u.v_next = bvec(j + 1);
+            u.w_cur = lvec(j); u.w_prev = lvec(j > 0 ? j - 1 : j); u.w_next = lvec(j + 1);
+            cudaEvent_t eu = prof_begin(c, st);
+            LQ_CUDA(c, launch_update(c->prec, u, st));
+            prof_end(c, PC_UPDATE, eu, st);
+            c->launches += 1;
+        }
+    }
+
+    NewtonArgs na = newton_args(c, k, nsrc, o->newton_max_iter, o->newton_tol);
+    LQ_CUDA(c, newton_init_tridiag(na, st));
+    c->launches += 1;
+    std::vector<double> scal;
+    int r = run_newton(c, na, st, scal);
+    if (r) return r;
+
+    RecArgs ra;
+    std::memset(&ra, 0, sizeof(ra));
+    ra.V = c->V; ra.nsrc = nsrc; ra.basis = c->basis; ra.src_stride_basis = sb; ra.vec_stride = vstride;
+    ra.state = c->state; ra.scale = c->scale; ra.kmax = c->kmax; ra.newton_X = c->nx_X; ra.ldx = c->kmax;
+    ra.y0 = y0; ra.y1 = y1;
+    cudaEvent_t er = prof_begin(c, st);
+    LQ_CUDA(c, launch_recombine(c->prec, nf, ra, st));
+    prof_end(c, PC_OTHER, er, st);
+    c->launches += 1;
+
+    std::vector<TslState> hs(nsrc);
+    LQ_CUDA(c, cudaMemcpyAsync(hs.data(), c->state, sizeof(TslState) * nsrc, cudaMemcpyDeviceToHost, st));
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    prof_collect(c);
+    if (rep) {
+        for (int s = 0; s < nsrc; ++s) {
+            lq_report& R = rep[s];
+            std::memset(&R, 0, sizeof(R));
+            R.k_eff = hs[s].k_eff;
+            R.x_norm = hs[s].xnorm;
+            R.newton_iters = (int)scal[(size_t)s * 16 + NS_ITERS];
+            R.newton_change = scal[(size_t)s * 16 + NS_CHANGE];
+            const int ts = hs[s].status;
+            const int ns = (int)scal[(size_t)s * 16 + NS_STATUS];
+            R.status = ts < 0 ? ts : (ns != 0 ? ns : LQ_OK);
+        }
+    }
+    return LQ_OK;
+}
+
+int check_opts(lq_ctx* c, const lq_opts* o) {
+    if (!o) return set_err(c, LQ_ERR_ARG, "null opts");
+    if (o->kmax < 1 || o->kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "opts.kmax must be in [1, reserved kmax]");
+    if (o->newton_max_iter < 1 || !(o->newton_tol > 0.0) || !(o->breakdown_tol >= 0.0)) return set_err(c, LQ_ERR_ARG, "invalid Newton / breakdown options");
+    if (o->deflate != 0) return set_err(c, LQ_ERR_ARG, "deflation is not available in this entry point");
+    return LQ_OK;
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------------
+extern "C" {
+
+void lq_default_opts(lq_opts* o) {
+    if (!o) return;
+    o->kmax = 0;
+    o->breakdown_tol = 1e-14;
+    o->newton_max_iter = 50;
+    o->newton_tol = 1e-13;
+    o->deflate = 0;
+}
+
+int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
+    if (!d || !out) return LQ_ERR_ARG;
+    *out = nullptr;
+    if (d->nt < 1 || d->nx < 1 || d->ny < 1 || d->nz < 1) return LQ_ERR_ARG;
+    if (d->r != 1.0) return LQ_ERR_ARG;
+    if (d->precision != LQ_FP64 && d->precision != LQ_MIXED) return LQ_ERR_ARG;
+    if (!std::isfinite(d->mu) || !std::isfinite(d->m_w)) return LQ_ERR_ARG;
+    const double vol = (double)d->nt * d->nx * d->ny * d->nz;
+    if (vol * 12.0 > 4.0e9) return LQ_ERR_ARG;
+    lq_ctx* c = new (std::nothrow) lq_ctx();
+    if (!c) return LQ_ERR_OOM;
+    c->desc = *d;
+    c->dims[0] = d->nx; c->dims[1] = d->ny; c->dims[2] = d->nz; c->dims[3] = d->nt;
+    c->V = (size_t)d->nt * d->nx * d->ny * d->nz;
+    c->prec = d->precision;
+    cudaGetDevice(&c->device);
+    *out = c;
+    return LQ_OK;
+}
+
+void lq_destroy(lq_ctx* c) {
+    if (!c) return;
+    free_workspace(c);
+    dfree(c->U);
+    dfree(c->Ub);
+    dfree(c->Y);
+    dfree(c->dir_scratch);
+    for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
+    delete c;
+}
+
+const char* lq_last_error(const lq_ctx* c) { return c ? c->err.c_str() : "null context"; }
+
+int lq_upload_gauge(lq_ctx* c, const double* U, void* stream) {
+    if (!c || !U) return set_err(c, LQ_ERR_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = c->V * 4 * 9 * 2;
+    if (!c->Ub) { int r = dalloc(c, &c->Ub, n); if (r) return r; }
+    if (!c->U) {
+        size_t cb = (c->prec == LQ_FP64 ? sizeof(double2) : sizeof(float2)) * c->V * 36;
+        void* p = nullptr;
+        if (cudaMalloc(&p, cb) != cudaSuccess) { cudaGetLastError(); return set_err(c, LQ_ERR_OOM, "gauge allocation failed"); }
+        c->U = p;
+    }
+    int r = stage_in(c, c->Ub, U, n, st);
+    if (r) return r;
+    LQ_CUDA(c, launch_links_internal(c->prec, c->Ub, c->U, c->V, st));
+    c->launches += 1;
+    c->gauge_ready = true;
+    if (c->dir_kind == LQ_DIR_SU3 || c->dir_kind == LQ_DIR_U1) c->dir_kind = -1;   // Y is stale
+    return LQ_OK;
+}
+
+int lq_set_mu(lq_ctx* c, double mu) {
+    if (!c || !std::isfinite(mu)) return set_err(c, LQ_ERR_ARG, "invalid mu");
+    c->desc.mu = mu;
+    return LQ_OK;
+}
+
+int lq_reserve(lq_ctx* c, int kmax, int nsrc, int block) {
+    if (!c || kmax < 1 || nsrc < 1 || (block != 0 && block != 1)) return set_err(c, LQ_ERR_ARG, "invalid reserve arguments");
+    free_workspace(c);
+    const int nf = block ? 2 : 1;
+    const size_t fbytes = fb(c);
+    int r;
+    auto alloc_fields = [&](void** p, size_t nfields) -> int {
+        size_t bytes = nfields * fbytes;
+        if (cudaMalloc(p, bytes) != cudaSuccess) {
+            cudaGetLastError();
+            *p = nullptr;
+            return set_err(c, LQ_ERR_OOM, "workspace allocation of " + std::to_string(bytes) + " bytes failed");
+        }
+        return LQ_OK;
+    };
+    if ((r = alloc_fields(&c->basis, (size_t)nsrc * kmax * nf))) { free_workspace(c); return r; }
+    if ((r = alloc_fields(&c->left, (size_t)nsrc * 3 * nf))) { free_workspace(c); return r; }
+    if ((r = alloc_fields(&c->rout, (size_t)nsrc * nf))) { free_workspace(c); return r; }
+    if ((r = alloc_fields(&c->lout, (size_t)nsrc * nf))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->io, (size_t)3 * nsrc * c->V * 24))) { free_workspace(c); return r; }
+    size_t pb = (c->V + kHopThreads - 1) / kHopThreads;
+    pb = std::max(pb, (size_t)kUpdBlocksPerSrc);
+    pb = std::max(pb, (c->V + kUpdThreads - 1) / kUpdThreads);
+    c->partial_blocks = pb;
+    if ((r = dalloc(c, &c->partials, (size_t)nsrc * pb * 8))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->counters, (size_t)4 * nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->state, (size_t)nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->alpha, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->beta, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->delta, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->scale, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    const size_t kk = (size_t)kmax * kmax;
+    if ((r = dalloc(c, &c->nx_X, (size_t)nsrc * kk))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nx_Y, (size_t)nsrc * kk))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nx_F, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nx_perm, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nx_scal, (size_t)nsrc * 16))) { free_workspace(c); return r; }
+    c->nx_partial_blocks = (kk + 255) / 256;
+    if ((r = dalloc(c, &c->nx_partials, (size_t)nsrc * c->nx_partial_blocks * 4))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nx_counters, (size_t)3 * nsrc))) { free_workspace(c); return r; }
+    LQ_CUDA(c, cudaMemset(c->counters, 0, sizeof(int) * 4 * nsrc));
+    LQ_CUDA(c, cudaMemset(c->nx_counters, 0, sizeof(int) * 3 * nsrc));
+    LQ_CUDA(c, cudaMemset(c->nx_scal, 0, sizeof(double) * 16 * nsrc));
+    LQ_CUDA(c, cudaMemset(c->state, 0, sizeof(TslState) * nsrc));
+    c->kmax = kmax;
+    c->nsrc = nsrc;
+    c->block = block;
+    return LQ_OK;
+}
+
+int lq_apply_H(lq_ctx* c, const double* x, double* y, int nsrc, int dagger, void* stream) {
+    if (!c || !x || !y) return set_err(c, LQ_ERR_ARG, "null argument");
+    int r = check_ready(c, nsrc, 0);
+    if (r) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)nsrc * c->V * 24;
+    double* io = c->io;
+    if ((r = stage_in(c, io, x, n, st))) return r;
+    LQ_CUDA(c, launch_to_internal(c->prec, io, c->rout, c->V, nsrc, st));
+    c->launches += 3;
+    HopArgs a = base_hop(c);
+    a.nsrc = nsrc;
+    a.nsides = 1;
+    a.side0 = 0;
+    set_side(a, 0, c, dagger ? 1 : 0, 0);
+    a.in[0] = c->rout;
+    a.out[0] = c->lout;
+    a.src_stride_in[0] = fe(c);
+    a.src_stride_out[0] = fe(c);
+    LQ_CUDA(c, launch_hop(c->prec, a, 1, 0, false, st));
+    LQ_CUDA(c, launch_to_boundary(c->prec, c->lout, io, c->V, nsrc, st));
+    return stage_out(c, y, io, n, st);
+}
+
+int lq_set_direction(lq_ctx* c, const lq_direction* d, void* stream) {
+    if (!c || !d) return set_err(c, LQ_ERR_ARG, "null argument");
+    if (d->kind == LQ_DIR_MU) { c->dir_kind = LQ_DIR_MU; return LQ_OK; }
+    if (d->kind != LQ_DIR_SU3 && d->kind != LQ_DIR_U1) return set_err(c, LQ_ERR_ARG, "unknown direction kind");
+    if (!d->field) return set_err(c, LQ_ERR_ARG, "direction field is null");
+    if (!c->gauge_ready) return set_err(c, LQ_ERR_NOT_READY, "gauge field not uploaded");
+    cudaStream_t st = (cudaStream_t)stream;
+    int r;
+    if (!c->dir_scratch && (r = dalloc(c, &c->dir_scratch, c->V * 4 * 8))) return r;
+    if (!c->Y) {
+        size_t cb = (c->prec == LQ_FP64 ? sizeof(double2) : sizeof(float2)) * c->V * 36;
+        void* p = nullptr;
+        if (cudaMalloc(&p, cb) != cudaSuccess) { cudaGetLastError(); return set_err(c, LQ_ERR_OOM, "direction allocation failed"); }
+        c->Y = p;
+    }
+    const size_t n = c->V * 4 * (d->kind == LQ_DIR_SU3 ? 8 : 1);
+    if ((r = stage_in(c, c->dir_scratch, d->field, n, st))) return r;
+    LQ_CUDA(c, launch_direction(c->prec, c->Ub, c->dir_scratch, d->kind, c->Y, c->V, st));
+    c->launches += 1;
+    c->dir_kind = d->kind;
+    return LQ_OK;
+}
+
+int lq_apply_block(lq_ctx* c, const double* xt, const double* xb, double* yt, double* yb, int nsrc, int dagger, void* stream) {
+    if (!c || !xt || !xb || !yt || !yb) return set_err(c, LQ_ERR_ARG, "null argument");
+    int r = check_ready(c, nsrc, 1);
+    if (r) return r;
+    if (c->dir_kind < 0) return set_err(c, LQ_ERR_NOT_READY, "no derivative direction set");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)c->V * 24;
+    double* io = c->io;
+    // stage as [src][2][V][12]: top, bottom
+    for (int s = 0; s < nsrc; ++s) {
+        if ((r = stage_in(c, io + (2 * (size_t)s) * n, xt + (size_t)s * n, n, st))) return r;
+        if ((r = stage_in(c, io + (2 * (size_t)s + 1) * n, xb + (size_t)s * n, n, st))) return r;
+    }
+    LQ_CUDA(c, launch_to_internal(c->prec, io, c->rout, c->V, 2 * nsrc, st));
+    c->launches += 3;
+    const int em = emode_of(c);
+    HopArgs a = base_hop(c);
+    a.nsrc = nsrc;
+    a.nsides = 1;
+    a.side0 = dagger ? 1 : 0;
+    set_side(a, a.side0, c, dagger ? 1 : 0, em);
+    a.in[a.side0] = c->rout;
+    a.out[a.side0] = c->lout;
+    a.src_stride_in[a.side0] = 2 * fe(c);
+    a.src_stride_out[a.side0] = 2 * fe(c);
+    LQ_CUDA(c, launch_hop(c->prec, a, 2, em, false, st));
+    LQ_CUDA(c, launch_to_boundary(c->prec, c->lout, io, c->V, 2 * nsrc, st));
+    for (int s = 0; s < nsrc; ++s) {
+        if ((r = stage_out(c, yt + (size_t)s * n, io + (2 * (size_t)s) * n, n, st))) return r;
+        if ((r = stage_out(c, yb + (size_t)s * n, io + (2 * (size_t)s + 1) * n, n, st))) return r;
+    }
+    return LQ_OK;
+}
+
+int lq_sign_apply(lq_ctx* c, const double* x, double* y, int nsrc, const lq_opts* o, lq_report* rep, void* stream) {
+    if (!c || !x || !y) return set_err(c, LQ_ERR_ARG, "null argument");
+    int r = check_ready(c, nsrc, 0);
+    if (r || (r = check_opts(c, o))) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)nsrc * c->V * 24;
+    double* y0 = c->io + (size_t)c->nsrc * c->V * 24;
+    if ((r = stage_in(c, c->io, x, n, st))) return r;
+    if ((r = run_tsl(c, 1, 0, nsrc, o, rep, y0, nullptr, st))) return r;
+    if ((r = stage_out(c, y, y0, n, st))) return r;
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_sign_derivative_apply(lq_ctx* c, const lq_direction* dir, const double* x, double* ys, double* yd, int nsrc,
+                              const lq_opts* o, lq_report* rep, void* stream) {
+    if (!c || !dir || !x || !ys || !yd) return set_err(c, LQ_ERR_ARG, "null argument");
+    int r = check_ready(c, nsrc, 1);
+    if (r || (r = check_opts(c, o))) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((r = lq_set_direction(c, dir, stream))) return r;
+    const size_t n = (size_t)nsrc * c->V * 24;
+    double* y0 = c->io + (size_t)c->nsrc * c->V * 24;
+    double* y1 = c->io + (size_t)2 * c->nsrc * c->V * 24;
+    if ((r = stage_in(c, c->io, x, n, st))) return r;
+    if ((r = run_tsl(c, 2, emode_of(c), nsrc, o, rep, y0, y1, st))) return r;
+    if ((r = stage_out(c, yd, y0, n, st))) return r;
+    if ((r = stage_out(c, ys, y1, n, st))) return r;
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_profile_enable(lq_ctx* c, int enable) {
+    if (!c) return LQ_ERR_ARG;
+    c->prof_on = enable ? 1 : 0;
+    c->launches = 0;
+    for (int i = 0; i < 4; ++i) { c->prof_ms[i] = 0.0; c->prof_n[i] = 0; }
+    c->pending.clear();
+    c->ev_used = 0;
+    return LQ_OK;
+}
+
+int lq_profile_read(lq_ctx* c, lq_profile* o) {
+    if (!c || !o) return set_err(c, LQ_ERR_ARG, "null argument");
+    std::memset(o, 0, sizeof(*o));
+    o->enabled = c->prof_on;
+    o->launches = c->launches;
+    o->hop_ms = c->prof_ms[PC_HOP];
+    o->hop_launches = c->prof_n[PC_HOP];
+    o->update_ms = c->prof_ms[PC_UPDATE];
+    o->update_launches = c->prof_n[PC_UPDATE];
+    o->newton_ms = c->prof_ms[PC_NEWTON];
+    o->newton_iterations = c->prof_n[PC_NEWTON];
+    o->other_ms = c->prof_ms[PC_OTHER];
+    o->other_launches = c->prof_n[PC_OTHER];
+    return LQ_OK;
+}
+
+int lq_tsl_coefficients(lq_ctx* c, int src, int k, double* alpha, double* beta, double* delta) {
+    if (!c || !alpha || !beta || !delta) return set_err(c, LQ_ERR_ARG, "null argument");
+    if (!c->alpha) return set_err(c, LQ_ERR_NOT_READY, "workspace not reserved (lq_reserve)");
+    if (src < 0 || src >= c->nsrc || k < 1 || k > c->kmax) return set_err(c, LQ_ERR_ARG, "src / k outside the reserved workspace");
+    TslState st;
+    LQ_CUDA(c, cudaMemcpy(&st, c->state + src, sizeof(st), cudaMemcpyDeviceToHost));
+    LQ_CUDA(c, cudaMemcpy(alpha, c->alpha + (size_t)src * c->kmax, sizeof(double2) * k, cudaMemcpyDeviceToHost));
+    LQ_CUDA(c, cudaMemcpy(beta, c->beta + (size_t)src * c->kmax, sizeof(double2) * k, cudaMemcpyDeviceToHost));
+    LQ_CUDA(c, cudaMemcpy(delta, c->delta + (size_t)src * c->kmax, sizeof(double) * k, cudaMemcpyDeviceToHost));
+    for (int j = 0; j < k; ++j) {
+        if (j >= st.k_eff) { alpha[2 * j] = alpha[2 * j + 1] = 0.0; }
+        if (j >= st.k_eff - 1) { beta[2 * j] = beta[2 * j + 1] = 0.0; delta[j] = 0.0; }
+    }
+    return LQ_OK;
+}
+
+int lq_newton_sign(lq_ctx* c, const double* X, double* S, int k, int nb, int max_iter, double tol, int* iters, void* stream) {
+    if (!c || !X || !S) return set_err(c, LQ_ERR_ARG, "null argument");
+    if (!c->nx_X) return set_err(c, LQ_ERR_NOT_READY, "workspace not reserved (lq_reserve)");
+    if (k < 1 || k > c->kmax || nb < 1 || nb > c->nsrc || max_iter < 1 || !(tol > 0.0))
+        return set_err(c, LQ_ERR_ARG, "k / nb outside the reserved workspace, or bad iteration limits");
+    if (!is_device_ptr(X) || !is_device_ptr(S)) return set_err(c, LQ_ERR_LAYOUT, "X and S must be device pointers");
+    cudaStream_t st = (cudaStream_t)stream;
+    NewtonArgs a = newton_args(c, k, nb, max_iter, tol);
+    LQ_CUDA(c, newton_init_dense(a, reinterpret_cast<const double2*>(X), st));
+    c->launches += 2;
+    std::vector<double> scal;
+    int r = run_newton(c, a, st, scal);
+    if (r) return r;
+    LQ_CUDA(c, newton_copy_out(a, reinterpret_cast<double2*>(S), st));
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    prof_collect(c);
+    int bad = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (iters) iters[b] = (int)scal[(size_t)b * 16 + NS_ITERS];
+        if (scal[(size_t)b * 16 + NS_STATUS] != 0.0) bad = 1;
+    }
+    return bad ? set_err(c, LQ_ERR_NEWTON, "Newton iteration did not converge for at least one matrix") : LQ_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,845 @@
+// Device kernels of the two-sided Lanczos path:
+//   * k_hop      -- the Wilson kernel H(mu) = gamma5 Dw(mu) (Eq. (1.1)), its adjoint H(-mu), and
+//                   the block operator B = [[A, dA], [0, A]] / B^dag of Eq. (2.5), for a batch of
+//                   sources, with the Lanczos alpha dot fused into the epilogue;
+//   * k_update   -- the three-term Lanczos recurrences (Sec. 2) with the omega dot and norms;
+//   * k_tsl_init -- boundary -> internal layout, start vectors and |x|;
+//   * k_recombine-- y = |x| V_k c (+ internal -> boundary layout);
+//   * layout / precision conversion of spinors, links and the derivative direction dU/dt.
+#include "lq_internal.cuh"
+#include "lq_launch.h"
+
+#include <cstdio>
+
+namespace lq {
+
+// ---------------------------------------------------------------------------------------
+// float-float accumulator with exact products (for FP32 data); double CSum for FP64 data
+// ---------------------------------------------------------------------------------------
+struct FF { float h, l; };
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) {
+    s = a + b;
+    float z = s - a;
+    t = (a - (s - z)) + (b - z);
+}
+__device__ __forceinline__ void ff_add_prod(FF& acc, float a, float b) {
+    float p = a * b;
+    float pe = fmaf(a, b, -p);
+    float s, t;
+    two_sum_f(acc.h, p, s, t);
+    acc.h = s;
+    acc.l += t + pe;
+}
+__device__ __forceinline__ FF ff_merge(FF a, FF b) {
+    float s, t;
+    two_sum_f(a.h, b.h, s, t);
+    FF r; r.h = s; r.l = a.l + b.l + t;
+    return r;
+}
+
+template <typename R> struct DotAcc;
+template <> struct DotAcc<double> {
+    CSum v;
+    __device__ __forceinline__ void zero() { v.s = 0.0; v.e = 0.0; }
+    __device__ __forceinline__ void add_prod(double a, double b) { cs_add_prod(v, a, b); }
+    // warp-level reduction then conversion to a double compensated sum (valid in lane 0)
+    __device__ __forceinline__ CSum warp_total() {
+        CSum r = v;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) r = cs_merge(r, cs_shfl_down(r, off));
+        return r;
+    }
+};
+template <> struct DotAcc<float> {
+    FF v;
+    __device__ __forceinline__ void zero() { v.h = 0.f; v.l = 0.f; }
+    __device__ __forceinline__ void add_prod(float a, float b) { ff_add_prod(v, a, b); }
+    __device__ __forceinline__ CSum warp_total() {
+        FF r = v;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            FF o; o.h = __shfl_down_sync(0xffffffffu, r.h, off); o.l = __shfl_down_sync(0xffffffffu, r.l, off);
+            r = ff_merge(r, o);
+        }
+        CSum c; c.s = (double)r.h; c.e = (double)r.l;
+        return c;
+    }
+};
+
+// Reduce NV per-thread accumulators to one compensated double per value for the block.
+// Valid in thread 0.  smem holds 32 * NV CSum.
+template <typename R, int NV>
+__device__ __forceinline__ void block_total(DotAcc<R> (&acc)[NV], CSum (&out)[NV], CSum* smem) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    CSum w[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) w[i] = acc[i].warp_total();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) smem[warp * NV + i] = w[i];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            if (lane < nw) w[i] = smem[lane * NV + i];
+            else { w[i].s = 0.0; w[i].e = 0.0; }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) w[i] = cs_merge(w[i], cs_shfl_down(w[i], off));
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i] = w[i];
+    }
+    __syncthreads();
+}
+
+// "Last block done" election: every block of a source publishes its partials, then the
+// block that finishes last (atomic counter) reduces them.  Returns true in that block.
+__device__ __forceinline__ bool last_block(int* counter, int nblocks) {
+    __shared__ int is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        int prev = atomicAdd(counter, 1);
+        is_last = (prev == nblocks - 1);
+        if (is_last) *counter = 0;   // reset for the next launch
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last != 0;
+}
+
+// Sum nb partials (stride NV values of (s, e) pairs) in a fixed order -> deterministic.
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int nb, double (&res)[NV], CSum* smem) {
+    CSum acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) { acc[i].s = 0.0; acc[i].e = 0.0; }
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            CSum p; p.s = __ldcg(part + (size_t)b * 2 * NV + 2 * i); p.e = __ldcg(part + (size_t)b * 2 * NV + 2 * i + 1);
+            acc[i] = cs_merge(acc[i], p);
+        }
+    block_reduce_cs<NV>(acc, smem);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) res[i] = acc[i].s + acc[i].e;
+}
+
+// ---------------------------------------------------------------------------------------
+// Spin structure in the chiral basis: gamma_nu = [[0, B_nu], [B_nu^dag, 0]] with
+// B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1.  Then
+// (1 + s gamma_nu) psi = (h, s B^dag h) with h = psi_up + s B psi_dn  (s = +-1),
+// so every hop only needs the two-component half spinor h (Wilson projector, r = 1).
+// ---------------------------------------------------------------------------------------
+template <typename C, int NU, int SP>
+__device__ __forceinline__ void project(const C (&p)[12], C (&h)[6]) {
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+        C u0 = p[col], u1 = p[3 + col], d2 = p[6 + col], d3 = p[9 + col];
+        C b0, b1;
+        if (NU == 0) { b0 = cmul_mi(d3); b1 = cmul_mi(d2); }
+        else if (NU == 1) { b0 = cmk<C>(-d3.x, -d3.y); b1 = d2; }
+        else if (NU == 2) { b0 = cmul_mi(d2); b1 = cmul_i(d3); }
+        else { b0 = d2; b1 = d3; }
+        if (SP > 0) { h[col] = cadd(u0, b0); h[3 + col] = cadd(u1, b1); }
+        else { h[col] = csub(u0, b0); h[3 + col] = csub(u1, b1); }
+    }
+}
+
+// acc += (g, s B^dag g)
+template <typename C, int NU, int SP>
+__device__ __forceinline__ void reconstruct_add(const C (&g)[6], C (&acc)[12]) {
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+        C g0 = g[col], g1 = g[3 + col];
+        C l0, l1;   // B^dag g
+        if (NU == 0) { l0 = cmul_i(g1); l1 = cmul_i(g0); }
+        else if (NU == 1) { l0 = g1; l1 = cmk<C>(-g0.x, -g0.y); }
+        else if (NU == 2) { l0 = cmul_i(g0); l1 = cmul_mi(g1); }
+        else { l0 = g0; l1 = g1; }
+        acc[col] = cadd(acc[col], g0);
+        acc[3 + col] = cadd(acc[3 + col], g1);
+        if (SP > 0) { acc[6 + col] = cadd(acc[6 + col], l0); acc[9 + col] = cadd(acc[9 + col], l1); }
+        else { acc[6 + col] = csub(acc[6 + col], l0); acc[9 + col] = csub(acc[9 + col], l1); }
+    }
+}
+
+template <typename C, bool DAG>
+__device__ __forceinline__ void su3_mul(const C (&u)[9], const C (&h)[6], C (&g)[6]) {
+#pragma unroll
+    for (int sc = 0; sc < 2; ++sc)
+#pragma unroll
+        for (int row = 0; row < 3; ++row) {
+            C a = cmk<C>(0, 0);
+#pragma unroll
+            for (int col = 0; col < 3; ++col) {
+                if (!DAG) a = cfma(u[row * 3 + col], h[sc * 3 + col], a);
+                else a = cfmac(u[col * 3 + row], h[sc * 3 + col], a);
+            }
+            g[sc * 3 + row] = a;
+        }
+}
+
+template <typename C>
+__device__ __forceinline__ void load_link(const C* __restrict__ L, size_t V, int nu, size_t s, C (&u)[9]) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u[e] = __ldg(L + ((size_t)nu * 9 + e) * V + s);
+}
+
+template <typename C>
+__device__ __forceinline__ void hscale(C (&h)[6], decltype(C::x) f) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) h[i] = cscale(h[i], f);
+}
+template <typename C>
+__device__ __forceinline__ void haxpy(C (&h)[6], decltype(C::x) f, const C (&x)[6]) {  // h += f x
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { h[i].x = fma(f, x[i].x, h[i].x); h[i].y = fma(f, x[i].y, h[i].y); }
+}
+
+// One hop direction (NU, SP = -1 forward / +1 backward) for NF fields per side.
+// EMODE 0: no derivative term; 1: d/dmu (time hops, links U); 2: link direction (links Y).
+// Right side (side 0): out0 = A in0 + E in1, out1 = A in1.
+// Left side  (side 1): out0 = A^dag in0,     out1 = A^dag in1 + E^dag in0.
+template <typename R, int NF, int EMODE, int NU, int SP>
+__device__ __forceinline__ void do_hop(const HopArgs& a, int side, size_t V, size_t nb, size_t lsite, R bsign,
+                                       const typename Tr<R>::Chunk* __restrict__ in0,
+                                       const typename Tr<R>::Chunk* __restrict__ in1,
+                                       typename Tr<R>::C (&acc0)[12], typename Tr<R>::C (&acc1)[12]) {
+    using C = typename Tr<R>::C;
+    constexpr bool DAG = SP > 0;   // backward hop uses the adjoint link at x - nu
+    const R fa = (R)((SP < 0 ? a.a_fwd[side][NU] : a.a_bwd[side][NU])) * bsign;
+    const R fe = (R)((SP < 0 ? a.e_fwd[side][NU] : a.e_bwd[side][NU])) * bsign;
+    const C* __restrict__ Lu = reinterpret_cast<const C*>(a.U);
+    C u[9];
+    load_link(Lu, V, NU, lsite, u);
+    C psi[12], h0[6], g[6];
+    load_spinor(in0, V, nb, psi);
+    project<C, NU, SP>(psi, h0);
+    if (NF == 1) {
+        hscale(h0, fa);
+        su3_mul<C, DAG>(u, h0, g);
+        reconstruct_add<C, NU, SP>(g, acc0);
+        return;
+    } else {
+        C h1[6];
+        load_spinor(in1, V, nb, psi);
+        project<C, NU, SP>(psi, h1);
+        const bool emu = (EMODE == 1) && (NU == 3);
+        if (side == 0) {
+            // out1 += U (fa h1);  out0 += U (fa h0 [+ fe h1 for d/dmu]) [+ Y (fe h1)]
+            C t0[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) t0[i] = cscale(h0[i], fa);
+            if (emu) haxpy(t0, fe, h1);
+            su3_mul<C, DAG>(u, t0, g);
+            reconstruct_add<C, NU, SP>(g, acc0);
+            if (EMODE == 2) {
+                C y[9], t1[6];
+                load_link(reinterpret_cast<const C*>(a.Y), V, NU, lsite, y);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) t1[i] = cscale(h1[i], fe);
+                su3_mul<C, DAG>(y, t1, g);
+                reconstruct_add<C, NU, SP>(g, acc0);
+            }
+            hscale(h1, fa);
+            su3_mul<C, DAG>(u, h1, g);
+            reconstruct_add<C, NU, SP>(g, acc1);
+        } else {
+            // out0 += U (fa h0);  out1 += U (fa h1 [+ fe h0]) [+ Y (fe h0)]
+            C t1[6];
+#pragma unroll
+            for (int i = 0; i < 6; ++i) t1[i] = cscale(h1[i], fa);
+            if (emu) haxpy(t1, fe, h0);
+            su3_mul<C, DAG>(u, t1, g);
+            reconstruct_add<C, NU, SP>(g, acc1);
+            if (EMODE == 2) {
+                C y[9], t0[6];
+                load_link(reinterpret_cast<const C*>(a.Y), V, NU, lsite, y);
+#pragma unroll
+                for (int i = 0; i < 6; ++i) t0[i] = cscale(h0[i], fe);
+                su3_mul<C, DAG>(y, t0, g);
+                reconstruct_add<C, NU, SP>(g, acc1);
+            }
+            hscale(h0, fa);
+            su3_mul<C, DAG>(u, h0, g);
+            reconstruct_add<C, NU, SP>(g, acc0);
+        }
+    }
+}
+
+template <typename R, int NF, int EMODE, int NU>
+__device__ __forceinline__ void do_dir(const HopArgs& a, int side, size_t V, size_t s, const int (&x)[4],
+                                       const typename Tr<R>::Chunk* in0, const typename Tr<R>::Chunk* in1,
+                                       typename Tr<R>::C (&acc0)[12], typename Tr<R>::C (&acc1)[12]) {
+    const int ext = a.dims[NU];
+    const size_t stride = a.strides[NU];
+    // forward neighbour
+    size_t sf = (x[NU] == ext - 1) ? s - (size_t)(ext - 1) * stride : s + stride;
+    R bf = (NU == 3 && a.apbc && x[NU] == ext - 1) ? (R)-1 : (R)1;
+    do_hop<R, NF, EMODE, NU, -1>(a, side, V, sf, s, bf, in0, in1, acc0, acc1);
+    // backward neighbour (link at x - nu)
+    size_t sb = (x[NU] == 0) ? s + (size_t)(ext - 1) * stride : s - stride;
+    R bb = (NU == 3 && a.apbc && x[NU] == 0) ? (R)-1 : (R)1;
+    do_hop<R, NF, EMODE, NU, +1>(a, side, V, sb, sb, bb, in0, in1, acc0, acc1);
+}
+
+// gamma5 [diag * psi + acc]
+template <typename C>
+__device__ __forceinline__ void finish(const C (&psi)[12], decltype(C::x) diag, C (&acc)[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        C v = cmk<C>(fma(diag, psi[c].x, acc[c].x), fma(diag, psi[c].y, acc[c].y));
+        acc[c] = (c < 6) ? v : cmk<C>(-v.x, -v.y);
+    }
+}
+
+template <typename R, int NF, int EMODE, bool DOT>
+__global__ void __launch_bounds__(kHopThreads) k_hop(HopArgs a) {
+    using C = typename Tr<R>::C;
+    using Chunk = typename Tr<R>::Chunk;
+    __shared__ CSum smem[32 * 2];
+    const int side = blockIdx.z + a.side0;
+    const int src = blockIdx.y;
+    if (a.state != nullptr && a.state[src].status != 0) return;   // source finished / failed
+    const size_t V = a.V;
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const bool active = s < V;
+    const Chunk* in0 = reinterpret_cast<const Chunk*>(a.in[side]) + (size_t)src * a.src_stride_in[side];
+    const Chunk* in1 = in0 + field_elems<R>(V);
+    Chunk* out0 = reinterpret_cast<Chunk*>(a.out[side]) + (size_t)src * a.src_stride_out[side];
+    Chunk* out1 = out0 + field_elems<R>(V);
+
+    C acc0[12], acc1[12];
+    DotAcc<R> d[2];
+    d[0].zero(); d[1].zero();
+    if (active) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) { acc0[c] = cmk<C>(0, 0); acc1[c] = cmk<C>(0, 0); }
+        int x[4];
+        {
+            size_t r = s;
+            x[0] = (int)(r % a.dims[0]); r /= a.dims[0];
+            x[1] = (int)(r % a.dims[1]); r /= a.dims[1];
+            x[2] = (int)(r % a.dims[2]); r /= a.dims[2];
+            x[3] = (int)r;
+        }
+        do_dir<R, NF, EMODE, 0>(a, side, V, s, x, in0, in1, acc0, acc1);
+        do_dir<R, NF, EMODE, 1>(a, side, V, s, x, in0, in1, acc0, acc1);
+        do_dir<R, NF, EMODE, 2>(a, side, V, s, x, in0, in1, acc0, acc1);
+        do_dir<R, NF, EMODE, 3>(a, side, V, s, x, in0, in1, acc0, acc1);
+        const R diag = (R)a.diag;
+        C psi[12];
+        load_spinor(in0, V, s, psi);
+        finish(psi, diag, acc0);
+        store_spinor(out0, V, s, acc0);
+        if (NF == 2) {
+            load_spinor(in1, V, s, psi);
+            finish(psi, diag, acc1);
+            store_spinor(out1, V, s, acc1);
+        }
+        if (DOT && side == 0) {
+            // <w_j, B vh_j> restricted to this site: left inputs at s (conj) times outputs
+            const Chunk* l0 = reinterpret_cast<const Chunk*>(a.in[1]) + (size_t)src * a.src_stride_in[1];
+            C w[12];
+            load_spinor(l0, V, s, w);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                d[0].add_prod(w[c].x, acc0[c].x); d[0].add_prod(w[c].y, acc0[c].y);
+                d[1].add_prod(w[c].x, acc0[c].y); d[1].add_prod(-w[c].y, acc0[c].x);
+            }
+            if (NF == 2) {
+                load_spinor(l0 + field_elems<R>(V), V, s, w);
+#pragma unroll
+                for (int c = 0; c < 12; ++c) {
+                    d[0].add_prod(w[c].x, acc1[c].x); d[0].add_prod(w[c].y, acc1[c].y);
+                    d[1].add_prod(w[c].x, acc1[c].y); d[1].add_prod(-w[c].y, acc1[c].x);
+                }
+            }
+        }
+    }
+    if (DOT && side == 0) {
+        CSum tot[2];
+        block_total<R, 2>(d, tot, smem);
+        double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 4;
+        if (threadIdx.x == 0) { part[0] = tot[0].s; part[1] = tot[0].e; part[2] = tot[1].s; part[3] = tot[1].e; }
+        if (last_block(a.counters + src, gridDim.x)) {
+            double res[2];
+            reduce_partials<2>(a.partials + (size_t)src * a.partial_stride * 4, gridDim.x, res, smem);
+            if (threadIdx.x == 0) tsl_alpha_step(a, src, res[0], res[1]);
+        }
+    }
+}
+
+// Lanczos scalar step after alpha_j: record alpha_j and prepare the update coefficients
+//   vh_{j+1} = s_j B vh_j - alpha_j s_j vh_j - beta_{j-1} s_{j-1} vh_{j-1}
+//   wh_{j+1} = u_j B^dag wh_j - conj(alpha_j) u_j wh_j - delta_{j-1} u_{j-1} wh_{j-1}
+__device__ void tsl_alpha_step(const HopArgs& a, int src, double dre, double dim) {
+    TslState& st = a.state[src];
+    const int j = a.j;
+    const double2 uj = st.u_cur;
+    const double sj = st.s_cur;
+    // alpha = conj(u_j) s_j <wh_j, B vh_j>
+    double2 al;
+    al.x = sj * (uj.x * dre + uj.y * dim);
+    al.y = sj * (uj.x * dim - uj.y * dre);
+    a.alpha[(size_t)src * a.kmax + j] = al;
+    a.scale[(size_t)src * a.kmax + j] = sj;
+    st.k_eff = j + 1;
+    if (!isfinite(al.x) || !isfinite(al.y)) { st.status = LQ_ERR_NONFINITE; return; }
+    st.cv[0] = make_double2(sj, 0.0);
+    st.cv[1] = make_double2(-al.x * sj, -al.y * sj);
+    st.cw[0] = uj;
+    // -conj(alpha) u_j
+    st.cw[1] = make_double2(-(al.x * uj.x + al.y * uj.y), -(al.x * uj.y - al.y * uj.x));
+    if (j > 0) {
+        st.cv[2] = make_double2(-st.beta_prev.x * st.s_prev, -st.beta_prev.y * st.s_prev);
+        st.cw[2] = make_double2(-st.delta_prev * st.u_prev.x, -st.delta_prev * st.u_prev.y);
+    } else {
+        st.cv[2] = make_double2(0.0, 0.0);
+        st.cw[2] = make_double2(0.0, 0.0);
+    }
+    if (j == a.kmax_run - 1) st.status = 1;   // k reached
+}
+
+// ---------------------------------------------------------------------------------------
+// Update: new right/left vectors and the omega dot, |vh|^2, |wh|^2.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ typename Tr<R>::Chunk axpy3(typename Tr<R>::Chunk r, typename Tr<R>::Chunk v, typename Tr<R>::Chunk p,
+                                                      const typename Tr<R>::C (&c)[3], bool has_prev);
+
+template <>
+__device__ __forceinline__ double2 axpy3<double>(double2 r, double2 v, double2 p, const double2 (&c)[3], bool has_prev) {
+    double2 o = cmul(c[0], r);
+    o = cfma(c[1], v, o);
+    if (has_prev) o = cfma(c[2], p, o);
+    return o;
+}
+template <>
+__device__ __forceinline__ float4 axpy3<float>(float4 r, float4 v, float4 p, const float2 (&c)[3], bool has_prev) {
+    float2 o0 = cmul(c[0], make_float2(r.x, r.y));
+    float2 o1 = cmul(c[0], make_float2(r.z, r.w));
+    o0 = cfma(c[1], make_float2(v.x, v.y), o0);
+    o1 = cfma(c[1], make_float2(v.z, v.w), o1);
+    if (has_prev) {
+        o0 = cfma(c[2], make_float2(p.x, p.y), o0);
+        o1 = cfma(c[2], make_float2(p.z, p.w), o1);
+    }
+    return make_float4(o0.x, o0.y, o1.x, o1.y);
+}
+
+template <typename R>
+__device__ __forceinline__ void dot_chunk(DotAcc<R> (&d)[4], typename Tr<R>::Chunk w, typename Tr<R>::Chunk v);
+template <>
+__device__ __forceinline__ void dot_chunk<double>(DotAcc<double> (&d)[4], double2 w, double2 v) {
+    d[0].add_prod(w.x, v.x); d[0].add_prod(w.y, v.y);
+    d[1].add_prod(w.x, v.y); d[1].add_prod(-w.y, v.x);
+    d[2].add_prod(v.x, v.x); d[2].add_prod(v.y, v.y);
+    d[3].add_prod(w.x, w.x); d[3].add_prod(w.y, w.y);
+}
+template <>
+__device__ __forceinline__ void dot_chunk<float>(DotAcc<float> (&d)[4], float4 w, float4 v) {
+    d[0].add_prod(w.x, v.x); d[0].add_prod(w.y, v.y); d[0].add_prod(w.z, v.z); d[0].add_prod(w.w, v.w);
+    d[1].add_prod(w.x, v.y); d[1].add_prod(-w.y, v.x); d[1].add_prod(w.z, v.w); d[1].add_prod(-w.w, v.z);
+    d[2].add_prod(v.x, v.x); d[2].add_prod(v.y, v.y); d[2].add_prod(v.z, v.z); d[2].add_prod(v.w, v.w);
+    d[3].add_prod(w.x, w.x); d[3].add_prod(w.y, w.y); d[3].add_prod(w.z, w.z); d[3].add_prod(w.w, w.w);
+}
+
+template <typename R>
+__global__ void __launch_bounds__(kUpdThreads) k_update(UpdArgs a) {
+    using C = typename Tr<R>::C;
+    using Chunk = typename Tr<R>::Chunk;
+    __shared__ CSum smem[32 * 4];
+    const int src = blockIdx.y;
+    TslState& st = a.state[src];
+    if (st.status != 0) return;
+    C cv[3], cw[3];
+#pragma unroll
+    for (int i = 0; i < 3; ++i) {
+        cv[i] = cmk<C>((R)st.cv[i].x, (R)st.cv[i].y);
+        cw[i] = cmk<C>((R)st.cw[i].x, (R)st.cw[i].y);
+    }
+    const bool has_prev = a.j > 0;
+    const size_t N = a.nelem;
+    const Chunk* r = reinterpret_cast<const Chunk*>(a.rout) + (size_t)src * a.src_stride_io;
+    const Chunk* l = reinterpret_cast<const Chunk*>(a.lout) + (size_t)src * a.src_stride_io;
+    const Chunk* v = reinterpret_cast<const Chunk*>(a.v_cur) + (size_t)src * a.src_stride_basis;
+    const Chunk* vp = reinterpret_cast<const Chunk*>(a.v_prev) + (size_t)src * a.src_stride_basis;
+    Chunk* vn = reinterpret_cast<Chunk*>(a.v_next) + (size_t)src * a.src_stride_basis;
+    const Chunk* w = reinterpret_cast<const Chunk*>(a.w_cur) + (size_t)src * a.src_stride_left;
+    const Chunk* wp = reinterpret_cast<const Chunk*>(a.w_prev) + (size_t)src * a.src_stride_left;
+    Chunk* wn = reinterpret_cast<Chunk*>(a.w_next) + (size_t)src * a.src_stride_left;
+    DotAcc<R> d[4];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) d[i].zero();
+    for (size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x; e < N; e += (size_t)gridDim.x * blockDim.x) {
+        Chunk zero{};
+        Chunk nv = axpy3<R>(__ldg(r + e), __ldg(v + e), has_prev ? __ldg(vp + e) : zero, cv, has_prev);
+        Chunk nw = axpy3<R>(__ldg(l + e), __ldg(w + e), has_prev ? __ldg(wp + e) : zero, cw, has_prev);
+        vn[e] = nv;
+        wn[e] = nw;
+        dot_chunk<R>(d, nw, nv);
+    }
+    CSum tot[4];
+    block_total<R, 4>(d, tot, smem);
+    double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 8;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i) { part[2 * i] = tot[i].s; part[2 * i + 1] = tot[i].e; }
+    if (last_block(a.counters + a.nsrc + src, gridDim.x)) {
+        double res[4];
+        reduce_partials<4>(a.partials + (size_t)src * a.partial_stride * 8, gridDim.x, res, smem);
+        if (threadIdx.x == 0) {
+            // omega = <wh_{j+1}, vh_{j+1}>; delta_j = sqrt|omega|; beta_j = omega / delta_j
+            const double om_re = res[0], om_im = res[1];
+            const double nv2 = res[2], nw2 = res[3];
+            const double om = hypot(om_re, om_im);
+            const int j = a.j;
+            if (!isfinite(om) || !isfinite(nv2) || !isfinite(nw2)) { st.status = LQ_ERR_NONFINITE; return; }
+            if (om < st.breakdown_tol * sqrt(nv2) * sqrt(nw2) || om == 0.0) { st.status = LQ_ERR_BREAKDOWN; return; }
+            const double dl = sqrt(om);
+            const double2 be = make_double2(om_re / dl, om_im / dl);
+            a.delta[(size_t)src * a.kmax + j] = dl;
+            a.beta[(size_t)src * a.kmax + j] = be;
+            st.s_prev = st.s_cur;
+            st.u_prev = st.u_cur;
+            st.beta_prev = be;
+            st.delta_prev = dl;
+            st.s_cur = 1.0 / dl;
+            // u_{j+1} = 1 / conj(beta_j)
+            const double bn = be.x * be.x + be.y * be.y;
+            st.u_cur = make_double2(be.x / bn, be.y / bn);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Start vectors.  Plain:  vh_1 = wh_1 = x.   Block: vh_1 = (0, x), wh_1 = (x, x).
+// s_1 = u_1 = 1/|x| so that v_1 = x/|x| (or (0,x)/|x|) and <w_1, v_1> = 1.
+// x arrives in the boundary layout (complex128 [nsrc][V][12]).
+// ---------------------------------------------------------------------------------------
+template <typename R, int NF>
+__global__ void __launch_bounds__(kUpdThreads) k_tsl_init(InitArgs a) {
+    using C = typename Tr<R>::C;
+    using Chunk = typename Tr<R>::Chunk;
+    __shared__ CSum smem[32];
+    const int src = blockIdx.y;
+    const size_t V = a.V;
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    DotAcc<double> d[1];
+    d[0].zero();
+    if (s < V) {
+        const double2* x = reinterpret_cast<const double2*>(a.x) + ((size_t)src * V + s) * 12;
+        C psi[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            double2 z = x[c];
+            psi[c] = cmk<C>((R)z.x, (R)z.y);
+            d[0].add_prod((double)psi[c].x, (double)psi[c].x);
+            d[0].add_prod((double)psi[c].y, (double)psi[c].y);
+        }
+        Chunk* v = reinterpret_cast<Chunk*>(a.v1) + (size_t)src * a.src_stride_basis;
+        Chunk* w = reinterpret_cast<Chunk*>(a.w1) + (size_t)src * a.src_stride_left;
+        if (NF == 1) {
+            store_spinor(v, V, s, psi);
+            store_spinor(w, V, s, psi);
+        } else {
+            C z[12];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) z[c] = cmk<C>(0, 0);
+            store_spinor(v, V, s, z);
+            store_spinor(v + field_elems<R>(V), V, s, psi);
+            store_spinor(w, V, s, psi);
+            store_spinor(w + field_elems<R>(V), V, s, psi);
+        }
+    }
+    // warp/block totals (products are of doubles converted from R: exact for float)
+    CSum tot[1];
+    {
+        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+        CSum w = d[0].warp_total();
+        if (lane == 0) smem[warp] = w;
+        __syncthreads();
+        if (warp == 0) {
+            w = (lane < nw) ? smem[lane] : CSum{0.0, 0.0};
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) w = cs_merge(w, cs_shfl_down(w, off));
+            if (lane == 0) tot[0] = w;
+        }
+        __syncthreads();
+    }
+    double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 2;
+    if (threadIdx.x == 0) { part[0] = tot[0].s; part[1] = tot[0].e; }
+    if (last_block(a.counters + 2 * a.nsrc + src, gridDim.x)) {
+        double res[1];
+        reduce_partials<1>(a.partials + (size_t)src * a.partial_stride * 2, gridDim.x, res, smem);
+        if (threadIdx.x == 0) {
+            TslState& st = a.state[src];
+            const double xn = sqrt(res[0]);
+            st.xnorm = xn;
+            st.k_eff = 0;
+            st.breakdown_tol = a.breakdown_tol;
+            if (!(xn > 0.0) || !isfinite(xn)) { st.status = LQ_ERR_ARG; return; }
+            st.status = 0;
+            st.s_cur = 1.0 / xn;
+            st.s_prev = 0.0;
+            st.u_cur = make_double2(1.0 / xn, 0.0);
+            st.u_prev = make_double2(0.0, 0.0);
+            st.beta_prev = make_double2(0.0, 0.0);
+            st.delta_prev = 0.0;
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Recombination y = |x| sum_j c_j s_j vh_j for each field, written in the boundary layout.
+// c = first column of sgn(T_k) (from the Newton workspace, row-major k x k per source).
+// FP64 basis: FP64 accumulation.  FP32 basis: float-float accumulation with exact products
+// of the split coefficient (hi + lo).
+// ---------------------------------------------------------------------------------------
+template <typename R, int NF>
+__global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
+    using C = typename Tr<R>::C;
+    using Chunk = typename Tr<R>::Chunk;
+    extern __shared__ double2 coef[];   // [keff] (double) or [keff][2] (float hi/lo)
+    const int src = blockIdx.y;
+    const int f = blockIdx.z;           // field index (0 top / 1 bottom)
+    const TslState& st = a.state[src];
+    const int keff = st.k_eff;
+    const size_t V = a.V;
+    const double xn = st.xnorm;
+    const double2* X = a.newton_X + (size_t)src * a.ldx * a.ldx;
+    for (int j = threadIdx.x; j < keff; j += blockDim.x) {
+        double2 c = X[(size_t)j * a.ldx];   // first column
+        double sc = a.scale[(size_t)src * a.kmax + j] * xn;
+        double2 cs = make_double2(c.x * sc, c.y * sc);
+        if (sizeof(R) == 8) coef[j] = cs;
+        else {
+            float hx = (float)cs.x, hy = (float)cs.y;
+            coef[2 * j] = cs;
+            coef[2 * j + 1] = make_double2((double)hx, (double)hy);
+        }
+    }
+    __syncthreads();
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (s >= V) return;
+    double2* y = reinterpret_cast<double2*>(f == 0 ? a.y0 : a.y1) + ((size_t)src * V + s) * 12;
+    if (keff <= 0) {
+#pragma unroll
+        for (int c = 0; c < 12; ++c) y[c] = make_double2(0.0, 0.0);
+        return;
+    }
+    const Chunk* base = reinterpret_cast<const Chunk*>(a.basis) + (size_t)src * a.src_stride_basis + (size_t)f * field_elems<R>(V);
+    if (sizeof(R) == 8) {
+        double2 acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = make_double2(0.0, 0.0);
+        for (int j = 0; j < keff; ++j) {
+            const double2* vj = reinterpret_cast<const double2*>(base + (size_t)j * a.vec_stride);
+            const double2 cj = coef[j];
+#pragma unroll
+            for (int c = 0; c < 12; ++c) acc[c] = cfma(cj, __ldg(vj + (size_t)c * V + s), acc[c]);
+        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c) y[c] = acc[c];
+    } else {
+        FF ar[12], ai[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) { ar[c] = FF{0.f, 0.f}; ai[c] = FF{0.f, 0.f}; }
+        for (int j = 0; j < keff; ++j) {
+            const float4* vj = reinterpret_cast<const float4*>(base + (size_t)j * a.vec_stride);
+            const double2 cd = coef[2 * j];
+            const float chx = (float)cd.x, chy = (float)cd.y;
+            const float clx = (float)(cd.x - (double)chx), cly = (float)(cd.y - (double)chy);
+#pragma unroll
+            for (int q = 0; q < 6; ++q) {
+                const float4 v4 = __ldg(vj + (size_t)q * V + s);
+                const float vx[2] = {v4.x, v4.z}, vy[2] = {v4.y, v4.w};
+#pragma unroll
+                for (int h = 0; h < 2; ++h) {
+                    const int c = 2 * q + h;
+                    // (ch + cl) * v, exact products of the high part, low part folded in
+                    ff_add_prod(ar[c], chx, vx[h]); ff_add_prod(ar[c], -chy, vy[h]);
+                    ff_add_prod(ai[c], chx, vy[h]); ff_add_prod(ai[c], chy, vx[h]);
+                    ar[c].l = fmaf(clx, vx[h], ar[c].l); ar[c].l = fmaf(-cly, vy[h], ar[c].l);
+                    ai[c].l = fmaf(clx, vy[h], ai[c].l); ai[c].l = fmaf(cly, vx[h], ai[c].l);
+                }
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c) y[c] = make_double2((double)ar[c].h + (double)ar[c].l, (double)ai[c].h + (double)ai[c].l);
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Layout conversions
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__global__ void k_to_internal(const double2* __restrict__ x, typename Tr<R>::Chunk* __restrict__ f, size_t V, int nfields) {
+    using C = typename Tr<R>::C;
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int fld = blockIdx.y;
+    if (s >= V || fld >= nfields) return;
+    C psi[12];
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        double2 z = x[((size_t)fld * V + s) * 12 + c];
+        psi[c] = cmk<C>((R)z.x, (R)z.y);
+    }
+    store_spinor(f + (size_t)fld * field_elems<R>(V), V, s, psi);
+}
+
+template <typename R>
+__global__ void k_to_boundary(const typename Tr<R>::Chunk* __restrict__ f, double2* __restrict__ x, size_t V, int nfields) {
+    using C = typename Tr<R>::C;
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int fld = blockIdx.y;
+    if (s >= V || fld >= nfields) return;
+    C psi[12];
+    load_spinor(f + (size_t)fld * field_elems<R>(V), V, s, psi);
+#pragma unroll
+    for (int c = 0; c < 12; ++c) x[((size_t)fld * V + s) * 12 + c] = make_double2((double)psi[c].x, (double)psi[c].y);
+}
+
+// links: boundary [4][V][3][3] complex128 -> internal [4][9][V]
+template <typename R>
+__global__ void k_links_internal(const double2* __restrict__ U, typename Tr<R>::C* __restrict__ L, size_t V) {
+    using C = typename Tr<R>::C;
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nu = blockIdx.y;
+    if (s >= V) return;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        double2 z = U[((size_t)nu * V + s) * 9 + e];
+        L[((size_t)nu * 9 + e) * V + s] = cmk<C>((R)z.x, (R)z.y);
+    }
+}
+
+// dU/dt = i Omega U with Omega = sum_a w^a lambda_a / 2 (su(3)) or theta * 1 (U(1)).
+// U (FP64 boundary copy), w: [4][V][8] or [4][V]; output Y internal.
+template <typename R>
+__global__ void k_direction(const double2* __restrict__ U, const double* __restrict__ w, int kind,
+                            typename Tr<R>::C* __restrict__ Y, size_t V) {
+    using C = typename Tr<R>::C;
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nu = blockIdx.y;
+    if (s >= V) return;
+    // M = i Omega (3x3)
+    double2 M[9];
+    if (kind == LQ_DIR_SU3) {
+        const double* c = w + ((size_t)nu * V + s) * 8;
+        const double r3 = 0.57735026918962576451;  // 1/sqrt(3)
+        // Omega = 1/2 sum_a c_a lambda_a (Gell-Mann), written element by element
+        double2 O[9];
+        O[0] = make_double2(0.5 * (c[2] + r3 * c[7]), 0.0);
+        O[4] = make_double2(0.5 * (-c[2] + r3 * c[7]), 0.0);
+        O[8] = make_double2(0.5 * (-2.0 * r3 * c[7]), 0.0);
+        O[1] = make_double2(0.5 * c[0], -0.5 * c[1]);
+        O[3] = make_double2(0.5 * c[0], 0.5 * c[1]);
+        O[2] = make_double2(0.5 * c[3], -0.5 * c[4]);
+        O[6] = make_double2(0.5 * c[3], 0.5 * c[4]);
+        O[5] = make_double2(0.5 * c[5], -0.5 * c[6]);
+        O[7] = make_double2(0.5 * c[5], 0.5 * c[6]);
+        for (int e = 0; e < 9; ++e) M[e] = make_double2(-O[e].y, O[e].x);
+    } else {
+        const double th = w[(size_t)nu * V + s];
+        for (int e = 0; e < 9; ++e) M[e] = make_double2(0.0, (e % 4 == 0) ? th : 0.0);
+    }
+    const double2* u = U + ((size_t)nu * V + s) * 9;
+    for (int r = 0; r < 3; ++r)
+        for (int c = 0; c < 3; ++c) {
+            double2 acc = make_double2(0.0, 0.0);
+            for (int k = 0; k < 3; ++k) acc = cfma(M[r * 3 + k], u[k * 3 + c], acc);
+            Y[((size_t)nu * 9 + r * 3 + c) * V + s] = cmk<C>((R)acc.x, (R)acc.y);
+        }
+}
+
+// ---------------------------------------------------------------------------------------
+// Host launchers
+// ---------------------------------------------------------------------------------------
+template <typename R>
+static cudaError_t launch_hop_t(const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st) {
+    dim3 grid((unsigned)((a.V + kHopThreads - 1) / kHopThreads), (unsigned)a.nsrc, (unsigned)a.nsides);
+    dim3 block(kHopThreads);
+#define LQ_HOP(NF, EM, D) k_hop<R, NF, EM, D><<<grid, block, 0, st>>>(a)
+    if (nf == 1) {
+        if (dot) LQ_HOP(1, 0, true); else LQ_HOP(1, 0, false);
+    } else {
+        if (emode == 0) { if (dot) LQ_HOP(2, 0, true); else LQ_HOP(2, 0, false); }
+        else if (emode == 1) { if (dot) LQ_HOP(2, 1, true); else LQ_HOP(2, 1, false); }
+        else { if (dot) LQ_HOP(2, 2, true); else LQ_HOP(2, 2, false); }
+    }
+#undef LQ_HOP
+    return cudaGetLastError();
+}
+
+cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st) {
+    return prec == LQ_FP64 ? launch_hop_t<double>(a, nf, emode, dot, st) : launch_hop_t<float>(a, nf, emode, dot, st);
+}
+
+unsigned update_grid(size_t nelem) {
+    size_t b = (nelem + kUpdThreads - 1) / kUpdThreads;
+    size_t cap = kUpdBlocksPerSrc;
+    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+}
+
+cudaError_t launch_update(int prec, const UpdArgs& a, cudaStream_t st) {
+    dim3 grid(update_grid(a.nelem), (unsigned)a.nsrc);
+    if (prec == LQ_FP64) k_update<double><<<grid, kUpdThreads, 0, st>>>(a);
+    else k_update<float><<<grid, kUpdThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_tsl_init(int prec, int nf, const InitArgs& a, cudaStream_t st) {
+    dim3 grid((unsigned)((a.V + kUpdThreads - 1) / kUpdThreads), (unsigned)a.nsrc);
+    if (prec == LQ_FP64) { if (nf == 1) k_tsl_init<double, 1><<<grid, kUpdThreads, 0, st>>>(a); else k_tsl_init<double, 2><<<grid, kUpdThreads, 0, st>>>(a); }
+    else { if (nf == 1) k_tsl_init<float, 1><<<grid, kUpdThreads, 0, st>>>(a); else k_tsl_init<float, 2><<<grid, kUpdThreads, 0, st>>>(a); }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_recombine(int prec, int nf, const RecArgs& a, cudaStream_t st) {
+    dim3 grid((unsigned)((a.V + kRecThreads - 1) / kRecThreads), (unsigned)a.nsrc, (unsigned)nf);
+    size_t sm = (size_t)a.kmax * sizeof(double2) * (prec == LQ_FP64 ? 1 : 2);
+    if (prec == LQ_FP64) {
+        if (nf == 1) { cudaFuncSetAttribute(k_recombine<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); k_recombine<double, 1><<<grid, kRecThreads, sm, st>>>(a); }
+        else { cudaFuncSetAttribute(k_recombine<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); k_recombine<double, 2><<<grid, kRecThreads, sm, st>>>(a); }
+    } else {
+        if (nf == 1) { cudaFuncSetAttribute(k_recombine<float, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); k_recombine<float, 1><<<grid, kRecThreads, sm, st>>>(a); }
+        else { cudaFuncSetAttribute(k_recombine<float, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); k_recombine<float, 2><<<grid, kRecThreads, sm, st>>>(a); }
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_internal(int prec, const double* x, void* f, size_t V, int nfields, cudaStream_t st) {
+    dim3 grid((unsigned)((V + 127) / 128), (unsigned)nfields);
+    if (prec == LQ_FP64) k_to_internal<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(f), V, nfields);
+    else k_to_internal<float><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(x), reinterpret_cast<float4*>(f), V, nfields);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_to_boundary(int prec, const void* f, double* x, size_t V, int nfields, cudaStream_t st) {
+    dim3 grid((unsigned)((V + 127) / 128), (unsigned)nfields);
+    if (prec == LQ_FP64) k_to_boundary<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(f), reinterpret_cast<double2*>(x), V, nfields);
+    else k_to_boundary<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float4*>(f), reinterpret_cast<double2*>(x), V, nfields);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links_internal(int prec, const double* U, void* L, size_t V, cudaStream_t st) {
+    dim3 grid((unsigned)((V + 127) / 128), 4);
+    if (prec == LQ_FP64) k_links_internal<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(U), reinterpret_cast<double2*>(L), V);
+    else k_links_internal<float><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(U), reinterpret_cast<float2*>(L), V);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_direction(int prec, const double* U, const double* w, int kind, void* Y, size_t V, cudaStream_t st) {
+    dim3 grid((unsigned)((V + 127) / 128), 4);
+    if (prec == LQ_FP64) k_direction<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(U), w, kind, reinterpret_cast<double2*>(Y), V);
+    else k_direction<float><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(U), w, kind, reinterpret_cast<float2*>(Y), V);
+    return cudaGetLastError();
+}
+
+}  // namespace lq

@@ -1,0 +1,128 @@
+// Kernel argument blocks and host launchers shared by the library's translation units.
+#pragma once
+#include <cuda_runtime.h>
+#include <cstddef>
+
+#include "lq_internal.cuh"
+
+namespace lq {
+
+constexpr int kHopThreads = 128;
+constexpr int kUpdThreads = 256;
+constexpr int kRecThreads = 128;
+constexpr int kUpdBlocksPerSrc = 304;      // 2 x 152 SMs: grid-stride update kernel
+
+// Arguments of the stencil kernel k_hop (Eq. (1.1), block operator of Eq. (2.5)).
+struct HopArgs {
+    int dims[4];           // x, y, z, t extents
+    size_t strides[4];     // site-index strides of the four directions
+    size_t V;
+    int apbc;
+    int nsrc, nsides;
+    int side0;             // side of blockIdx.z == 0 (0 = right / A, 1 = left / A^dag)
+    double diag;           // 4r + m_w
+    // hop factors, including the -1/2 of Dw: [side][direction]
+    double a_fwd[2][4], a_bwd[2][4];   // operator A (side 0) / A^dag (side 1)
+    double e_fwd[2][4], e_bwd[2][4];   // derivative E (side 0) / E^dag (side 1)
+    const void* U;         // links (internal)
+    const void* Y;         // dU/dt (internal), EMODE 2
+    const void* in[2];     // per side: NF consecutive fields of source 0
+    void* out[2];
+    size_t src_stride_in[2], src_stride_out[2];   // Chunk units between sources
+    // Lanczos alpha dot (DOT)
+    TslState* state;       // may be null (plain operator application)
+    double* partials;
+    size_t partial_stride; // blocks per source capacity
+    int* counters;
+    double2* alpha;
+    double* scale;
+    int kmax;              // row length of alpha/beta/delta/scale
+    int kmax_run;          // k of this run
+    int j;                 // 0-based Lanczos step
+};
+
+struct UpdArgs {
+    size_t nelem;          // Chunk elements per source and side (NF fields)
+    int nsrc;
+    int j;
+    const void* rout; const void* lout;
+    const void* v_cur; const void* v_prev; void* v_next;
+    const void* w_cur; const void* w_prev; void* w_next;
+    size_t src_stride_io, src_stride_basis, src_stride_left;
+    TslState* state;
+    double* partials;
+    size_t partial_stride;
+    int* counters;
+    double2* beta;
+    double* delta;
+    int kmax;
+};
+
+struct InitArgs {
+    size_t V;
+    int nsrc;
+    const double* x;       // boundary layout, device
+    void* v1; void* w1;
+    size_t src_stride_basis, src_stride_left;
+    TslState* state;
+    double* partials;
+    size_t partial_stride;
+    int* counters;
+    double breakdown_tol;
+};
+
+struct RecArgs {
+    size_t V;
+    int nsrc;
+    const void* basis;
+    size_t src_stride_basis;   // Chunk units
+    size_t vec_stride;         // Chunk units between consecutive Krylov vectors
+    const TslState* state;
+    const double* scale;
+    int kmax;
+    const double2* newton_X;
+    int ldx;
+    double* y0; double* y1;    // boundary layout outputs (device), field 0 / field 1
+};
+
+__device__ void tsl_alpha_step(const HopArgs& a, int src, double dre, double dim);
+
+cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st);
+cudaError_t launch_update(int prec, const UpdArgs& a, cudaStream_t st);
+cudaError_t launch_tsl_init(int prec, int nf, const InitArgs& a, cudaStream_t st);
+cudaError_t launch_recombine(int prec, int nf, const RecArgs& a, cudaStream_t st);
+cudaError_t launch_to_internal(int prec, const double* x, void* f, size_t V, int nfields, cudaStream_t st);
+cudaError_t launch_to_boundary(int prec, const void* f, double* x, size_t V, int nfields, cudaStream_t st);
+cudaError_t launch_links_internal(int prec, const double* U, void* L, size_t V, cudaStream_t st);
+cudaError_t launch_direction(int prec, const double* U, const double* w, int kind, void* Y, size_t V, cudaStream_t st);
+unsigned update_grid(size_t nelem);
+
+// Newton sign iteration (lq_newton.cu)
+struct NewtonArgs {
+    int k;                 // matrix dimension (padded)
+    int nb;                // batch
+    int ld;                // leading dimension of the per-matrix storage (>= k)
+    double2* X;            // [nb][ld][ld] iterate
+    double2* Y;            // [nb][ld][ld] work (inverse)
+    double2* F;            // [nb][ld] multipliers
+    int* perm;             // [nb][ld]
+    double* scal;          // [nb][16] scalars
+    double* partials;
+    size_t partial_stride;
+    int* counters;
+    double tol;
+    int max_iter;
+    // tridiagonal source (Lanczos): may be null when X is initialised densely
+    const TslState* state;
+    const double2* alpha; const double2* beta; const double* delta;
+    int kmax;
+};
+// scal layout per matrix
+enum { NS_NORMX = 0, NS_NORMY, NS_MU, NS_CHANGE, NS_DONE, NS_ITERS, NS_SCALING, NS_STATUS, NS_PREVCHANGE, NS_KEFF };
+
+cudaError_t newton_init_tridiag(const NewtonArgs& a, cudaStream_t st);
+cudaError_t newton_init_dense(const NewtonArgs& a, const double2* Xin, cudaStream_t st);
+cudaError_t newton_iteration(const NewtonArgs& a, cudaStream_t st);
+cudaError_t newton_copy_out(const NewtonArgs& a, double2* Sout, cudaStream_t st);
+
+}  // namespace lq

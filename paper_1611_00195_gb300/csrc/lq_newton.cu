@@ -1,0 +1,326 @@
+// Batched FP64 matrix sign by the scaled Newton iteration (Higham 2008, ch. 5):
+//     X_0 = T,   X_{i+1} = (m_i X_i + (m_i X_i)^{-1}) / 2,   m_i = sqrt(||X_i^{-1}||_F / ||X_i||_F),
+// the projected step sgn(T_k) e_1 of the two-sided Lanczos approximation (Sec. 2).
+// Norm scaling is switched off once the relative change drops below 1e-2; the iteration
+// stops when the relative Frobenius change is <= tol, or when (unscaled) it no longer
+// decreases quadratically below 1e-6 (rounding floor), or at max_iter (status LQ_ERR_NEWTON).
+//
+// The inverse is an in-place Gauss-Jordan elimination with partial (row) pivoting over the
+// whole device: one launch per pivot step eliminates column p from every other row of every
+// matrix in the batch; the block that finishes last for a matrix (atomic counter) chooses and
+// normalises the next pivot row.  After k steps the row interchanges are undone by column
+// interchanges in reverse order.
+#include "lq_internal.cuh"
+#include "lq_launch.h"
+
+namespace lq {
+
+constexpr int kNtThreads = 256;
+
+__device__ __forceinline__ bool nt_last_block(int* counter, int nblocks) {
+    __shared__ int is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        int prev = atomicAdd(counter, 1);
+        is_last = (prev == nblocks - 1);
+        if (is_last) *counter = 0;
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last != 0;
+}
+
+__device__ __forceinline__ double2 ld2cg(const double2* p) { return __ldcg(p); }
+
+// Pivot step p on matrix b, executed by a single block after every elimination of step p-1
+// is visible: choose the row r >= p with the largest |Y[r][p]|, swap rows p and r, scale row p
+// so that its pivot entry holds 1/piv (in-place inverse), store the column-p multipliers in F
+// and clear column p below/above the pivot.
+__device__ void nt_pivot(const NewtonArgs& a, int b, int p) {
+    __shared__ double sval[kNtThreads];
+    __shared__ int sidx[kNtThreads];
+    __shared__ double2 spiv;
+    const int k = a.k, ld = a.ld;
+    double2* Y = a.Y + (size_t)b * ld * ld;
+    double2* F = a.F + (size_t)b * ld;
+    double best = -1.0;
+    int bi = p;
+    for (int i = p + threadIdx.x; i < k; i += blockDim.x) {
+        double2 v = ld2cg(Y + (size_t)i * ld + p);
+        double m = v.x * v.x + v.y * v.y;
+        if (m > best) { best = m; bi = i; }
+    }
+    sval[threadIdx.x] = best;
+    sidx[threadIdx.x] = bi;
+    __syncthreads();
+    for (int off = blockDim.x / 2; off > 0; off >>= 1) {
+        if (threadIdx.x < off) {
+            double o = sval[threadIdx.x + off];
+            int oi = sidx[threadIdx.x + off];
+            if (o > sval[threadIdx.x] || (o == sval[threadIdx.x] && oi < sidx[threadIdx.x])) {
+                sval[threadIdx.x] = o;
+                sidx[threadIdx.x] = oi;
+            }
+        }
+        __syncthreads();
+    }
+    const int r = sidx[0];
+    if (threadIdx.x == 0) a.perm[(size_t)b * ld + p] = r;
+    if (r != p) {
+        for (int c = threadIdx.x; c < k; c += blockDim.x) {
+            double2 t = ld2cg(Y + (size_t)p * ld + c);
+            Y[(size_t)p * ld + c] = ld2cg(Y + (size_t)r * ld + c);
+            Y[(size_t)r * ld + c] = t;
+        }
+    }
+    __threadfence_block();
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        double2 piv = ld2cg(Y + (size_t)p * ld + p);
+        double n = piv.x * piv.x + piv.y * piv.y;
+        if (!(n > 0.0) || !isfinite(n)) {
+            a.scal[b * 16 + NS_STATUS] = (double)LQ_ERR_NEWTON;
+            spiv = make_double2(1.0, 0.0);
+        } else {
+            spiv = make_double2(piv.x / n, -piv.y / n);   // 1/piv
+        }
+    }
+    __syncthreads();
+    const double2 inv = spiv;
+    for (int c = threadIdx.x; c < k; c += blockDim.x) {
+        double2 v = (c == p) ? make_double2(1.0, 0.0) : ld2cg(Y + (size_t)p * ld + c);
+        Y[(size_t)p * ld + c] = cmul(v, inv);
+    }
+    for (int i = threadIdx.x; i < k; i += blockDim.x) {
+        if (i == p) { F[i] = make_double2(0.0, 0.0); continue; }
+        F[i] = ld2cg(Y + (size_t)i * ld + p);
+        Y[(size_t)i * ld + p] = make_double2(0.0, 0.0);
+    }
+}
+
+__device__ __forceinline__ bool nt_done(const NewtonArgs& a, int b) { return a.scal[b * 16 + NS_DONE] != 0.0; }
+
+// X_0 = T_k from the Lanczos coefficients (identity padding beyond k_eff).
+__global__ void k_nt_init_tridiag(NewtonArgs a) {
+    const int b = blockIdx.y;
+    const int k = a.k, ld = a.ld;
+    const int keff = a.state[b].k_eff;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e == 0) {
+        double* s = a.scal + b * 16;
+        for (int i = 0; i < 16; ++i) s[i] = 0.0;
+        s[NS_SCALING] = 1.0;
+        s[NS_PREVCHANGE] = 1e300;
+        s[NS_KEFF] = keff;
+        if (keff <= 0) { s[NS_DONE] = 1.0; s[NS_STATUS] = (double)LQ_ERR_NOT_READY; }
+    }
+    if (e >= (size_t)k * k) return;
+    const int i = (int)(e / k), c = (int)(e % k);
+    double2 v = make_double2(0.0, 0.0);
+    if (i < keff && c < keff) {
+        if (i == c) v = a.alpha[(size_t)b * a.kmax + i];
+        else if (c == i + 1) v = a.beta[(size_t)b * a.kmax + i];
+        else if (i == c + 1) v = make_double2(a.delta[(size_t)b * a.kmax + c], 0.0);
+    } else if (i == c) {
+        v = make_double2(1.0, 0.0);
+    }
+    a.X[(size_t)b * ld * ld + (size_t)i * ld + c] = v;
+}
+
+__global__ void k_nt_init_dense(NewtonArgs a, const double2* __restrict__ Xin) {
+    const int b = blockIdx.y;
+    const int k = a.k, ld = a.ld;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e == 0) {
+        double* s = a.scal + b * 16;
+        for (int i = 0; i < 16; ++i) s[i] = 0.0;
+        s[NS_SCALING] = 1.0;
+        s[NS_PREVCHANGE] = 1e300;
+        s[NS_KEFF] = k;
+    }
+    if (e >= (size_t)k * k) return;
+    const int i = (int)(e / k), c = (int)(e % k);
+    a.X[(size_t)b * ld * ld + (size_t)i * ld + c] = Xin[(size_t)b * k * k + e];
+}
+
+// Y = X, ||X||_F^2; last block pivots step 0.
+__global__ void __launch_bounds__(kNtThreads) k_nt_copy(NewtonArgs a) {
+    __shared__ CSum smem[32];
+    const int b = blockIdx.y;
+    if (nt_done(a, b)) return;
+    const int k = a.k, ld = a.ld;
+    CSum acc{0.0, 0.0};
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (size_t)k * k) {
+        const size_t o = (size_t)b * ld * ld + (e / k) * ld + (e % k);
+        double2 v = a.X[o];
+        a.Y[o] = v;
+        cs_add_prod(acc, v.x, v.x);
+        cs_add_prod(acc, v.y, v.y);
+    }
+    CSum v1[1] = {acc};
+    block_reduce_cs<1>(v1, smem);
+    double* part = a.partials + ((size_t)b * a.partial_stride + blockIdx.x) * 2;
+    if (threadIdx.x == 0) { part[0] = v1[0].s; part[1] = v1[0].e; }
+    if (nt_last_block(a.counters + b, gridDim.x)) {
+        CSum t{0.0, 0.0};
+        for (int i = threadIdx.x; i < (int)gridDim.x; i += blockDim.x) {
+            CSum p; p.s = __ldcg(a.partials + ((size_t)b * a.partial_stride + i) * 2); p.e = __ldcg(a.partials + ((size_t)b * a.partial_stride + i) * 2 + 1);
+            t = cs_merge(t, p);
+        }
+        CSum tv[1] = {t};
+        block_reduce_cs<1>(tv, smem);
+        if (threadIdx.x == 0) a.scal[b * 16 + NS_NORMX] = sqrt(tv[0].s + tv[0].e);
+        __syncthreads();
+        nt_pivot(a, b, 0);
+    }
+}
+
+// Eliminate column p from every row i != p: Y[i][c] -= F[i] * Y[p][c].  Last block pivots p+1.
+__global__ void __launch_bounds__(kNtThreads) k_nt_elim(NewtonArgs a, int p) {
+    const int b = blockIdx.y;
+    if (nt_done(a, b)) return;
+    const int k = a.k, ld = a.ld;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (size_t)k * k) {
+        const int i = (int)(e / k), c = (int)(e % k);
+        if (i != p) {
+            double2* Y = a.Y + (size_t)b * ld * ld;
+            const double2 f = a.F[(size_t)b * ld + i];
+            const double2 pr = Y[(size_t)p * ld + c];
+            double2 y = Y[(size_t)i * ld + c];
+            y.x = fma(-f.x, pr.x, y.x); y.x = fma(f.y, pr.y, y.x);
+            y.y = fma(-f.x, pr.y, y.y); y.y = fma(-f.y, pr.x, y.y);
+            Y[(size_t)i * ld + c] = y;
+        }
+    }
+    if (p + 1 < k && nt_last_block(a.counters + b, gridDim.x)) nt_pivot(a, b, p + 1);
+}
+
+// Undo the row interchanges (column swaps in reverse order, one thread per row) and
+// accumulate ||X^{-1}||_F^2; the last block sets the scaling m.
+__global__ void __launch_bounds__(kNtThreads) k_nt_unscramble(NewtonArgs a) {
+    __shared__ CSum smem[32];
+    const int b = blockIdx.y;
+    if (nt_done(a, b)) return;
+    const int k = a.k, ld = a.ld;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    CSum acc{0.0, 0.0};
+    if (i < k) {
+        double2* row = a.Y + (size_t)b * ld * ld + (size_t)i * ld;
+        const int* perm = a.perm + (size_t)b * ld;
+        for (int p = k - 1; p >= 0; --p) {
+            int r = perm[p];
+            if (r != p) { double2 t = row[p]; row[p] = row[r]; row[r] = t; }
+        }
+        for (int c = 0; c < k; ++c) { double2 v = row[c]; cs_add_prod(acc, v.x, v.x); cs_add_prod(acc, v.y, v.y); }
+    }
+    CSum v1[1] = {acc};
+    block_reduce_cs<1>(v1, smem);
+    double* part = a.partials + ((size_t)b * a.partial_stride + blockIdx.x) * 2;
+    if (threadIdx.x == 0) { part[0] = v1[0].s; part[1] = v1[0].e; }
+    if (nt_last_block(a.counters + a.nb + b, gridDim.x)) {
+        CSum t{0.0, 0.0};
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x) {
+            CSum p; p.s = __ldcg(a.partials + ((size_t)b * a.partial_stride + q) * 2); p.e = __ldcg(a.partials + ((size_t)b * a.partial_stride + q) * 2 + 1);
+            t = cs_merge(t, p);
+        }
+        CSum tv[1] = {t};
+        block_reduce_cs<1>(tv, smem);
+        if (threadIdx.x == 0) {
+            double* s = a.scal + b * 16;
+            const double ny = sqrt(tv[0].s + tv[0].e);
+            s[NS_NORMY] = ny;
+            s[NS_MU] = (s[NS_SCALING] != 0.0) ? sqrt(ny / s[NS_NORMX]) : 1.0;
+        }
+    }
+}
+
+// X_{i+1} = (m X + Y / m) / 2 with change / norm partials; last block updates the state.
+__global__ void __launch_bounds__(kNtThreads) k_nt_combine(NewtonArgs a) {
+    __shared__ CSum smem[32 * 2];
+    const int b = blockIdx.y;
+    if (nt_done(a, b)) return;
+    const int k = a.k, ld = a.ld;
+    const double m = a.scal[b * 16 + NS_MU];
+    const double h1 = 0.5 * m, h2 = 0.5 / m;
+    CSum acc[2] = {{0.0, 0.0}, {0.0, 0.0}};
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e < (size_t)k * k) {
+        const size_t o = (size_t)b * ld * ld + (e / k) * ld + (e % k);
+        const double2 x = a.X[o], y = a.Y[o];
+        const double2 xn = make_double2(h1 * x.x + h2 * y.x, h1 * x.y + h2 * y.y);
+        a.X[o] = xn;
+        const double dx = xn.x - x.x, dy = xn.y - x.y;
+        cs_add_prod(acc[0], dx, dx); cs_add_prod(acc[0], dy, dy);
+        cs_add_prod(acc[1], xn.x, xn.x); cs_add_prod(acc[1], xn.y, xn.y);
+    }
+    block_reduce_cs<2>(acc, smem);
+    double* part = a.partials + ((size_t)b * a.partial_stride + blockIdx.x) * 4;
+    if (threadIdx.x == 0) { part[0] = acc[0].s; part[1] = acc[0].e; part[2] = acc[1].s; part[3] = acc[1].e; }
+    if (nt_last_block(a.counters + 2 * a.nb + b, gridDim.x)) {
+        CSum t[2] = {{0.0, 0.0}, {0.0, 0.0}};
+        for (int q = threadIdx.x; q < (int)gridDim.x; q += blockDim.x)
+            for (int v = 0; v < 2; ++v) {
+                CSum p; p.s = __ldcg(a.partials + ((size_t)b * a.partial_stride + q) * 4 + 2 * v); p.e = __ldcg(a.partials + ((size_t)b * a.partial_stride + q) * 4 + 2 * v + 1);
+                t[v] = cs_merge(t[v], p);
+            }
+        block_reduce_cs<2>(t, smem);
+        if (threadIdx.x == 0) {
+            double* s = a.scal + b * 16;
+            const double ch = sqrt(t[0].s + t[0].e) / sqrt(t[1].s + t[1].e);
+            const double prev = s[NS_PREVCHANGE];
+            s[NS_ITERS] += 1.0;
+            s[NS_CHANGE] = ch;
+            const bool scaled = s[NS_SCALING] != 0.0;
+            bool done = false;
+            if (!isfinite(ch)) { s[NS_STATUS] = (double)LQ_ERR_NONFINITE; done = true; }
+            else if (ch <= a.tol) done = true;
+            else if (!scaled && ch < 1e-6 && ch > 0.5 * prev) done = true;   // rounding floor
+            if (scaled && ch < 1e-2) s[NS_SCALING] = 0.0;
+            s[NS_PREVCHANGE] = ch;
+            if (!done && s[NS_ITERS] >= a.max_iter) { s[NS_STATUS] = (double)LQ_ERR_NEWTON; done = true; }
+            if (s[NS_STATUS] != 0.0) done = true;
+            if (done) s[NS_DONE] = 1.0;
+        }
+    }
+}
+
+__global__ void k_nt_copy_out(NewtonArgs a, double2* __restrict__ S) {
+    const int b = blockIdx.y;
+    const int k = a.k, ld = a.ld;
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= (size_t)k * k) return;
+    S[(size_t)b * k * k + e] = a.X[(size_t)b * ld * ld + (e / k) * ld + (e % k)];
+}
+
+static inline dim3 nt_grid_elems(const NewtonArgs& a) {
+    return dim3((unsigned)(((size_t)a.k * a.k + kNtThreads - 1) / kNtThreads), (unsigned)a.nb);
+}
+
+cudaError_t newton_init_tridiag(const NewtonArgs& a, cudaStream_t st) {
+    k_nt_init_tridiag<<<nt_grid_elems(a), kNtThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t newton_init_dense(const NewtonArgs& a, const double2* Xin, cudaStream_t st) {
+    k_nt_init_dense<<<nt_grid_elems(a), kNtThreads, 0, st>>>(a, Xin);
+    return cudaGetLastError();
+}
+
+cudaError_t newton_iteration(const NewtonArgs& a, cudaStream_t st) {
+    const dim3 ge = nt_grid_elems(a);
+    k_nt_copy<<<ge, kNtThreads, 0, st>>>(a);
+    for (int p = 0; p < a.k; ++p) k_nt_elim<<<ge, kNtThreads, 0, st>>>(a, p);
+    k_nt_unscramble<<<dim3((unsigned)((a.k + kNtThreads - 1) / kNtThreads), (unsigned)a.nb), kNtThreads, 0, st>>>(a);
+    k_nt_combine<<<ge, kNtThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t newton_copy_out(const NewtonArgs& a, double2* Sout, cudaStream_t st) {
+    k_nt_copy_out<<<nt_grid_elems(a), kNtThreads, 0, st>>>(a, Sout);
+    return cudaGetLastError();
+}
+
+}  // namespace lq

@@ -1,0 +1,298 @@
+"""ctypes binding of liblq.so: argument marshalling only.
+
+Every step of the computation runs in the library's CUDA kernels; this module converts
+torch tensors / numpy arrays to pointers, sizes and streams, allocates caller-owned output
+buffers, and maps error codes to exceptions.  There is no fallback: if liblq.so cannot be
+loaded, every call raises.
+
+Field conventions (see include/lq.h): spinor batches are complex128 [nsrc][V][4][3]; gauge
+fields complex128 [4][V][3][3]; su(3) directions float64 [4][V][8]; U(1) directions
+float64 [4][V].  Inputs may live on the host (numpy or CPU tensors) or on the context's GPU
+(CUDA tensors); outputs are created on the same side as the input.
+"""
+import ctypes
+import os
+
+import numpy as np
+
+try:
+    import torch
+except Exception:  # the binding also works with numpy-only callers
+    torch = None
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "liblq.so")
+
+LQ_OK = 0
+ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_CUDA", -5: "LQ_ERR_BREAKDOWN",
+          -6: "LQ_ERR_NEWTON", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NOT_READY", -9: "LQ_ERR_NONFINITE"}
+LQ_FP64, LQ_MIXED = 0, 1
+LQ_DIR_MU, LQ_DIR_SU3, LQ_DIR_U1 = 0, 1, 2
+
+EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_upload_gauge", "lq_set_mu",
+            "lq_reserve", "lq_apply_H", "lq_set_direction", "lq_apply_block", "lq_sign_apply",
+            "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
+            "lq_profile_read"]
+
+
+class LatticeDesc(ctypes.Structure):
+    _fields_ = [("nt", ctypes.c_int), ("nx", ctypes.c_int), ("ny", ctypes.c_int), ("nz", ctypes.c_int),
+                ("m_w", ctypes.c_double), ("r", ctypes.c_double), ("mu", ctypes.c_double),
+                ("t_antiperiodic", ctypes.c_int), ("precision", ctypes.c_int)]
+
+
+class Opts(ctypes.Structure):
+    _fields_ = [("kmax", ctypes.c_int), ("breakdown_tol", ctypes.c_double), ("newton_max_iter", ctypes.c_int),
+                ("newton_tol", ctypes.c_double), ("deflate", ctypes.c_int)]
+
+
+class Report(ctypes.Structure):
+    _fields_ = [("k_eff", ctypes.c_int), ("newton_iters", ctypes.c_int), ("status", ctypes.c_int),
+                ("reserved", ctypes.c_int), ("newton_change", ctypes.c_double), ("x_norm", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class Profile(ctypes.Structure):
+    _fields_ = [("enabled", ctypes.c_int), ("reserved", ctypes.c_int), ("launches", ctypes.c_longlong),
+                ("hop_ms", ctypes.c_double), ("hop_launches", ctypes.c_longlong),
+                ("update_ms", ctypes.c_double), ("update_launches", ctypes.c_longlong),
+                ("newton_ms", ctypes.c_double), ("newton_iterations", ctypes.c_longlong),
+                ("other_ms", ctypes.c_double), ("other_launches", ctypes.c_longlong)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class Direction(ctypes.Structure):
+    _fields_ = [("kind", ctypes.c_int), ("field", ctypes.c_void_p)]
+
+
+_lib = None
+
+
+def lib():
+    """Load liblq.so (built in-tree by paper_1611_00195_gb300.build); raise if it is missing."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError("liblq.so is not built (%s); run paper_1611_00195_gb300.build.build()" % LIB_PATH)
+        L = ctypes.CDLL(LIB_PATH)
+        P, I, D = ctypes.c_void_p, ctypes.c_int, ctypes.c_double
+        L.lq_default_opts.argtypes = [ctypes.POINTER(Opts)]
+        L.lq_default_opts.restype = None
+        L.lq_create.argtypes = [ctypes.POINTER(LatticeDesc), ctypes.POINTER(P)]
+        L.lq_destroy.argtypes = [P]
+        L.lq_destroy.restype = None
+        L.lq_last_error.argtypes = [P]
+        L.lq_last_error.restype = ctypes.c_char_p
+        L.lq_upload_gauge.argtypes = [P, P, P]
+        L.lq_set_mu.argtypes = [P, D]
+        L.lq_reserve.argtypes = [P, I, I, I]
+        L.lq_apply_H.argtypes = [P, P, P, I, I, P]
+        L.lq_set_direction.argtypes = [P, ctypes.POINTER(Direction), P]
+        L.lq_apply_block.argtypes = [P, P, P, P, P, I, I, P]
+        L.lq_sign_apply.argtypes = [P, P, P, I, ctypes.POINTER(Opts), ctypes.POINTER(Report), P]
+        L.lq_sign_derivative_apply.argtypes = [P, ctypes.POINTER(Direction), P, P, P, I, ctypes.POINTER(Opts),
+                                               ctypes.POINTER(Report), P]
+        L.lq_tsl_coefficients.argtypes = [P, I, I, P, P, P]
+        L.lq_profile_enable.argtypes = [P, I]
+        L.lq_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
+        L.lq_newton_sign.argtypes = [P, P, P, I, I, I, D, ctypes.POINTER(I), P]
+        for name in EXPORTED:
+            if name not in ("lq_default_opts", "lq_destroy", "lq_last_error"):
+                getattr(L, name).restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+class LQError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__("%s (%d): %s" % (ERRORS.get(code, "LQ_ERR"), code, msg))
+        self.code = code
+
+
+# ---- marshalling helpers -------------------------------------------------------------------
+
+def _is_tensor(x):
+    return torch is not None and isinstance(x, torch.Tensor)
+
+
+def _ptr(x):
+    if x is None:
+        return None
+    if _is_tensor(x):
+        if not x.is_contiguous():
+            raise ValueError("tensor must be contiguous")
+        return ctypes.c_void_p(x.data_ptr())
+    if isinstance(x, np.ndarray):
+        if not x.flags["C_CONTIGUOUS"]:
+            raise ValueError("array must be C-contiguous")
+        return ctypes.c_void_p(x.ctypes.data)
+    raise TypeError("expected a torch.Tensor or numpy.ndarray, got %r" % type(x))
+
+
+def _as_c128(x):
+    if _is_tensor(x):
+        return x.to(torch.complex128).contiguous()
+    return np.ascontiguousarray(x, dtype=np.complex128)
+
+
+def _as_f64(x):
+    if _is_tensor(x):
+        return x.to(torch.float64).contiguous()
+    return np.ascontiguousarray(x, dtype=np.float64)
+
+
+def _empty_like(x, shape=None):
+    shape = tuple(x.shape) if shape is None else tuple(shape)
+    if _is_tensor(x):
+        return torch.empty(shape, dtype=x.dtype, device=x.device)
+    return np.empty(shape, dtype=x.dtype)
+
+
+def _stream(x=None):
+    if torch is not None and torch.cuda.is_available():
+        dev = x.device if (_is_tensor(x) and x.is_cuda) else None
+        return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
+    return ctypes.c_void_p(0)
+
+
+class Context:
+    """One lattice, gauge field, Wilson parameters and workspace on the current CUDA device.
+
+    dims = (nt, nx, ny, nz); precision = LQ_FP64 or LQ_MIXED (include/lq.h)."""
+
+    def __init__(self, dims, m_w=-2.0, mu=0.0, precision=LQ_FP64, antiperiodic_t=True, r=1.0):
+        self._L = lib()
+        nt, nx, ny, nz = (int(d) for d in dims)
+        self.dims = (nt, nx, ny, nz)
+        self.V = nt * nx * ny * nz
+        self.precision = precision
+        d = LatticeDesc(nt, nx, ny, nz, float(m_w), float(r), float(mu), int(bool(antiperiodic_t)), int(precision))
+        h = ctypes.c_void_p()
+        self._check(self._L.lq_create(ctypes.byref(d), ctypes.byref(h)), None)
+        self._h = h
+        self.mu = float(mu)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._L.lq_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, code, h="self"):
+        if code != LQ_OK:
+            msg = ""
+            handle = self._h if h == "self" else h
+            if handle:
+                m = self._L.lq_last_error(handle)
+                msg = m.decode() if m else ""
+            raise LQError(code, msg)
+
+    # --- set-up -----------------------------------------------------------------------
+    def upload_gauge(self, U):
+        U = _as_c128(U)
+        self._U = U
+        self._check(self._L.lq_upload_gauge(self._h, _ptr(U), _stream(U)))
+
+    def set_mu(self, mu):
+        self._check(self._L.lq_set_mu(self._h, float(mu)))
+        self.mu = float(mu)
+
+    def reserve(self, kmax, nsrc, block=True):
+        self._check(self._L.lq_reserve(self._h, int(kmax), int(nsrc), int(bool(block))))
+
+    def _direction(self, kind, field):
+        if kind == LQ_DIR_MU:
+            return Direction(LQ_DIR_MU, None), None
+        f = _as_f64(field)
+        return Direction(kind, _ptr(f)), f
+
+    def set_direction(self, kind, field=None):
+        d, keep = self._direction(kind, field)
+        self._check(self._L.lq_set_direction(self._h, ctypes.byref(d), _stream(keep)))
+        self._dir_keep = keep
+
+    # --- operators ----------------------------------------------------------------------
+    def apply_H(self, x, dagger=False):
+        """H(mu) x (or H(mu)^dag x) for x of shape [nsrc][V][4][3]."""
+        x = _as_c128(x)
+        nsrc = x.shape[0]
+        y = _empty_like(x)
+        self._check(self._L.lq_apply_H(self._h, _ptr(x), _ptr(y), int(nsrc), int(bool(dagger)), _stream(x)))
+        return y
+
+    def apply_block(self, top, bottom, dagger=False):
+        """B (top, bottom) = (A top + dA bottom, A bottom), or B^dag, along the current direction."""
+        top, bottom = _as_c128(top), _as_c128(bottom)
+        yt, yb = _empty_like(top), _empty_like(bottom)
+        self._check(self._L.lq_apply_block(self._h, _ptr(top), _ptr(bottom), _ptr(yt), _ptr(yb), int(top.shape[0]),
+                                           int(bool(dagger)), _stream(top)))
+        return yt, yb
+
+    @staticmethod
+    def opts(k, breakdown_tol=1e-14, newton_max_iter=50, newton_tol=1e-13):
+        o = Opts()
+        lib().lq_default_opts(ctypes.byref(o))
+        o.kmax = int(k)
+        o.breakdown_tol = float(breakdown_tol)
+        o.newton_max_iter = int(newton_max_iter)
+        o.newton_tol = float(newton_tol)
+        return o
+
+    def sign_apply(self, x, k, **kw):
+        """sgn(H(mu)) x by k steps of two-sided Lanczos; returns (y, reports)."""
+        x = _as_c128(x)
+        nsrc = x.shape[0]
+        y = _empty_like(x)
+        o = self.opts(k, **kw)
+        rep = (Report * nsrc)()
+        self._check(self._L.lq_sign_apply(self._h, _ptr(x), _ptr(y), int(nsrc), ctypes.byref(o), rep, _stream(x)))
+        return y, [r.as_dict() for r in rep]
+
+    def sign_derivative_apply(self, x, k, kind=LQ_DIR_MU, field=None, **kw):
+        """Eq. (2.6): returns (sgn(H) x, d_t sgn(H) x, reports) along the direction (kind, field)."""
+        x = _as_c128(x)
+        nsrc = x.shape[0]
+        ys, yd = _empty_like(x), _empty_like(x)
+        d, keep = self._direction(kind, field)
+        o = self.opts(k, **kw)
+        rep = (Report * nsrc)()
+        self._check(self._L.lq_sign_derivative_apply(self._h, ctypes.byref(d), _ptr(x), _ptr(ys), _ptr(yd), int(nsrc),
+                                                     ctypes.byref(o), rep, _stream(x)))
+        del keep
+        return ys, yd, [r.as_dict() for r in rep]
+
+    def profile_enable(self, enable=True):
+        """Reset the kernel-time totals and launch count; enable CUDA-event timing."""
+        self._check(self._L.lq_profile_enable(self._h, int(bool(enable))))
+
+    def profile(self):
+        p = Profile()
+        self._check(self._L.lq_profile_read(self._h, ctypes.byref(p)))
+        return p.as_dict()
+
+    def tsl_coefficients(self, src, k):
+        """(alpha, beta, delta) of the projected tridiagonal T_k from the last solve."""
+        a = np.zeros(k, np.complex128)
+        b = np.zeros(k, np.complex128)
+        d = np.zeros(k, np.float64)
+        self._check(self._L.lq_tsl_coefficients(self._h, int(src), int(k), _ptr(a), _ptr(b), _ptr(d)))
+        return a, b[:k - 1], d[:k - 1]
+
+    def newton_sign(self, X, max_iter=50, tol=1e-13):
+        """Batched dense sign of complex k x k matrices X [nb][k][k] (CUDA tensor)."""
+        X = _as_c128(X)
+        nb, k = X.shape[0], X.shape[1]
+        S = _empty_like(X)
+        iters = (ctypes.c_int * nb)()
+        self._check(self._L.lq_newton_sign(self._h, _ptr(X), _ptr(S), int(k), int(nb), int(max_iter), float(tol),
+                                           iters, _stream(X)))
+        return S, list(iters)
