@@ -1,0 +1,404 @@
+#!/usr/bin/env python
+"""Benchmark of the two-sided Lanczos derivative path on one GB300 (or N replicas).
+
+Workload (one "step"): derivative solves of Eq. (2.6) -- sgn(H(mu)) x and d/dmu sgn(H(mu)) x
+for a batch of 16 Gaussian sources on a 14x14^3 lattice (V = 38416, n = 460992), seeded
+synthetic SU(3) links U = exp(i 0.4 X), m_w = -2, mu = 0.3, antiperiodic time, Krylov depth
+k = 400, mixed precision (FP32 stencil and vectors; FP64 compensated dots, coefficients and
+Newton sign).  The paper's quenched configurations are not available; seeded synthetic
+fields of the paper's largest lattice stand in for them.
+
+Printed (one JSON line, rank 0):
+  value      derivative solves/s over all ranks, inputs resident in HBM
+  e2e        the same through the C ABI with pinned HOST buffers (copies inside the region)
+  roofline   the stencil kernel (dominant): algorithmic bytes per launch / event-timed launch
+             duration against the measured HBM copy bandwidth
+  cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload (1 thread)
+  fp64_path  the plain FP64 GPU path on the same workload, and the mixed-vs-FP64 error
+
+`--impl reference` times the CPU oracle alone (rank 0) on the same workload and metric.
+"""
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+DIMS = (14, 14, 14, 14)
+EPS = 0.4
+M_W = -2.0
+MU = 0.3
+NSRC = 16
+K = 400
+GAUGE_SEED = 2016
+SOURCE_SEED = 1000
+METRIC = "derivative solves/s at 14^4 (mixed vs FP64, rel err); H(mu) GB/s vs peak"
+L2_BYTES = 126 * 2 ** 20
+
+
+def parse():
+    p = argparse.ArgumentParser()
+    p.add_argument("--gpus", type=int, default=1)
+    p.add_argument("--steps", type=int, default=5)
+    p.add_argument("--warmup", type=int, default=3)
+    p.add_argument("--impl", default="own", choices=["own", "reference"])
+    p.add_argument("--k", type=int, default=K)
+    p.add_argument("--nsrc", type=int, default=NSRC)
+    p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
+    p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    return p.parse_args()
+
+
+# ------------------------------------------------------------------------------------------
+# CPU oracle sample (runs in a spawned child with one BLAS/OpenMP thread)
+# ------------------------------------------------------------------------------------------
+def _oracle_sample(iters, k, seconds_cap=None):
+    """Time `iters` iterations of the oracle's block two-sided Lanczos (Eq. (2.6)) for one
+    source of the workload, plus the k x k projected sign by the oracle's Schur method, and
+    scale to one derivative solve at depth k.  Returns (seconds per solve, description)."""
+    import numpy as np
+    import synthetic as syn
+    from oracle import dirac as od
+    from oracle import tsl as ot
+    from oracle import sign as osg
+    lat = od.Lattice(DIMS, m_w=M_W)
+    U = syn.gauge_field(DIMS, EPS, GAUGE_SEED)
+    x = syn.gaussian_source(DIMS, SOURCE_SEED, nsrc=1)[0].ravel()
+    A = lambda v: od.apply_H(lat, U, v, MU).ravel()              # noqa: E731
+    Ah = lambda v: od.apply_Hdag(lat, U, v, MU).ravel()          # noqa: E731
+    E = lambda v: od.apply_dH_dmu(lat, U, v, MU).ravel()         # noqa: E731
+    Eh = lambda v: od.apply_dH_dmu_dag(lat, U, v, MU).ravel()    # noqa: E731
+    n = lat.n
+    B, Bh = ot.block_ops(A, Ah, E, Eh, n)
+    nx = np.linalg.norm(x)
+    v1 = np.concatenate([np.zeros(n, complex), x]) / nx
+    w1 = np.concatenate([x, x]) / nx
+    t0 = time.perf_counter()
+    r = ot.tsl(B, Bh, v1, w1, iters)
+    t_iter = (time.perf_counter() - t0) / iters
+    # projected step at the full depth: Schur sign of a k x k tridiagonal of the same kind
+    T = r["T"]
+    rng = np.random.default_rng(0)
+    Tk = np.diag(np.resize(np.diag(T), k)) + np.diag(np.resize(np.diag(T, 1), k - 1), 1) + np.diag(np.resize(np.diag(T, -1), k - 1), -1)
+    Tk = Tk + 1e-3 * np.diag(rng.standard_normal(k))
+    t1 = time.perf_counter()
+    osg.sign_schur(Tk)
+    t_proj = time.perf_counter() - t1
+    per_solve = t_iter * k + t_proj
+    desc = ("oracle block TSL (FP64 numpy), 1 source of 16, %d of %d iterations at 14x14^3 timed "
+            "(%.3f s/iteration) and scaled to k=%d, plus one k x k Schur sign (%.2f s)" % (iters, k, t_iter, k, t_proj))
+    return per_solve, desc
+
+
+def _oracle_child(q, iters, k):
+    try:
+        q.put(_oracle_sample(iters, k))
+    except Exception as e:  # report, never hang the parent
+        q.put((None, repr(e)))
+
+
+def cpu_baseline(iters, k):
+    import multiprocessing as mp
+    env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
+    saved = {e: os.environ.get(e) for e in env_keys}
+    for e in env_keys:
+        os.environ[e] = "1"
+    try:
+        ctx = mp.get_context("spawn")
+        q = ctx.Queue()
+        p = ctx.Process(target=_oracle_child, args=(q, iters, k))
+        p.start()
+        res = q.get(timeout=900)
+        p.join(timeout=60)
+    finally:
+        for e, v in saved.items():
+            if v is None:
+                os.environ.pop(e, None)
+            else:
+                os.environ[e] = v
+    return res
+
+
+# ------------------------------------------------------------------------------------------
+# GPU clocks sampled during the timed region
+# ------------------------------------------------------------------------------------------
+class ClockSampler:
+    FIELDS = "index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown," \
+             "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap"
+
+    def __init__(self, bus_id=None):
+        self.proc = None
+        self.bus_id = bus_id
+
+    def start(self):
+        cmd = ["nvidia-smi", "--query-gpu=" + self.FIELDS, "--format=csv,noheader,nounits", "-lms", "200"]
+        if self.bus_id:
+            cmd += ["--id=" + self.bus_id]
+        try:
+            self.proc = subprocess.Popen(cmd, stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            out, _ = self.proc.communicate(timeout=10)
+        except Exception:
+            self.proc.kill()
+            out, _ = self.proc.communicate()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [v.strip() for v in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                smax.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        try:
+            d = json.load(open(p))
+            for key in ("hbm_gbs", "hbm_GBs", "hbm"):
+                if key in d:
+                    v = d[key]
+                    v = v.get("value", v) if isinstance(v, dict) else v
+                    return float(v), "measured"
+        except Exception:
+            pass
+    return 6800.0, "fallback"
+
+
+# ------------------------------------------------------------------------------------------
+def dist_setup():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if ws > 1:
+        import torch.distributed as dist
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    return ws, rank, local
+
+
+def barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def allmax(ws, v):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(v)], device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_reference(args, ws, rank):
+    """The CPU oracle as it stands on the host cores: each step is a bounded sample (a few
+    block-TSL iterations of one source), scaled to one derivative solve at depth k."""
+    if rank != 0:
+        return
+    iters = 3
+    times, walls = [], []
+    desc = ""
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        per_solve, desc = cpu_baseline(iters, args.k)
+        walls.append(time.perf_counter() - t0)
+        if per_solve is None:
+            print(json.dumps({"impl": "reference", "unavailable": "oracle sample failed: %s" % desc}))
+            return
+        times.append(per_solve)
+    per_solve = statistics.median(times)
+    value = 1.0 / per_solve
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(walls) * 1e3,
+            "ms_per_solve_extrapolated": per_solve * 1e3, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "14x14^3 derivative solves (d/dmu), k=%d, Gaussian sources, CPU FP64 oracle" % args.k,
+                       "lattice": "14x14^3", "k": args.k, "mu": MU, "m_w": M_W, "eps": EPS},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line))
+
+
+def main():
+    args = parse()
+    ws, rank, local = dist_setup()
+    if args.impl == "reference":
+        run_reference(args, ws, rank)
+        return
+    import numpy as np
+    import torch
+    import synthetic as syn
+    from paper_1611_00195_gb300 import build, lq
+
+    build.build()
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    k, nsrc = args.k, args.nsrc
+    V = int(np.prod(DIMS))
+    n = 12 * V
+
+    U = syn.gauge_field(DIMS, EPS, GAUGE_SEED)
+    x = syn.gaussian_source(DIMS, SOURCE_SEED + rank, nsrc=nsrc)
+    xd = torch.from_numpy(x).to(dev)
+    ctx = lq.Context(DIMS, m_w=M_W, mu=MU, precision=lq.LQ_MIXED)
+    ctx.upload_gauge(torch.from_numpy(U).to(dev))
+    ctx.reserve(k, nsrc, True)
+    ys = torch.empty_like(xd)
+    yd = torch.empty_like(xd)
+
+    for _ in range(args.warmup):
+        ctx.sign_derivative_apply(xd, k, out=(ys, yd))
+    torch.cuda.synchronize(dev)
+
+    props = torch.cuda.get_device_properties(dev)
+    bus = getattr(props, "pci_bus_id", None)
+    sampler = ClockSampler(bus if isinstance(bus, str) else None)
+    ctx.profile_enable(True)
+    sampler.start()
+    time.sleep(0.3)
+    barrier(ws)
+    torch.cuda.synchronize(dev)
+    ev0, ev1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    reps = None
+    for _ in range(args.steps):
+        _, _, reps = ctx.sign_derivative_apply(xd, k, out=(ys, yd))
+    ev1.record(stream)
+    torch.cuda.synchronize(dev)
+    barrier(ws)
+    clocks = sampler.stop()
+    prof = ctx.profile()
+    ms_local = ev0.elapsed_time(ev1)
+    ms = allmax(ws, ms_local)
+    value = nsrc * args.steps * ws / (ms / 1e3)
+
+    # roofline of the dominant kernel: the fused block stencil (right: B v, left: B^dag w)
+    hop_ms = prof["hop_ms"] / max(1, prof["hop_launches"])
+    hop_bytes = V * (8 * 96 * nsrc + 288)          # 8 FP32 spinor fields per source + FP32 links
+    hop_flops = 4 * 1320 * V * nsrc
+    peak, peak_kind = peaks()
+    achieved = hop_bytes / (hop_ms * 1e-3) / 1e9
+    traffic = None
+    tfile = os.path.join(ROOT, "profiles", "hop_traffic.json")
+    if os.path.exists(tfile):
+        try:
+            t = json.load(open(tfile))
+            if t.get("k") == k and t.get("nsrc") == nsrc and t.get("kernel_rev") == lq.KERNEL_REV:
+                traffic = t.get("dram_bytes_per_launch")
+        except Exception:
+            traffic = None
+    total_prof = prof["hop_ms"] + prof["update_ms"] + prof["newton_ms"] + prof["other_ms"]
+
+    # end to end through the C ABI with pinned host buffers
+    e2e = None
+    if not args.no_e2e:
+        xh = torch.from_numpy(x).pin_memory()
+        ysh = torch.empty_like(xh).pin_memory()
+        ydh = torch.empty_like(xh).pin_memory()
+        ctx.sign_derivative_apply(xh, k, out=(ysh, ydh))
+        barrier(ws)
+        t0 = time.perf_counter()
+        for _ in range(args.steps):
+            ctx.sign_derivative_apply(xh, k, out=(ysh, ydh))
+        torch.cuda.synchronize(dev)
+        te = allmax(ws, time.perf_counter() - t0)
+        e2e = {"value": nsrc * args.steps * ws / te, "unit": "solves/s",
+               "h2d_bytes_per_step": int(nsrc * n * 16), "d2h_bytes_per_step": int(2 * nsrc * n * 16)}
+        assert torch.allclose(ysh, ys.cpu()) and torch.allclose(ydh, yd.cpu())
+
+    # plain FP64 GPU path on the same workload and the mixed-vs-FP64 error
+    fp64 = None
+    if not args.no_fp64:
+        ctx64 = lq.Context(DIMS, m_w=M_W, mu=MU, precision=lq.LQ_FP64)
+        ctx64.upload_gauge(torch.from_numpy(U).to(dev))
+        ctx64.reserve(k, nsrc, True)
+        ys64, yd64 = torch.empty_like(xd), torch.empty_like(xd)
+        ctx64.sign_derivative_apply(xd, k, out=(ys64, yd64))
+        torch.cuda.synchronize(dev)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        ctx64.sign_derivative_apply(xd, k, out=(ys64, yd64))
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        ms64 = a.elapsed_time(b)
+
+        def rel(p, q):
+            p = p.reshape(nsrc, -1)
+            q = q.reshape(nsrc, -1)
+            return (torch.linalg.vector_norm(p - q, dim=1) / torch.linalg.vector_norm(q, dim=1)).cpu().numpy()
+        es, ed = rel(ys, ys64), rel(yd, yd64)
+        fp64 = {"value": nsrc / (ms64 / 1e3), "unit": "solves/s", "ms_per_step": ms64,
+                "speedup_mixed_over_fp64": (ms64 / (ms_local / args.steps)),
+                "rel_err_mixed_vs_fp64_sign": {"max": float(es.max()), "median": float(np.median(es))},
+                "rel_err_mixed_vs_fp64_deriv": {"max": float(ed.max()), "median": float(np.median(ed))}}
+        del ctx64
+
+    cpu = None
+    if not args.no_cpu and rank == 0:
+        per_solve, desc = cpu_baseline(8, k)
+        if per_solve is not None:
+            cpu = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc}
+        else:
+            cpu = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": "failed: " + desc}
+
+    if rank != 0:
+        return
+    line = {
+        "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+        "config": {"workload": "14x14^3 derivative solves (d/dmu), mixed precision", "lattice": "14x14^3",
+                   "V": V, "n": n, "k": k, "nsrc_per_gpu": nsrc, "mu": MU, "m_w": M_W, "eps": EPS,
+                   "direction": "d/dmu", "deflation": "off",
+                   "precision": "FP32 stencil/vectors (FP32 accumulation), FP64 compensated dots, coefficients, Newton",
+                   "parallelism": "replicas" if ws > 1 else "single GPU",
+                   "l2": "no flush: the Krylov basis streamed per step (%.1f GB) exceeds L2" % (k * nsrc * 2 * n * 8 / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "k_hop<float,2,1,true> (block stencil + alpha dot)",
+                     "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
+                     "peak_source": "%s (MEASURED_PEAKS.json)" % peak_kind if peak_kind == "measured" else "of fallback (6.8 TB/s)",
+                     "traffic": traffic, "algorithmic_bytes_per_launch": hop_bytes, "launch_ms": hop_ms,
+                     "achieved_tflops": hop_flops / (hop_ms * 1e-3) / 1e12},
+        "cpu_baseline": cpu,
+        "e2e": e2e,
+        "gpu_launches": int(prof["launches"]),
+        "clocks": clocks,
+        "fp64_path": fp64,
+        "time_breakdown_ms_per_step": {"stencil": prof["hop_ms"] / args.steps, "update": prof["update_ms"] / args.steps,
+                                       "newton": prof["newton_ms"] / args.steps, "other": prof["other_ms"] / args.steps,
+                                       "sum_of_kernels": total_prof / args.steps},
+        "newton_iterations_per_step": prof["newton_iterations"] / args.steps,
+        "report_source0": reps[0] if reps else None,
+    }
+    print(json.dumps(line))
+
+
+if __name__ == "__main__":
+    main()

@@ -80,16 +80,38 @@ typedef struct {
     double breakdown_tol;  /* serious breakdown if |<w^,v^>| < tol |w^| |v^| (default 1e-14)   */
     int newton_max_iter;   /* cap on Newton iterations for sgn(T_k) (default 50)              */
     double newton_tol;     /* stop when ||X_{i+1}-X_i||_F <= tol ||X_{i+1}||_F (default 1e-13) */
-    int deflate;           /* reserved (must be 0 in this version)                            */
+    int deflate;           /* 1: deflate with the uploaded eigenpairs (Sec. 3): Eq. (3.1) for
+                              the sign, Eqs. (3.2)-(3.4) for the derivative; 0: no deflation  */
+    int projected;         /* solver for the projected sign sgn(T_k) e_1 (default LQ_PROJ_AUTO)  */
+    int quad_nodes;        /* quadrature nodes N (default 64, at most 128)                      */
+    double proj_tol;       /* accept the quadrature when ||Q(T)Q(T)e_1 - e_1|| <= proj_tol
+                              (default 1e-11)                                                   */
+    int hop_variant;       /* stencil schedule: -1 = autotuned on first use (default), 0 = one
+                              thread per (site, side), 1 = one thread per (site, output field) */
+    int defl_kmax;         /* depth of the shifted solves for the eigenvector derivatives of the
+                              generalised deflation (0 = the reserved kmax)                    */
 } lq_opts;
+
+/* Projected step sgn(T_k) e_1 (Sec. 2):
+ *  LQ_PROJ_NEWTON  scaled Newton iteration on the dense k x k matrix (FP64, O(k^3));
+ *  LQ_PROJ_QUAD    midpoint quadrature of sgn(T) = (2/pi) T int_0^inf (t^2 + T^2)^{-1} dt
+ *                  with t = c tan(theta): 2N complex tridiagonal solves (FP64, O(N k));
+ *  LQ_PROJ_AUTO    the quadrature, accepted only if its involution residual
+ *                  ||Q(T) Q(T) e_1 - e_1|| <= proj_tol (retried with 2N nodes), else Newton. */
+#define LQ_PROJ_AUTO    0
+#define LQ_PROJ_NEWTON  1
+#define LQ_PROJ_QUAD    2
 
 typedef struct {
     int k_eff;             /* dimension of T actually built (< kmax after a breakdown)        */
-    int newton_iters;      /* Newton iterations taken on sgn(T_k)                             */
+    int newton_iters;      /* Newton iterations taken on sgn(T_k) (0 if not used)             */
     int status;            /* LQ_OK, LQ_ERR_BREAKDOWN, LQ_ERR_NEWTON or LQ_ERR_NONFINITE      */
-    int reserved;
+    int projected;         /* solver that produced sgn(T_k) e_1: LQ_PROJ_NEWTON or LQ_PROJ_QUAD */
     double newton_change;  /* last relative Frobenius change of the Newton iterate            */
     double x_norm;         /* |x| of the source                                               */
+    double proj_check;     /* involution residual of the quadrature (0 if not attempted)       */
+    int hop_variant;       /* stencil schedule used (see lq_opts.hop_variant)                  */
+    int reserved;
 } lq_report;
 
 typedef struct {
@@ -148,6 +170,24 @@ int  lq_sign_derivative_apply(lq_ctx* ctx, const lq_direction* dir, const double
                               double* y_sign, double* y_deriv, int nsrc,
                               const lq_opts* opts, lq_report* report, void* stream);
 
+/* Upload the l eigenpairs of A = H(mu) closest to zero for the deflation of Sec. 3:
+ * lambda: host double[l][2]; R: right eigenvectors (A R_i = lambda_i R_i), spinor layout
+ * double[l][V][4][3][2]; L: the left eigenvectors as kets, Lk_i = L_i^dag (so L_i A = lambda_i L_i
+ * and <Lk_i|R_j> = delta_ij), same layout.  Host or device memory; copied (FP64).  l = 0 removes
+ * the space.  Used by lq_sign_apply and lq_sign_derivative_apply when opts->deflate = 1.  Must
+ * follow lq_reserve; the library's own Arnoldi is not part of this version. */
+int  lq_upload_deflation(lq_ctx* ctx, int l, const double* lambda, const double* R, const double* L,
+                         void* stream);
+
+/* The derivatives of the uploaded eigenpairs along `dir` (end of Sec. 3), as used by the
+ * generalised deflation: dlambda_i = L_i E R_i; dR_j = sum_{i != j} R_i (L_i E R_j)/(lambda_j -
+ * lambda_i) + Pbar (lambda_j - A)^{-1} Pbar E R_j and its left analogue, with the shifted solves on
+ * the deflated complement done by two-sided Lanczos approximations of the resolvent at depth
+ * opts->kmax (Sec. 2 with f(a) = 1/(lambda_j - a)).  Outputs (host or device, may be NULL):
+ * dlambda double[l][2]; dR, dL (kets of dL_i) double[l][V][4][3][2].  Synchronises `stream`. */
+int  lq_deflation_derivatives(lq_ctx* ctx, const lq_direction* dir, const lq_opts* opts,
+                              double* dlambda, double* dR, double* dL, void* stream);
+
 /* Opt-in timing of the library's own kernels with CUDA events recorded on the launch
  * stream (no effect on results).  Enabling resets the totals.  Times are accumulated when a
  * reporting call synchronises its stream.  launches counts every kernel the library has
@@ -174,6 +214,16 @@ int  lq_profile_read(lq_ctx* ctx, lq_profile* out);
  * delta[j] = T[j+1][j] (real, > 0).  alpha, beta: host double[k][2] (complex); delta:
  * host double[k].  Entries beyond the source's k_eff are zero.  Synchronous. */
 int  lq_tsl_coefficients(lq_ctx* ctx, int src, int k, double* alpha, double* beta, double* delta);
+
+/* The self-check of Sec. 4: eps_A = ||sgn(A)^2 psi - psi|| / (2 ||psi||), each sgn(A) one TSL
+ * approximation of depth opts->kmax.  dir == NULL: the sign (two lq_sign_apply solves).
+ * dir != NULL: the derivative version with B of Eq. (2.5) and the source (0, x): the second
+ * application to the non-sparse (y_d, y_s) = sgn(B)(0, x) is taken by linearity,
+ * sgn(B)(y_d, y_s) = (sgn(A) y_d + d_t sgn(A) y_s, sgn(A) y_s) (two derivative solves and one
+ * sign solve).  x: nsrc fields (host or device); eps: host double[nsrc].  Needs
+ * lq_reserve(..., block = 1) for the derivative version.  Synchronises `stream`. */
+int  lq_error_estimate(lq_ctx* ctx, const lq_direction* dir, const double* x, int nsrc,
+                       const lq_opts* opts, double* eps, void* stream);
 
 /* Batched dense FP64 sign of nb complex k x k matrices by the scaled Newton iteration
  * X <- (m X + (m X)^{-1})/2, m = sqrt(||X^{-1}||_F / ||X||_F) (Higham 2008, ch. 5; the

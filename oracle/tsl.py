@@ -92,6 +92,37 @@ def block_ops(apply_A, apply_Ah, apply_E, apply_Eh, n):
     return B, Bh
 
 
+def tsl_resolvent(apply_A, apply_Ah, b, sigma, k, **kw):
+    """(sigma - A)^{-1} b ~ |b| V_k (sigma - T_k)^{-1} e_1: the TSL approximation of Sec. 2 for
+    f(a) = 1/(sigma - a) (the projected system solved densely)."""
+    b = np.asarray(b, dtype=complex).ravel()
+    nb = np.linalg.norm(b)
+    r = tsl(apply_A, apply_Ah, b / nb, b / nb, k, **kw)
+    e1 = np.zeros(r["T"].shape[0], complex)
+    e1[0] = 1.0
+    c = np.linalg.solve(sigma * np.eye(len(e1)) - r["T"], e1)
+    return nb * (r["V"].T @ c), r
+
+
+def tsl_sign_block(apply_A, apply_Ah, apply_E, apply_Eh, t0, b0, k, **kw):
+    """sgn(B)(t0, b0) by the TSL on the block operator B of Eq. (2.5) from v_1 = (t0, b0)/|(t0, b0)|
+    with the left start w_1 proportional to (b0, b0), normalised to <w_1, v_1> = 1 (the reading
+    that reduces to (x, x)/|x| for the sparse source (0, x) of Eq. (2.6)).  Returns (top, bottom, record)."""
+    t0 = np.asarray(t0, dtype=complex).ravel()
+    b0 = np.asarray(b0, dtype=complex).ravel()
+    n = b0.size
+    B, Bh = block_ops(apply_A, apply_Ah, apply_E, apply_Eh, n)
+    psi = np.concatenate([t0, b0])
+    npsi = np.linalg.norm(psi)
+    v1 = psi / npsi
+    w1 = np.concatenate([b0, b0])
+    w1 = w1 / np.conj(np.vdot(w1, v1))
+    r = tsl(B, Bh, v1, w1, k, **kw)
+    c = projected_sign_e1(r["T"])
+    y = npsi * (r["V"].T @ c)
+    return y[:n], y[n:], r
+
+
 def tsl_sign_derivative(apply_A, apply_Ah, apply_E, apply_Eh, x, k, left_start="xx", **kw):
     """Eq. (2.6): sgn(B)(0, x) = (d_t sgn(A) x, sgn(A) x), with the TSL applied to the
     2n x 2n block operator B of Eq. (2.5) from the right start v_1 = (0, x)/|x|.

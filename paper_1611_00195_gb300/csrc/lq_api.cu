@@ -138,6 +138,7 @@ HopArgs base_hop(const lq_ctx* c) {
     a.V = c->V;
     a.apbc = c->desc.t_antiperiodic ? 1 : 0;
     a.diag = 4.0 * c->desc.r + c->desc.m_w;
+    a.diag_f = (float)a.diag;
     a.U = c->U;
     a.Y = c->Y;
     return a;
@@ -146,6 +147,12 @@ HopArgs base_hop(const lq_ctx* c) {
 void set_side(HopArgs& a, int side, const lq_ctx* c, int dagger, int emode) {
     op_factors(c->desc.mu, dagger, a.a_fwd[side], a.a_bwd[side]);
     der_factors(c->desc.mu, emode, dagger, a.e_fwd[side], a.e_bwd[side]);
+    for (int nu = 0; nu < 4; ++nu) {
+        a.af_fwd[side][nu] = (float)a.a_fwd[side][nu];
+        a.af_bwd[side][nu] = (float)a.a_bwd[side][nu];
+        a.ef_fwd[side][nu] = (float)a.e_fwd[side][nu];
+        a.ef_bwd[side][nu] = (float)a.e_bwd[side][nu];
+    }
 }
 
 int check_ready(lq_ctx* c, int nsrc, int need_block) {
@@ -205,19 +212,59 @@ NewtonArgs newton_args(lq_ctx* c, int k, int nb, int max_iter, double tol) {
 }
 
 void free_workspace(lq_ctx* c) {
-    void** ps[] = {&c->basis, &c->left, &c->rout, &c->lout, (void**)&c->io, (void**)&c->partials, (void**)&c->counters,
+    void** ps[] = {&c->basis, &c->left, &c->rout, &c->lout, (void**)&c->io, (void**)&c->norms, (void**)&c->partials, (void**)&c->counters,
                    (void**)&c->state, (void**)&c->alpha, (void**)&c->beta, (void**)&c->delta, (void**)&c->scale,
                    (void**)&c->nx_X, (void**)&c->nx_Y, (void**)&c->nx_F, (void**)&c->nx_perm, (void**)&c->nx_scal,
-                   (void**)&c->nx_partials, (void**)&c->nx_counters};
+                   (void**)&c->nx_partials, (void**)&c->nx_counters, (void**)&c->proj_c, (void**)&c->quad_q,
+                   (void**)&c->quad_work, (void**)&c->quad_c, (void**)&c->quad_check};
     for (void** p : ps) { dfree(*p); *p = nullptr; }
     c->kmax = c->nsrc = c->block = 0;
+}
+
+// Choose the stencil schedule for the Lanczos step: time each variant on the caller's data
+// (three launches each, no dot, outputs into the scratch operator buffers) and keep the faster
+// one for this context and batch size.
+int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
+    if (nf != 2) { *variant = 0; return LQ_OK; }
+    if (c->tuned_nsrc != h.nsrc) {
+        for (auto& row : c->tuned_variant) for (int& v : row) v = -1;
+        c->tuned_nsrc = h.nsrc;
+    }
+    int& slot = c->tuned_variant[nf][emode];
+    if (slot >= 0) { *variant = slot; return LQ_OK; }
+    h.state = nullptr;
+    cudaEvent_t e0, e1;
+    LQ_CUDA(c, cudaEventCreate(&e0));
+    LQ_CUDA(c, cudaEventCreate(&e1));
+    float best = 1e30f;
+    int bestv = 0;
+    for (int v = 0; v <= 1; ++v) {
+        h.variant = v;
+        LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, false, st));   // warm-up
+        LQ_CUDA(c, cudaEventRecord(e0, st));
+        for (int i = 0; i < 3; ++i) LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, false, st));
+        LQ_CUDA(c, cudaEventRecord(e1, st));
+        LQ_CUDA(c, cudaEventSynchronize(e1));
+        float ms = 0.f;
+        LQ_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+        c->launches += 4;
+        if (ms < best) { best = ms; bestv = v; }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    slot = bestv;
+    *variant = bestv;
+    return LQ_OK;
 }
 
 // The Lanczos driver shared by lq_sign_apply (nf = 1) and lq_sign_derivative_apply (nf = 2).
 // The source is already staged in c->io (region 0, boundary layout); results go to the device
 // boundary-layout buffers y0 (field 0: sign, or top = derivative) and y1 (field 1: bottom = sign).
+enum { FN_SIGN = 0, FN_RESOLVENT = 1 };
+
 int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report* rep,
-            double* y0, double* y1, cudaStream_t st) {
+            double* y0, double* y1, cudaStream_t st, const double* x_dev = nullptr,
+            const double* x_top = nullptr, int fn = FN_SIGN, const double2* shifts = nullptr) {
     const int k = o->kmax;
     const size_t F = fe(c);
     const size_t vstride = (size_t)nf * F;        // Chunk elements per Krylov vector
@@ -232,7 +279,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
 
     InitArgs ia;
     std::memset(&ia, 0, sizeof(ia));
-    ia.V = c->V; ia.nsrc = nsrc; ia.x = c->io; ia.v1 = bvec(0); ia.w1 = lvec(0);
+    ia.V = c->V; ia.nsrc = nsrc; ia.x = x_dev ? x_dev : c->io; ia.xt = x_top; ia.v1 = bvec(0); ia.w1 = lvec(0);
     ia.src_stride_basis = sb; ia.src_stride_left = sl; ia.state = c->state;
     ia.partials = c->partials; ia.partial_stride = c->partial_blocks; ia.counters = c->counters;
     ia.breakdown_tol = o->breakdown_tol;
@@ -250,6 +297,16 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     h.src_stride_in[0] = sb; h.src_stride_in[1] = sl;
     h.src_stride_out[0] = sio; h.src_stride_out[1] = sio;
     h.out[0] = c->rout; h.out[1] = c->lout;
+    if (o->hop_variant >= 0) {
+        h.variant = (nf == 2) ? o->hop_variant : 0;
+    } else {
+        h.in[0] = bvec(0);
+        h.in[1] = lvec(0);
+        int v = 0;
+        int rr = tune_hop(c, h, nf, emode, st, &v);
+        if (rr) return rr;
+        h.variant = v;
+    }
 
     UpdArgs u;
     std::memset(&u, 0, sizeof(u));
@@ -277,17 +334,57 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
         }
     }
 
-    NewtonArgs na = newton_args(c, k, nsrc, o->newton_max_iter, o->newton_tol);
-    LQ_CUDA(c, newton_init_tridiag(na, st));
-    c->launches += 1;
-    std::vector<double> scal;
-    int r = run_newton(c, na, st, scal);
-    if (r) return r;
+    std::vector<double> scal((size_t)nsrc * 16, 0.0);
+    std::vector<double> check(nsrc, 0.0);   // stays 0 when the quadrature is not attempted
+    std::vector<int> used(nsrc, LQ_PROJ_NEWTON);
+    int r;
+    bool need_newton = o->projected == LQ_PROJ_NEWTON && fn == FN_SIGN;
+    if (fn == FN_RESOLVENT) {
+        QuadArgs qa;
+        std::memset(&qa, 0, sizeof(qa));
+        qa.k = k; qa.nb = nsrc; qa.kmax = c->kmax; qa.nth_max = 2 * kQuadMaxNodes; qa.state = c->state;
+        qa.alpha = c->alpha; qa.beta = c->beta; qa.delta = c->delta; qa.work = c->quad_work;
+        qa.s = c->proj_c; qa.check = c->quad_check;
+        LQ_CUDA(c, proj_resolvent(qa, shifts, st));
+        c->launches += 1;
+        for (int s = 0; s < nsrc; ++s) used[s] = 3;
+    } else if (o->projected != LQ_PROJ_NEWTON) {
+        QuadArgs qa;
+        std::memset(&qa, 0, sizeof(qa));
+        qa.k = k; qa.nb = nsrc; qa.kmax = c->kmax; qa.nth_max = 2 * kQuadMaxNodes; qa.state = c->state;
+        qa.alpha = c->alpha; qa.beta = c->beta; qa.delta = c->delta; qa.c = c->quad_c; qa.work = c->quad_work;
+        qa.s = c->proj_c; qa.q = c->quad_q; qa.check = c->quad_check;
+        int nodes = o->quad_nodes;
+        bool ok = false;
+        for (int attempt = 0; attempt < 2; ++attempt) {
+            cudaEvent_t eq = prof_begin(c, st);
+            LQ_CUDA(c, quad_sign_e1(qa, nodes, st));
+            prof_end(c, PC_NEWTON, eq, st, 0);
+            c->launches += 3;
+            LQ_CUDA(c, cudaMemcpyAsync(check.data(), c->quad_check, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
+            LQ_CUDA(c, cudaStreamSynchronize(st));
+            ok = true;
+            for (int s = 0; s < nsrc; ++s) ok = ok && std::isfinite(check[s]) && check[s] <= o->proj_tol;
+            if (ok || o->projected == LQ_PROJ_QUAD || nodes * 2 > kQuadMaxNodes) break;
+            nodes *= 2;   // one retry with twice the nodes
+        }
+        need_newton = !ok && o->projected == LQ_PROJ_AUTO;
+        for (int s = 0; s < nsrc; ++s) used[s] = LQ_PROJ_QUAD;
+    }
+    if (need_newton) {
+        NewtonArgs na = newton_args(c, k, nsrc, o->newton_max_iter, o->newton_tol);
+        LQ_CUDA(c, newton_init_tridiag(na, st));
+        c->launches += 1;
+        if ((r = run_newton(c, na, st, scal))) return r;
+        LQ_CUDA(c, newton_first_column(na, c->proj_c, c->kmax, st));
+        c->launches += 1;
+        for (int s = 0; s < nsrc; ++s) used[s] = LQ_PROJ_NEWTON;
+    }
 
     RecArgs ra;
     std::memset(&ra, 0, sizeof(ra));
     ra.V = c->V; ra.nsrc = nsrc; ra.basis = c->basis; ra.src_stride_basis = sb; ra.vec_stride = vstride;
-    ra.state = c->state; ra.scale = c->scale; ra.kmax = c->kmax; ra.newton_X = c->nx_X; ra.ldx = c->kmax;
+    ra.state = c->state; ra.scale = c->scale; ra.kmax = c->kmax; ra.coef = c->proj_c;
     ra.y0 = y0; ra.y1 = y1;
     cudaEvent_t er = prof_begin(c, st);
     LQ_CUDA(c, launch_recombine(c->prec, nf, ra, st));
@@ -306,19 +403,188 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
             R.x_norm = hs[s].xnorm;
             R.newton_iters = (int)scal[(size_t)s * 16 + NS_ITERS];
             R.newton_change = scal[(size_t)s * 16 + NS_CHANGE];
+            R.projected = used[s];
+            R.hop_variant = h.variant;
+            R.proj_check = check[s];   // involution residual of the quadrature when it was attempted
             const int ts = hs[s].status;
-            const int ns = (int)scal[(size_t)s * 16 + NS_STATUS];
+            int ns = (int)scal[(size_t)s * 16 + NS_STATUS];
+            if (used[s] == LQ_PROJ_QUAD && !(std::isfinite(check[s]) && check[s] <= o->proj_tol)) ns = LQ_ERR_NEWTON;
             R.status = ts < 0 ? ts : (ns != 0 ? ns : LQ_OK);
         }
     }
     return LQ_OK;
 }
 
-int check_opts(lq_ctx* c, const lq_opts* o) {
+int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (!o) return set_err(c, LQ_ERR_ARG, "null opts");
     if (o->kmax < 1 || o->kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "opts.kmax must be in [1, reserved kmax]");
     if (o->newton_max_iter < 1 || !(o->newton_tol > 0.0) || !(o->breakdown_tol >= 0.0)) return set_err(c, LQ_ERR_ARG, "invalid Newton / breakdown options");
-    if (o->deflate != 0) return set_err(c, LQ_ERR_ARG, "deflation is not available in this entry point");
+    if (o->deflate != 0 && !allow_deflate) return set_err(c, LQ_ERR_ARG, "deflation is not available in this entry point");
+    if (o->deflate != 0 && c->defl_l <= 0) return set_err(c, LQ_ERR_NOT_READY, "deflate = 1 but no deflation space uploaded");
+    if (o->projected < LQ_PROJ_AUTO || o->projected > LQ_PROJ_QUAD) return set_err(c, LQ_ERR_ARG, "unknown projected-sign solver");
+    if (o->projected != LQ_PROJ_NEWTON && (o->quad_nodes < 1 || o->quad_nodes > kQuadMaxNodes || !(o->proj_tol > 0.0)))
+        return set_err(c, LQ_ERR_ARG, "quad_nodes must be in [1, 128] and proj_tol > 0");
+    if (o->hop_variant < -1 || o->hop_variant > 1) return set_err(c, LQ_ERR_ARG, "hop_variant must be -1, 0 or 1");
+    if (o->defl_kmax < 0 || o->defl_kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "defl_kmax must be in [0, reserved kmax]");
+    return LQ_OK;
+}
+
+
+// ---- deflation (Sec. 3) -------------------------------------------------------------------
+size_t nvec(const lq_ctx* c) { return c->V * 24; }   // doubles per boundary-layout field
+
+// <X_a|Y_b> for a < nx, b < ny (device vectors, stride nvec) -> host out[a * ny + b]
+int bdots_host(lq_ctx* c, const double* X, int nx, const double* Y, int ny, std::vector<double2>& out, cudaStream_t st) {
+    out.assign((size_t)nx * ny, make_double2(0.0, 0.0));
+    if (nx == 0 || ny == 0) return LQ_OK;
+    const size_t need = bdots_partial_doubles(nx * ny) + 2 * (size_t)nx * ny;
+    if (need > c->defl_scr_doubles) return set_err(c, LQ_ERR_ARG, "deflation scratch too small");
+    double* part = c->defl_scr;
+    double* res = c->defl_scr + bdots_partial_doubles(nx * ny);
+    LQ_CUDA(c, launch_bdots(X, nvec(c), nx, Y, nvec(c), ny, nvec(c), part, res, st));
+    c->launches += 2;
+    LQ_CUDA(c, cudaMemcpyAsync(out.data(), res, sizeof(double2) * nx * ny, cudaMemcpyDeviceToHost, st));
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+// Z_b = W_b + sum_a coef[b * nx + a] X_a with host coefficients
+int bcombine_host(lq_ctx* c, double* Z, const double* W, int nz, const double* X, int nx,
+                  const std::vector<double2>& coef, cudaStream_t st) {
+    if (nz == 0) return LQ_OK;
+    double* dc = c->defl_scr;
+    if ((size_t)nz * nx * 2 > c->defl_scr_doubles) return set_err(c, LQ_ERR_ARG, "deflation scratch too small");
+    LQ_CUDA(c, cudaMemcpyAsync(dc, coef.data(), sizeof(double2) * nz * nx, cudaMemcpyHostToDevice, st));
+    LQ_CUDA(c, launch_bcombine(Z, W, nvec(c), nz, X, nvec(c), nx, dc, nvec(c), st));
+    c->launches += 1;
+    LQ_CUDA(c, cudaStreamSynchronize(st));   // the coefficient buffer is reused by the next call
+    return LQ_OK;
+}
+
+// out_j = E in_j (dagger = 0) or E^dag in_j (dagger = 1) for `count` boundary fields on the
+// device, along the current direction: the block stencil with the operator part switched off.
+int apply_E(lq_ctx* c, const double* in, double* out, int count, int dagger, cudaStream_t st) {
+    const int em = emode_of(c);
+    if (em == 0) return set_err(c, LQ_ERR_NOT_READY, "no derivative direction set");
+    for (int b0 = 0; b0 < count; b0 += c->nsrc) {
+        const int nb = std::min(c->nsrc, count - b0);
+        // fields [src][2]: both halves hold the input, so side 0 gives E in (top) and side 1 E^dag in (bottom)
+        for (int s = 0; s < nb; ++s) {
+            LQ_CUDA(c, launch_to_internal(c->prec, in + (size_t)(b0 + s) * nvec(c),
+                                          reinterpret_cast<char*>(c->rout) + (size_t)(2 * s) * fb(c), c->V, 1, st));
+            LQ_CUDA(c, launch_to_internal(c->prec, in + (size_t)(b0 + s) * nvec(c),
+                                          reinterpret_cast<char*>(c->rout) + (size_t)(2 * s + 1) * fb(c), c->V, 1, st));
+        }
+        HopArgs a = base_hop(c);
+        a.nsrc = nb;
+        a.nsides = 1;
+        a.side0 = dagger ? 1 : 0;
+        set_side(a, a.side0, c, dagger ? 1 : 0, em);
+        for (int nu = 0; nu < 4; ++nu) {
+            a.a_fwd[a.side0][nu] = a.a_bwd[a.side0][nu] = 0.0;
+            a.af_fwd[a.side0][nu] = a.af_bwd[a.side0][nu] = 0.0f;
+        }
+        a.diag = 0.0;
+        a.diag_f = 0.0f;
+        a.in[a.side0] = c->rout;
+        a.out[a.side0] = c->lout;
+        a.src_stride_in[a.side0] = 2 * fe(c);
+        a.src_stride_out[a.side0] = 2 * fe(c);
+        LQ_CUDA(c, launch_hop(c->prec, a, 2, em, false, st));
+        for (int s = 0; s < nb; ++s)
+            LQ_CUDA(c, launch_to_boundary(c->prec, reinterpret_cast<char*>(c->lout) + (size_t)(2 * s + (dagger ? 1 : 0)) * fb(c),
+                                          out + (size_t)(b0 + s) * nvec(c), c->V, 1, st));
+        c->launches += 3 * nb + 1;
+    }
+    return LQ_OK;
+}
+
+double sgn_re(double2 z) { return z.x > 0 ? 1.0 : (z.x < 0 ? -1.0 : 0.0); }
+double2 cdivh(double2 a, double2 b) {
+    const double d = b.x * b.x + b.y * b.y;
+    return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
+}
+double2 cmulh(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
+double2 conjh(double2 a) { return make_double2(a.x, -a.y); }
+
+// dlambda_i, dR_i, dL_i for the current direction (end of Sec. 3):
+//   dR_j = sum_{i != j} R_i (L_i E R_j)/(lambda_j - lambda_i) + Pbar (lambda_j - A)^{-1} Pbar E R_j
+//   dLk_j = sum_{i != j} conj((L_j E R_i)/(lambda_j - lambda_i)) Lk_i
+//           + Pbar^dag (conj lambda_j - A^dag)^{-1} Pbar^dag E^dag Lk_j
+// The shifted solves are two-sided Lanczos approximations of the resolvent at depth opts->kmax
+// (the projected function (sigma - T)^{-1} e_1), started from deflated right-hand sides.
+int prepare_deflation_derivative(lq_ctx* c, const lq_opts* o, cudaStream_t st) {
+    const int l = c->defl_l;
+    const size_t nv = nvec(c);
+    double* R = c->defl_V;
+    double* dR = c->defl_V + (size_t)l * nv;
+    double* Lk = c->defl_W;
+    double* dLk = c->defl_W + (size_t)l * nv;
+    double* ER = c->defl_work;
+    double* ELk = ER + (size_t)l * nv;
+    double* bR = ELk + (size_t)l * nv;
+    double* bL = bR + (size_t)l * nv;
+    double* zR = bL + (size_t)l * nv;
+    double* zL = zR + (size_t)l * nv;
+    int r;
+    if ((r = apply_E(c, R, ER, l, 0, st))) return r;
+    if ((r = apply_E(c, Lk, ELk, l, 1, st))) return r;
+    std::vector<double2> C, D, coef;
+    if ((r = bdots_host(c, Lk, l, ER, l, C, st))) return r;          // C[i*l+j] = <Lk_i|E R_j>
+    if ((r = bdots_host(c, R, l, ELk, l, D, st))) return r;          // D[i*l+j] = <R_i|E^dag Lk_j>
+    c->defl_dlam.resize(l);
+    for (int j = 0; j < l; ++j) c->defl_dlam[j] = C[(size_t)j * l + j];
+    // deflated right-hand sides b_j = Pbar E R_j, b'_j = Pbar^dag E^dag Lk_j
+    coef.assign((size_t)l * l, make_double2(0.0, 0.0));
+    for (int j = 0; j < l; ++j) for (int i = 0; i < l; ++i) coef[(size_t)j * l + i] = make_double2(-C[(size_t)i * l + j].x, -C[(size_t)i * l + j].y);
+    if ((r = bcombine_host(c, bR, ER, l, R, l, coef, st))) return r;
+    for (int j = 0; j < l; ++j) for (int i = 0; i < l; ++i) coef[(size_t)j * l + i] = make_double2(-D[(size_t)i * l + j].x, -D[(size_t)i * l + j].y);
+    if ((r = bcombine_host(c, bL, ELk, l, Lk, l, coef, st))) return r;
+    // shifted solves, in batches of the reserved number of sources
+    lq_opts so = *o;
+    so.projected = LQ_PROJ_NEWTON;   // unused by the resolvent; keeps the sign solvers idle
+    so.kmax = o->defl_kmax > 0 ? o->defl_kmax : c->kmax;
+    const double mu0 = c->desc.mu;
+    for (int side = 0; side < 2; ++side) {
+        const double* bin = side == 0 ? bR : bL;
+        double* zout = side == 0 ? zR : zL;
+        if (side == 1) c->desc.mu = -mu0;             // A^dag = H(-mu)
+        for (int b0 = 0; b0 < l; b0 += c->nsrc) {
+            const int nb = std::min(c->nsrc, l - b0);
+            std::vector<double2> sh(nb);
+            for (int q = 0; q < nb; ++q) sh[q] = side == 0 ? c->defl_lam[b0 + q] : conjh(c->defl_lam[b0 + q]);
+            cudaError_t e = cudaMemcpyAsync(c->defl_shift, sh.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice, st);
+            if (e != cudaSuccess) { c->desc.mu = mu0; return set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e)); }
+            r = run_tsl(c, 1, 0, nb, &so, nullptr, zout + (size_t)b0 * nv, nullptr, st, bin + (size_t)b0 * nv,
+                        nullptr, FN_RESOLVENT, c->defl_shift);
+            if (r) { c->desc.mu = mu0; return r; }
+        }
+        c->desc.mu = mu0;
+    }
+    // project the solutions and add the sums over the deflated eigenvectors
+    std::vector<double2> PZ, PZL;
+    if ((r = bdots_host(c, Lk, l, zR, l, PZ, st))) return r;          // <Lk_i|z_j>
+    if ((r = bdots_host(c, R, l, zL, l, PZL, st))) return r;          // <R_i|z'_j>
+    for (int j = 0; j < l; ++j)
+        for (int i = 0; i < l; ++i) {
+            double2 v = make_double2(-PZ[(size_t)i * l + j].x, -PZ[(size_t)i * l + j].y);
+            if (i != j) {
+                const double2 q = cdivh(C[(size_t)i * l + j], make_double2(c->defl_lam[j].x - c->defl_lam[i].x, c->defl_lam[j].y - c->defl_lam[i].y));
+                v.x += q.x; v.y += q.y;
+            }
+            coef[(size_t)j * l + i] = v;
+        }
+    if ((r = bcombine_host(c, dR, zR, l, R, l, coef, st))) return r;
+    for (int j = 0; j < l; ++j)
+        for (int i = 0; i < l; ++i) {
+            double2 v = make_double2(-PZL[(size_t)i * l + j].x, -PZL[(size_t)i * l + j].y);
+            if (i != j) {
+                const double2 q = conjh(cdivh(C[(size_t)j * l + i], make_double2(c->defl_lam[j].x - c->defl_lam[i].x, c->defl_lam[j].y - c->defl_lam[i].y)));
+                v.x += q.x; v.y += q.y;
+            }
+            coef[(size_t)j * l + i] = v;
+        }
+    if ((r = bcombine_host(c, dLk, zL, l, Lk, l, coef, st))) return r;
     return LQ_OK;
 }
 
@@ -334,6 +600,11 @@ void lq_default_opts(lq_opts* o) {
     o->newton_max_iter = 50;
     o->newton_tol = 1e-13;
     o->deflate = 0;
+    o->projected = LQ_PROJ_AUTO;
+    o->quad_nodes = 64;
+    o->proj_tol = 1e-11;
+    o->hop_variant = -1;
+    o->defl_kmax = 0;
 }
 
 int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
@@ -363,6 +634,7 @@ void lq_destroy(lq_ctx* c) {
     dfree(c->Ub);
     dfree(c->Y);
     dfree(c->dir_scratch);
+    dfree(c->defl_V); dfree(c->defl_W); dfree(c->defl_work); dfree(c->defl_scr); dfree(c->defl_shift);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
     delete c;
 }
@@ -414,9 +686,10 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int block) {
     if ((r = alloc_fields(&c->left, (size_t)nsrc * 3 * nf))) { free_workspace(c); return r; }
     if ((r = alloc_fields(&c->rout, (size_t)nsrc * nf))) { free_workspace(c); return r; }
     if ((r = alloc_fields(&c->lout, (size_t)nsrc * nf))) { free_workspace(c); return r; }
-    if ((r = dalloc(c, &c->io, (size_t)3 * nsrc * c->V * 24))) { free_workspace(c); return r; }
-    size_t pb = (c->V + kHopThreads - 1) / kHopThreads;
-    pb = std::max(pb, (size_t)kUpdBlocksPerSrc);
+    if ((r = dalloc(c, &c->io, (size_t)6 * nsrc * c->V * 24))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->norms, (size_t)3 * nsrc))) { free_workspace(c); return r; }
+    size_t pb = (c->V + 31) / 32;   // finest stencil grid (32 sites per block)
+    pb = std::max(pb, (size_t)kUpdBlocksPerSrc);   // update grid
     pb = std::max(pb, (c->V + kUpdThreads - 1) / kUpdThreads);
     c->partial_blocks = pb;
     if ((r = dalloc(c, &c->partials, (size_t)nsrc * pb * 8))) { free_workspace(c); return r; }
@@ -435,6 +708,11 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int block) {
     c->nx_partial_blocks = (kk + 255) / 256;
     if ((r = dalloc(c, &c->nx_partials, (size_t)nsrc * c->nx_partial_blocks * 4))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->nx_counters, (size_t)3 * nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->proj_c, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->quad_q, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->quad_work, (size_t)nsrc * kmax * 4 * 2 * kQuadMaxNodes))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->quad_c, (size_t)nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->quad_check, (size_t)nsrc))) { free_workspace(c); return r; }
     LQ_CUDA(c, cudaMemset(c->counters, 0, sizeof(int) * 4 * nsrc));
     LQ_CUDA(c, cudaMemset(c->nx_counters, 0, sizeof(int) * 3 * nsrc));
     LQ_CUDA(c, cudaMemset(c->nx_scal, 0, sizeof(double) * 16 * nsrc));
@@ -529,12 +807,29 @@ int lq_apply_block(lq_ctx* c, const double* xt, const double* xb, double* yt, do
 int lq_sign_apply(lq_ctx* c, const double* x, double* y, int nsrc, const lq_opts* o, lq_report* rep, void* stream) {
     if (!c || !x || !y) return set_err(c, LQ_ERR_ARG, "null argument");
     int r = check_ready(c, nsrc, 0);
-    if (r || (r = check_opts(c, o))) return r;
+    if (r || (r = check_opts(c, o, true))) return r;
     cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)nsrc * c->V * 24;
     double* y0 = c->io + (size_t)c->nsrc * c->V * 24;
     if ((r = stage_in(c, c->io, x, n, st))) return r;
-    if ((r = run_tsl(c, 1, 0, nsrc, o, rep, y0, nullptr, st))) return r;
+    const int l = o->deflate ? c->defl_l : 0;
+    std::vector<double2> cx, coef;
+    if (l > 0) {
+        // Eq. (3.1): x' = Pbar x = x - sum_i R_i <Lk_i|x>
+        if ((r = bdots_host(c, c->defl_W, l, c->io, nsrc, cx, st))) return r;
+        coef.assign((size_t)nsrc * l, make_double2(0.0, 0.0));
+        for (int s = 0; s < nsrc; ++s) for (int i = 0; i < l; ++i) coef[(size_t)s * l + i] = make_double2(-cx[(size_t)i * nsrc + s].x, -cx[(size_t)i * nsrc + s].y);
+        if ((r = bcombine_host(c, c->io, c->io, nsrc, c->defl_V, l, coef, st))) return r;
+    }
+    if ((r = run_tsl(c, 1, 0, nsrc, o, rep, y0, nullptr, st, c->io))) return r;
+    if (l > 0) {
+        // + sum_i sgn(lambda_i) R_i <Lk_i|x>
+        for (int s = 0; s < nsrc; ++s) for (int i = 0; i < l; ++i) {
+            const double sg = sgn_re(c->defl_lam[i]);
+            coef[(size_t)s * l + i] = make_double2(sg * cx[(size_t)i * nsrc + s].x, sg * cx[(size_t)i * nsrc + s].y);
+        }
+        if ((r = bcombine_host(c, y0, y0, nsrc, c->defl_V, l, coef, st))) return r;
+    }
     if ((r = stage_out(c, y, y0, n, st))) return r;
     LQ_CUDA(c, cudaStreamSynchronize(st));
     return LQ_OK;
@@ -544,14 +839,53 @@ int lq_sign_derivative_apply(lq_ctx* c, const lq_direction* dir, const double* x
                               const lq_opts* o, lq_report* rep, void* stream) {
     if (!c || !dir || !x || !ys || !yd) return set_err(c, LQ_ERR_ARG, "null argument");
     int r = check_ready(c, nsrc, 1);
-    if (r || (r = check_opts(c, o))) return r;
+    if (r || (r = check_opts(c, o, true))) return r;
     cudaStream_t st = (cudaStream_t)stream;
     if ((r = lq_set_direction(c, dir, stream))) return r;
     const size_t n = (size_t)nsrc * c->V * 24;
-    double* y0 = c->io + (size_t)c->nsrc * c->V * 24;
-    double* y1 = c->io + (size_t)2 * c->nsrc * c->V * 24;
+    const size_t reg = (size_t)c->nsrc * c->V * 24;
+    double* y0 = c->io + reg;
+    double* y1 = c->io + 2 * reg;
     if ((r = stage_in(c, c->io, x, n, st))) return r;
-    if ((r = run_tsl(c, 2, emode_of(c), nsrc, o, rep, y0, y1, st))) return r;
+    const int l = o->deflate ? c->defl_l : 0;
+    if (l == 0) {
+        if ((r = run_tsl(c, 2, emode_of(c), nsrc, o, rep, y0, y1, st))) return r;
+    } else {
+        // generalised deflation, Eqs. (3.2)-(3.4), for psi = (0, x):
+        //   Pbar psi = (-sum_i [R_i <dLk_i|x> + dR_i <Lk_i|x>],  x - sum_i R_i <Lk_i|x>)
+        //   exact    = ( sum_i sgn_i [R_i <dLk_i|x> + dR_i <Lk_i|x>],  sum_i sgn_i R_i <Lk_i|x>)
+        if ((r = prepare_deflation_derivative(c, o, st))) return r;
+        std::vector<double2> cd;   // [2l][nsrc]: <Lk_i|x>, then <dLk_i|x>
+        if ((r = bdots_host(c, c->defl_W, 2 * l, c->io, nsrc, cd, st))) return r;
+        double* xt = c->io + 3 * reg;
+        double* xb = c->io + 4 * reg;
+        std::vector<double2> ct((size_t)nsrc * 2 * l), cb((size_t)nsrc * 2 * l);
+        for (int s = 0; s < nsrc; ++s)
+            for (int i = 0; i < l; ++i) {
+                const double2 a = cd[(size_t)i * nsrc + s], b = cd[(size_t)(l + i) * nsrc + s];
+                ct[(size_t)s * 2 * l + i] = make_double2(-b.x, -b.y);        // R_i <dLk_i|x>
+                ct[(size_t)s * 2 * l + l + i] = make_double2(-a.x, -a.y);    // dR_i <Lk_i|x>
+                cb[(size_t)s * 2 * l + i] = make_double2(-a.x, -a.y);
+                cb[(size_t)s * 2 * l + l + i] = make_double2(0.0, 0.0);
+            }
+        if ((r = bcombine_host(c, xt, nullptr, nsrc, c->defl_V, 2 * l, ct, st))) return r;
+        if ((r = bcombine_host(c, xb, c->io, nsrc, c->defl_V, 2 * l, cb, st))) return r;
+        if ((r = run_tsl(c, 2, emode_of(c), nsrc, o, rep, y0, y1, st, xb, xt))) return r;
+        for (auto& v : ct) v = make_double2(-v.x, -v.y);
+        for (auto& v : cb) v = make_double2(-v.x, -v.y);
+        for (int s = 0; s < nsrc; ++s)
+            for (int i = 0; i < l; ++i) {
+                const double sg = sgn_re(c->defl_lam[i]);
+                for (int h = 0; h < 2; ++h) {
+                    double2& u = ct[(size_t)s * 2 * l + h * l + i];
+                    u = make_double2(sg * u.x, sg * u.y);
+                }
+                double2& u = cb[(size_t)s * 2 * l + i];
+                u = make_double2(sg * u.x, sg * u.y);
+            }
+        if ((r = bcombine_host(c, y0, y0, nsrc, c->defl_V, 2 * l, ct, st))) return r;
+        if ((r = bcombine_host(c, y1, y1, nsrc, c->defl_V, 2 * l, cb, st))) return r;
+    }
     if ((r = stage_out(c, yd, y0, n, st))) return r;
     if ((r = stage_out(c, ys, y1, n, st))) return r;
     LQ_CUDA(c, cudaStreamSynchronize(st));
@@ -584,6 +918,53 @@ int lq_profile_read(lq_ctx* c, lq_profile* o) {
     return LQ_OK;
 }
 
+int lq_upload_deflation(lq_ctx* c, int l, const double* lambda, const double* R, const double* L, void* stream) {
+    if (!c || l < 0) return set_err(c, LQ_ERR_ARG, "invalid deflation arguments");
+    if (l == 0) { c->defl_l = 0; return LQ_OK; }
+    if (!lambda || !R || !L) return set_err(c, LQ_ERR_ARG, "null deflation data");
+    if (!c->basis) return set_err(c, LQ_ERR_NOT_READY, "workspace not reserved (lq_reserve)");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nv = nvec(c);
+    int r;
+    if (l > c->defl_cap) {
+        if ((r = dalloc(c, &c->defl_V, (size_t)2 * l * nv))) return r;
+        if ((r = dalloc(c, &c->defl_W, (size_t)2 * l * nv))) return r;
+        if ((r = dalloc(c, &c->defl_work, (size_t)6 * l * nv))) return r;
+        c->defl_scr_doubles = std::max(bdots_partial_doubles(l * std::max(l, c->nsrc) * 2) + (size_t)8 * l * std::max(l, c->nsrc),
+                                       (size_t)2 * 2 * l * std::max(l, c->nsrc));
+        if ((r = dalloc(c, &c->defl_scr, c->defl_scr_doubles))) return r;
+        if ((r = dalloc(c, &c->defl_shift, (size_t)std::max(c->nsrc, l)))) return r;
+        c->defl_cap = l;
+    }
+    if ((r = stage_in(c, c->defl_V, R, (size_t)l * nv, st))) return r;
+    if ((r = stage_in(c, c->defl_W, L, (size_t)l * nv, st))) return r;
+    LQ_CUDA(c, cudaMemsetAsync(c->defl_V + (size_t)l * nv, 0, sizeof(double) * l * nv, st));
+    LQ_CUDA(c, cudaMemsetAsync(c->defl_W + (size_t)l * nv, 0, sizeof(double) * l * nv, st));
+    c->defl_lam.resize(l);
+    for (int i = 0; i < l; ++i) c->defl_lam[i] = make_double2(lambda[2 * i], lambda[2 * i + 1]);
+    c->defl_dlam.assign(l, make_double2(0.0, 0.0));
+    c->defl_l = l;
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_deflation_derivatives(lq_ctx* c, const lq_direction* dir, const lq_opts* o, double* dlambda, double* dR,
+                             double* dL, void* stream) {
+    if (!c || !dir) return set_err(c, LQ_ERR_ARG, "null argument");
+    if (c->defl_l <= 0) return set_err(c, LQ_ERR_NOT_READY, "no deflation space uploaded");
+    int r = check_ready(c, 1, 1);
+    if (r || (r = check_opts(c, o, true))) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    if ((r = lq_set_direction(c, dir, stream))) return r;
+    if ((r = prepare_deflation_derivative(c, o, st))) return r;
+    const int l = c->defl_l;
+    if (dlambda) for (int i = 0; i < l; ++i) { dlambda[2 * i] = c->defl_dlam[i].x; dlambda[2 * i + 1] = c->defl_dlam[i].y; }
+    if (dR && (r = stage_out(c, dR, c->defl_V + (size_t)l * nvec(c), (size_t)l * nvec(c), st))) return r;
+    if (dL && (r = stage_out(c, dL, c->defl_W + (size_t)l * nvec(c), (size_t)l * nvec(c), st))) return r;
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
 int lq_tsl_coefficients(lq_ctx* c, int src, int k, double* alpha, double* beta, double* delta) {
     if (!c || !alpha || !beta || !delta) return set_err(c, LQ_ERR_ARG, "null argument");
     if (!c->alpha) return set_err(c, LQ_ERR_NOT_READY, "workspace not reserved (lq_reserve)");
@@ -597,6 +978,48 @@ int lq_tsl_coefficients(lq_ctx* c, int src, int k, double* alpha, double* beta, 
         if (j >= st.k_eff) { alpha[2 * j] = alpha[2 * j + 1] = 0.0; }
         if (j >= st.k_eff - 1) { beta[2 * j] = beta[2 * j + 1] = 0.0; delta[j] = 0.0; }
     }
+    return LQ_OK;
+}
+
+int lq_error_estimate(lq_ctx* c, const lq_direction* dir, const double* x, int nsrc, const lq_opts* o, double* eps,
+                      void* stream) {
+    if (!c || !x || !eps) return set_err(c, LQ_ERR_ARG, "null argument");
+    int r = check_ready(c, nsrc, dir ? 1 : 0);
+    if (r || (r = check_opts(c, o))) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t n = (size_t)c->V * 12;              // complex entries per field
+    const size_t reg = (size_t)c->nsrc * n * 2;      // doubles per staging region
+    double* io[6];
+    for (int i = 0; i < 6; ++i) io[i] = c->io + (size_t)i * reg;
+    if ((r = stage_in(c, io[0], x, (size_t)nsrc * n * 2, st))) return r;
+    std::vector<double> num(nsrc), num2(nsrc), den(nsrc);
+    if (!dir) {
+        if ((r = run_tsl(c, 1, 0, nsrc, o, nullptr, io[1], nullptr, st, io[0]))) return r;
+        if ((r = run_tsl(c, 1, 0, nsrc, o, nullptr, io[2], nullptr, st, io[1]))) return r;
+        LQ_CUDA(c, launch_norm2(io[2], io[0], -1.0, n, nsrc, c->norms, st));
+        LQ_CUDA(c, launch_norm2(io[0], nullptr, 0.0, n, nsrc, c->norms + c->nsrc, st));
+        c->launches += 2;
+        LQ_CUDA(c, cudaMemcpyAsync(num.data(), c->norms, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(c, cudaMemcpyAsync(den.data(), c->norms + c->nsrc, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(c, cudaStreamSynchronize(st));
+        for (int s = 0; s < nsrc; ++s) eps[s] = std::sqrt(num[s]) / (2.0 * std::sqrt(den[s]));
+        return LQ_OK;
+    }
+    if ((r = lq_set_direction(c, dir, stream))) return r;
+    const int em = emode_of(c);
+    // (y_d, y_s) = sgn(B)(0, x);  (z_d, z_s) = sgn(B)(0, y_s);  s_d = sgn(A) y_d
+    if ((r = run_tsl(c, 2, em, nsrc, o, nullptr, io[1], io[2], st, io[0]))) return r;
+    if ((r = run_tsl(c, 2, em, nsrc, o, nullptr, io[3], io[4], st, io[2]))) return r;
+    if ((r = run_tsl(c, 1, 0, nsrc, o, nullptr, io[5], nullptr, st, io[1]))) return r;
+    LQ_CUDA(c, launch_norm2(io[5], io[3], 1.0, n, nsrc, c->norms, st));              // top: s_d + z_d
+    LQ_CUDA(c, launch_norm2(io[4], io[0], -1.0, n, nsrc, c->norms + c->nsrc, st));   // bottom: z_s - x
+    LQ_CUDA(c, launch_norm2(io[0], nullptr, 0.0, n, nsrc, c->norms + 2 * c->nsrc, st));
+    c->launches += 3;
+    LQ_CUDA(c, cudaMemcpyAsync(num.data(), c->norms, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
+    LQ_CUDA(c, cudaMemcpyAsync(num2.data(), c->norms + c->nsrc, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
+    LQ_CUDA(c, cudaMemcpyAsync(den.data(), c->norms + 2 * c->nsrc, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    for (int s = 0; s < nsrc; ++s) eps[s] = std::sqrt(num[s] + num2[s]) / (2.0 * std::sqrt(den[s]));
     return LQ_OK;
 }
 

@@ -1,0 +1,83 @@
+// Deflation of Sec. 3 on FP64 vectors in the boundary layout:
+//   * k_bdots      -- all inner products <X_a | Y_b> of two sets of vectors (compensated FP64);
+//   * k_bcombine   -- Z_b = W_b + sum_a coef[b][a] X_a (several vector sets at once).
+// The projections Pbar x = x - sum_i R_i <L_i|x>, the exact parts of Eqs. (3.1) and (3.4) and
+// the eigenvector-derivative assembly are all combinations of these two operations, with the
+// small coefficient matrices formed on the host.
+#include "lq_internal.cuh"
+#include "lq_launch.h"
+
+namespace lq {
+
+constexpr int kDotThreads = 256;
+
+// partial[pair][blockIdx.x] for pair = a * ny + b, then k_bdots_finish sums the partials.
+__global__ void __launch_bounds__(kDotThreads) k_bdots(const double2* __restrict__ X, size_t xs, int nx,
+                                                       const double2* __restrict__ Y, size_t ys, int ny, size_t n,
+                                                       double* __restrict__ partial) {
+    __shared__ CSum smem[32 * 2];
+    const int pair = blockIdx.y;
+    const int a = pair / ny, b = pair % ny;
+    const double2* x = X + (size_t)a * xs;
+    const double2* y = Y + (size_t)b * ys;
+    CSum acc[2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 u = x[i], v = y[i];
+        cs_add_prod(acc[0], u.x, v.x); cs_add_prod(acc[0], u.y, v.y);     // Re conj(u) v
+        cs_add_prod(acc[1], u.x, v.y); cs_add_prod(acc[1], -u.y, v.x);    // Im conj(u) v
+    }
+    block_reduce_cs<2>(acc, smem);
+    if (threadIdx.x == 0) {
+        double* p = partial + ((size_t)pair * gridDim.x + blockIdx.x) * 4;
+        p[0] = acc[0].s; p[1] = acc[0].e; p[2] = acc[1].s; p[3] = acc[1].e;
+    }
+}
+
+__global__ void k_bdots_finish(const double* __restrict__ partial, int nblocks, int npairs, double2* __restrict__ out) {
+    const int pair = blockIdx.x * blockDim.x + threadIdx.x;
+    if (pair >= npairs) return;
+    CSum re{0.0, 0.0}, im{0.0, 0.0};
+    for (int q = 0; q < nblocks; ++q) {
+        const double* p = partial + ((size_t)pair * nblocks + q) * 4;
+        re = cs_merge(re, CSum{p[0], p[1]});
+        im = cs_merge(im, CSum{p[2], p[3]});
+    }
+    out[pair] = make_double2(re.s + re.e, im.s + im.e);
+}
+
+// Z_b = W_b + sum_{a < nx} coef[b * nx + a] X_a  (W may alias Z; W null means 0)
+__global__ void k_bcombine(double2* __restrict__ Z, const double2* W, size_t zs, int nz,
+                           const double2* __restrict__ X, size_t xs, int nx, const double2* __restrict__ coef, size_t n) {
+    const int b = blockIdx.y;
+    const double2* cb = coef + (size_t)b * nx;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 acc = W ? W[(size_t)b * zs + i] : make_double2(0.0, 0.0);
+        for (int a = 0; a < nx; ++a) acc = cfma(__ldg(cb + a), __ldg(X + (size_t)a * xs + i), acc);
+        Z[(size_t)b * zs + i] = acc;
+    }
+}
+
+constexpr int kDotBlocks = 32;
+
+cudaError_t launch_bdots(const double* X, size_t xs, int nx, const double* Y, size_t ys, int ny, size_t n,
+                         double* partial, double* out, cudaStream_t st) {
+    if (nx <= 0 || ny <= 0) return cudaSuccess;
+    dim3 grid(kDotBlocks, (unsigned)(nx * ny));
+    k_bdots<<<grid, kDotThreads, 0, st>>>(reinterpret_cast<const double2*>(X), xs / 2, nx,
+                                          reinterpret_cast<const double2*>(Y), ys / 2, ny, n / 2, partial);
+    k_bdots_finish<<<(nx * ny + 127) / 128, 128, 0, st>>>(partial, kDotBlocks, nx * ny, reinterpret_cast<double2*>(out));
+    return cudaGetLastError();
+}
+
+cudaError_t launch_bcombine(double* Z, const double* W, size_t zs, int nz, const double* X, size_t xs, int nx,
+                            const double* coef, size_t n, cudaStream_t st) {
+    if (nz <= 0) return cudaSuccess;
+    dim3 grid(256, (unsigned)nz);
+    k_bcombine<<<grid, 256, 0, st>>>(reinterpret_cast<double2*>(Z), reinterpret_cast<const double2*>(W), zs / 2, nz,
+                                     reinterpret_cast<const double2*>(X), xs / 2, nx, reinterpret_cast<const double2*>(coef), n / 2);
+    return cudaGetLastError();
+}
+
+size_t bdots_partial_doubles(int npairs) { return (size_t)npairs * kDotBlocks * 4; }
+
+}  // namespace lq

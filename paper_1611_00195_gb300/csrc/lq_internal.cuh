@@ -47,6 +47,15 @@ template <typename C> __device__ __forceinline__ C cadd(C a, C b) { return cmk<C
 template <typename C> __device__ __forceinline__ C csub(C a, C b) { return cmk<C>(a.x - b.x, a.y - b.y); }
 template <typename C> __device__ __forceinline__ C cmul(C a, C b) { return cmk<C>(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 template <typename C> __device__ __forceinline__ C cmulc(C a, C b) { return cmk<C>(a.x * b.x + a.y * b.y, a.x * b.y - a.y * b.x); }  // conj(a)*b
+template <typename C> __device__ __forceinline__ C cdiv(C a, C b) {   // a / b (Smith's scaling)
+    if (fabs(b.x) >= fabs(b.y)) {
+        auto r = b.y / b.x, d = b.x + b.y * r;
+        return cmk<C>((a.x + a.y * r) / d, (a.y - a.x * r) / d);
+    } else {
+        auto r = b.x / b.y, d = b.x * r + b.y;
+        return cmk<C>((a.x * r + a.y) / d, (a.y * r - a.x) / d);
+    }
+}
 template <typename C> __device__ __forceinline__ C cscale(C a, decltype(C::x) s) { return cmk<C>(a.x * s, a.y * s); }
 template <typename C> __device__ __forceinline__ C cmul_i(C a) { return cmk<C>(-a.y, a.x); }      // i*a
 template <typename C> __device__ __forceinline__ C cmul_mi(C a) { return cmk<C>(a.y, -a.x); }     // -i*a
@@ -187,7 +196,8 @@ struct lq_ctx {
     void* left = nullptr;            // [nsrc][3][NF] fields (ring)
     void* rout = nullptr;            // [nsrc][NF] fields: B vh_j
     void* lout = nullptr;            // [nsrc][NF] fields: B^dag wh_j
-    double* io = nullptr;            // [nsrc][2][V][12] complex128 boundary staging (device)
+    double* io = nullptr;            // [6][nsrc][V][12] complex128 boundary staging (device)
+    double* norms = nullptr;         // [3][nsrc] norm results
     double* partials = nullptr;      // reduction partials
     int* counters = nullptr;         // last-block counters
     lq::TslState* state = nullptr;   // [nsrc]
@@ -203,8 +213,30 @@ struct lq_ctx {
     double* nx_scal = nullptr;       // [nsrc][16] Newton scalars
     double* nx_partials = nullptr;   // Newton reduction partials
     int* nx_counters = nullptr;
+    // projected coefficients and quadrature workspace
+    double2* proj_c = nullptr;       // [nsrc][kmax] sgn(T_k) e_1
+    double2* quad_q = nullptr;       // [nsrc][kmax] involution check vector
+    double2* quad_work = nullptr;    // [nsrc][4][kmax][2 * kQuadMaxNodes]
+    double* quad_c = nullptr;        // [nsrc]
+    double* quad_check = nullptr;    // [nsrc]
     size_t partial_blocks = 0;       // capacity per source of the TSL partials
     size_t nx_partial_blocks = 0;
+
+    // deflation space (Sec. 3), FP64 boundary layout: V = [R_0..R_{l-1}, dR_0..dR_{l-1}],
+    // W = [Lk_0..Lk_{l-1}, dLk_0..dLk_{l-1}] with <Lk_i|R_j> = delta_ij (Lk_i = L_i^dag)
+    int defl_l = 0, defl_cap = 0;
+    std::vector<double2> defl_lam, defl_dlam;
+    double* defl_V = nullptr;
+    double* defl_W = nullptr;
+    double* defl_work = nullptr;     // [6][cap][n] scratch vectors for the derivative preparation
+    double* defl_scr = nullptr;      // dot partials and coefficient matrices
+    size_t defl_scr_doubles = 0;
+    double2* defl_shift = nullptr;   // [nsrc] resolvent shifts
+    double defl_resid = 0.0;         // largest relative residual of the last shifted solves
+
+    // stencil autotuning: chosen variant per (nf, emode) of the Lanczos step, -1 = not tuned
+    int tuned_variant[3][3] = {{-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}};
+    int tuned_nsrc = -1;
 
     // profiling (lq_profile_enable): event pairs per kernel class, summed at sync points
     int prof_on = 0;

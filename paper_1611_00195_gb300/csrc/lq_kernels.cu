@@ -54,14 +54,15 @@ template <> struct DotAcc<float> {
     FF v;
     __device__ __forceinline__ void zero() { v.h = 0.f; v.l = 0.f; }
     __device__ __forceinline__ void add_prod(float a, float b) { ff_add_prod(v, a, b); }
-    __device__ __forceinline__ CSum warp_total() {
+    __device__ __forceinline__ CSum warp_total() {   // valid in lane 0 only
         FF r = v;
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1) {
             FF o; o.h = __shfl_down_sync(0xffffffffu, r.h, off); o.l = __shfl_down_sync(0xffffffffu, r.l, off);
             r = ff_merge(r, o);
         }
-        CSum c; c.s = (double)r.h; c.e = (double)r.l;
+        CSum c{0.0, 0.0};
+        if ((threadIdx.x & 31) == 0) { c.s = (double)r.h; c.e = (double)r.l; }
         return c;
     }
 };
@@ -201,6 +202,27 @@ __device__ __forceinline__ void haxpy(C (&h)[6], decltype(C::x) f, const C (&x)[
     for (int i = 0; i < 6; ++i) { h[i].x = fma(f, x[i].x, h[i].x); h[i].y = fma(f, x[i].y, h[i].y); }
 }
 
+// Hop factors in the kernel's precision (FP32 copies are prepared on the host).
+template <typename R> __device__ __forceinline__ R fac_a(const HopArgs& a, int side, int nu, bool fwd);
+template <> __device__ __forceinline__ double fac_a<double>(const HopArgs& a, int side, int nu, bool fwd) { return fwd ? a.a_fwd[side][nu] : a.a_bwd[side][nu]; }
+template <> __device__ __forceinline__ float fac_a<float>(const HopArgs& a, int side, int nu, bool fwd) { return fwd ? a.af_fwd[side][nu] : a.af_bwd[side][nu]; }
+template <typename R> __device__ __forceinline__ R fac_e(const HopArgs& a, int side, int nu, bool fwd);
+template <> __device__ __forceinline__ double fac_e<double>(const HopArgs& a, int side, int nu, bool fwd) { return fwd ? a.e_fwd[side][nu] : a.e_bwd[side][nu]; }
+template <> __device__ __forceinline__ float fac_e<float>(const HopArgs& a, int side, int nu, bool fwd) { return fwd ? a.ef_fwd[side][nu] : a.ef_bwd[side][nu]; }
+template <typename R> __device__ __forceinline__ R fac_diag(const HopArgs& a);
+template <> __device__ __forceinline__ double fac_diag<double>(const HopArgs& a) { return a.diag; }
+template <> __device__ __forceinline__ float fac_diag<float>(const HopArgs& a) { return a.diag_f; }
+
+// Site coordinates (x, y, z, t) from the linear site index (32-bit arithmetic: V < 2^31).
+__device__ __forceinline__ void site_coords(const HopArgs& a, size_t s, int (&x)[4]) {
+    unsigned r = (unsigned)s;
+    const unsigned d0 = (unsigned)a.dims[0], d1 = (unsigned)a.dims[1], d2 = (unsigned)a.dims[2];
+    unsigned q = r / d0; x[0] = (int)(r - q * d0); r = q;
+    q = r / d1; x[1] = (int)(r - q * d1); r = q;
+    q = r / d2; x[2] = (int)(r - q * d2);
+    x[3] = (int)q;
+}
+
 // One hop direction (NU, SP = -1 forward / +1 backward) for NF fields per side.
 // EMODE 0: no derivative term; 1: d/dmu (time hops, links U); 2: link direction (links Y).
 // Right side (side 0): out0 = A in0 + E in1, out1 = A in1.
@@ -212,8 +234,8 @@ __device__ __forceinline__ void do_hop(const HopArgs& a, int side, size_t V, siz
                                        typename Tr<R>::C (&acc0)[12], typename Tr<R>::C (&acc1)[12]) {
     using C = typename Tr<R>::C;
     constexpr bool DAG = SP > 0;   // backward hop uses the adjoint link at x - nu
-    const R fa = (R)((SP < 0 ? a.a_fwd[side][NU] : a.a_bwd[side][NU])) * bsign;
-    const R fe = (R)((SP < 0 ? a.e_fwd[side][NU] : a.e_bwd[side][NU])) * bsign;
+    const R fa = fac_a<R>(a, side, NU, SP < 0) * bsign;
+    const R fe = fac_e<R>(a, side, NU, SP < 0) * bsign;
     const C* __restrict__ Lu = reinterpret_cast<const C*>(a.U);
     C u[9];
     load_link(Lu, V, NU, lsite, u);
@@ -321,18 +343,12 @@ __global__ void __launch_bounds__(kHopThreads) k_hop(HopArgs a) {
 #pragma unroll
         for (int c = 0; c < 12; ++c) { acc0[c] = cmk<C>(0, 0); acc1[c] = cmk<C>(0, 0); }
         int x[4];
-        {
-            size_t r = s;
-            x[0] = (int)(r % a.dims[0]); r /= a.dims[0];
-            x[1] = (int)(r % a.dims[1]); r /= a.dims[1];
-            x[2] = (int)(r % a.dims[2]); r /= a.dims[2];
-            x[3] = (int)r;
-        }
+        site_coords(a, s, x);
         do_dir<R, NF, EMODE, 0>(a, side, V, s, x, in0, in1, acc0, acc1);
         do_dir<R, NF, EMODE, 1>(a, side, V, s, x, in0, in1, acc0, acc1);
         do_dir<R, NF, EMODE, 2>(a, side, V, s, x, in0, in1, acc0, acc1);
         do_dir<R, NF, EMODE, 3>(a, side, V, s, x, in0, in1, acc0, acc1);
-        const R diag = (R)a.diag;
+        const R diag = fac_diag<R>(a);
         C psi[12];
         load_spinor(in0, V, s, psi);
         finish(psi, diag, acc0);
@@ -363,6 +379,123 @@ __global__ void __launch_bounds__(kHopThreads) k_hop(HopArgs a) {
         }
     }
     if (DOT && side == 0) {
+        CSum tot[2];
+        block_total<R, 2>(d, tot, smem);
+        double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 4;
+        if (threadIdx.x == 0) { part[0] = tot[0].s; part[1] = tot[0].e; part[2] = tot[1].s; part[3] = tot[1].e; }
+        if (last_block(a.counters + src, gridDim.x)) {
+            double res[2];
+            reduce_partials<2>(a.partials + (size_t)src * a.partial_stride * 4, gridDim.x, res, smem);
+            if (threadIdx.x == 0) tsl_alpha_step(a, src, res[0], res[1]);
+        }
+    }
+}
+
+// ---------------------------------------------------------------------------------------
+// Role-split block stencil: one thread per (site, output field, source).  The four outputs
+// of a site for the block operator of Eq. (2.5) are
+//   role 0: A t + E b      role 1: A b          (right side, operator A = H(mu))
+//   role 2: A^dag p        role 3: A^dag q + E^dag p   (left side, A^dag = H(-mu))
+// A block holds kRoleSites sites x 4 roles (one warp per role), so the four warps read the
+// same links and neighbour sites and share them in L1.  The alpha dot is accumulated by the
+// right-side roles: conj(p(x)) . (A t + E b)(x) + conj(q(x)) . (A b)(x).
+// ---------------------------------------------------------------------------------------
+constexpr int kRoleSites = 32;
+
+template <typename R, int EMODE, int NU, int SP>
+__device__ __forceinline__ void role_hop(const HopArgs& a, int side, bool with_e, size_t V, size_t nb, size_t lsite, R bsign,
+                                         const typename Tr<R>::Chunk* __restrict__ fa_in,
+                                         const typename Tr<R>::Chunk* __restrict__ fe_in,
+                                         typename Tr<R>::C (&acc)[12]) {
+    using C = typename Tr<R>::C;
+    constexpr bool DAG = SP > 0;
+    const R fa = fac_a<R>(a, side, NU, SP < 0) * bsign;
+    const bool ehop = with_e && (EMODE == 2 || (EMODE == 1 && NU == 3));
+    C u[9], psi[12], h[6], g[6];
+    load_link(reinterpret_cast<const C*>(a.U), V, NU, lsite, u);
+    load_spinor(fa_in, V, nb, psi);
+    project<C, NU, SP>(psi, h);
+    hscale(h, fa);
+    if (ehop) {
+        const R fe = fac_e<R>(a, side, NU, SP < 0) * bsign;
+        C he[6];
+        load_spinor(fe_in, V, nb, psi);
+        project<C, NU, SP>(psi, he);
+        if (EMODE == 1) {
+            haxpy(h, fe, he);                 // same link: combine before the multiply
+        } else {
+            C y[9];
+            load_link(reinterpret_cast<const C*>(a.Y), V, NU, lsite, y);
+            hscale(he, fe);
+            su3_mul<C, DAG>(y, he, g);
+            reconstruct_add<C, NU, SP>(g, acc);
+        }
+    }
+    su3_mul<C, DAG>(u, h, g);
+    reconstruct_add<C, NU, SP>(g, acc);
+}
+
+template <typename R, int EMODE, int NU>
+__device__ __forceinline__ void role_dir(const HopArgs& a, int side, bool with_e, size_t V, size_t s, const int (&x)[4],
+                                         const typename Tr<R>::Chunk* fa_in, const typename Tr<R>::Chunk* fe_in,
+                                         typename Tr<R>::C (&acc)[12]) {
+    const int ext = a.dims[NU];
+    const size_t stride = a.strides[NU];
+    const size_t sf = (x[NU] == ext - 1) ? s - (size_t)(ext - 1) * stride : s + stride;
+    const R bf = (NU == 3 && a.apbc && x[NU] == ext - 1) ? (R)-1 : (R)1;
+    role_hop<R, EMODE, NU, -1>(a, side, with_e, V, sf, s, bf, fa_in, fe_in, acc);
+    const size_t sb = (x[NU] == 0) ? s + (size_t)(ext - 1) * stride : s - stride;
+    const R bb = (NU == 3 && a.apbc && x[NU] == 0) ? (R)-1 : (R)1;
+    role_hop<R, EMODE, NU, +1>(a, side, with_e, V, sb, sb, bb, fa_in, fe_in, acc);
+}
+
+template <typename R, int EMODE, bool DOT>
+__global__ void __launch_bounds__(4 * kRoleSites) k_hop_roles(HopArgs a) {
+    using C = typename Tr<R>::C;
+    using Chunk = typename Tr<R>::Chunk;
+    __shared__ CSum smem[32 * 2];
+    const int src = blockIdx.y;
+    if (a.state != nullptr && a.state[src].status != 0) return;
+    const int role = threadIdx.x / kRoleSites;       // warp-uniform
+    const int side = role >> 1;                       // 0 right, 1 left
+    const int fld = role & 1;                         // output field within the side
+    const size_t V = a.V;
+    const size_t s = (size_t)blockIdx.x * kRoleSites + (threadIdx.x % kRoleSites);
+    const bool active = s < V;
+    const size_t F = field_elems<R>(V);
+    const Chunk* in0 = reinterpret_cast<const Chunk*>(a.in[side]) + (size_t)src * a.src_stride_in[side];
+    Chunk* out = reinterpret_cast<Chunk*>(a.out[side]) + (size_t)src * a.src_stride_out[side] + (size_t)fld * F;
+    // operator input and derivative input of this role
+    const Chunk* fa_in = in0 + (size_t)fld * F;
+    const bool with_e = (EMODE != 0) && ((side == 0 && fld == 0) || (side == 1 && fld == 1));
+    const Chunk* fe_in = (side == 0) ? in0 + F : in0;   // right: E acts on the bottom; left: E^dag on the top
+    DotAcc<R> d[2];
+    d[0].zero(); d[1].zero();
+    if (active) {
+        C acc[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) acc[c] = cmk<C>(0, 0);
+        int x[4];
+        site_coords(a, s, x);
+        role_dir<R, EMODE, 0>(a, side, with_e, V, s, x, fa_in, fe_in, acc);
+        role_dir<R, EMODE, 1>(a, side, with_e, V, s, x, fa_in, fe_in, acc);
+        role_dir<R, EMODE, 2>(a, side, with_e, V, s, x, fa_in, fe_in, acc);
+        role_dir<R, EMODE, 3>(a, side, with_e, V, s, x, fa_in, fe_in, acc);
+        C psi[12];
+        load_spinor(fa_in, V, s, psi);
+        finish(psi, fac_diag<R>(a), acc);
+        store_spinor(out, V, s, acc);
+        if (DOT && side == 0) {
+            const Chunk* w = reinterpret_cast<const Chunk*>(a.in[1]) + (size_t)src * a.src_stride_in[1] + (size_t)fld * F;
+            load_spinor(w, V, s, psi);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                d[0].add_prod(psi[c].x, acc[c].x); d[0].add_prod(psi[c].y, acc[c].y);
+                d[1].add_prod(psi[c].x, acc[c].y); d[1].add_prod(-psi[c].y, acc[c].x);
+            }
+        }
+    }
+    if (DOT) {
         CSum tot[2];
         block_total<R, 2>(d, tot, smem);
         double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 4;
@@ -526,21 +659,21 @@ template <typename R, int NF>
 __global__ void __launch_bounds__(kUpdThreads) k_tsl_init(InitArgs a) {
     using C = typename Tr<R>::C;
     using Chunk = typename Tr<R>::Chunk;
-    __shared__ CSum smem[32];
+    __shared__ CSum smem[32 * 4];
     const int src = blockIdx.y;
     const size_t V = a.V;
     const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
-    DotAcc<double> d[1];
-    d[0].zero();
+    // sums of the stored (rounded) values: |t|^2, |b|^2, Re <b,t>, Im <b,t>
+    CSum acc[4] = {{0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}, {0.0, 0.0}};
     if (s < V) {
         const double2* x = reinterpret_cast<const double2*>(a.x) + ((size_t)src * V + s) * 12;
-        C psi[12];
+        C psi[12], top[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) {
             double2 z = x[c];
             psi[c] = cmk<C>((R)z.x, (R)z.y);
-            d[0].add_prod((double)psi[c].x, (double)psi[c].x);
-            d[0].add_prod((double)psi[c].y, (double)psi[c].y);
+            cs_add_prod(acc[1], (double)psi[c].x, (double)psi[c].x);
+            cs_add_prod(acc[1], (double)psi[c].y, (double)psi[c].y);
         }
         Chunk* v = reinterpret_cast<Chunk*>(a.v1) + (size_t)src * a.src_stride_basis;
         Chunk* w = reinterpret_cast<Chunk*>(a.w1) + (size_t)src * a.src_stride_left;
@@ -548,46 +681,50 @@ __global__ void __launch_bounds__(kUpdThreads) k_tsl_init(InitArgs a) {
             store_spinor(v, V, s, psi);
             store_spinor(w, V, s, psi);
         } else {
-            C z[12];
+            const double2* xt = a.xt ? reinterpret_cast<const double2*>(a.xt) + ((size_t)src * V + s) * 12 : nullptr;
 #pragma unroll
-            for (int c = 0; c < 12; ++c) z[c] = cmk<C>(0, 0);
-            store_spinor(v, V, s, z);
+            for (int c = 0; c < 12; ++c) {
+                double2 z = xt ? xt[c] : make_double2(0.0, 0.0);
+                top[c] = cmk<C>((R)z.x, (R)z.y);
+                const double tx = (double)top[c].x, ty = (double)top[c].y;
+                const double bx = (double)psi[c].x, by = (double)psi[c].y;
+                cs_add_prod(acc[0], tx, tx); cs_add_prod(acc[0], ty, ty);
+                cs_add_prod(acc[2], bx, tx); cs_add_prod(acc[2], by, ty);     // Re conj(b) t
+                cs_add_prod(acc[3], bx, ty); cs_add_prod(acc[3], -by, tx);    // Im conj(b) t
+            }
+            store_spinor(v, V, s, top);
             store_spinor(v + field_elems<R>(V), V, s, psi);
             store_spinor(w, V, s, psi);
             store_spinor(w + field_elems<R>(V), V, s, psi);
         }
     }
-    // warp/block totals (products are of doubles converted from R: exact for float)
-    CSum tot[1];
-    {
-        const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-        CSum w = d[0].warp_total();
-        if (lane == 0) smem[warp] = w;
-        __syncthreads();
-        if (warp == 0) {
-            w = (lane < nw) ? smem[lane] : CSum{0.0, 0.0};
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) w = cs_merge(w, cs_shfl_down(w, off));
-            if (lane == 0) tot[0] = w;
-        }
-        __syncthreads();
-    }
-    double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 2;
-    if (threadIdx.x == 0) { part[0] = tot[0].s; part[1] = tot[0].e; }
+    block_reduce_cs<4>(acc, smem);
+    double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 8;
+    if (threadIdx.x == 0)
+        for (int i = 0; i < 4; ++i) { part[2 * i] = acc[i].s; part[2 * i + 1] = acc[i].e; }
     if (last_block(a.counters + 2 * a.nsrc + src, gridDim.x)) {
-        double res[1];
-        reduce_partials<1>(a.partials + (size_t)src * a.partial_stride * 2, gridDim.x, res, smem);
+        double res[4];
+        reduce_partials<4>(a.partials + (size_t)src * a.partial_stride * 8, gridDim.x, res, smem);
         if (threadIdx.x == 0) {
+            // v_1 = s_1 vh_1 with |v_1| = 1;  <w_1, v_1> = 1 with w_1 = u_1 wh_1, wh_1 = (b, b) or b
             TslState& st = a.state[src];
-            const double xn = sqrt(res[0]);
-            st.xnorm = xn;
+            const double nt = res[0], nb = res[1];
+            const double vn = sqrt(nt + nb);
+            st.xnorm = vn;
             st.k_eff = 0;
             st.breakdown_tol = a.breakdown_tol;
-            if (!(xn > 0.0) || !isfinite(xn)) { st.status = LQ_ERR_ARG; return; }
+            if (!(vn > 0.0) || !isfinite(vn)) { st.status = LQ_ERR_ARG; return; }
+            const double s1 = 1.0 / vn;
+            double2 wv = make_double2(nb, 0.0);                  // <wh_1, vh_1>
+            if (NF == 2) { wv.x += res[2]; wv.y += res[3]; }
+            // u_1 = 1 / conj(s_1 <wh_1, vh_1>)
+            const double2 q = make_double2(s1 * wv.x, -s1 * wv.y);
+            const double qn = q.x * q.x + q.y * q.y;
+            if (!(qn > 0.0) || !isfinite(qn)) { st.status = LQ_ERR_BREAKDOWN; return; }
             st.status = 0;
-            st.s_cur = 1.0 / xn;
+            st.s_cur = s1;
             st.s_prev = 0.0;
-            st.u_cur = make_double2(1.0 / xn, 0.0);
+            st.u_cur = make_double2(q.x / qn, -q.y / qn);
             st.u_prev = make_double2(0.0, 0.0);
             st.beta_prev = make_double2(0.0, 0.0);
             st.delta_prev = 0.0;
@@ -597,7 +734,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_tsl_init(InitArgs a) {
 
 // ---------------------------------------------------------------------------------------
 // Recombination y = |x| sum_j c_j s_j vh_j for each field, written in the boundary layout.
-// c = first column of sgn(T_k) (from the Newton workspace, row-major k x k per source).
+// c = sgn(T_k) e_1 (from the Newton iteration or the quadrature), one row per source.
 // FP64 basis: FP64 accumulation.  FP32 basis: float-float accumulation with exact products
 // of the split coefficient (hi + lo).
 // ---------------------------------------------------------------------------------------
@@ -612,9 +749,8 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
     const int keff = st.k_eff;
     const size_t V = a.V;
     const double xn = st.xnorm;
-    const double2* X = a.newton_X + (size_t)src * a.ldx * a.ldx;
     for (int j = threadIdx.x; j < keff; j += blockDim.x) {
-        double2 c = X[(size_t)j * a.ldx];   // first column
+        double2 c = a.coef[(size_t)src * a.kmax + j];
         double sc = a.scale[(size_t)src * a.kmax + j] * xn;
         double2 cs = make_double2(c.x * sc, c.y * sc);
         if (sizeof(R) == 8) coef[j] = cs;
@@ -673,6 +809,33 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
 #pragma unroll
         for (int c = 0; c < 12; ++c) y[c] = make_double2((double)ar[c].h + (double)ar[c].l, (double)ai[c].h + (double)ai[c].l);
     }
+}
+
+// ---------------------------------------------------------------------------------------
+// out[src] = || a + sigma b ||^2 over one boundary-layout field per source (b may be null),
+// compensated FP64.  One block per source.
+// ---------------------------------------------------------------------------------------
+__global__ void __launch_bounds__(1024) k_norm2(const double2* __restrict__ a, const double2* __restrict__ b, double sigma,
+                                                size_t n, double* __restrict__ out) {
+    __shared__ CSum smem[32];
+    const int src = blockIdx.x;
+    const double2* pa = a + (size_t)src * n;
+    const double2* pb = b ? b + (size_t)src * n : nullptr;
+    CSum acc{0.0, 0.0};
+    for (size_t i = threadIdx.x; i < n; i += blockDim.x) {
+        double2 v = pa[i];
+        if (pb) { double2 w = pb[i]; v.x += sigma * w.x; v.y += sigma * w.y; }
+        cs_add_prod(acc, v.x, v.x);
+        cs_add_prod(acc, v.y, v.y);
+    }
+    CSum v1[1] = {acc};
+    block_reduce_cs<1>(v1, smem);
+    if (threadIdx.x == 0) out[src] = v1[0].s + v1[0].e;
+}
+
+cudaError_t launch_norm2(const double* a, const double* b, double sigma, size_t n, int nsrc, double* out, cudaStream_t st) {
+    k_norm2<<<nsrc, 1024, 0, st>>>(reinterpret_cast<const double2*>(a), reinterpret_cast<const double2*>(b), sigma, n, out);
+    return cudaGetLastError();
 }
 
 // ---------------------------------------------------------------------------------------
@@ -777,8 +940,27 @@ static cudaError_t launch_hop_t(const HopArgs& a, int nf, int emode, bool dot, c
     return cudaGetLastError();
 }
 
+template <typename R>
+static cudaError_t launch_roles_t(const HopArgs& a, int emode, bool dot, cudaStream_t st) {
+    dim3 grid((unsigned)((a.V + kRoleSites - 1) / kRoleSites), (unsigned)a.nsrc, 1);
+    dim3 block(4 * kRoleSites);
+#define LQ_ROLE(EM, D) k_hop_roles<R, EM, D><<<grid, block, 0, st>>>(a)
+    if (emode == 0) { if (dot) LQ_ROLE(0, true); else LQ_ROLE(0, false); }
+    else if (emode == 1) { if (dot) LQ_ROLE(1, true); else LQ_ROLE(1, false); }
+    else { if (dot) LQ_ROLE(2, true); else LQ_ROLE(2, false); }
+#undef LQ_ROLE
+    return cudaGetLastError();
+}
+
 cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st) {
+    if (nf == 2 && a.nsides == 2 && a.side0 == 0 && a.variant == 1)
+        return prec == LQ_FP64 ? launch_roles_t<double>(a, emode, dot, st) : launch_roles_t<float>(a, emode, dot, st);
     return prec == LQ_FP64 ? launch_hop_t<double>(a, nf, emode, dot, st) : launch_hop_t<float>(a, nf, emode, dot, st);
+}
+
+size_t hop_blocks(const HopArgs& a, int nf) {
+    if (nf == 2 && a.nsides == 2 && a.side0 == 0 && a.variant == 1) return (a.V + kRoleSites - 1) / kRoleSites;
+    return (a.V + kHopThreads - 1) / kHopThreads;
 }
 
 unsigned update_grid(size_t nelem) {

@@ -10,7 +10,7 @@ namespace lq {
 constexpr int kHopThreads = 128;
 constexpr int kUpdThreads = 256;
 constexpr int kRecThreads = 128;
-constexpr int kUpdBlocksPerSrc = 304;      // 2 x 152 SMs: grid-stride update kernel
+constexpr int kUpdBlocksPerSrc = 64;       // grid-stride update kernel: ~30 chunks per thread at 14^4
 
 // Arguments of the stencil kernel k_hop (Eq. (1.1), block operator of Eq. (2.5)).
 struct HopArgs {
@@ -20,10 +20,13 @@ struct HopArgs {
     int apbc;
     int nsrc, nsides;
     int side0;             // side of blockIdx.z == 0 (0 = right / A, 1 = left / A^dag)
+    int variant;           // 0: one thread per (site, side); 1: one thread per (site, output field)
     double diag;           // 4r + m_w
     // hop factors, including the -1/2 of Dw: [side][direction]
     double a_fwd[2][4], a_bwd[2][4];   // operator A (side 0) / A^dag (side 1)
     double e_fwd[2][4], e_bwd[2][4];   // derivative E (side 0) / E^dag (side 1)
+    float af_fwd[2][4], af_bwd[2][4], ef_fwd[2][4], ef_bwd[2][4];   // FP32 copies (no conversion in kernels)
+    float diag_f;
     const void* U;         // links (internal)
     const void* Y;         // dU/dt (internal), EMODE 2
     const void* in[2];     // per side: NF consecutive fields of source 0
@@ -61,7 +64,8 @@ struct UpdArgs {
 struct InitArgs {
     size_t V;
     int nsrc;
-    const double* x;       // boundary layout, device
+    const double* x;       // boundary layout, device (bottom of a block source)
+    const double* xt;      // top of a block source (boundary layout) or null for (0, x)
     void* v1; void* w1;
     size_t src_stride_basis, src_stride_left;
     TslState* state;
@@ -80,8 +84,7 @@ struct RecArgs {
     const TslState* state;
     const double* scale;
     int kmax;
-    const double2* newton_X;
-    int ldx;
+    const double2* coef;       // [nsrc][kmax] sgn(T_k) e_1
     double* y0; double* y1;    // boundary layout outputs (device), field 0 / field 1
 };
 
@@ -96,6 +99,15 @@ cudaError_t launch_to_boundary(int prec, const void* f, double* x, size_t V, int
 cudaError_t launch_links_internal(int prec, const double* U, void* L, size_t V, cudaStream_t st);
 cudaError_t launch_direction(int prec, const double* U, const double* w, int kind, void* Y, size_t V, cudaStream_t st);
 unsigned update_grid(size_t nelem);
+// Deflation vector algebra on FP64 boundary-layout vectors (lq_deflate.cu).  Sizes and strides
+// are in doubles (2 per complex number).
+cudaError_t launch_bdots(const double* X, size_t xs, int nx, const double* Y, size_t ys, int ny, size_t n,
+                         double* partial, double* out, cudaStream_t st);      // out[a * ny + b] = <X_a|Y_b>
+cudaError_t launch_bcombine(double* Z, const double* W, size_t zs, int nz, const double* X, size_t xs, int nx,
+                            const double* coef, size_t n, cudaStream_t st);   // Z_b = W_b + sum_a coef[b*nx+a] X_a
+size_t bdots_partial_doubles(int npairs);
+cudaError_t launch_norm2(const double* a, const double* b, double sigma, size_t n, int nsrc, double* out, cudaStream_t st);
+size_t hop_blocks(const HopArgs& a, int nf);
 
 // Newton sign iteration (lq_newton.cu)
 struct NewtonArgs {
@@ -119,6 +131,26 @@ struct NewtonArgs {
 };
 // scal layout per matrix
 enum { NS_NORMX = 0, NS_NORMY, NS_MU, NS_CHANGE, NS_DONE, NS_ITERS, NS_SCALING, NS_STATUS, NS_PREVCHANGE, NS_KEFF };
+
+// Quadrature projected sign (lq_newton.cu)
+struct QuadArgs {
+    int k;                 // padded dimension
+    int nb;
+    int kmax;              // row stride of alpha/beta/delta/s/q
+    int nth_max;           // thread capacity of the work array (2 * max nodes)
+    const TslState* state; // [nb] per-source dimension (k_eff)
+    const double2* alpha; const double2* beta; const double* delta;
+    double* c;             // [nb] contour scale
+    double2* work;         // [nb][4][kmax][nth_max]
+    double2* s;            // [nb][kmax] sgn(T) e_1
+    double2* q;            // [nb][kmax] sgn(T) s (involution check)
+    double* check;         // [nb] ||q - e_1||
+};
+constexpr int kQuadMaxNodes = 128;
+cudaError_t quad_sign_e1(const QuadArgs& a, int nodes, cudaStream_t st);
+// c = (sigma_src - T)^{-1} e_1 into a.s (per-source complex shifts, device array)
+cudaError_t proj_resolvent(const QuadArgs& a, const double2* shifts, cudaStream_t st);
+cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st);
 
 cudaError_t newton_init_tridiag(const NewtonArgs& a, cudaStream_t st);
 cudaError_t newton_init_dense(const NewtonArgs& a, const double2* Xin, cudaStream_t st);

@@ -13,6 +13,8 @@
 #include "lq_internal.cuh"
 #include "lq_launch.h"
 
+#include <cstring>
+
 namespace lq {
 
 constexpr int kNtThreads = 256;
@@ -293,6 +295,227 @@ __global__ void k_nt_copy_out(NewtonArgs a, double2* __restrict__ S) {
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= (size_t)k * k) return;
     S[(size_t)b * k * k + e] = a.X[(size_t)b * ld * ld + (e / k) * ld + (e % k)];
+}
+
+// ---------------------------------------------------------------------------------------------
+// Projected sign by quadrature (an alternative to Newton, checked by the involution residual).
+// For T without eigenvalues on the imaginary axis,
+//     sgn(T) = (2/pi) T int_0^inf (t^2 + T^2)^{-1} dt,
+// and with t = c tan(theta) the integrand becomes pi-periodic and analytic in theta, so the
+// midpoint rule with N nodes theta_j = (j + 1/2) pi / (2N) converges geometrically:
+//     sgn(T) b ~ (c / 2N) sum_j cos(theta_j)^{-2} [ (T + i tau_j)^{-1} + (T - i tau_j)^{-1} ] b,
+//     tau_j = c tan(theta_j).
+// Each term is one complex tridiagonal solve (Gaussian elimination with partial pivoting,
+// O(k)).  One block per source, one thread per (node, sign); the U factors live in a
+// [row][thread] scratch so that a warp's accesses at one row are contiguous.
+// ---------------------------------------------------------------------------------------------
+// Solve (T + shift) x = b for the tridiagonal T (sub-diagonal de real, diagonal al, super-
+// diagonal be) by Gaussian elimination with partial pivoting (row interchanges create a second
+// super-diagonal).  b(i) is read in row order, so the right-hand side may alias sx.  The U
+// factors go to sd/s1/s2 and w * x to sx, all at stride ld.
+template <class RHS>
+__device__ __forceinline__ void tri_solve(const double2* __restrict__ al, const double2* __restrict__ be,
+                                          const double* __restrict__ de, int n, double2 shift, RHS b,
+                                          double2* sd, double2* s1, double2* s2, double2* sx, size_t ld, double w) {
+    auto D = [&](int i) -> double2 { double2 v = al[i]; v.x += shift.x; v.y += shift.y; return v; };
+    double2 cd = D(0), cu = (n > 1) ? be[0] : make_double2(0.0, 0.0), cx = b(0);
+    for (int i = 0; i < n - 1; ++i) {
+        const double2 l = make_double2(de[i], 0.0);
+        const double2 nd = D(i + 1);
+        const double2 nu = (i + 1 < n - 1) ? be[i + 1] : make_double2(0.0, 0.0);
+        const double2 nx = b(i + 1);
+        const size_t o = (size_t)i * ld;
+        if (l.x * l.x > cd.x * cd.x + cd.y * cd.y) {
+            // pivot on the sub-diagonal row: stored row i = (l, nd, nu | nx)
+            const double2 f = cdiv(cd, l);
+            sd[o] = l; s1[o] = nd; s2[o] = nu; sx[o] = nx;
+            const double2 ncd = csub(cu, cmul(f, nd));
+            const double2 ncu = make_double2(-(f.x * nu.x - f.y * nu.y), -(f.x * nu.y + f.y * nu.x));
+            cx = csub(cx, cmul(f, nx));
+            cd = ncd;
+            cu = ncu;
+        } else {
+            const double2 f = cdiv(l, cd);
+            sd[o] = cd; s1[o] = cu; s2[o] = make_double2(0.0, 0.0); sx[o] = cx;
+            cd = csub(nd, cmul(f, cu));
+            cu = nu;
+            cx = csub(nx, cmul(f, cx));
+        }
+    }
+    double2 x1 = cdiv(cx, cd), x2 = make_double2(0.0, 0.0);
+    sx[(size_t)(n - 1) * ld] = cscale(x1, w);
+    for (int i = n - 2; i >= 0; --i) {
+        const size_t o = (size_t)i * ld;
+        double2 v = csub(sx[o], cmul(s1[o], x1));
+        v = csub(v, cmul(s2[o], x2));
+        v = cdiv(v, sd[o]);
+        sx[o] = cscale(v, w);
+        x2 = x1;
+        x1 = v;
+    }
+}
+
+__global__ void k_quad(QuadArgs a, int pass) {
+    const int src = blockIdx.x;
+    const int t = threadIdx.x;           // 0 .. 2N-1
+    const int nth = blockDim.x;
+    const int N = nth / 2;
+    const int k = a.k;
+    const int keff = a.state[src].k_eff;
+    if (keff <= 0) return;
+    const double2* al = a.alpha + (size_t)src * a.kmax;
+    const double2* be = a.beta + (size_t)src * a.kmax;
+    const double* de = a.delta + (size_t)src * a.kmax;
+    double2* sd = a.work + (size_t)src * a.kmax * 4 * a.nth_max;   // [row][thread] x 4 arrays
+    double2* s1 = sd + (size_t)a.kmax * a.nth_max;
+    double2* s2 = s1 + (size_t)a.kmax * a.nth_max;
+    double2* sx = s2 + (size_t)a.kmax * a.nth_max;
+    const double2* rhs = (pass == 0) ? nullptr : a.s + (size_t)src * a.kmax;
+    const int j = t >> 1;
+    const double sg = (t & 1) ? -1.0 : 1.0;
+    const double c = a.c[src];
+    const double th = (j + 0.5) * 3.14159265358979323846 / (2.0 * N);
+    const double ct = cos(th);
+    const double tau = sg * c * tan(th);
+    const double w = c / (2.0 * N) / (ct * ct);
+    const int n = keff;   // rows beyond keff are the identity padding: they only carry the rhs
+    auto B = [&](int i) -> double2 { return pass == 0 ? make_double2(i == 0 ? 1.0 : 0.0, 0.0) : rhs[i]; };
+    tri_solve(al, be, de, n, make_double2(0.0, tau), B, sd + t, s1 + t, s2 + t, sx + t, a.nth_max, w);
+    __syncthreads();
+    // sum over nodes, row by row (fixed order: deterministic)
+    __shared__ double red[256];
+    double2* out = (pass == 0 ? a.s : a.q) + (size_t)src * a.kmax;
+    double loc = 0.0;
+    for (int i = t; i < k; i += nth) {
+        double2 acc = make_double2(0.0, 0.0);
+        if (i < n) {
+            for (int q = 0; q < nth; ++q) acc = cadd(acc, sx[(size_t)i * a.nth_max + q]);
+        } else {
+            acc = B(i);      // identity padding: sgn(1) = 1
+        }
+        out[i] = acc;
+        if (pass == 1) {
+            const double ex = (i == 0) ? 1.0 : 0.0;
+            loc += (acc.x - ex) * (acc.x - ex) + acc.y * acc.y;
+        }
+    }
+    if (pass == 1) {
+        red[t] = loc;
+        __syncthreads();
+        for (int off = nth / 2; off > 0; off >>= 1) {
+            if (t < off) red[t] += red[t + off];
+            __syncthreads();
+        }
+        if (t == 0) a.check[src] = sqrt(red[0]);
+    }
+}
+
+// Contour scale c = sqrt(lambda_lo * lambda_hi): the midpoint error for an eigenvalue lambda
+// decays like exp(-4 N atanh(min(|lambda|/c, c/|lambda|))), so c is placed at the geometric
+// centre of the spectrum.  lambda_hi: ||T x|| after six power-iteration steps; lambda_lo:
+// 1 / ||T^{-1} x|| after six inverse-iteration steps (tridiagonal solves).  Only the scale
+// matters (a factor 2 costs little), so a few steps suffice.  One thread per source, in the
+// first column of the quadrature workspace.
+__global__ void k_quad_scale(QuadArgs a) {
+    const int src = blockIdx.x * blockDim.x + threadIdx.x;
+    if (src >= a.nb) return;
+    const int n = a.state[src].k_eff;
+    if (n <= 0) { a.c[src] = 1.0; return; }
+    const double2* al = a.alpha + (size_t)src * a.kmax;
+    const double2* be = a.beta + (size_t)src * a.kmax;
+    const double* de = a.delta + (size_t)src * a.kmax;
+    double2* sd = a.work + (size_t)src * a.kmax * 4 * a.nth_max;
+    double2* s1 = sd + (size_t)a.kmax * a.nth_max;
+    double2* s2 = s1 + (size_t)a.kmax * a.nth_max;
+    double2* sx = s2 + (size_t)a.kmax * a.nth_max;
+    const size_t ld = a.nth_max;
+    const double x0 = 1.0 / sqrt((double)n);
+    // lambda_hi: power iteration with T (x in sx, T x into s1)
+    for (int i = 0; i < n; ++i) sx[(size_t)i * ld] = make_double2(x0, (i & 1) ? x0 : -x0);
+    double hi = 1.0, nx = sqrt(2.0);
+    for (int it = 0; it < 6; ++it) {
+        double ny = 0.0;
+        for (int i = 0; i < n; ++i) {
+            double2 v = cmul(al[i], sx[(size_t)i * ld]);
+            if (i + 1 < n) v = cadd(v, cmul(be[i], sx[(size_t)(i + 1) * ld]));
+            if (i > 0) v = cadd(v, cscale(sx[(size_t)(i - 1) * ld], de[i - 1]));
+            s1[(size_t)i * ld] = v;
+            ny += v.x * v.x + v.y * v.y;
+        }
+        ny = sqrt(ny);
+        if (!(ny > 0.0) || !isfinite(ny)) break;
+        hi = ny / nx;
+        for (int i = 0; i < n; ++i) sx[(size_t)i * ld] = cscale(s1[(size_t)i * ld], 1.0 / ny);
+        nx = 1.0;
+    }
+    // lambda_lo: inverse iteration (tridiagonal solves in place)
+    for (int i = 0; i < n; ++i) sx[(size_t)i * ld] = make_double2(x0, (i & 1) ? x0 : -x0);
+    double lo = hi;
+    nx = sqrt(2.0);
+    for (int it = 0; it < 6; ++it) {
+        auto B = [&](int i) -> double2 { return sx[(size_t)i * ld]; };
+        tri_solve(al, be, de, n, make_double2(0.0, 0.0), B, sd, s1, s2, sx, ld, 1.0);
+        double ny = 0.0;
+        for (int i = 0; i < n; ++i) { double2 v = sx[(size_t)i * ld]; ny += v.x * v.x + v.y * v.y; }
+        ny = sqrt(ny);
+        if (!(ny > 0.0) || !isfinite(ny)) break;
+        lo = nx / ny;
+        for (int i = 0; i < n; ++i) sx[(size_t)i * ld] = cscale(sx[(size_t)i * ld], 1.0 / ny);
+        nx = 1.0;
+    }
+    lo = fmin(lo, hi);
+    const double c = sqrt(lo * hi);
+    a.c[src] = (c > 0.0 && isfinite(c)) ? c : 1.0;
+}
+
+// Projected resolvent c = (sigma - T)^{-1} e_1 = -(T - sigma)^{-1} e_1: the two-sided Lanczos
+// approximation of (sigma - A)^{-1} b (Sec. 2 applied to f(a) = 1/(sigma - a)).  One thread per
+// source; rows beyond k_eff are zero.
+__global__ void k_proj_resolvent(QuadArgs a, const double2* __restrict__ shifts) {
+    const int src = blockIdx.x * blockDim.x + threadIdx.x;
+    if (src >= a.nb) return;
+    const int n = a.state[src].k_eff;
+    double2* out = a.s + (size_t)src * a.kmax;
+    for (int i = 0; i < a.k; ++i) out[i] = make_double2(0.0, 0.0);
+    if (n <= 0) { a.check[src] = 0.0; return; }
+    const double2* al = a.alpha + (size_t)src * a.kmax;
+    const double2* be = a.beta + (size_t)src * a.kmax;
+    const double* de = a.delta + (size_t)src * a.kmax;
+    double2* sd = a.work + (size_t)src * a.kmax * 4 * a.nth_max;
+    double2* s1 = sd + (size_t)a.kmax * a.nth_max;
+    double2* s2 = s1 + (size_t)a.kmax * a.nth_max;
+    double2* sx = s2 + (size_t)a.kmax * a.nth_max;
+    const double2 sg = shifts[src];
+    auto B = [&](int i) -> double2 { return make_double2(i == 0 ? 1.0 : 0.0, 0.0); };
+    tri_solve(al, be, de, n, make_double2(-sg.x, -sg.y), B, sd, s1, s2, sx, a.nth_max, -1.0);
+    double nrm = 0.0;
+    for (int i = 0; i < n; ++i) { double2 v = sx[(size_t)i * a.nth_max]; out[i] = v; nrm += v.x * v.x + v.y * v.y; }
+    a.check[src] = isfinite(nrm) ? 0.0 : 1.0;
+}
+
+cudaError_t proj_resolvent(const QuadArgs& a, const double2* shifts, cudaStream_t st) {
+    k_proj_resolvent<<<(a.nb + 31) / 32, 32, 0, st>>>(a, shifts);
+    return cudaGetLastError();
+}
+
+// Newton result -> projected coefficient vector: first column of X.
+__global__ void k_nt_first_column(NewtonArgs a, double2* __restrict__ out, int ldo) {
+    const int b = blockIdx.y;
+    const int i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= a.k) return;
+    out[(size_t)b * ldo + i] = a.X[(size_t)b * a.ld * a.ld + (size_t)i * a.ld];
+}
+
+cudaError_t quad_sign_e1(const QuadArgs& a, int nodes, cudaStream_t st) {
+    k_quad_scale<<<(a.nb + 31) / 32, 32, 0, st>>>(a);
+    k_quad<<<a.nb, 2 * nodes, 0, st>>>(a, 0);
+    k_quad<<<a.nb, 2 * nodes, 0, st>>>(a, 1);
+    return cudaGetLastError();
+}
+
+cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st) {
+    k_nt_first_column<<<dim3((unsigned)((a.k + 127) / 128), (unsigned)a.nb), 128, 0, st>>>(a, out, ldo);
+    return cudaGetLastError();
 }
 
 static inline dim3 nt_grid_elems(const NewtonArgs& a) {

@@ -24,15 +24,19 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblq.so")
 
 LQ_OK = 0
+# Revision tag of the stencil kernel; stored ncu traffic figures are only valid for this one.
+KERNEL_REV = "hop-v1"
 ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_CUDA", -5: "LQ_ERR_BREAKDOWN",
           -6: "LQ_ERR_NEWTON", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NOT_READY", -9: "LQ_ERR_NONFINITE"}
 LQ_FP64, LQ_MIXED = 0, 1
 LQ_DIR_MU, LQ_DIR_SU3, LQ_DIR_U1 = 0, 1, 2
+LQ_PROJ_AUTO, LQ_PROJ_NEWTON, LQ_PROJ_QUAD = 0, 1, 2
 
 EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_upload_gauge", "lq_set_mu",
             "lq_reserve", "lq_apply_H", "lq_set_direction", "lq_apply_block", "lq_sign_apply",
             "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
-            "lq_profile_read"]
+            "lq_profile_read", "lq_error_estimate",
+            "lq_upload_deflation", "lq_deflation_derivatives"]
 
 
 class LatticeDesc(ctypes.Structure):
@@ -43,12 +47,15 @@ class LatticeDesc(ctypes.Structure):
 
 class Opts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_int), ("breakdown_tol", ctypes.c_double), ("newton_max_iter", ctypes.c_int),
-                ("newton_tol", ctypes.c_double), ("deflate", ctypes.c_int)]
+                ("newton_tol", ctypes.c_double), ("deflate", ctypes.c_int), ("projected", ctypes.c_int),
+                ("quad_nodes", ctypes.c_int), ("proj_tol", ctypes.c_double), ("hop_variant", ctypes.c_int),
+                ("defl_kmax", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
     _fields_ = [("k_eff", ctypes.c_int), ("newton_iters", ctypes.c_int), ("status", ctypes.c_int),
-                ("reserved", ctypes.c_int), ("newton_change", ctypes.c_double), ("x_norm", ctypes.c_double)]
+                ("projected", ctypes.c_int), ("newton_change", ctypes.c_double), ("x_norm", ctypes.c_double),
+                ("proj_check", ctypes.c_double), ("hop_variant", ctypes.c_int), ("reserved", ctypes.c_int)]
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
@@ -100,6 +107,9 @@ def lib():
         L.lq_profile_enable.argtypes = [P, I]
         L.lq_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
         L.lq_newton_sign.argtypes = [P, P, P, I, I, I, D, ctypes.POINTER(I), P]
+        L.lq_error_estimate.argtypes = [P, ctypes.POINTER(Direction), P, I, ctypes.POINTER(Opts), P, P]
+        L.lq_upload_deflation.argtypes = [P, I, P, P, P, P]
+        L.lq_deflation_derivatives.argtypes = [P, ctypes.POINTER(Direction), ctypes.POINTER(Opts), P, P, P, P]
         for name in EXPORTED:
             if name not in ("lq_default_opts", "lq_destroy", "lq_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -238,30 +248,38 @@ class Context:
         return yt, yb
 
     @staticmethod
-    def opts(k, breakdown_tol=1e-14, newton_max_iter=50, newton_tol=1e-13):
+    def opts(k, breakdown_tol=1e-14, newton_max_iter=50, newton_tol=1e-13, projected=LQ_PROJ_AUTO, quad_nodes=64,
+             proj_tol=1e-11, hop_variant=-1, deflate=0, defl_kmax=0):
         o = Opts()
         lib().lq_default_opts(ctypes.byref(o))
         o.kmax = int(k)
         o.breakdown_tol = float(breakdown_tol)
         o.newton_max_iter = int(newton_max_iter)
         o.newton_tol = float(newton_tol)
+        o.projected = int(projected)
+        o.quad_nodes = int(quad_nodes)
+        o.proj_tol = float(proj_tol)
+        o.hop_variant = int(hop_variant)
+        o.deflate = int(deflate)
+        o.defl_kmax = int(defl_kmax)
         return o
 
-    def sign_apply(self, x, k, **kw):
+    def sign_apply(self, x, k, out=None, **kw):
         """sgn(H(mu)) x by k steps of two-sided Lanczos; returns (y, reports)."""
         x = _as_c128(x)
         nsrc = x.shape[0]
-        y = _empty_like(x)
+        y = _empty_like(x) if out is None else out
         o = self.opts(k, **kw)
         rep = (Report * nsrc)()
         self._check(self._L.lq_sign_apply(self._h, _ptr(x), _ptr(y), int(nsrc), ctypes.byref(o), rep, _stream(x)))
         return y, [r.as_dict() for r in rep]
 
-    def sign_derivative_apply(self, x, k, kind=LQ_DIR_MU, field=None, **kw):
-        """Eq. (2.6): returns (sgn(H) x, d_t sgn(H) x, reports) along the direction (kind, field)."""
+    def sign_derivative_apply(self, x, k, kind=LQ_DIR_MU, field=None, out=None, **kw):
+        """Eq. (2.6): returns (sgn(H) x, d_t sgn(H) x, reports) along the direction (kind, field).
+        out = (y_sign, y_deriv) lets the caller supply the output buffers (host or device)."""
         x = _as_c128(x)
         nsrc = x.shape[0]
-        ys, yd = _empty_like(x), _empty_like(x)
+        ys, yd = (_empty_like(x), _empty_like(x)) if out is None else out
         d, keep = self._direction(kind, field)
         o = self.opts(k, **kw)
         rep = (Report * nsrc)()
@@ -286,6 +304,41 @@ class Context:
         d = np.zeros(k, np.float64)
         self._check(self._L.lq_tsl_coefficients(self._h, int(src), int(k), _ptr(a), _ptr(b), _ptr(d)))
         return a, b[:k - 1], d[:k - 1]
+
+    def upload_deflation(self, lam, R, L):
+        """Eigenpairs for the deflation of Sec. 3: lam [l] complex, R [l][V][4][3] right
+        eigenvectors, L [l][V][4][3] left eigenvectors as kets (<L_i|R_j> = delta_ij)."""
+        lam = np.ascontiguousarray(np.asarray(lam, dtype=np.complex128))
+        R, L = _as_c128(R), _as_c128(L)
+        self._defl_keep = (lam, R, L)
+        self._check(self._L.lq_upload_deflation(self._h, int(lam.shape[0]), _ptr(lam), _ptr(R), _ptr(L), _stream(R)))
+
+    def deflation_derivatives(self, k, kind=LQ_DIR_MU, field=None, **kw):
+        """(dlambda [l], dR [l][V][4][3], dL kets [l][V][4][3]) along the direction (host arrays)."""
+        l = self._defl_keep[0].shape[0]
+        dlam = np.zeros(l, np.complex128)
+        dR = np.zeros((l, self.V, 4, 3), np.complex128)
+        dL = np.zeros((l, self.V, 4, 3), np.complex128)
+        d, keep = self._direction(kind, field)
+        o = self.opts(k, **kw)
+        self._check(self._L.lq_deflation_derivatives(self._h, ctypes.byref(d), ctypes.byref(o), _ptr(dlam), _ptr(dR),
+                                                     _ptr(dL), _stream(None)))
+        return dlam, dR, dL
+
+    def error_estimate(self, x, k, kind=None, field=None, **kw):
+        """eps_A of Sec. 4 per source: the sign (kind None) or the derivative version (kind = LQ_DIR_*)."""
+        x = _as_c128(x)
+        nsrc = x.shape[0]
+        eps = np.zeros(nsrc, np.float64)
+        o = self.opts(k, **kw)
+        if kind is None:
+            code = self._L.lq_error_estimate(self._h, None, _ptr(x), int(nsrc), ctypes.byref(o), _ptr(eps), _stream(x))
+        else:
+            d, keep = self._direction(kind, field)
+            code = self._L.lq_error_estimate(self._h, ctypes.byref(d), _ptr(x), int(nsrc), ctypes.byref(o), _ptr(eps),
+                                             _stream(x))
+        self._check(code)
+        return eps
 
     def newton_sign(self, X, max_iter=50, tol=1e-13):
         """Batched dense sign of complex k x k matrices X [nb][k][k] (CUDA tensor)."""

@@ -81,7 +81,8 @@ def test_sign_apply_fp64_parity(lqlib, dims, k, nsrc):
 
 @pytest.mark.parametrize("dims,k,nsrc", CASES)
 @pytest.mark.parametrize("kind", [0, 1])
-def test_sign_derivative_fp64_parity(lqlib, dims, k, nsrc, kind):
+@pytest.mark.parametrize("variant", [0, 1])
+def test_sign_derivative_fp64_parity(lqlib, dims, k, nsrc, kind, variant):
     from paper_1611_00195_gb300 import lq
     mu = 0.3
     U = syn.gauge_field(dims, 0.4, 3)
@@ -91,7 +92,8 @@ def test_sign_derivative_fp64_parity(lqlib, dims, k, nsrc, kind):
     c.upload_gauge(torch.from_numpy(U).cuda())
     c.reserve(k, nsrc, True)
     ys, yd, rep = c.sign_derivative_apply(torch.from_numpy(x).cuda(), k, kind=kind,
-                                          field=None if field is None else torch.from_numpy(field).cuda())
+                                          field=None if field is None else torch.from_numpy(field).cuda(),
+                                          hop_variant=variant)
     ys, yd = ys.cpu().numpy(), yd.cpu().numpy()
     lat, A, Ah, E, Eh = oracle_ops(dims, U, mu, kind, field)
     for s in range(nsrc):
@@ -131,3 +133,76 @@ def test_mixed_converges_to_exact(lqlib):
     print("mixed vs exact at k=%d: sign %.3g deriv %.3g" % (k, es, ed))
     assert rep[0]["status"] == 0
     assert es < 1e-6 and ed < 1e-5
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("dims,k", [((4, 4, 4, 4), 64), ((6, 3, 5, 2), 120), ((3, 2, 2, 2), 1), ((3, 2, 2, 2), 2)])
+def test_projected_quadrature_matches_newton(lqlib, prec, dims, k):
+    """The same Lanczos run finished by the Newton iteration and by the quadrature of
+    sgn(T) = (2/pi) T int (t^2 + T^2)^{-1} dt must give the same sgn(T_k) e_1 (to rounding),
+    and the automatic choice must accept the quadrature through its involution check."""
+    from paper_1611_00195_gb300 import lq
+    mu = 0.3
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = torch.from_numpy(syn.gaussian_source(dims, 5, nsrc=2)).cuda()
+    c = lq.Context(dims, mu=mu, precision=prec)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(k, 2, True)
+    out = {}
+    for proj in (lq.LQ_PROJ_NEWTON, lq.LQ_PROJ_QUAD, lq.LQ_PROJ_AUTO):
+        ys, yd, rep = c.sign_derivative_apply(x, k, projected=proj)
+        out[proj] = (ys.cpu().numpy(), yd.cpu().numpy(), rep)
+    for s in range(2):
+        rq = out[lq.LQ_PROJ_QUAD][2][s]
+        errs = []
+        for i in (0, 1):
+            a, b = out[lq.LQ_PROJ_QUAD][i][s], out[lq.LQ_PROJ_NEWTON][i][s]
+            errs.append(0.0 if np.linalg.norm(b) == 0 else relerr(a, b))
+        print("quadrature k=%d: check %.3g, vs Newton sign %.3g deriv %.3g, auto used %d"
+              % (k, rq["proj_check"], errs[1], errs[0], out[lq.LQ_PROJ_AUTO][2][s]["projected"]))
+        assert out[lq.LQ_PROJ_NEWTON][2][s]["projected"] == lq.LQ_PROJ_NEWTON
+        assert rq["projected"] == lq.LQ_PROJ_QUAD
+        assert rq["proj_check"] < 1e-11
+        assert out[lq.LQ_PROJ_AUTO][2][s]["projected"] == lq.LQ_PROJ_QUAD
+        assert max(errs) < 1e-11
+        for i in (0, 1):
+            assert np.array_equal(out[lq.LQ_PROJ_AUTO][i][s], out[lq.LQ_PROJ_QUAD][i][s])
+
+
+def test_projected_auto_falls_back_to_newton(lqlib):
+    """With a quadrature too coarse to pass the involution check (2 nodes, tiny tolerance)
+    the automatic choice must finish with the Newton iteration and say so."""
+    from paper_1611_00195_gb300 import lq
+    dims, k, mu = (4, 4, 4, 4), 64, 0.3
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = torch.from_numpy(syn.gaussian_source(dims, 5, nsrc=1)).cuda()
+    c = lq.Context(dims, mu=mu)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(k, 1, False)
+    yn, rn = c.sign_apply(x, k, projected=lq.LQ_PROJ_NEWTON)
+    ya, ra = c.sign_apply(x, k, projected=lq.LQ_PROJ_AUTO, quad_nodes=2, proj_tol=1e-14)
+    assert ra[0]["projected"] == lq.LQ_PROJ_NEWTON and ra[0]["status"] == 0
+    assert relerr(ya.cpu().numpy(), yn.cpu().numpy()) < 1e-15
+
+
+@pytest.mark.parametrize("dims,k", [((3, 2, 2, 2), 40), ((4, 4, 4, 4), 64)])
+@pytest.mark.parametrize("deriv", [False, True])
+def test_error_estimate_parity(lqlib, dims, k, deriv):
+    """eps_A of Sec. 4 (sign, and the derivative version with B and (0, x)) against the
+    oracle's own estimate at the same depth."""
+    from paper_1611_00195_gb300 import lq
+    mu = 0.3
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = syn.gaussian_source(dims, 5, nsrc=2)
+    c = lq.Context(dims, mu=mu)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(k, 2, True)
+    eps = c.error_estimate(torch.from_numpy(x).cuda(), k, kind=lq.LQ_DIR_MU if deriv else None)
+    lat, A, Ah, E, Eh = oracle_ops(dims, U, mu)
+    for s in range(2):
+        if deriv:
+            ref = ot.error_estimate_derivative(A, Ah, E, Eh, x[s], k)
+        else:
+            ref = ot.error_estimate(A, Ah, x[s], k)
+        print("eps_A %s k=%d: gpu %.6e oracle %.6e" % ("deriv" if deriv else "sign", k, eps[s], ref))
+        assert abs(eps[s] - ref) <= 1e-6 * ref
