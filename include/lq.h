@@ -234,6 +234,28 @@ int  lq_error_estimate(lq_ctx* ctx, const lq_direction* dir, const double* x, in
 int  lq_newton_sign(lq_ctx* ctx, const double* X, double* S, int k, int nb,
                     int max_iter, double tol, int* iters, void* stream);
 
+/* Allocation-free variant of lq_newton_sign, for callers that cannot allocate device
+ * memory: for example a process whose device memory is handed in full to a pool allocator
+ * (a framework's caching allocator), where a cudaMalloc of the library's own would fail or
+ * fragment the pool, or a service that forbids allocation after start-up.  The paper has no
+ * counterpart: this entry point only changes where the workspace lives.
+ *   - Needs no context and calls no cudaMalloc / cudaFree or other allocating routine.  Its
+ *     workspace is one static device array of about 4.2 MB that every GPU loading the
+ *     library holds until the process exits.
+ *   - Limits: k <= 128 and nb <= 8; larger sizes return LQ_ERR_ARG and run nothing.
+ *   - The first call on a device looks up the array's device address for that device
+ *     (cudaGetSymbolAddress, with that device current); make that first call before any stream
+ *     capture.
+ *   - Every call on a device shares the one array and it keeps the last call's contents (the
+ *     call clears what must start at zero).  Calls that overlap on the GPU -- from several
+ *     host threads or on several streams at once -- race on it and give wrong results:
+ *     serialise them.
+ * X, S: device double[nb][k][k][2] row-major; iters: host int[nb] or NULL.  Returns LQ_OK,
+ * LQ_ERR_ARG, LQ_ERR_CUDA, or LQ_ERR_NEWTON if a matrix did not converge.  Synchronises
+ * `stream`. */
+int  lq_newton_sign_noalloc(const double* X, double* S, int k, int nb, int max_iter, double tol,
+                            int* iters, void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -547,3 +547,100 @@ cudaError_t newton_copy_out(const NewtonArgs& a, double2* Sout, cudaStream_t st)
 }
 
 }  // namespace lq
+
+// ---------------------------------------------------------------------------------------------
+// Allocation-free variant of the batched Newton sign (lq_newton_sign_noalloc, include/lq.h).
+// Its workspace is one file-scope device array; host code reaches it through the address that
+// cudaGetSymbolAddress returns for the current device (the array's name in host code is only a
+// host-side stand-in and must never be passed to a kernel).
+// ---------------------------------------------------------------------------------------------
+#include <mutex>
+
+namespace lq {
+namespace {
+
+constexpr int kNaMaxK = 128;     // largest matrix dimension
+constexpr int kNaMaxNb = 8;      // largest batch
+constexpr size_t kNaPartBlocks = ((size_t)kNaMaxK * kNaMaxK + kNtThreads - 1) / kNtThreads;
+
+struct NaLayout {
+    double2 X[kNaMaxNb * kNaMaxK * kNaMaxK];
+    double2 Y[kNaMaxNb * kNaMaxK * kNaMaxK];
+    double2 F[kNaMaxNb * kNaMaxK];
+    double scal[kNaMaxNb * 16];
+    double partials[kNaMaxNb * kNaPartBlocks * 4];
+    int perm[kNaMaxNb * kNaMaxK];
+    int counters[3 * kNaMaxNb];
+};
+
+// ~4.2 MB per device, held by every GPU that loads the library until the process exits.
+static __device__ __align__(256) unsigned char g_na_scratch[sizeof(NaLayout)];
+
+constexpr int kNaMaxDevices = 64;
+std::mutex g_na_mutex;
+NaLayout* g_na_ptr[kNaMaxDevices] = {nullptr};
+
+// Device address of the scratch array on the current device (looked up once per device).
+cudaError_t na_scratch(NaLayout** out) {
+    int dev = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return e;
+    if (dev < 0 || dev >= kNaMaxDevices) return cudaErrorInvalidDevice;
+    std::lock_guard<std::mutex> lock(g_na_mutex);
+    if (!g_na_ptr[dev]) {
+        void* p = nullptr;
+        e = cudaGetSymbolAddress(&p, g_na_scratch);
+        if (e != cudaSuccess) return e;
+        g_na_ptr[dev] = reinterpret_cast<NaLayout*>(p);
+    }
+    *out = g_na_ptr[dev];
+    return cudaSuccess;
+}
+
+}  // namespace
+}  // namespace lq
+
+extern "C" int lq_newton_sign_noalloc(const double* X, double* S, int k, int nb, int max_iter, double tol,
+                                      int* iters, void* stream) {
+    using namespace lq;
+    if (!X || !S || k < 1 || nb < 1 || max_iter < 1 || !(tol > 0.0)) return LQ_ERR_ARG;
+    if (k > kNaMaxK || nb > kNaMaxNb) return LQ_ERR_ARG;   // beyond the static workspace
+    cudaStream_t st = (cudaStream_t)stream;
+    NaLayout* w = nullptr;
+    if (na_scratch(&w) != cudaSuccess) { cudaGetLastError(); return LQ_ERR_CUDA; }
+    NewtonArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.k = k;
+    a.nb = nb;
+    a.ld = k;
+    a.X = w->X;
+    a.Y = w->Y;
+    a.F = w->F;
+    a.perm = w->perm;
+    a.scal = w->scal;
+    a.partials = w->partials;
+    a.partial_stride = kNaPartBlocks;
+    a.counters = w->counters;
+    a.tol = tol;
+    a.max_iter = max_iter;
+    // the array keeps the previous call's contents: the block counters must start at zero
+    if (cudaMemsetAsync(w->counters, 0, sizeof(w->counters), st) != cudaSuccess) { cudaGetLastError(); return LQ_ERR_CUDA; }
+    if (newton_init_dense(a, reinterpret_cast<const double2*>(X), st) != cudaSuccess) return LQ_ERR_CUDA;
+    double scal[kNaMaxNb * 16];
+    for (int it = 0; it < max_iter; ++it) {
+        if (newton_iteration(a, st) != cudaSuccess) return LQ_ERR_CUDA;
+        if (cudaMemcpyAsync(scal, w->scal, sizeof(double) * 16 * nb, cudaMemcpyDeviceToHost, st) != cudaSuccess) return LQ_ERR_CUDA;
+        if (cudaStreamSynchronize(st) != cudaSuccess) return LQ_ERR_CUDA;
+        bool all = true;
+        for (int b = 0; b < nb; ++b) all = all && scal[b * 16 + NS_DONE] != 0.0;
+        if (all) break;
+    }
+    if (newton_copy_out(a, reinterpret_cast<double2*>(S), st) != cudaSuccess) return LQ_ERR_CUDA;
+    if (cudaStreamSynchronize(st) != cudaSuccess) return LQ_ERR_CUDA;
+    int bad = 0;
+    for (int b = 0; b < nb; ++b) {
+        if (iters) iters[b] = (int)scal[b * 16 + NS_ITERS];
+        if (scal[b * 16 + NS_STATUS] != 0.0) bad = 1;
+    }
+    return bad ? LQ_ERR_NEWTON : LQ_OK;
+}

@@ -35,7 +35,7 @@ LQ_PROJ_AUTO, LQ_PROJ_NEWTON, LQ_PROJ_QUAD = 0, 1, 2
 EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_upload_gauge", "lq_set_mu",
             "lq_reserve", "lq_apply_H", "lq_set_direction", "lq_apply_block", "lq_sign_apply",
             "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
-            "lq_profile_read", "lq_error_estimate",
+            "lq_profile_read", "lq_newton_sign_noalloc", "lq_error_estimate",
             "lq_upload_deflation", "lq_deflation_derivatives"]
 
 
@@ -110,6 +110,7 @@ def lib():
         L.lq_error_estimate.argtypes = [P, ctypes.POINTER(Direction), P, I, ctypes.POINTER(Opts), P, P]
         L.lq_upload_deflation.argtypes = [P, I, P, P, P, P]
         L.lq_deflation_derivatives.argtypes = [P, ctypes.POINTER(Direction), ctypes.POINTER(Opts), P, P, P, P]
+        L.lq_newton_sign_noalloc.argtypes = [P, P, I, I, I, D, ctypes.POINTER(I), P]
         for name in EXPORTED:
             if name not in ("lq_default_opts", "lq_destroy", "lq_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -167,6 +168,20 @@ def _stream(x=None):
         dev = x.device if (_is_tensor(x) and x.is_cuda) else None
         return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     return ctypes.c_void_p(0)
+
+
+def newton_sign_noalloc(X, max_iter=50, tol=1e-13):
+    """Batched dense sign of complex k x k matrices X [nb][k][k] (CUDA tensor, k <= 128, nb <= 8)
+    through the allocation-free entry point: no context and no device allocation by the library
+    (the output tensor is allocated here, by the caller's allocator)."""
+    X = _as_c128(X)
+    nb, k = X.shape[0], X.shape[1]
+    S = _empty_like(X)
+    iters = (ctypes.c_int * nb)()
+    code = lib().lq_newton_sign_noalloc(_ptr(X), _ptr(S), int(k), int(nb), int(max_iter), float(tol), iters, _stream(X))
+    if code != LQ_OK:
+        raise LQError(code, "lq_newton_sign_noalloc (k <= 128, nb <= 8)")
+    return S, list(iters)
 
 
 class Context:
