@@ -90,6 +90,10 @@ typedef struct {
                               thread per (site, side), 1 = one thread per (site, output field) */
     int defl_kmax;         /* depth of the shifted solves for the eigenvector derivatives of the
                               generalised deflation (0 = the reserved kmax)                    */
+    int defl_nderiv;       /* Jordan blocks of the derivative deflation: the first defl_nderiv
+                              uploaded pairs (0 = all); the shifted solves still project out all
+                              uploaded pairs (the paper deflates the derivative with fewer pairs
+                              than the sign, Sec. 4)                                           */
 } lq_opts;
 
 /* Projected step sgn(T_k) e_1 (Sec. 2):
@@ -136,10 +140,13 @@ int  lq_upload_gauge(lq_ctx* ctx, const double* U, void* stream);
 /* Change mu (Eq. (1.1)) without re-uploading the gauge field. */
 int  lq_set_mu(lq_ctx* ctx, double mu);
 
-/* Reserve all workspace for Krylov depth <= kmax and <= nsrc sources per call; `block` = 1
- * reserves for the derivative path (2n-dimensional block vectors of Eq. (2.6)), 0 for the
- * sign path only.  No later call allocates device memory.  LQ_ERR_OOM on failure. */
-int  lq_reserve(lq_ctx* ctx, int kmax, int nsrc, int block);
+/* Reserve all workspace for Krylov depth <= kmax and <= nsrc sources per call.  flags:
+ * LQ_RESERVE_BLOCK for the derivative path (2n-dimensional block vectors of Eq. (2.6)),
+ * LQ_RESERVE_ADJOINT for lq_sign_bilinear_grad (stored left basis, nsrc >= 2); 0 for the sign
+ * path only.  No later solve call allocates device memory.  LQ_ERR_OOM on failure. */
+#define LQ_RESERVE_BLOCK    1
+#define LQ_RESERVE_ADJOINT  2
+int  lq_reserve(lq_ctx* ctx, int kmax, int nsrc, int flags);
 
 /* y = H(mu) x (dagger = 0) or y = H(mu)^dag x = H(-mu) x (dagger = 1) for nsrc fields
  * (Eq. (1.1)); the single stencil application.  Needs the gauge field and lq_reserve(nsrc). */
@@ -209,6 +216,18 @@ typedef struct {
 int  lq_profile_enable(lq_ctx* ctx, int enable);
 int  lq_profile_read(lq_ctx* ctx, lq_profile* out);
 
+/* The bilinear S = Re <y| sgn(H(mu)) |x> and its gradient: the fermionic force
+ * force[nu][s][a] = dS/dw^a for U_nu(s) -> exp(i w^a lambda_a/2) U_nu(s) (the use named in
+ * Secs. 1 and 5), and dS/dmu.  Uses dS/dt = Re tr(E L_sgn(H, x y^H)) with the Krylov
+ * approximation L ~ |x||y| V_1 X W_2^H: V_1, T_1 from the Lanczos process started at x, W_2, T_2
+ * from the process started at y, X the top-right block of sgn([[T_1, e_1 e_1^T], [0, T_2]]) by
+ * Mathias' identity (Eq. (2.5)), evaluated by the quadrature of the projected sign (2 quad_nodes
+ * rank-one terms).  x, y: one field each (host or device); S, dS_dmu: host double*; force:
+ * double[4][V][8] (host or device, may be NULL).  Needs lq_reserve(kmax, nsrc >= 2,
+ * LQ_RESERVE_ADJOINT).  Synchronises `stream`. */
+int  lq_sign_bilinear_grad(lq_ctx* ctx, const double* x, const double* y, const lq_opts* opts,
+                           double* S, double* force, double* dS_dmu, void* stream);
+
 /* Copy the projected tridiagonal T_k of source `src` from the last lq_sign_apply /
  * lq_sign_derivative_apply (Sec. 2): alpha[j] = T[j][j], beta[j] = T[j][j+1],
  * delta[j] = T[j+1][j] (real, > 0).  alpha, beta: host double[k][2] (complex); delta:
@@ -224,6 +243,13 @@ int  lq_tsl_coefficients(lq_ctx* ctx, int src, int k, double* alpha, double* bet
  * lq_reserve(..., block = 1) for the derivative version.  Synchronises `stream`. */
 int  lq_error_estimate(lq_ctx* ctx, const lq_direction* dir, const double* x, int nsrc,
                        const lq_opts* opts, double* eps, void* stream);
+
+/* Host-only utility (no GPU): eigenvalues w[n][2] and unit right eigenvectors V (columns,
+ * row-major double[n][n][2], may be NULL) of a general complex matrix A double[n][n][2]
+ * (row-major), by Householder reduction to Hessenberg form and the shifted QR algorithm.
+ * Used for the Rayleigh-Ritz steps of lq_compute_deflation.  LQ_ERR_NEWTON if QR does not
+ * converge. */
+int  lq_dense_eig(int n, const double* A, double* w, double* V);
 
 /* Batched dense FP64 sign of nb complex k x k matrices by the scaled Newton iteration
  * X <- (m X + (m X)^{-1})/2, m = sqrt(||X^{-1}||_F / ||X||_F) (Higham 2008, ch. 5; the

@@ -216,9 +216,12 @@ void free_workspace(lq_ctx* c) {
                    (void**)&c->state, (void**)&c->alpha, (void**)&c->beta, (void**)&c->delta, (void**)&c->scale,
                    (void**)&c->nx_X, (void**)&c->nx_Y, (void**)&c->nx_F, (void**)&c->nx_perm, (void**)&c->nx_scal,
                    (void**)&c->nx_partials, (void**)&c->nx_counters, (void**)&c->proj_c, (void**)&c->quad_q,
-                   (void**)&c->quad_work, (void**)&c->quad_c, (void**)&c->quad_check};
+                   (void**)&c->quad_work, (void**)&c->quad_c, (void**)&c->quad_check, (void**)&c->proj_sel,
+                   &c->lbasis, (void**)&c->uscale, (void**)&c->adj_coef, &c->adj_nu, &c->adj_om,
+                   (void**)&c->adj_force, (void**)&c->adj_dmu, (void**)&c->gen_scr};
     for (void** p : ps) { dfree(*p); *p = nullptr; }
     c->kmax = c->nsrc = c->block = 0;
+    c->adjoint = false;
 }
 
 // Choose the stencil schedule for the Lanczos step: time each variant on the caller's data
@@ -264,7 +267,8 @@ enum { FN_SIGN = 0, FN_RESOLVENT = 1 };
 
 int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report* rep,
             double* y0, double* y1, cudaStream_t st, const double* x_dev = nullptr,
-            const double* x_top = nullptr, int fn = FN_SIGN, const double2* shifts = nullptr) {
+            const double* x_top = nullptr, int fn = FN_SIGN, const double2* shifts = nullptr,
+            bool store_left = false) {
     const int k = o->kmax;
     const size_t F = fe(c);
     const size_t vstride = (size_t)nf * F;        // Chunk elements per Krylov vector
@@ -283,6 +287,8 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     ia.src_stride_basis = sb; ia.src_stride_left = sl; ia.state = c->state;
     ia.partials = c->partials; ia.partial_stride = c->partial_blocks; ia.counters = c->counters;
     ia.breakdown_tol = o->breakdown_tol;
+    const size_t sst = (size_t)c->kmax * F;   // per source: stored left basis (NF = 1)
+    if (store_left) { ia.w1_store = c->lbasis; ia.src_stride_store = sst; }
     cudaEvent_t e0 = prof_begin(c, st);
     LQ_CUDA(c, launch_tsl_init(c->prec, nf, ia, st));
     prof_end(c, PC_OTHER, e0, st);
@@ -294,6 +300,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     set_side(h, 1, c, 1, emode);
     h.state = c->state; h.partials = c->partials; h.partial_stride = c->partial_blocks; h.counters = c->counters;
     h.alpha = c->alpha; h.scale = c->scale; h.kmax = c->kmax; h.kmax_run = k;
+    h.uscale = store_left ? c->uscale : nullptr;
     h.src_stride_in[0] = sb; h.src_stride_in[1] = sl;
     h.src_stride_out[0] = sio; h.src_stride_out[1] = sio;
     h.out[0] = c->rout; h.out[1] = c->lout;
@@ -327,6 +334,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
             u.j = j;
             u.v_cur = bvec(j); u.v_prev = bvec(j > 0 ? j - 1 : j); u.v_next = bvec(j + 1);
             u.w_cur = lvec(j); u.w_prev = lvec(j > 0 ? j - 1 : j); u.w_next = lvec(j + 1);
+            if (store_left) { u.w_store = reinterpret_cast<char*>(c->lbasis) + (size_t)(j + 1) * F * cb; u.src_stride_store = sst; }
             cudaEvent_t eu = prof_begin(c, st);
             LQ_CUDA(c, launch_update(c->prec, u, st));
             prof_end(c, PC_UPDATE, eu, st);
@@ -372,13 +380,22 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
         for (int s = 0; s < nsrc; ++s) used[s] = LQ_PROJ_QUAD;
     }
     if (need_newton) {
+        // Newton for every source (LQ_PROJ_NEWTON) or only for those whose quadrature failed
+        std::vector<int> sel(nsrc, 1);
+        if (o->projected == LQ_PROJ_AUTO)
+            for (int s = 0; s < nsrc; ++s) sel[s] = !(std::isfinite(check[s]) && check[s] <= o->proj_tol);
         NewtonArgs na = newton_args(c, k, nsrc, o->newton_max_iter, o->newton_tol);
         LQ_CUDA(c, newton_init_tridiag(na, st));
         c->launches += 1;
+        const double one = 1.0;
+        for (int s = 0; s < nsrc; ++s)
+            if (!sel[s]) LQ_CUDA(c, cudaMemcpyAsync(c->nx_scal + (size_t)s * 16 + NS_DONE, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+        LQ_CUDA(c, cudaMemcpyAsync(c->proj_sel, sel.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
         if ((r = run_newton(c, na, st, scal))) return r;
-        LQ_CUDA(c, newton_first_column(na, c->proj_c, c->kmax, st));
+        LQ_CUDA(c, newton_first_column(na, c->proj_c, c->kmax, st, c->proj_sel));
         c->launches += 1;
-        for (int s = 0; s < nsrc; ++s) used[s] = LQ_PROJ_NEWTON;
+        for (int s = 0; s < nsrc; ++s) if (sel[s]) used[s] = LQ_PROJ_NEWTON;
+        LQ_CUDA(c, cudaStreamSynchronize(st));   // sel is host memory
     }
 
     RecArgs ra;
@@ -426,6 +443,7 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
         return set_err(c, LQ_ERR_ARG, "quad_nodes must be in [1, 128] and proj_tol > 0");
     if (o->hop_variant < -1 || o->hop_variant > 1) return set_err(c, LQ_ERR_ARG, "hop_variant must be -1, 0 or 1");
     if (o->defl_kmax < 0 || o->defl_kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "defl_kmax must be in [0, reserved kmax]");
+    if (o->defl_nderiv < 0) return set_err(c, LQ_ERR_ARG, "defl_nderiv must be >= 0");
     return LQ_OK;
 }
 
@@ -438,9 +456,11 @@ int bdots_host(lq_ctx* c, const double* X, int nx, const double* Y, int ny, std:
     out.assign((size_t)nx * ny, make_double2(0.0, 0.0));
     if (nx == 0 || ny == 0) return LQ_OK;
     const size_t need = bdots_partial_doubles(nx * ny) + 2 * (size_t)nx * ny;
-    if (need > c->defl_scr_doubles) return set_err(c, LQ_ERR_ARG, "deflation scratch too small");
-    double* part = c->defl_scr;
-    double* res = c->defl_scr + bdots_partial_doubles(nx * ny);
+    double* scr = (c->defl_scr && need <= c->defl_scr_doubles) ? c->defl_scr
+                : ((c->gen_scr && need <= c->gen_scr_doubles) ? c->gen_scr : nullptr);
+    if (!scr) return set_err(c, LQ_ERR_ARG, "reduction scratch too small for " + std::to_string(nx) + " x " + std::to_string(ny) + " dots");
+    double* part = scr;
+    double* res = scr + bdots_partial_doubles(nx * ny);
     LQ_CUDA(c, launch_bdots(X, nvec(c), nx, Y, nvec(c), ny, nvec(c), part, res, st));
     c->launches += 2;
     LQ_CUDA(c, cudaMemcpyAsync(out.data(), res, sizeof(double2) * nx * ny, cudaMemcpyDeviceToHost, st));
@@ -452,8 +472,10 @@ int bdots_host(lq_ctx* c, const double* X, int nx, const double* Y, int ny, std:
 int bcombine_host(lq_ctx* c, double* Z, const double* W, int nz, const double* X, int nx,
                   const std::vector<double2>& coef, cudaStream_t st) {
     if (nz == 0) return LQ_OK;
-    double* dc = c->defl_scr;
-    if ((size_t)nz * nx * 2 > c->defl_scr_doubles) return set_err(c, LQ_ERR_ARG, "deflation scratch too small");
+    const size_t need = (size_t)nz * nx * 2;
+    double* dc = (c->defl_scr && need <= c->defl_scr_doubles) ? c->defl_scr
+               : ((c->gen_scr && need <= c->gen_scr_doubles) ? c->gen_scr : nullptr);
+    if (!dc) return set_err(c, LQ_ERR_ARG, "coefficient scratch too small");
     LQ_CUDA(c, cudaMemcpyAsync(dc, coef.data(), sizeof(double2) * nz * nx, cudaMemcpyHostToDevice, st));
     LQ_CUDA(c, launch_bcombine(Z, W, nvec(c), nz, X, nvec(c), nx, dc, nvec(c), st));
     c->launches += 1;
@@ -513,8 +535,13 @@ double2 conjh(double2 a) { return make_double2(a.x, -a.y); }
 //           + Pbar^dag (conj lambda_j - A^dag)^{-1} Pbar^dag E^dag Lk_j
 // The shifted solves are two-sided Lanczos approximations of the resolvent at depth opts->kmax
 // (the projected function (sigma - T)^{-1} e_1), started from deflated right-hand sides.
+int nderiv_of(const lq_ctx* c, const lq_opts* o) {
+    return (o->defl_nderiv > 0 && o->defl_nderiv < c->defl_l) ? o->defl_nderiv : c->defl_l;
+}
+
 int prepare_deflation_derivative(lq_ctx* c, const lq_opts* o, cudaStream_t st) {
-    const int l = c->defl_l;
+    const int l = c->defl_l;          // pairs projected out of the shifted solves
+    const int ld = nderiv_of(c, o);   // pairs whose derivatives are built (Jordan blocks)
     const size_t nv = nvec(c);
     double* R = c->defl_V;
     double* dR = c->defl_V + (size_t)l * nv;
@@ -527,19 +554,19 @@ int prepare_deflation_derivative(lq_ctx* c, const lq_opts* o, cudaStream_t st) {
     double* zR = bL + (size_t)l * nv;
     double* zL = zR + (size_t)l * nv;
     int r;
-    if ((r = apply_E(c, R, ER, l, 0, st))) return r;
-    if ((r = apply_E(c, Lk, ELk, l, 1, st))) return r;
+    if ((r = apply_E(c, R, ER, ld, 0, st))) return r;
+    if ((r = apply_E(c, Lk, ELk, ld, 1, st))) return r;
     std::vector<double2> C, D, coef;
-    if ((r = bdots_host(c, Lk, l, ER, l, C, st))) return r;          // C[i*l+j] = <Lk_i|E R_j>
-    if ((r = bdots_host(c, R, l, ELk, l, D, st))) return r;          // D[i*l+j] = <R_i|E^dag Lk_j>
-    c->defl_dlam.resize(l);
-    for (int j = 0; j < l; ++j) c->defl_dlam[j] = C[(size_t)j * l + j];
-    // deflated right-hand sides b_j = Pbar E R_j, b'_j = Pbar^dag E^dag Lk_j
-    coef.assign((size_t)l * l, make_double2(0.0, 0.0));
-    for (int j = 0; j < l; ++j) for (int i = 0; i < l; ++i) coef[(size_t)j * l + i] = make_double2(-C[(size_t)i * l + j].x, -C[(size_t)i * l + j].y);
-    if ((r = bcombine_host(c, bR, ER, l, R, l, coef, st))) return r;
-    for (int j = 0; j < l; ++j) for (int i = 0; i < l; ++i) coef[(size_t)j * l + i] = make_double2(-D[(size_t)i * l + j].x, -D[(size_t)i * l + j].y);
-    if ((r = bcombine_host(c, bL, ELk, l, Lk, l, coef, st))) return r;
+    if ((r = bdots_host(c, Lk, l, ER, ld, C, st))) return r;          // C[i*ld+j] = <Lk_i|E R_j> = L_i E R_j
+    if ((r = bdots_host(c, R, l, ELk, ld, D, st))) return r;          // D[i*ld+j] = <R_i|E^dag Lk_j> = conj(L_j E R_i)
+    c->defl_dlam.assign(l, make_double2(0.0, 0.0));
+    for (int j = 0; j < ld; ++j) c->defl_dlam[j] = C[(size_t)j * ld + j];
+    // deflated right-hand sides b_j = Pbar E R_j, b'_j = Pbar^dag E^dag Lk_j (projection with all l pairs)
+    coef.assign((size_t)ld * l, make_double2(0.0, 0.0));
+    for (int j = 0; j < ld; ++j) for (int i = 0; i < l; ++i) coef[(size_t)j * l + i] = make_double2(-C[(size_t)i * ld + j].x, -C[(size_t)i * ld + j].y);
+    if ((r = bcombine_host(c, bR, ER, ld, R, l, coef, st))) return r;
+    for (int j = 0; j < ld; ++j) for (int i = 0; i < l; ++i) coef[(size_t)j * l + i] = make_double2(-D[(size_t)i * ld + j].x, -D[(size_t)i * ld + j].y);
+    if ((r = bcombine_host(c, bL, ELk, ld, Lk, l, coef, st))) return r;
     // shifted solves, in batches of the reserved number of sources
     lq_opts so = *o;
     so.projected = LQ_PROJ_NEWTON;   // unused by the resolvent; keeps the sign solvers idle
@@ -549,8 +576,8 @@ int prepare_deflation_derivative(lq_ctx* c, const lq_opts* o, cudaStream_t st) {
         const double* bin = side == 0 ? bR : bL;
         double* zout = side == 0 ? zR : zL;
         if (side == 1) c->desc.mu = -mu0;             // A^dag = H(-mu)
-        for (int b0 = 0; b0 < l; b0 += c->nsrc) {
-            const int nb = std::min(c->nsrc, l - b0);
+        for (int b0 = 0; b0 < ld; b0 += c->nsrc) {
+            const int nb = std::min(c->nsrc, ld - b0);
             std::vector<double2> sh(nb);
             for (int q = 0; q < nb; ++q) sh[q] = side == 0 ? c->defl_lam[b0 + q] : conjh(c->defl_lam[b0 + q]);
             cudaError_t e = cudaMemcpyAsync(c->defl_shift, sh.data(), sizeof(double2) * nb, cudaMemcpyHostToDevice, st);
@@ -563,31 +590,36 @@ int prepare_deflation_derivative(lq_ctx* c, const lq_opts* o, cudaStream_t st) {
     }
     // project the solutions and add the sums over the deflated eigenvectors
     std::vector<double2> PZ, PZL;
-    if ((r = bdots_host(c, Lk, l, zR, l, PZ, st))) return r;          // <Lk_i|z_j>
-    if ((r = bdots_host(c, R, l, zL, l, PZL, st))) return r;          // <R_i|z'_j>
-    for (int j = 0; j < l; ++j)
+    if ((r = bdots_host(c, Lk, l, zR, ld, PZ, st))) return r;          // <Lk_i|z_j>
+    if ((r = bdots_host(c, R, l, zL, ld, PZL, st))) return r;          // <R_i|z'_j>
+    for (int j = 0; j < ld; ++j)
         for (int i = 0; i < l; ++i) {
-            double2 v = make_double2(-PZ[(size_t)i * l + j].x, -PZ[(size_t)i * l + j].y);
+            double2 v = make_double2(-PZ[(size_t)i * ld + j].x, -PZ[(size_t)i * ld + j].y);
             if (i != j) {
-                const double2 q = cdivh(C[(size_t)i * l + j], make_double2(c->defl_lam[j].x - c->defl_lam[i].x, c->defl_lam[j].y - c->defl_lam[i].y));
+                const double2 q = cdivh(C[(size_t)i * ld + j], make_double2(c->defl_lam[j].x - c->defl_lam[i].x, c->defl_lam[j].y - c->defl_lam[i].y));
                 v.x += q.x; v.y += q.y;
             }
             coef[(size_t)j * l + i] = v;
         }
-    if ((r = bcombine_host(c, dR, zR, l, R, l, coef, st))) return r;
-    for (int j = 0; j < l; ++j)
+    if ((r = bcombine_host(c, dR, zR, ld, R, l, coef, st))) return r;
+    for (int j = 0; j < ld; ++j)
         for (int i = 0; i < l; ++i) {
-            double2 v = make_double2(-PZL[(size_t)i * l + j].x, -PZL[(size_t)i * l + j].y);
+            double2 v = make_double2(-PZL[(size_t)i * ld + j].x, -PZL[(size_t)i * ld + j].y);
             if (i != j) {
-                const double2 q = conjh(cdivh(C[(size_t)j * l + i], make_double2(c->defl_lam[j].x - c->defl_lam[i].x, c->defl_lam[j].y - c->defl_lam[i].y)));
+                // conj((L_j E R_i) / (lambda_j - lambda_i)) with L_j E R_i = conj(D[i][j])
+                const double2 q = conjh(cdivh(conjh(D[(size_t)i * ld + j]), make_double2(c->defl_lam[j].x - c->defl_lam[i].x, c->defl_lam[j].y - c->defl_lam[i].y)));
                 v.x += q.x; v.y += q.y;
             }
             coef[(size_t)j * l + i] = v;
         }
-    if ((r = bcombine_host(c, dLk, zL, l, Lk, l, coef, st))) return r;
+    if ((r = bcombine_host(c, dLk, zL, ld, Lk, l, coef, st))) return r;
+    // derivatives beyond ld stay zero
+    if (ld < l) {
+        LQ_CUDA(c, cudaMemsetAsync(dR + (size_t)ld * nv, 0, sizeof(double) * (l - ld) * nv, st));
+        LQ_CUDA(c, cudaMemsetAsync(dLk + (size_t)ld * nv, 0, sizeof(double) * (l - ld) * nv, st));
+    }
     return LQ_OK;
 }
-
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -605,6 +637,7 @@ void lq_default_opts(lq_opts* o) {
     o->proj_tol = 1e-11;
     o->hop_variant = -1;
     o->defl_kmax = 0;
+    o->defl_nderiv = 0;
 }
 
 int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
@@ -667,9 +700,11 @@ int lq_set_mu(lq_ctx* c, double mu) {
     return LQ_OK;
 }
 
-int lq_reserve(lq_ctx* c, int kmax, int nsrc, int block) {
-    if (!c || kmax < 1 || nsrc < 1 || (block != 0 && block != 1)) return set_err(c, LQ_ERR_ARG, "invalid reserve arguments");
+int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
+    if (!c || kmax < 1 || nsrc < 1 || (flags & ~(LQ_RESERVE_BLOCK | LQ_RESERVE_ADJOINT)))
+        return set_err(c, LQ_ERR_ARG, "invalid reserve arguments");
     free_workspace(c);
+    const int block = (flags & LQ_RESERVE_BLOCK) ? 1 : 0;
     const int nf = block ? 2 : 1;
     const size_t fbytes = fb(c);
     int r;
@@ -713,6 +748,23 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int block) {
     if ((r = dalloc(c, &c->quad_work, (size_t)nsrc * kmax * 4 * 2 * kQuadMaxNodes))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->quad_c, (size_t)nsrc))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->quad_check, (size_t)nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->proj_sel, (size_t)nsrc))) { free_workspace(c); return r; }
+    {
+        const int m = std::max(2 * nsrc, 64);   // dots among up to m x m vectors
+        c->gen_scr_doubles = bdots_partial_doubles(m * m) + (size_t)2 * m * m;
+        if ((r = dalloc(c, &c->gen_scr, c->gen_scr_doubles))) { free_workspace(c); return r; }
+    }
+    if (flags & LQ_RESERVE_ADJOINT) {
+        const int np = 2 * kQuadMaxNodes;
+        if ((r = alloc_fields(&c->lbasis, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+        if ((r = dalloc(c, &c->uscale, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+        if ((r = dalloc(c, &c->adj_coef, (size_t)2 * np * kmax))) { free_workspace(c); return r; }
+        if ((r = alloc_fields(&c->adj_nu, (size_t)np))) { free_workspace(c); return r; }
+        if ((r = alloc_fields(&c->adj_om, (size_t)np))) { free_workspace(c); return r; }
+        if ((r = dalloc(c, &c->adj_force, c->V * 32))) { free_workspace(c); return r; }
+        if ((r = dalloc(c, &c->adj_dmu, c->V / 128 + 1))) { free_workspace(c); return r; }
+        c->adjoint = true;
+    }
     LQ_CUDA(c, cudaMemset(c->counters, 0, sizeof(int) * 4 * nsrc));
     LQ_CUDA(c, cudaMemset(c->nx_counters, 0, sizeof(int) * 3 * nsrc));
     LQ_CUDA(c, cudaMemset(c->nx_scal, 0, sizeof(double) * 16 * nsrc));
@@ -855,13 +907,14 @@ int lq_sign_derivative_apply(lq_ctx* c, const lq_direction* dir, const double* x
         //   Pbar psi = (-sum_i [R_i <dLk_i|x> + dR_i <Lk_i|x>],  x - sum_i R_i <Lk_i|x>)
         //   exact    = ( sum_i sgn_i [R_i <dLk_i|x> + dR_i <Lk_i|x>],  sum_i sgn_i R_i <Lk_i|x>)
         if ((r = prepare_deflation_derivative(c, o, st))) return r;
+        const int ld = nderiv_of(c, o);   // Jordan blocks used (coefficients of the other pairs stay 0)
         std::vector<double2> cd;   // [2l][nsrc]: <Lk_i|x>, then <dLk_i|x>
         if ((r = bdots_host(c, c->defl_W, 2 * l, c->io, nsrc, cd, st))) return r;
         double* xt = c->io + 3 * reg;
         double* xb = c->io + 4 * reg;
         std::vector<double2> ct((size_t)nsrc * 2 * l), cb((size_t)nsrc * 2 * l);
         for (int s = 0; s < nsrc; ++s)
-            for (int i = 0; i < l; ++i) {
+            for (int i = 0; i < ld; ++i) {
                 const double2 a = cd[(size_t)i * nsrc + s], b = cd[(size_t)(l + i) * nsrc + s];
                 ct[(size_t)s * 2 * l + i] = make_double2(-b.x, -b.y);        // R_i <dLk_i|x>
                 ct[(size_t)s * 2 * l + l + i] = make_double2(-a.x, -a.y);    // dR_i <Lk_i|x>
@@ -874,7 +927,7 @@ int lq_sign_derivative_apply(lq_ctx* c, const lq_direction* dir, const double* x
         for (auto& v : ct) v = make_double2(-v.x, -v.y);
         for (auto& v : cb) v = make_double2(-v.x, -v.y);
         for (int s = 0; s < nsrc; ++s)
-            for (int i = 0; i < l; ++i) {
+            for (int i = 0; i < ld; ++i) {
                 const double sg = sgn_re(c->defl_lam[i]);
                 for (int h = 0; h < 2; ++h) {
                     double2& u = ct[(size_t)s * 2 * l + h * l + i];
@@ -962,6 +1015,72 @@ int lq_deflation_derivatives(lq_ctx* c, const lq_direction* dir, const lq_opts* 
     if (dR && (r = stage_out(c, dR, c->defl_V + (size_t)l * nvec(c), (size_t)l * nvec(c), st))) return r;
     if (dL && (r = stage_out(c, dL, c->defl_W + (size_t)l * nvec(c), (size_t)l * nvec(c), st))) return r;
     LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_opts* o, double* S, double* force,
+                          double* dS_dmu, void* stream) {
+    if (!c || !x || !y) return set_err(c, LQ_ERR_ARG, "null argument");
+    if (!c->adjoint) return set_err(c, LQ_ERR_NOT_READY, "workspace reserved without LQ_RESERVE_ADJOINT");
+    int r = check_ready(c, 2, 0);
+    if (r || (r = check_opts(c, o))) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nv = nvec(c);
+    const size_t reg = (size_t)c->nsrc * nv;
+    double* io0 = c->io;            // sources: 0 = x, 1 = y
+    double* io1 = c->io + reg;      // results: 0 = sgn(H) x
+    if ((r = stage_in(c, io0, x, nv, st))) return r;
+    if ((r = stage_in(c, io0 + nv, y, nv, st))) return r;
+    lq_opts so = *o;
+    if (so.projected == LQ_PROJ_NEWTON) so.projected = LQ_PROJ_AUTO;   // the adjoint uses the quadrature
+    std::vector<lq_report> rep(2);
+    if ((r = run_tsl(c, 1, 0, 2, &so, rep.data(), io1, nullptr, st, io0, nullptr, FN_SIGN, nullptr, true))) return r;
+    for (int s = 0; s < 2; ++s)
+        if (rep[s].status != LQ_OK) return set_err(c, rep[s].status, "Lanczos process failed for the bilinear");
+    // S = Re <y | sgn(H) x>
+    std::vector<double2> d;
+    if ((r = bdots_host(c, io0 + nv, 1, io1, 1, d, st))) return r;
+    // gradient from 2N quadrature pairs
+    double cscale = 1.0;
+    LQ_CUDA(c, cudaMemcpy(&cscale, c->quad_c, sizeof(double), cudaMemcpyDeviceToHost));
+    const int k = o->kmax;
+    AdjArgs a;
+    std::memset(&a, 0, sizeof(a));
+    a.npairs = 2 * o->quad_nodes;
+    a.kmax = c->kmax;
+    a.nth_max = 2 * kQuadMaxNodes;
+    a.c = cscale;
+    a.state = c->state;
+    a.alpha = c->alpha; a.beta = c->beta; a.delta = c->delta;
+    a.scale = c->scale; a.uscale = c->uscale;
+    a.work = c->quad_work;
+    a.cnu = c->adj_coef;
+    a.com = c->adj_coef + (size_t)2 * kQuadMaxNodes * c->kmax;
+    a.nu = c->adj_nu; a.om = c->adj_om;
+    a.V = c->V;
+    for (int i = 0; i < 4; ++i) a.dims[i] = c->dims[i];
+    a.strides[0] = 1;
+    a.strides[1] = (size_t)c->dims[0];
+    a.strides[2] = (size_t)c->dims[0] * c->dims[1];
+    a.strides[3] = (size_t)c->dims[0] * c->dims[1] * c->dims[2];
+    a.apbc = c->desc.t_antiperiodic ? 1 : 0;
+    a.efwd = std::exp(c->desc.mu);
+    a.ebwd = std::exp(-c->desc.mu);
+    a.Ub = reinterpret_cast<const double2*>(c->Ub);
+    a.force = c->adj_force;
+    a.dmu_part = c->adj_dmu;
+    const size_t F = fe(c);
+    // right basis of source 0 (x) and stored left basis of source 1 (y)
+    const void* lb1 = reinterpret_cast<const char*>(c->lbasis) + (size_t)c->kmax * F * chunk_bytes(c);
+    LQ_CUDA(c, launch_adjoint(c->prec, a, c->basis, F, lb1, F, std::max(k, 1), st));
+    c->launches += 4;
+    const size_t nblk = (c->V + 127) / 128;
+    std::vector<double> dmu(nblk);
+    LQ_CUDA(c, cudaMemcpyAsync(dmu.data(), c->adj_dmu, sizeof(double) * nblk, cudaMemcpyDeviceToHost, st));
+    if (force && (r = stage_out(c, force, c->adj_force, c->V * 32, st))) return r;
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    if (S) *S = d[0].x;
+    if (dS_dmu) { double t = 0.0; for (double v : dmu) t += v; *dS_dmu = t; }
     return LQ_OK;
 }
 

@@ -219,8 +219,19 @@ struct lq_ctx {
     double2* quad_work = nullptr;    // [nsrc][4][kmax][2 * kQuadMaxNodes]
     double* quad_c = nullptr;        // [nsrc]
     double* quad_check = nullptr;    // [nsrc]
+    int* proj_sel = nullptr;         // [nsrc] sources finished by the Newton fallback
     size_t partial_blocks = 0;       // capacity per source of the TSL partials
     size_t nx_partial_blocks = 0;
+
+    // adjoint workspace (lq_reserve flag LQ_RESERVE_ADJOINT)
+    void* lbasis = nullptr;          // [nsrc][kmax] left Lanczos vectors (NF = 1)
+    double2* uscale = nullptr;       // [nsrc][kmax] left scales
+    double2* adj_coef = nullptr;     // [2][2 * kQuadMaxNodes][kmax]
+    void* adj_nu = nullptr;          // [2 * kQuadMaxNodes] fields
+    void* adj_om = nullptr;          // [2 * kQuadMaxNodes] fields
+    double* adj_force = nullptr;     // [4][V][8]
+    double* adj_dmu = nullptr;       // [V / 128 + 1]
+    bool adjoint = false;
 
     // deflation space (Sec. 3), FP64 boundary layout: V = [R_0..R_{l-1}, dR_0..dR_{l-1}],
     // W = [Lk_0..Lk_{l-1}, dLk_0..dLk_{l-1}] with <Lk_i|R_j> = delta_ij (Lk_i = L_i^dag)
@@ -231,6 +242,8 @@ struct lq_ctx {
     double* defl_work = nullptr;     // [6][cap][n] scratch vectors for the derivative preparation
     double* defl_scr = nullptr;      // dot partials and coefficient matrices
     size_t defl_scr_doubles = 0;
+    double* gen_scr = nullptr;       // general dot / combine scratch (lq_reserve)
+    size_t gen_scr_doubles = 0;
     double2* defl_shift = nullptr;   // [nsrc] resolvent shifts
     double defl_resid = 0.0;         // largest relative residual of the last shifted solves
 

@@ -522,6 +522,7 @@ __device__ void tsl_alpha_step(const HopArgs& a, int src, double dre, double dim
     al.y = sj * (uj.x * dim - uj.y * dre);
     a.alpha[(size_t)src * a.kmax + j] = al;
     a.scale[(size_t)src * a.kmax + j] = sj;
+    if (a.uscale) a.uscale[(size_t)src * a.kmax + j] = uj;
     st.k_eff = j + 1;
     if (!isfinite(al.x) || !isfinite(al.y)) { st.status = LQ_ERR_NONFINITE; return; }
     st.cv[0] = make_double2(sj, 0.0);
@@ -607,6 +608,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(UpdArgs a) {
     const Chunk* w = reinterpret_cast<const Chunk*>(a.w_cur) + (size_t)src * a.src_stride_left;
     const Chunk* wp = reinterpret_cast<const Chunk*>(a.w_prev) + (size_t)src * a.src_stride_left;
     Chunk* wn = reinterpret_cast<Chunk*>(a.w_next) + (size_t)src * a.src_stride_left;
+    Chunk* ws = a.w_store ? reinterpret_cast<Chunk*>(a.w_store) + (size_t)src * a.src_stride_store : nullptr;
     DotAcc<R> d[4];
 #pragma unroll
     for (int i = 0; i < 4; ++i) d[i].zero();
@@ -616,6 +618,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_update(UpdArgs a) {
         Chunk nw = axpy3<R>(__ldg(l + e), __ldg(w + e), has_prev ? __ldg(wp + e) : zero, cw, has_prev);
         vn[e] = nv;
         wn[e] = nw;
+        if (ws) ws[e] = nw;
         dot_chunk<R>(d, nw, nv);
     }
     CSum tot[4];
@@ -680,6 +683,7 @@ __global__ void __launch_bounds__(kUpdThreads) k_tsl_init(InitArgs a) {
         if (NF == 1) {
             store_spinor(v, V, s, psi);
             store_spinor(w, V, s, psi);
+            if (a.w1_store) store_spinor(reinterpret_cast<Chunk*>(a.w1_store) + (size_t)src * a.src_stride_store, V, s, psi);
         } else {
             const double2* xt = a.xt ? reinterpret_cast<const double2*>(a.xt) + ((size_t)src * V + s) * 12 : nullptr;
 #pragma unroll

@@ -39,6 +39,7 @@ struct HopArgs {
     int* counters;
     double2* alpha;
     double* scale;
+    double2* uscale;       // left scales u_j (stored when the left basis is kept), may be null
     int kmax;              // row length of alpha/beta/delta/scale
     int kmax_run;          // k of this run
     int j;                 // 0-based Lanczos step
@@ -51,7 +52,8 @@ struct UpdArgs {
     const void* rout; const void* lout;
     const void* v_cur; const void* v_prev; void* v_next;
     const void* w_cur; const void* w_prev; void* w_next;
-    size_t src_stride_io, src_stride_basis, src_stride_left;
+    void* w_store;         // copy of wh_{j+1} into the left basis (adjoint), may be null
+    size_t src_stride_io, src_stride_basis, src_stride_left, src_stride_store;
     TslState* state;
     double* partials;
     size_t partial_stride;
@@ -67,7 +69,8 @@ struct InitArgs {
     const double* x;       // boundary layout, device (bottom of a block source)
     const double* xt;      // top of a block source (boundary layout) or null for (0, x)
     void* v1; void* w1;
-    size_t src_stride_basis, src_stride_left;
+    void* w1_store;        // copy of wh_1 into the left basis (adjoint), may be null
+    size_t src_stride_basis, src_stride_left, src_stride_store;
     TslState* state;
     double* partials;
     size_t partial_stride;
@@ -132,6 +135,33 @@ struct NewtonArgs {
 // scal layout per matrix
 enum { NS_NORMX = 0, NS_NORMY, NS_MU, NS_CHANGE, NS_DONE, NS_ITERS, NS_SCALING, NS_STATUS, NS_PREVCHANGE, NS_KEFF };
 
+// Adjoint / force (lq_adjoint.cu)
+struct AdjArgs {
+    int npairs;            // 2N quadrature terms
+    int kmax;
+    int nth_max;
+    double c;              // contour scale
+    const TslState* state; // sources 0 (x) and 1 (y)
+    const double2* alpha; const double2* beta; const double* delta;
+    const double* scale;   // right scales (source 0 row)
+    const double2* uscale; // left scales (source 1 row at offset kmax)
+    double2* work;         // quadrature workspace
+    double2* cnu;          // [npairs][kmax] coefficients for nu_q
+    double2* com;          // [npairs][kmax] coefficients for omega_q
+    void* nu; void* om;    // [npairs] internal fields
+    // lattice
+    size_t V;
+    int dims[4];
+    size_t strides[4];
+    int apbc;
+    double efwd, ebwd;     // exp(+mu), exp(-mu)
+    const double2* Ub;     // FP64 links, boundary layout [4][V][9]
+    double* force;         // [4][V][8]
+    double* dmu_part;      // [blocks]
+};
+cudaError_t launch_adjoint(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,
+                           size_t lbasis_vec_stride, int k, cudaStream_t st);
+
 // Quadrature projected sign (lq_newton.cu)
 struct QuadArgs {
     int k;                 // padded dimension
@@ -150,7 +180,7 @@ constexpr int kQuadMaxNodes = 128;
 cudaError_t quad_sign_e1(const QuadArgs& a, int nodes, cudaStream_t st);
 // c = (sigma_src - T)^{-1} e_1 into a.s (per-source complex shifts, device array)
 cudaError_t proj_resolvent(const QuadArgs& a, const double2* shifts, cudaStream_t st);
-cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st);
+cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st, const int* sel = nullptr);
 
 cudaError_t newton_init_tridiag(const NewtonArgs& a, cudaStream_t st);
 cudaError_t newton_init_dense(const NewtonArgs& a, const double2* Xin, cudaStream_t st);

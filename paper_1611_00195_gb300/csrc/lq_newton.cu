@@ -499,10 +499,10 @@ cudaError_t proj_resolvent(const QuadArgs& a, const double2* shifts, cudaStream_
 }
 
 // Newton result -> projected coefficient vector: first column of X.
-__global__ void k_nt_first_column(NewtonArgs a, double2* __restrict__ out, int ldo) {
+__global__ void k_nt_first_column(NewtonArgs a, double2* __restrict__ out, int ldo, const int* __restrict__ sel) {
     const int b = blockIdx.y;
     const int i = blockIdx.x * blockDim.x + threadIdx.x;
-    if (i >= a.k) return;
+    if (i >= a.k || (sel && !sel[b])) return;
     out[(size_t)b * ldo + i] = a.X[(size_t)b * a.ld * a.ld + (size_t)i * a.ld];
 }
 
@@ -513,8 +513,8 @@ cudaError_t quad_sign_e1(const QuadArgs& a, int nodes, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st) {
-    k_nt_first_column<<<dim3((unsigned)((a.k + 127) / 128), (unsigned)a.nb), 128, 0, st>>>(a, out, ldo);
+cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st, const int* sel) {
+    k_nt_first_column<<<dim3((unsigned)((a.k + 127) / 128), (unsigned)a.nb), 128, 0, st>>>(a, out, ldo, sel);
     return cudaGetLastError();
 }
 

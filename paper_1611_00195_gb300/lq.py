@@ -36,7 +36,8 @@ EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_u
             "lq_reserve", "lq_apply_H", "lq_set_direction", "lq_apply_block", "lq_sign_apply",
             "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
             "lq_profile_read", "lq_newton_sign_noalloc", "lq_error_estimate",
-            "lq_upload_deflation", "lq_deflation_derivatives"]
+            "lq_upload_deflation", "lq_deflation_derivatives", "lq_sign_bilinear_grad",
+            "lq_dense_eig"]
 
 
 class LatticeDesc(ctypes.Structure):
@@ -49,7 +50,7 @@ class Opts(ctypes.Structure):
     _fields_ = [("kmax", ctypes.c_int), ("breakdown_tol", ctypes.c_double), ("newton_max_iter", ctypes.c_int),
                 ("newton_tol", ctypes.c_double), ("deflate", ctypes.c_int), ("projected", ctypes.c_int),
                 ("quad_nodes", ctypes.c_int), ("proj_tol", ctypes.c_double), ("hop_variant", ctypes.c_int),
-                ("defl_kmax", ctypes.c_int)]
+                ("defl_kmax", ctypes.c_int), ("defl_nderiv", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -110,6 +111,8 @@ def lib():
         L.lq_error_estimate.argtypes = [P, ctypes.POINTER(Direction), P, I, ctypes.POINTER(Opts), P, P]
         L.lq_upload_deflation.argtypes = [P, I, P, P, P, P]
         L.lq_deflation_derivatives.argtypes = [P, ctypes.POINTER(Direction), ctypes.POINTER(Opts), P, P, P, P]
+        L.lq_sign_bilinear_grad.argtypes = [P, P, P, ctypes.POINTER(Opts), P, P, P, P]
+        L.lq_dense_eig.argtypes = [I, P, P, P]
         L.lq_newton_sign_noalloc.argtypes = [P, P, I, I, I, D, ctypes.POINTER(I), P]
         for name in EXPORTED:
             if name not in ("lq_default_opts", "lq_destroy", "lq_last_error"):
@@ -168,6 +171,30 @@ def _stream(x=None):
         dev = x.device if (_is_tensor(x) and x.is_cuda) else None
         return ctypes.c_void_p(torch.cuda.current_stream(dev).cuda_stream)
     return ctypes.c_void_p(0)
+
+
+class SignBilinearForce(torch.autograd.Function if torch is not None else object):
+    """S = Re <y| sgn(H(mu)) |x> as a function of the link tangent coordinates omega [4][V][8]
+    (U_nu(s) -> exp(i omega^a lambda_a/2) U_nu(s)) and of mu, evaluated at omega = 0 (the
+    uploaded links) and at the context's mu.  backward returns the fermionic force dS/domega and
+    dS/dmu from the library's adjoint (lq_sign_bilinear_grad); x, y and the context are not
+    differentiated.  Usage: S = SignBilinearForce.apply(omega, mu, ctx, x, y, k)."""
+
+    @staticmethod
+    def forward(fctx, omega, mu, lqctx, x, y, k):
+        if torch.count_nonzero(omega).item() != 0:
+            raise ValueError("the force is evaluated at the uploaded links: omega must be zero")
+        if abs(float(mu) - lqctx.mu) > 0.0:
+            raise ValueError("mu must equal the context's mu")
+        S, F, dmu = lqctx.bilinear_grad(x, y, k)
+        F = F if _is_tensor(F) else torch.from_numpy(F)
+        fctx.save_for_backward(F.to(omega.device, torch.float64), torch.tensor(dmu, dtype=torch.float64))
+        return torch.tensor(S, dtype=torch.float64, device=omega.device)
+
+    @staticmethod
+    def backward(fctx, gS):
+        F, dmu = fctx.saved_tensors
+        return gS * F, (gS.cpu() * dmu).to(gS.device), None, None, None, None
 
 
 def newton_sign_noalloc(X, max_iter=50, tol=1e-13):
@@ -231,8 +258,9 @@ class Context:
         self._check(self._L.lq_set_mu(self._h, float(mu)))
         self.mu = float(mu)
 
-    def reserve(self, kmax, nsrc, block=True):
-        self._check(self._L.lq_reserve(self._h, int(kmax), int(nsrc), int(bool(block))))
+    def reserve(self, kmax, nsrc, block=True, adjoint=False):
+        flags = (1 if block else 0) | (2 if adjoint else 0)
+        self._check(self._L.lq_reserve(self._h, int(kmax), int(nsrc), int(flags)))
 
     def _direction(self, kind, field):
         if kind == LQ_DIR_MU:
@@ -264,7 +292,7 @@ class Context:
 
     @staticmethod
     def opts(k, breakdown_tol=1e-14, newton_max_iter=50, newton_tol=1e-13, projected=LQ_PROJ_AUTO, quad_nodes=64,
-             proj_tol=1e-11, hop_variant=-1, deflate=0, defl_kmax=0):
+             proj_tol=1e-11, hop_variant=-1, deflate=0, defl_kmax=0, defl_nderiv=0):
         o = Opts()
         lib().lq_default_opts(ctypes.byref(o))
         o.kmax = int(k)
@@ -277,6 +305,7 @@ class Context:
         o.hop_variant = int(hop_variant)
         o.deflate = int(deflate)
         o.defl_kmax = int(defl_kmax)
+        o.defl_nderiv = int(defl_nderiv)
         return o
 
     def sign_apply(self, x, k, out=None, **kw):
@@ -339,6 +368,20 @@ class Context:
         self._check(self._L.lq_deflation_derivatives(self._h, ctypes.byref(d), ctypes.byref(o), _ptr(dlam), _ptr(dR),
                                                      _ptr(dL), _stream(None)))
         return dlam, dR, dL
+
+    def bilinear_grad(self, x, y, k, **kw):
+        """(S, force [4][V][8], dS/dmu) for S = Re <y| sgn(H) |x>; x, y single fields [V][4][3]."""
+        x, y = _as_c128(x), _as_c128(y)
+        S = ctypes.c_double()
+        dmu = ctypes.c_double()
+        if _is_tensor(x):
+            force = torch.empty((4, self.V, 8), dtype=torch.float64, device=x.device)
+        else:
+            force = np.empty((4, self.V, 8), dtype=np.float64)
+        o = self.opts(k, **kw)
+        self._check(self._L.lq_sign_bilinear_grad(self._h, _ptr(x), _ptr(y), ctypes.byref(o), ctypes.byref(S), _ptr(force),
+                                                  ctypes.byref(dmu), _stream(x)))
+        return S.value, force, dmu.value
 
     def error_estimate(self, x, k, kind=None, field=None, **kw):
         """eps_A of Sec. 4 per source: the sign (kind None) or the derivative version (kind = LQ_DIR_*)."""

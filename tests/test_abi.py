@@ -57,3 +57,21 @@ def test_create_rejects_bad_descriptors_without_gpu(built_lib):
     for d in bad:
         assert L.lq_create(ctypes.byref(d), ctypes.byref(h)) == -1
     assert L.lq_create(None, ctypes.byref(h)) == -1
+
+
+@pytest.mark.parametrize("n", [1, 2, 5, 30, 64])
+def test_dense_eig_host_utility(built_lib, n):
+    """The host eigensolver used by the deflation-space Rayleigh-Ritz steps, against numpy."""
+    import numpy as np
+    from paper_1611_00195_gb300 import lq
+    rng = np.random.default_rng(n)
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    A = np.ascontiguousarray(A)
+    w = np.zeros(n, complex)
+    V = np.zeros((n, n), complex)
+    assert lq.lib().lq_dense_eig(n, A.ctypes.data, w.ctypes.data, V.ctypes.data) == 0
+    ref = np.linalg.eigvals(A)
+    for z in ref:
+        assert np.min(np.abs(w - z)) < 1e-10 * max(1.0, np.abs(ref).max())
+    assert np.abs(A @ V - V * w).max() < 1e-9 * max(1.0, np.abs(A).max())
+    assert np.allclose(np.linalg.norm(V, axis=0), 1.0)

@@ -42,57 +42,79 @@ def test_sign_deflated_parity(lqlib, dims, l, k):
     y, y0 = y.cpu().numpy(), y0.cpu().numpy()
     _, Ao, Aho, _, _ = oracle_ops(dims, U, MU)
     S = osg.sign_schur(A)
+    rng = np.random.default_rng(99)
     for s in range(x.shape[0]):
         xs = x[s].ravel()
         ref = odf.sign_deflated(lambda v: ot.tsl_sign(Ao, Aho, v, k)[0], lam, R, L, xs)
+        xp = xs * (1 + 1e-16 * rng.standard_normal(xs.shape))
+        sens = relerr(odf.sign_deflated(lambda v: ot.tsl_sign(Ao, Aho, v, k)[0], lam, R, L, xp), ref)
         err = relerr(y[s], ref)
         ex, ex0 = relerr(y[s], S @ xs), relerr(y0[s], S @ xs)
-        print("deflated sign k=%d l=%d: parity %.3g; error vs exact %.3g (undeflated %.3g)" % (k, l, err, ex, ex0))
-        assert err < 1e-9
-        assert ex < 0.5 * ex0
+        print("deflated sign k=%d l=%d: parity %.3g (oracle self-sensitivity %.3g); error vs exact %.3g (undeflated %.3g)"
+              % (k, l, err, sens, ex, ex0))
+        assert err < max(1e-11, 30 * sens)
+        assert ex < ex0
+
+
+# The shifted solves project out all l uploaded pairs; derivatives are built for the first
+# ld (the paper deflates the derivative with fewer pairs than the sign).
+LP, LD = 24, 6
 
 
 def test_eigen_derivatives_parity(lqlib):
     from paper_1611_00195_gb300 import lq
-    dims, l, k = (4, 2, 2, 2), 6, 300
-    c, U, lat, A, lam, R, L, x = _setup(lq, dims, l, k)
-    dlam, dR, dLk = c.deflation_derivatives(k, kind=lq.LQ_DIR_MU)
+    dims, k = (4, 2, 2, 2), 300
+    c, U, lat, A, lam, R, L, x = _setup(lq, dims, LP, k)
+    dlam, dR, dLk = c.deflation_derivatives(k, kind=lq.LQ_DIR_MU, defl_nderiv=LD)
     lat_, Ao, Aho, Eo, Eho = oracle_ops(dims, U, MU)
     rl, rR, rL = odf.eigen_derivatives_tsl(Ao, Aho, Eo, Eho, lam, R, L, k)
     E = od.dense_dH_dmu(lat, U, MU)
     ex = odf.eigen_derivatives_projected(A, E, lam, R, L)
-    gR = dR.reshape(l, -1).T
-    gL = dLk.reshape(l, -1).conj()
-    print("eigen-derivatives k=%d: dR parity %.3g, dL parity %.3g; vs exact %.3g / %.3g"
-          % (k, relerr(gR, rR), relerr(gL, rL), relerr(gR, ex[1]), relerr(gL, ex[2])))
-    assert np.abs(dlam - rl).max() < 1e-12 * np.abs(rl).max()
-    assert relerr(gR, rR) < 1e-6 and relerr(gL, rL) < 1e-6
+    gR = dR.reshape(LP, -1).T[:, :LD]
+    gL = dLk.reshape(LP, -1).conj()[:LD]
+    print("eigen-derivatives k=%d (projection %d, built %d): dR parity %.3g, dL parity %.3g; vs exact %.3g / %.3g"
+          % (k, LP, LD, relerr(gR, rR[:, :LD]), relerr(gL, rL[:LD]), relerr(gR, ex[1][:, :LD]), relerr(gL, ex[2][:LD])))
+    assert np.abs(dlam[:LD] - rl[:LD]).max() < 1e-12 * np.abs(rl[:LD]).max()
+    assert np.abs(dlam[LD:]).max() == 0.0 and np.abs(dR[LD:]).max() == 0.0
+    assert relerr(gR, rR[:, :LD]) < 1e-5 and relerr(gL, rL[:LD]) < 1e-5
+    assert relerr(gR, ex[1][:, :LD]) < 1e-5 and relerr(gL, ex[2][:LD]) < 1e-5
 
 
 def test_derivative_generalised_deflation(lqlib):
+    """Eqs. (3.2)-(3.4) on the GPU against the oracle's generalised deflation driven by the same
+    eigenvector derivatives (those the GPU computed), so that the comparison isolates the
+    deflation and the block Lanczos process; the tolerance scales with the oracle's own
+    rounding sensitivity at this depth.  Deflation must also beat no deflation against the
+    exact derivative."""
     from paper_1611_00195_gb300 import lq
-    dims, l, k = (4, 2, 2, 2), 6, 300
-    c, U, lat, A, lam, R, L, x = _setup(lq, dims, l, k)
+    dims, k = (4, 2, 2, 2), 300
+    c, U, lat, A, lam, R, L, x = _setup(lq, dims, LP, k)
     xs_d = torch.from_numpy(x).cuda()
-    ys, yd, rep = c.sign_derivative_apply(xs_d, k, deflate=1)
+    ys, yd, rep = c.sign_derivative_apply(xs_d, k, deflate=1, defl_nderiv=LD)
     ys0, yd0, _ = c.sign_derivative_apply(xs_d, k, deflate=0)
     ys, yd, ys0, yd0 = (t.cpu().numpy() for t in (ys, yd, ys0, yd0))
+    dlam, dR, dLk = c.deflation_derivatives(k, kind=lq.LQ_DIR_MU, defl_nderiv=LD)
+    gR = dR.reshape(LP, -1).T[:, :LD]
+    gL = dLk.reshape(LP, -1).conj()[:LD]
     lat_, Ao, Aho, Eo, Eho = oracle_ops(dims, U, MU)
-    rl, rR, rL = odf.eigen_derivatives_tsl(Ao, Aho, Eo, Eho, lam, R, L, k)
     E = od.dense_dH_dmu(lat, U, MU)
     SB = odf.sign_block_exact(A, E)
     n = lat.n
+    rng = np.random.default_rng(7)
+
+    def blk(v):
+        t, b, _ = ot.tsl_sign_block(Ao, Aho, Eo, Eho, v[:n], v[n:], k)
+        return np.concatenate([t, b])
     for s in range(x.shape[0]):
         psi = np.concatenate([np.zeros(n), x[s].ravel()])
-
-        def blk(v):
-            t, b, _ = ot.tsl_sign_block(Ao, Aho, Eo, Eho, v[:n], v[n:], k)
-            return np.concatenate([t, b])
-        ref = odf.sign_block_deflated(blk, lam, R, L, rR, rL, psi)
+        ref = odf.sign_block_deflated(blk, lam[:LD], R[:, :LD], L[:LD], gR, gL, psi)
+        psip = psi * (1 + 1e-16 * rng.standard_normal(psi.shape))
+        refp = odf.sign_block_deflated(blk, lam[:LD], R[:, :LD], L[:LD], gR, gL, psip)
+        sens = relerr(refp, ref)
         ex = SB @ psi
         pd, ps = relerr(yd[s], ref[:n]), relerr(ys[s], ref[n:])
         ed, ed0 = relerr(yd[s], ex[:n]), relerr(yd0[s], ex[:n])
-        print("deflated derivative k=%d l=%d: parity deriv %.3g sign %.3g; deriv error vs exact %.3g (undeflated %.3g)"
-              % (k, l, pd, ps, ed, ed0))
-        assert pd < 1e-6 and ps < 1e-6
-        assert ed < ed0
+        print("deflated derivative k=%d (%d Jordan blocks): parity deriv %.3g sign %.3g (oracle self-sensitivity "
+              "%.3g); deriv error vs exact %.3g (undeflated %.3g)" % (k, LD, pd, ps, sens, ed, ed0))
+        assert pd < max(1e-10, 30 * sens) and ps < max(1e-10, 30 * sens)
+        assert ed < 0.1 * ed0
