@@ -53,6 +53,10 @@ def parse():
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
+    p.add_argument("--no-deflation", action="store_true", help="skip the deflated run")
+    p.add_argument("--nev", type=int, default=20, help="eigenpairs of the deflation space")
+    p.add_argument("--nderiv", type=int, default=6, help="Jordan blocks of the derivative deflation")
+    p.add_argument("--eig-iter", type=int, default=20, help="eigensolver iterations for the deflation space")
     return p.parse_args()
 
 
@@ -361,6 +365,55 @@ def main():
                 "rel_err_mixed_vs_fp64_deriv": {"max": float(ed.max()), "median": float(np.median(ed))}}
         del ctx64
 
+    # accuracy: eps_A of Sec. 4 (sign and derivative) on two of the sources, no deflation
+    x2 = xd[:2].contiguous()
+    eps_sign = c_eps = None
+    try:
+        eps_sign = ctx.error_estimate(x2, k).tolist()
+        c_eps = ctx.error_estimate(x2, k, kind=lq.LQ_DIR_MU).tolist()
+    except Exception as e:  # report, do not fail the benchmark
+        eps_sign = c_eps = "failed: %s" % e
+
+    # deflated run: the library's eigensolver, then solves with the generalised deflation
+    defl = None
+    if not args.no_deflation:
+        X0 = torch.from_numpy(syn.gaussian_source(DIMS, 777, nsrc=args.nev + 12)).to(dev)
+        torch.cuda.synchronize(dev)
+        t0 = time.perf_counter()
+        lam, res = ctx.compute_deflation(args.nev, X0, nsub=args.nev + 12, max_iter=args.eig_iter)
+        t_eig = time.perf_counter() - t0
+        defl = {"nev": args.nev, "jordan_blocks_derivative": args.nderiv, "eigensolver_s": t_eig,
+                "eigensolver_iterations": args.eig_iter, "eigensolver_max_residual": float(np.max(res)),
+                "smallest_abs_lambda": float(np.abs(lam).min()), "largest_deflated_abs_lambda": float(np.abs(lam).max()),
+                "arg_lambda_range": [float(np.angle(lam).min()), float(np.angle(lam).max())]}
+        if float(np.max(res)) > 1e-8:
+            # the generalised deflation of the derivative needs eigenpairs accurate to about
+            # FP64 rounding; a space that did not converge would only corrupt the solve
+            defl["skipped"] = ("eigensolver did not converge (max residual %.2g > 1e-8): the smallest eigenvalues "
+                               "of H(mu) lie at all phases around zero, where a polynomial filter cannot "
+                               "separate them" % float(np.max(res)))
+        else:
+            ctx.sign_derivative_apply(xd, k, deflate=1, defl_nderiv=args.nderiv, out=(ys, yd))
+            torch.cuda.synchronize(dev)
+            a0, b0 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            a0.record(stream)
+            ctx.sign_derivative_apply(xd, k, deflate=1, defl_nderiv=args.nderiv, out=(ys, yd))
+            b0.record(stream)
+            torch.cuda.synchronize(dev)
+            msd = a0.elapsed_time(b0)
+
+            def eps_deflated(xs):
+                o = dict(deflate=1, defl_nderiv=args.nderiv)
+                s1, d1, _ = ctx.sign_derivative_apply(xs, k, **o)
+                s2, d2, _ = ctx.sign_derivative_apply(s1, k, **o)
+                sd, _ = ctx.sign_apply(d1, k, deflate=1)
+                top = (sd + d2).reshape(xs.shape[0], -1)
+                bot = (s2 - xs).reshape(xs.shape[0], -1)
+                num = torch.sqrt(torch.linalg.vector_norm(top, dim=1) ** 2 + torch.linalg.vector_norm(bot, dim=1) ** 2)
+                return (num / (2 * torch.linalg.vector_norm(xs.reshape(xs.shape[0], -1), dim=1))).cpu().tolist()
+            defl.update({"value": nsrc / (msd / 1e3), "unit": "solves/s", "ms_per_step": msd,
+                         "eps_A_deriv": eps_deflated(x2)})
+
     cpu = None
     if not args.no_cpu and rank == 0:
         per_solve, desc = cpu_baseline(8, k)
@@ -391,10 +444,15 @@ def main():
         "gpu_launches": int(prof["launches"]),
         "clocks": clocks,
         "fp64_path": fp64,
+        "accuracy": {"eps_A_sign": eps_sign, "eps_A_deriv": c_eps,
+                     "note": "eps_A = ||sgn(A)^2 psi - psi|| / (2 ||psi||) (Sec. 4) on 2 of the sources, k as configured"},
+        "deflated": defl,
         "time_breakdown_ms_per_step": {"stencil": prof["hop_ms"] / args.steps, "update": prof["update_ms"] / args.steps,
-                                       "newton": prof["newton_ms"] / args.steps, "other": prof["other_ms"] / args.steps,
+                                       "projected_sign": prof["newton_ms"] / args.steps, "other": prof["other_ms"] / args.steps,
                                        "sum_of_kernels": total_prof / args.steps},
         "newton_iterations_per_step": prof["newton_iterations"] / args.steps,
+        "projected_solver_counts": {"quadrature": sum(1 for r in reps if r["projected"] == lq.LQ_PROJ_QUAD),
+                                    "newton": sum(1 for r in reps if r["projected"] == lq.LQ_PROJ_NEWTON)} if reps else None,
         "report_source0": reps[0] if reps else None,
     }
     print(json.dumps(line))

@@ -87,7 +87,8 @@ typedef struct {
     double proj_tol;       /* accept the quadrature when ||Q(T)Q(T)e_1 - e_1|| <= proj_tol
                               (default 1e-11)                                                   */
     int hop_variant;       /* stencil schedule: -1 = autotuned on first use (default), 0 = one
-                              thread per (site, side), 1 = one thread per (site, output field) */
+                              thread per (site, side), 1 = one thread per (site, output field),
+                              2 / 3 = as 0 with at least 5 / 6 resident blocks per SM (FP32) */
     int defl_kmax;         /* depth of the shifted solves for the eigenvector derivatives of the
                               generalised deflation (0 = the reserved kmax)                    */
     int defl_nderiv;       /* Jordan blocks of the derivative deflation: the first defl_nderiv
@@ -100,8 +101,9 @@ typedef struct {
  *  LQ_PROJ_NEWTON  scaled Newton iteration on the dense k x k matrix (FP64, O(k^3));
  *  LQ_PROJ_QUAD    midpoint quadrature of sgn(T) = (2/pi) T int_0^inf (t^2 + T^2)^{-1} dt
  *                  with t = c tan(theta): 2N complex tridiagonal solves (FP64, O(N k));
- *  LQ_PROJ_AUTO    the quadrature, accepted only if its involution residual
- *                  ||Q(T) Q(T) e_1 - e_1|| <= proj_tol (retried with 2N nodes), else Newton. */
+ *  LQ_PROJ_AUTO    the quadrature, accepted per source only if its involution residual
+ *                  ||Q(T) Q(T) e_1 - e_1|| <= proj_tol; a failing source is retried with
+ *                  twice the nodes, up to 512, and only what still fails goes to Newton.  */
 #define LQ_PROJ_AUTO    0
 #define LQ_PROJ_NEWTON  1
 #define LQ_PROJ_QUAD    2
@@ -185,6 +187,32 @@ int  lq_sign_derivative_apply(lq_ctx* ctx, const lq_direction* dir, const double
  * follow lq_reserve; the library's own Arnoldi is not part of this version. */
 int  lq_upload_deflation(lq_ctx* ctx, int l, const double* lambda, const double* R, const double* L,
                          void* stream);
+
+/* Options of lq_compute_deflation. */
+typedef struct {
+    int nev;          /* eigenpairs wanted: the nev eigenvalues of H(mu) closest to zero          */
+    int nsub;         /* subspace size (>= nev + 2; default min(nev + 12, 64))                   */
+    int degree;       /* Chebyshev filter degree in H^2 (default 40)                              */
+    int max_iter;     /* filtered subspace iterations (default 60)                                */
+    double tol;       /* stop when ||H r - lambda r|| <= tol * |H|_est for the nev pairs
+                         (default 1e-10; the stencil of the eigensolver is FP64 in both precisions) */
+} lq_eig_opts;
+
+/* Compute and install the deflation space of Sec. 3 with the library's own eigensolver (the
+ * paper uses ARPACK's Arnoldi): the nev right eigenpairs of H(mu) closest to zero and the
+ * matching left eigenvectors (from H(mu)^dag = H(-mu)), biorthonormalised so that
+ * <Lk_i|R_j> = delta_ij.  Method: Chebyshev-filtered subspace iteration on H^2 (the wanted
+ * eigenvalues are the smallest of H^2; the filter damps [a^2, b^2] with b^2 from a power
+ * iteration and a^2 the largest Ritz value of the current subspace), each step closed by a
+ * Rayleigh-Ritz projection (lq_dense_eig).  X0: nsub start fields (host or device, spinor layout
+ * double[nsub][V][4][3][2]; random numbers are the caller's).  lambda, resid: host outputs
+ * double[nev][2] and double[nev] (may be NULL); resid is the larger of the right and left
+ * relative residuals.  The operator applications run in FP64 whatever the context's precision
+ * (a mixed-precision context converts its FP64 copy of the links for the call): the generalised
+ * deflation of the derivative needs eigenpairs accurate to FP64 rounding.  Allocates its own
+ * temporary workspace (a set-up call).  Synchronises. */
+int  lq_compute_deflation(lq_ctx* ctx, const lq_eig_opts* eo, const double* X0, double* lambda,
+                          double* resid, void* stream);
 
 /* The derivatives of the uploaded eigenpairs along `dir` (end of Sec. 3), as used by the
  * generalised deflation: dlambda_i = L_i E R_i; dR_j = sum_{i != j} R_i (L_i E R_j)/(lambda_j -

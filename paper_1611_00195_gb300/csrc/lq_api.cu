@@ -1,15 +1,19 @@
 // Host implementation of the C ABI declared in include/lq.h.
 #include <cuda_runtime.h>
 
+#include <algorithm>
 #include <cmath>
 #include <cstdio>
+#include <complex>
 #include <cstring>
+#include <numeric>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "lq_internal.cuh"
 #include "lq_launch.h"
+#include "lq_dense.h"
 
 using namespace lq;
 
@@ -216,7 +220,7 @@ void free_workspace(lq_ctx* c) {
                    (void**)&c->state, (void**)&c->alpha, (void**)&c->beta, (void**)&c->delta, (void**)&c->scale,
                    (void**)&c->nx_X, (void**)&c->nx_Y, (void**)&c->nx_F, (void**)&c->nx_perm, (void**)&c->nx_scal,
                    (void**)&c->nx_partials, (void**)&c->nx_counters, (void**)&c->proj_c, (void**)&c->quad_q,
-                   (void**)&c->quad_work, (void**)&c->quad_c, (void**)&c->quad_check, (void**)&c->proj_sel,
+                   (void**)&c->quad_work, (void**)&c->quad_c, (void**)&c->quad_check, (void**)&c->quad_nodes, (void**)&c->proj_sel,
                    &c->lbasis, (void**)&c->uscale, (void**)&c->adj_coef, &c->adj_nu, &c->adj_om,
                    (void**)&c->adj_force, (void**)&c->adj_dmu, (void**)&c->gen_scr};
     for (void** p : ps) { dfree(*p); *p = nullptr; }
@@ -229,6 +233,7 @@ void free_workspace(lq_ctx* c) {
 // one for this context and batch size.
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
+    const int nvar = (c->prec == LQ_FP64) ? 2 : 4;
     if (c->tuned_nsrc != h.nsrc) {
         for (auto& row : c->tuned_variant) for (int& v : row) v = -1;
         c->tuned_nsrc = h.nsrc;
@@ -241,7 +246,7 @@ int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* vari
     LQ_CUDA(c, cudaEventCreate(&e1));
     float best = 1e30f;
     int bestv = 0;
-    for (int v = 0; v <= 1; ++v) {
+    for (int v = 0; v < nvar; ++v) {
         h.variant = v;
         LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, false, st));   // warm-up
         LQ_CUDA(c, cudaEventRecord(e0, st));
@@ -361,20 +366,30 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
         std::memset(&qa, 0, sizeof(qa));
         qa.k = k; qa.nb = nsrc; qa.kmax = c->kmax; qa.nth_max = 2 * kQuadMaxNodes; qa.state = c->state;
         qa.alpha = c->alpha; qa.beta = c->beta; qa.delta = c->delta; qa.c = c->quad_c; qa.work = c->quad_work;
-        qa.s = c->proj_c; qa.q = c->quad_q; qa.check = c->quad_check;
-        int nodes = o->quad_nodes;
+        qa.s = c->proj_c; qa.q = c->quad_q; qa.check = c->quad_check; qa.nodes = c->quad_nodes;
+        // LQ_PROJ_QUAD: one pass with opts.quad_nodes.  LQ_PROJ_AUTO: a source whose involution
+        // residual exceeds proj_tol is retried with twice the nodes (up to kQuadRetryMaxNodes),
+        // the others keep their result; what still fails goes to the Newton iteration below.
+        std::vector<int> nodes(nsrc, o->quad_nodes);
         bool ok = false;
-        for (int attempt = 0; attempt < 2; ++attempt) {
+        for (int attempt = 0;; ++attempt) {
+            LQ_CUDA(c, cudaMemcpyAsync(c->quad_nodes, nodes.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
             cudaEvent_t eq = prof_begin(c, st);
-            LQ_CUDA(c, quad_sign_e1(qa, nodes, st));
+            LQ_CUDA(c, quad_sign_e1(qa, attempt == 0, st));
             prof_end(c, PC_NEWTON, eq, st, 0);
-            c->launches += 3;
+            c->launches += attempt == 0 ? 3 : 2;
             LQ_CUDA(c, cudaMemcpyAsync(check.data(), c->quad_check, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
-            LQ_CUDA(c, cudaStreamSynchronize(st));
+            LQ_CUDA(c, cudaStreamSynchronize(st));   // nodes and check are host memory
             ok = true;
-            for (int s = 0; s < nsrc; ++s) ok = ok && std::isfinite(check[s]) && check[s] <= o->proj_tol;
-            if (ok || o->projected == LQ_PROJ_QUAD || nodes * 2 > kQuadMaxNodes) break;
-            nodes *= 2;   // one retry with twice the nodes
+            bool retry = false;
+            for (int s = 0; s < nsrc; ++s) {
+                const bool pass = std::isfinite(check[s]) && check[s] <= o->proj_tol;
+                ok = ok && pass;
+                if (pass || nodes[s] == 0) { nodes[s] = 0; continue; }
+                if (o->projected == LQ_PROJ_AUTO && 2 * nodes[s] <= kQuadRetryMaxNodes) { nodes[s] *= 2; retry = true; }
+                else nodes[s] = 0;
+            }
+            if (ok || !retry) break;
         }
         need_newton = !ok && o->projected == LQ_PROJ_AUTO;
         for (int s = 0; s < nsrc; ++s) used[s] = LQ_PROJ_QUAD;
@@ -441,7 +456,7 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->projected < LQ_PROJ_AUTO || o->projected > LQ_PROJ_QUAD) return set_err(c, LQ_ERR_ARG, "unknown projected-sign solver");
     if (o->projected != LQ_PROJ_NEWTON && (o->quad_nodes < 1 || o->quad_nodes > kQuadMaxNodes || !(o->proj_tol > 0.0)))
         return set_err(c, LQ_ERR_ARG, "quad_nodes must be in [1, 128] and proj_tol > 0");
-    if (o->hop_variant < -1 || o->hop_variant > 1) return set_err(c, LQ_ERR_ARG, "hop_variant must be -1, 0 or 1");
+    if (o->hop_variant < -1 || o->hop_variant > 3) return set_err(c, LQ_ERR_ARG, "hop_variant must be in [-1, 3]");
     if (o->defl_kmax < 0 || o->defl_kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "defl_kmax must be in [0, reserved kmax]");
     if (o->defl_nderiv < 0) return set_err(c, LQ_ERR_ARG, "defl_nderiv must be >= 0");
     return LQ_OK;
@@ -620,6 +635,162 @@ int prepare_deflation_derivative(lq_ctx* c, const lq_opts* o, cudaStream_t st) {
     }
     return LQ_OK;
 }
+// ---- deflation-space eigensolver --------------------------------------------------------------
+using cplx = std::complex<double>;
+
+// out_b = H x_b (dagger = 0) or H^dag x_b for `count` boundary FP64 vectors on the device, with
+// the stencil in precision `prec` on the internal links `links` (the eigensolver always passes
+// FP64: the deflation space must be accurate whatever precision the Lanczos path runs in).
+int apply_H_batch(lq_ctx* c, const double* in, double* out, int count, int dagger, cudaStream_t st,
+                  int prec, const void* links) {
+    const size_t fb_ctx = fb(c);
+    const size_t fb_op = prec == LQ_FP64 ? field_bytes<double>(c->V) : field_bytes<float>(c->V);
+    const int cap = std::max(1, (int)((size_t)c->nsrc * (c->block ? 2 : 1) * fb_ctx / fb_op));
+    const size_t nv = nvec(c);
+    const size_t fe_op = prec == LQ_FP64 ? field_elems<double>(c->V) : field_elems<float>(c->V);
+    for (int b0 = 0; b0 < count; b0 += cap) {
+        const int nb = std::min(cap, count - b0);
+        LQ_CUDA(c, launch_to_internal(prec, in + (size_t)b0 * nv, c->rout, c->V, nb, st));
+        HopArgs a = base_hop(c);
+        a.U = links;
+        a.nsrc = nb;
+        a.nsides = 1;
+        a.side0 = 0;
+        set_side(a, 0, c, dagger ? 1 : 0, 0);
+        a.in[0] = c->rout;
+        a.out[0] = c->lout;
+        a.src_stride_in[0] = fe_op;
+        a.src_stride_out[0] = fe_op;
+        LQ_CUDA(c, launch_hop(prec, a, 1, 0, false, st));
+        LQ_CUDA(c, launch_to_boundary(prec, c->lout, out + (size_t)b0 * nv, c->V, nb, st));
+        c->launches += 3;
+    }
+    return LQ_OK;
+}
+
+// X <- X L^{-H} with G = X^H X = L L^H (Cholesky QR), twice for stability.  tmp: m vectors.
+int orthonormalise(lq_ctx* c, double* X, double* tmp, int m, cudaStream_t st) {
+    const size_t nv = nvec(c);
+    for (int pass = 0; pass < 2; ++pass) {
+        std::vector<double2> G;
+        int r;
+        if ((r = bdots_host(c, X, m, X, m, G, st))) return r;
+        std::vector<cplx> L(m * m);
+        for (int i = 0; i < m * m; ++i) L[i] = cplx(G[i].x, G[i].y);
+        // G[a*m+b] = <X_a|X_b>; Cholesky of the Hermitian G (row-major a, b)
+        if (dense_cholesky(m, L.data()) != LQ_OK) return set_err(c, LQ_ERR_BREAKDOWN, "subspace lost rank in the eigensolver");
+        // C = L^{-H} (upper triangular): solve L^H C = I column by column
+        std::vector<cplx> Cm(m * m, 0.0);
+        for (int col = 0; col < m; ++col) {
+            for (int i = m - 1; i >= 0; --i) {
+                cplx s = (i == col) ? 1.0 : 0.0;
+                for (int k = i + 1; k < m; ++k) s -= std::conj(L[k * m + i]) * Cm[k * m + col];
+                Cm[i * m + col] = s / std::conj(L[i * m + i]);
+            }
+        }
+        std::vector<double2> coef(m * m);
+        for (int b = 0; b < m; ++b) for (int a = 0; a < m; ++a) coef[b * m + a] = make_double2(Cm[a * m + b].real(), Cm[a * m + b].imag());
+        if ((r = bcombine_host(c, tmp, nullptr, m, X, m, coef, st))) return r;
+        LQ_CUDA(c, cudaMemcpyAsync(X, tmp, sizeof(double) * nv * m, cudaMemcpyDeviceToDevice, st));
+    }
+    return LQ_OK;
+}
+
+// Chebyshev-filtered subspace iteration on H^2 (dagger selects H^dag) for the nev eigenpairs
+// of smallest modulus; returns Ritz values (sorted by modulus) and Ritz vectors in Z.
+int eig_subspace(lq_ctx* c, const lq_eig_opts* eo, const double* X0, int dagger, double* W, std::vector<cplx>& theta,
+                 std::vector<double>& res, double* Z, cudaStream_t st, const void* links64) {
+    auto applyH = [&](const double* in, double* out, int count) { return apply_H_batch(c, in, out, count, dagger, st, LQ_FP64, links64); };
+    const int m = eo->nsub, nev = eo->nev;
+    const size_t nv = nvec(c);
+    double* X = W;
+    double* Y0 = W + (size_t)m * nv;
+    double* Y1 = Y0 + (size_t)m * nv;
+    double* H1 = Y1 + (size_t)m * nv;
+    double* H2 = H1 + (size_t)m * nv;
+    int r;
+    LQ_CUDA(c, cudaMemcpyAsync(X, X0, sizeof(double) * nv * m, cudaMemcpyDeviceToDevice, st));
+    if ((r = orthonormalise(c, X, Y0, m, st))) return r;
+    // b^2: power iteration with H^2 on the first start vector
+    double b2 = 0.0;
+    {
+        LQ_CUDA(c, cudaMemcpyAsync(Y1, X, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+        for (int it = 0; it < 12; ++it) {
+            if ((r = applyH(Y1, H1, 1))) return r;
+            if ((r = applyH(H1, H2, 1))) return r;
+            std::vector<double2> nn;
+            if ((r = bdots_host(c, H2, 1, H2, 1, nn, st))) return r;
+            std::vector<double2> n1;
+            if ((r = bdots_host(c, Y1, 1, Y1, 1, n1, st))) return r;
+            b2 = std::sqrt(nn[0].x / n1[0].x);
+            std::vector<double2> sc(1, make_double2(1.0 / std::sqrt(nn[0].x), 0.0));
+            if ((r = bcombine_host(c, Y1, nullptr, 1, H2, 1, sc, st))) return r;
+        }
+        b2 *= 1.15;
+    }
+    double a2 = b2 / 25.0;
+    theta.assign(m, 0.0);
+    res.assign(m, 1.0);
+    const double hn = std::sqrt(b2);
+    for (int it = 0; it <= eo->max_iter; ++it) {
+        if (it > 0) {
+            // Y = T_d((H^2 - cen) / e) X, three-term recurrence; eigenvalues of H^2 below a2 are amplified
+            const double cen = 0.5 * (b2 + a2), e = 0.5 * (b2 - a2);
+            if ((r = applyH(X, H1, m))) return r;
+            if ((r = applyH(H1, H2, m))) return r;
+            LQ_CUDA(c, launch_axpby3(Y1, 1.0 / e, H2, -cen / e, X, 0.0, nullptr, nv * m, st));
+            LQ_CUDA(c, cudaMemcpyAsync(Y0, X, sizeof(double) * nv * m, cudaMemcpyDeviceToDevice, st));
+            for (int d = 2; d <= eo->degree; ++d) {
+                if ((r = applyH(Y1, H1, m))) return r;
+                if ((r = applyH(H1, H2, m))) return r;
+                // Y2 = 2 (H^2 Y1 - cen Y1)/e - Y0, written over Y0
+                LQ_CUDA(c, launch_axpby3(Y0, 2.0 / e, H2, -2.0 * cen / e, Y1, -1.0, Y0, nv * m, st));
+                std::swap(Y0, Y1);
+                c->launches += 1;
+            }
+            LQ_CUDA(c, cudaMemcpyAsync(X, Y1, sizeof(double) * nv * m, cudaMemcpyDeviceToDevice, st));
+            if ((r = orthonormalise(c, X, Y0, m, st))) return r;
+        }
+        // Rayleigh-Ritz with H (or H^dag)
+        if ((r = applyH(X, H1, m))) return r;
+        std::vector<double2> M;
+        if ((r = bdots_host(c, X, m, H1, m, M, st))) return r;      // M[a*m+b] = <X_a|H X_b>
+        std::vector<cplx> Mc(m * m), w(m), Vr(m * m);
+        for (int i = 0; i < m * m; ++i) Mc[i] = cplx(M[i].x, M[i].y);
+        if (dense_eig(m, Mc.data(), w.data(), Vr.data()) != LQ_OK) return set_err(c, LQ_ERR_NEWTON, "Rayleigh-Ritz eigensolver failed");
+        std::vector<int> ord(m);
+        std::iota(ord.begin(), ord.end(), 0);
+        std::stable_sort(ord.begin(), ord.end(), [&](int i, int j) { return std::abs(w[i]) < std::abs(w[j]); });
+        std::vector<double2> coef(m * m), coefr(m * m);
+        for (int b = 0; b < m; ++b)
+            for (int a = 0; a < m; ++a) {
+                const cplx y = Vr[a * m + ord[b]];
+                coef[b * m + a] = make_double2(y.real(), y.imag());
+                const cplx yl = -w[ord[b]] * y;
+                coefr[b * m + a] = make_double2(yl.real(), yl.imag());
+            }
+        // Z = X Y (Ritz vectors), residual vectors H X Y - theta X Y in Y0
+        if ((r = bcombine_host(c, Z, nullptr, m, X, m, coef, st))) return r;
+        if ((r = bcombine_host(c, Y0, nullptr, m, H1, m, coef, st))) return r;
+        if ((r = bcombine_host(c, Y0, Y0, m, X, m, coefr, st))) return r;
+        LQ_CUDA(c, launch_norm2(Y0, nullptr, 0.0, nv / 2, m, c->gen_scr, st));
+        std::vector<double> rn(m);
+        LQ_CUDA(c, cudaMemcpyAsync(rn.data(), c->gen_scr, sizeof(double) * m, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(c, cudaStreamSynchronize(st));
+        double worst = 0.0;
+        for (int b = 0; b < m; ++b) {
+            theta[b] = w[ord[b]];
+            res[b] = std::sqrt(rn[b]) / hn;
+            if (b < nev) worst = std::max(worst, res[b]);
+        }
+        LQ_CUDA(c, cudaMemcpyAsync(X, Z, sizeof(double) * nv * m, cudaMemcpyDeviceToDevice, st));
+        if (worst <= eo->tol) break;
+        a2 = std::norm(theta[m - 1]) * 1.02;         // largest Ritz value bounds the damped interval
+        if (!(a2 < b2)) a2 = b2 / 25.0;
+    }
+    return LQ_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -748,6 +919,7 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     if ((r = dalloc(c, &c->quad_work, (size_t)nsrc * kmax * 4 * 2 * kQuadMaxNodes))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->quad_c, (size_t)nsrc))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->quad_check, (size_t)nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->quad_nodes, (size_t)nsrc))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->proj_sel, (size_t)nsrc))) { free_workspace(c); return r; }
     {
         const int m = std::max(2 * nsrc, 64);   // dots among up to m x m vectors
@@ -998,6 +1170,91 @@ int lq_upload_deflation(lq_ctx* c, int l, const double* lambda, const double* R,
     c->defl_dlam.assign(l, make_double2(0.0, 0.0));
     c->defl_l = l;
     LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_compute_deflation(lq_ctx* c, const lq_eig_opts* eo_in, const double* X0, double* lambda, double* resid, void* stream) {
+    if (!c || !eo_in || !X0) return set_err(c, LQ_ERR_ARG, "null argument");
+    lq_eig_opts eo = *eo_in;
+    if (eo.nsub <= 0) eo.nsub = std::min(eo.nev + 12, 64);
+    if (eo.degree <= 0) eo.degree = 40;
+    if (eo.max_iter <= 0) eo.max_iter = 60;
+    if (!(eo.tol > 0.0)) eo.tol = 1e-10;
+    if (eo.nev < 1 || eo.nsub < eo.nev + 2 || eo.nsub > 64) return set_err(c, LQ_ERR_ARG, "need 1 <= nev and nev + 2 <= nsub <= 64");
+    int r = check_ready(c, 1, 0);
+    if (r) return r;
+    if ((size_t)eo.nsub * eo.nsub > (size_t)std::max(2 * c->nsrc, 64) * std::max(2 * c->nsrc, 64))
+        return set_err(c, LQ_ERR_ARG, "nsub too large for the reserved reduction scratch");
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t nv = nvec(c);
+    const int m = eo.nsub, nev = eo.nev;
+    double* W = nullptr;      // X, Y0, Y1, H1, H2 | ZR, ZL | X0 copy
+    if (cudaMalloc(&W, sizeof(double) * nv * m * 8) != cudaSuccess) { cudaGetLastError(); return set_err(c, LQ_ERR_OOM, "eigensolver workspace"); }
+    double* ZR = W + (size_t)5 * m * nv;
+    double* ZL = ZR + (size_t)m * nv;
+    double* X0d = ZL + (size_t)m * nv;
+    // the eigensolver's stencil runs in FP64: a mixed-precision context gets a temporary FP64 copy
+    // of the links in the internal layout
+    void* U64 = nullptr;
+    if (c->prec != LQ_FP64) {
+        if (cudaMalloc(&U64, sizeof(double2) * c->V * 36) != cudaSuccess) { cudaGetLastError(); cudaFree(W); return set_err(c, LQ_ERR_OOM, "eigensolver links"); }
+        cudaError_t e = launch_links_internal(LQ_FP64, c->Ub, U64, c->V, st);
+        if (e != cudaSuccess) { cudaFree(U64); cudaFree(W); return set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e)); }
+    }
+    const void* links64 = U64 ? U64 : c->U;
+    auto fail = [&](int code) { cudaFree(W); if (U64) cudaFree(U64); return code; };
+    if ((r = stage_in(c, X0d, X0, nv * m, st))) return fail(r);
+    std::vector<cplx> thR, thL;
+    std::vector<double> resR, resL;
+    if ((r = eig_subspace(c, &eo, X0d, 0, W, thR, resR, ZR, st, links64))) return fail(r);
+    if ((r = eig_subspace(c, &eo, X0d, 1, W, thL, resL, ZL, st, links64))) return fail(r);
+    // pair right eigenvalue lambda_i with the left Ritz value conj(theta_j) closest to it
+    std::vector<int> pick(nev, -1);
+    std::vector<char> used(m, 0);
+    for (int i = 0; i < nev; ++i) {
+        double best = 1e300;
+        for (int j = 0; j < m; ++j) {
+            if (used[j]) continue;
+            const double d = std::abs(thR[i] - std::conj(thL[j]));
+            if (d < best) { best = d; pick[i] = j; }
+        }
+        used[pick[i]] = 1;
+    }
+    // install: defl_V = R (first nev right Ritz vectors), defl_W = the paired left vectors
+    if (nev > c->defl_cap) {
+        if ((r = dalloc(c, &c->defl_V, (size_t)2 * nev * nv))) return fail(r);
+        if ((r = dalloc(c, &c->defl_W, (size_t)2 * nev * nv))) return fail(r);
+        if ((r = dalloc(c, &c->defl_work, (size_t)6 * nev * nv))) return fail(r);
+        c->defl_scr_doubles = std::max(bdots_partial_doubles(nev * std::max(nev, c->nsrc) * 2) + (size_t)8 * nev * std::max(nev, c->nsrc),
+                                       (size_t)2 * 2 * nev * std::max(nev, c->nsrc));
+        if ((r = dalloc(c, &c->defl_scr, c->defl_scr_doubles))) return fail(r);
+        if ((r = dalloc(c, &c->defl_shift, (size_t)std::max(c->nsrc, nev)))) return fail(r);
+        c->defl_cap = nev;
+    }
+    LQ_CUDA(c, cudaMemcpyAsync(c->defl_V, ZR, sizeof(double) * nv * nev, cudaMemcpyDeviceToDevice, st));
+    for (int i = 0; i < nev; ++i)
+        LQ_CUDA(c, cudaMemcpyAsync(c->defl_W + (size_t)i * nv, ZL + (size_t)pick[i] * nv, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+    // biorthonormalise: Lk <- Lk G^{-H} with G = Lk^H R
+    std::vector<double2> G;
+    if ((r = bdots_host(c, c->defl_W, nev, c->defl_V, nev, G, st))) return fail(r);
+    std::vector<cplx> Gi(nev * nev);
+    for (int i = 0; i < nev * nev; ++i) Gi[i] = cplx(G[i].x, G[i].y);
+    if (dense_inverse(nev, Gi.data()) != LQ_OK) return fail(set_err(c, LQ_ERR_BREAKDOWN, "left and right eigenvectors are not biorthogonal"));
+    std::vector<double2> coef(nev * nev);
+    for (int j = 0; j < nev; ++j) for (int i = 0; i < nev; ++i) coef[j * nev + i] = make_double2(Gi[j * nev + i].real(), -Gi[j * nev + i].imag());
+    if ((r = bcombine_host(c, ZL, nullptr, nev, c->defl_W, nev, coef, st))) return fail(r);
+    LQ_CUDA(c, cudaMemcpyAsync(c->defl_W, ZL, sizeof(double) * nv * nev, cudaMemcpyDeviceToDevice, st));
+    LQ_CUDA(c, cudaMemsetAsync(c->defl_V + (size_t)nev * nv, 0, sizeof(double) * nev * nv, st));
+    LQ_CUDA(c, cudaMemsetAsync(c->defl_W + (size_t)nev * nv, 0, sizeof(double) * nev * nv, st));
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    c->defl_lam.resize(nev);
+    for (int i = 0; i < nev; ++i) c->defl_lam[i] = make_double2(thR[i].real(), thR[i].imag());
+    c->defl_dlam.assign(nev, make_double2(0.0, 0.0));
+    c->defl_l = nev;
+    if (lambda) for (int i = 0; i < nev; ++i) { lambda[2 * i] = thR[i].real(); lambda[2 * i + 1] = thR[i].imag(); }
+    if (resid) for (int i = 0; i < nev; ++i) resid[i] = std::max(resR[i], resL[pick[i]]);
+    cudaFree(W);
+    if (U64) cudaFree(U64);
     return LQ_OK;
 }
 

@@ -57,6 +57,22 @@ __global__ void k_bcombine(double2* __restrict__ Z, const double2* W, size_t zs,
     }
 }
 
+// Z = a1 X1 + a2 X2 + a3 X3 elementwise over n doubles (real coefficients; X3 may be null)
+__global__ void k_axpby3(double* __restrict__ Z, double a1, const double* __restrict__ X1, double a2,
+                         const double* __restrict__ X2, double a3, const double* __restrict__ X3, size_t n) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double v = a1 * X1[i] + a2 * X2[i];
+        if (X3) v += a3 * X3[i];
+        Z[i] = v;
+    }
+}
+
+cudaError_t launch_axpby3(double* Z, double a1, const double* X1, double a2, const double* X2, double a3, const double* X3,
+                          size_t n, cudaStream_t st) {
+    k_axpby3<<<1216, 256, 0, st>>>(Z, a1, X1, a2, X2, a3, X3, n);
+    return cudaGetLastError();
+}
+
 constexpr int kDotBlocks = 32;
 
 cudaError_t launch_bdots(const double* X, size_t xs, int nx, const double* Y, size_t ys, int ny, size_t n,

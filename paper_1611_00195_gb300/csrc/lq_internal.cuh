@@ -219,6 +219,7 @@ struct lq_ctx {
     double2* quad_work = nullptr;    // [nsrc][4][kmax][2 * kQuadMaxNodes]
     double* quad_c = nullptr;        // [nsrc]
     double* quad_check = nullptr;    // [nsrc]
+    int* quad_nodes = nullptr;       // [nsrc] nodes of the current quadrature pass per source
     int* proj_sel = nullptr;         // [nsrc] sources finished by the Newton fallback
     size_t partial_blocks = 0;       // capacity per source of the TSL partials
     size_t nx_partial_blocks = 0;

@@ -109,6 +109,8 @@ cudaError_t launch_bdots(const double* X, size_t xs, int nx, const double* Y, si
 cudaError_t launch_bcombine(double* Z, const double* W, size_t zs, int nz, const double* X, size_t xs, int nx,
                             const double* coef, size_t n, cudaStream_t st);   // Z_b = W_b + sum_a coef[b*nx+a] X_a
 size_t bdots_partial_doubles(int npairs);
+cudaError_t launch_axpby3(double* Z, double a1, const double* X1, double a2, const double* X2, double a3, const double* X3,
+                          size_t n, cudaStream_t st);
 cudaError_t launch_norm2(const double* a, const double* b, double sigma, size_t n, int nsrc, double* out, cudaStream_t st);
 size_t hop_blocks(const HopArgs& a, int nf);
 
@@ -172,12 +174,17 @@ struct QuadArgs {
     const double2* alpha; const double2* beta; const double* delta;
     double* c;             // [nb] contour scale
     double2* work;         // [nb][4][kmax][nth_max]
+    const int* nodes;      // [nb] quadrature nodes per source (0: skip the source), k_quad only
     double2* s;            // [nb][kmax] sgn(T) e_1
     double2* q;            // [nb][kmax] sgn(T) s (involution check)
     double* check;         // [nb] ||q - e_1||
 };
-constexpr int kQuadMaxNodes = 128;
-cudaError_t quad_sign_e1(const QuadArgs& a, int nodes, cudaStream_t st);
+constexpr int kQuadMaxNodes = 128;        // opts.quad_nodes and the adjoint's rank-one terms
+constexpr int kQuadRetryMaxNodes = 512;   // LQ_PROJ_AUTO doubles a failing source's nodes up to this
+constexpr int kQuadChunk = 2 * kQuadMaxNodes;   // shifted solves per pass of k_quad (= work columns)
+// sgn(T) e_1 and the involution check for the sources with a.nodes[src] > 0 (contour scales
+// recomputed when `scale`)
+cudaError_t quad_sign_e1(const QuadArgs& a, bool scale, cudaStream_t st);
 // c = (sigma_src - T)^{-1} e_1 into a.s (per-source complex shifts, device array)
 cudaError_t proj_resolvent(const QuadArgs& a, const double2* shifts, cudaStream_t st);
 cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st, const int* sel = nullptr);

@@ -355,54 +355,64 @@ __device__ __forceinline__ void tri_solve(const double2* __restrict__ al, const 
     }
 }
 
-__global__ void k_quad(QuadArgs a, int pass) {
+__global__ void __launch_bounds__(kQuadChunk) k_quad(QuadArgs a, int pass) {
     const int src = blockIdx.x;
-    const int t = threadIdx.x;           // 0 .. 2N-1
-    const int nth = blockDim.x;
-    const int N = nth / 2;
-    const int k = a.k;
+    const int N = a.nodes[src];          // nodes for this source; 0: already accepted, skip
+    if (N <= 0) return;
     const int keff = a.state[src].k_eff;
     if (keff <= 0) return;
+    const int t = threadIdx.x;
+    const int k = a.k;
     const double2* al = a.alpha + (size_t)src * a.kmax;
     const double2* be = a.beta + (size_t)src * a.kmax;
     const double* de = a.delta + (size_t)src * a.kmax;
-    double2* sd = a.work + (size_t)src * a.kmax * 4 * a.nth_max;   // [row][thread] x 4 arrays
+    double2* sd = a.work + (size_t)src * a.kmax * 4 * a.nth_max;   // [row][column] x 4 arrays
     double2* s1 = sd + (size_t)a.kmax * a.nth_max;
     double2* s2 = s1 + (size_t)a.kmax * a.nth_max;
     double2* sx = s2 + (size_t)a.kmax * a.nth_max;
     const double2* rhs = (pass == 0) ? nullptr : a.s + (size_t)src * a.kmax;
-    const int j = t >> 1;
-    const double sg = (t & 1) ? -1.0 : 1.0;
     const double c = a.c[src];
-    const double th = (j + 0.5) * 3.14159265358979323846 / (2.0 * N);
-    const double ct = cos(th);
-    const double tau = sg * c * tan(th);
-    const double w = c / (2.0 * N) / (ct * ct);
     const int n = keff;   // rows beyond keff are the identity padding: they only carry the rhs
     auto B = [&](int i) -> double2 { return pass == 0 ? make_double2(i == 0 ? 1.0 : 0.0, 0.0) : rhs[i]; };
-    tri_solve(al, be, de, n, make_double2(0.0, tau), B, sd + t, s1 + t, s2 + t, sx + t, a.nth_max, w);
-    __syncthreads();
-    // sum over nodes, row by row (fixed order: deterministic)
-    __shared__ double red[256];
     double2* out = (pass == 0 ? a.s : a.q) + (size_t)src * a.kmax;
-    double loc = 0.0;
-    for (int i = t; i < k; i += nth) {
-        double2 acc = make_double2(0.0, 0.0);
-        if (i < n) {
-            for (int q = 0; q < nth; ++q) acc = cadd(acc, sx[(size_t)i * a.nth_max + q]);
-        } else {
-            acc = B(i);      // identity padding: sgn(1) = 1
+    // the 2N shifted solves (T +- i tau_j)^{-1} b, kQuadChunk at a time; each chunk's columns are
+    // summed row by row into out in a fixed order (deterministic)
+    const int nterms = 2 * N;
+    for (int c0 = 0; c0 < nterms; c0 += kQuadChunk) {
+        const int width = min(kQuadChunk, nterms - c0);
+        if (t < width) {
+            const int term = c0 + t;
+            const int j = term >> 1;
+            const double sg = (term & 1) ? -1.0 : 1.0;
+            const double th = (j + 0.5) * 3.14159265358979323846 / (2.0 * N);
+            const double ct = cos(th);
+            const double tau = sg * c * tan(th);
+            const double w = c / (2.0 * N) / (ct * ct);
+            tri_solve(al, be, de, n, make_double2(0.0, tau), B, sd + t, s1 + t, s2 + t, sx + t, a.nth_max, w);
         }
-        out[i] = acc;
-        if (pass == 1) {
-            const double ex = (i == 0) ? 1.0 : 0.0;
-            loc += (acc.x - ex) * (acc.x - ex) + acc.y * acc.y;
+        __syncthreads();
+        for (int i = t; i < k; i += blockDim.x) {
+            double2 acc = (c0 == 0) ? make_double2(0.0, 0.0) : out[i];
+            if (i < n) {
+                for (int q = 0; q < width; ++q) acc = cadd(acc, sx[(size_t)i * a.nth_max + q]);
+            } else if (c0 == 0) {
+                acc = B(i);      // identity padding: sgn(1) = 1
+            }
+            out[i] = acc;
         }
+        __syncthreads();         // the next chunk reuses the work columns
     }
     if (pass == 1) {
+        __shared__ double red[kQuadChunk];
+        double loc = 0.0;
+        for (int i = t; i < k; i += blockDim.x) {
+            const double2 v = out[i];
+            const double ex = (i == 0) ? 1.0 : 0.0;
+            loc += (v.x - ex) * (v.x - ex) + v.y * v.y;
+        }
         red[t] = loc;
         __syncthreads();
-        for (int off = nth / 2; off > 0; off >>= 1) {
+        for (int off = blockDim.x / 2; off > 0; off >>= 1) {
             if (t < off) red[t] += red[t + off];
             __syncthreads();
         }
@@ -506,10 +516,10 @@ __global__ void k_nt_first_column(NewtonArgs a, double2* __restrict__ out, int l
     out[(size_t)b * ldo + i] = a.X[(size_t)b * a.ld * a.ld + (size_t)i * a.ld];
 }
 
-cudaError_t quad_sign_e1(const QuadArgs& a, int nodes, cudaStream_t st) {
-    k_quad_scale<<<(a.nb + 31) / 32, 32, 0, st>>>(a);
-    k_quad<<<a.nb, 2 * nodes, 0, st>>>(a, 0);
-    k_quad<<<a.nb, 2 * nodes, 0, st>>>(a, 1);
+cudaError_t quad_sign_e1(const QuadArgs& a, bool scale, cudaStream_t st) {
+    if (scale) k_quad_scale<<<(a.nb + 31) / 32, 32, 0, st>>>(a);
+    k_quad<<<a.nb, kQuadChunk, 0, st>>>(a, 0);
+    k_quad<<<a.nb, kQuadChunk, 0, st>>>(a, 1);
     return cudaGetLastError();
 }
 

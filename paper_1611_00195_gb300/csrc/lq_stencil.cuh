@@ -1,0 +1,231 @@
+// Device helpers shared by the stencil kernels of the two-sided Lanczos path: compensated
+// accumulators for the inner products, block / grid reductions, and the spin-colour algebra of
+// one Wilson hop (projection to half spinors, SU(3) multiply, reconstruction).
+#pragma once
+#include "lq_internal.cuh"
+#include "lq_launch.h"
+
+namespace lq {
+
+// ---------------------------------------------------------------------------------------
+// float-float accumulator with exact products (for FP32 data); double CSum for FP64 data
+// ---------------------------------------------------------------------------------------
+struct FF { float h, l; };
+__device__ __forceinline__ void two_sum_f(float a, float b, float& s, float& t) {
+    s = a + b;
+    float z = s - a;
+    t = (a - (s - z)) + (b - z);
+}
+__device__ __forceinline__ void ff_add_prod(FF& acc, float a, float b) {
+    float p = a * b;
+    float pe = fmaf(a, b, -p);
+    float s, t;
+    two_sum_f(acc.h, p, s, t);
+    acc.h = s;
+    acc.l += t + pe;
+}
+__device__ __forceinline__ FF ff_merge(FF a, FF b) {
+    float s, t;
+    two_sum_f(a.h, b.h, s, t);
+    FF r; r.h = s; r.l = a.l + b.l + t;
+    return r;
+}
+
+template <typename R> struct DotAcc;
+template <> struct DotAcc<double> {
+    CSum v;
+    __device__ __forceinline__ void zero() { v.s = 0.0; v.e = 0.0; }
+    __device__ __forceinline__ void add_prod(double a, double b) { cs_add_prod(v, a, b); }
+    // warp-level reduction then conversion to a double compensated sum (valid in lane 0)
+    __device__ __forceinline__ CSum warp_total() {
+        CSum r = v;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) r = cs_merge(r, cs_shfl_down(r, off));
+        return r;
+    }
+};
+template <> struct DotAcc<float> {
+    FF v;
+    __device__ __forceinline__ void zero() { v.h = 0.f; v.l = 0.f; }
+    __device__ __forceinline__ void add_prod(float a, float b) { ff_add_prod(v, a, b); }
+    __device__ __forceinline__ CSum warp_total() {   // valid in lane 0 only
+        FF r = v;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            FF o; o.h = __shfl_down_sync(0xffffffffu, r.h, off); o.l = __shfl_down_sync(0xffffffffu, r.l, off);
+            r = ff_merge(r, o);
+        }
+        CSum c{0.0, 0.0};
+        if ((threadIdx.x & 31) == 0) { c.s = (double)r.h; c.e = (double)r.l; }
+        return c;
+    }
+};
+
+// Reduce NV per-thread accumulators to one compensated double per value for the block.
+// Valid in thread 0.  smem holds 32 * NV CSum.
+template <typename R, int NV>
+__device__ __forceinline__ void block_total(DotAcc<R> (&acc)[NV], CSum (&out)[NV], CSum* smem) {
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    CSum w[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) w[i] = acc[i].warp_total();
+    if (lane == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) smem[warp * NV + i] = w[i];
+    __syncthreads();
+    if (warp == 0) {
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            if (lane < nw) w[i] = smem[lane * NV + i];
+            else { w[i].s = 0.0; w[i].e = 0.0; }
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) w[i] = cs_merge(w[i], cs_shfl_down(w[i], off));
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) out[i] = w[i];
+    }
+    __syncthreads();
+}
+
+// "Last block done" election: every block of a source publishes its partials, then the
+// block that finishes last (atomic counter) reduces them.  Returns true in that block.
+__device__ __forceinline__ bool last_block(int* counter, int nblocks) {
+    __shared__ int is_last;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        __threadfence();
+        int prev = atomicAdd(counter, 1);
+        is_last = (prev == nblocks - 1);
+        if (is_last) *counter = 0;   // reset for the next launch
+    }
+    __syncthreads();
+    if (is_last) __threadfence();
+    return is_last != 0;
+}
+
+// Sum nb partials (stride NV values of (s, e) pairs) in a fixed order -> deterministic.
+template <int NV>
+__device__ __forceinline__ void reduce_partials(const double* __restrict__ part, int nb, double (&res)[NV], CSum* smem) {
+    CSum acc[NV];
+#pragma unroll
+    for (int i = 0; i < NV; ++i) { acc[i].s = 0.0; acc[i].e = 0.0; }
+    for (int b = threadIdx.x; b < nb; b += blockDim.x)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) {
+            CSum p; p.s = __ldcg(part + (size_t)b * 2 * NV + 2 * i); p.e = __ldcg(part + (size_t)b * 2 * NV + 2 * i + 1);
+            acc[i] = cs_merge(acc[i], p);
+        }
+    block_reduce_cs<NV>(acc, smem);
+    if (threadIdx.x == 0)
+#pragma unroll
+        for (int i = 0; i < NV; ++i) res[i] = acc[i].s + acc[i].e;
+}
+
+// ---------------------------------------------------------------------------------------
+// Spin structure in the chiral basis: gamma_nu = [[0, B_nu], [B_nu^dag, 0]] with
+// B_x = -i sigma_1, B_y = -i sigma_2, B_z = -i sigma_3, B_t = 1.  Then
+// (1 + s gamma_nu) psi = (h, s B^dag h) with h = psi_up + s B psi_dn  (s = +-1),
+// so every hop only needs the two-component half spinor h (Wilson projector, r = 1).
+// ---------------------------------------------------------------------------------------
+template <typename C, int NU, int SP>
+__device__ __forceinline__ void project(const C (&p)[12], C (&h)[6]) {
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+        C u0 = p[col], u1 = p[3 + col], d2 = p[6 + col], d3 = p[9 + col];
+        C b0, b1;
+        if (NU == 0) { b0 = cmul_mi(d3); b1 = cmul_mi(d2); }
+        else if (NU == 1) { b0 = cmk<C>(-d3.x, -d3.y); b1 = d2; }
+        else if (NU == 2) { b0 = cmul_mi(d2); b1 = cmul_i(d3); }
+        else { b0 = d2; b1 = d3; }
+        if (SP > 0) { h[col] = cadd(u0, b0); h[3 + col] = cadd(u1, b1); }
+        else { h[col] = csub(u0, b0); h[3 + col] = csub(u1, b1); }
+    }
+}
+
+// acc += (g, s B^dag g)
+template <typename C, int NU, int SP>
+__device__ __forceinline__ void reconstruct_add(const C (&g)[6], C (&acc)[12]) {
+#pragma unroll
+    for (int col = 0; col < 3; ++col) {
+        C g0 = g[col], g1 = g[3 + col];
+        C l0, l1;   // B^dag g
+        if (NU == 0) { l0 = cmul_i(g1); l1 = cmul_i(g0); }
+        else if (NU == 1) { l0 = g1; l1 = cmk<C>(-g0.x, -g0.y); }
+        else if (NU == 2) { l0 = cmul_i(g0); l1 = cmul_mi(g1); }
+        else { l0 = g0; l1 = g1; }
+        acc[col] = cadd(acc[col], g0);
+        acc[3 + col] = cadd(acc[3 + col], g1);
+        if (SP > 0) { acc[6 + col] = cadd(acc[6 + col], l0); acc[9 + col] = cadd(acc[9 + col], l1); }
+        else { acc[6 + col] = csub(acc[6 + col], l0); acc[9 + col] = csub(acc[9 + col], l1); }
+    }
+}
+
+template <typename C, bool DAG>
+__device__ __forceinline__ void su3_mul(const C (&u)[9], const C (&h)[6], C (&g)[6]) {
+#pragma unroll
+    for (int sc = 0; sc < 2; ++sc)
+#pragma unroll
+        for (int row = 0; row < 3; ++row) {
+            C a = cmk<C>(0, 0);
+#pragma unroll
+            for (int col = 0; col < 3; ++col) {
+                if (!DAG) a = cfma(u[row * 3 + col], h[sc * 3 + col], a);
+                else a = cfmac(u[col * 3 + row], h[sc * 3 + col], a);
+            }
+            g[sc * 3 + row] = a;
+        }
+}
+
+template <typename C>
+__device__ __forceinline__ void load_link(const C* __restrict__ L, size_t V, int nu, size_t s, C (&u)[9]) {
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u[e] = __ldg(L + ((size_t)nu * 9 + e) * V + s);
+}
+
+template <typename C>
+__device__ __forceinline__ void hscale(C (&h)[6], decltype(C::x) f) {
+#pragma unroll
+    for (int i = 0; i < 6; ++i) h[i] = cscale(h[i], f);
+}
+template <typename C>
+__device__ __forceinline__ void haxpy(C (&h)[6], decltype(C::x) f, const C (&x)[6]) {  // h += f x
+#pragma unroll
+    for (int i = 0; i < 6; ++i) { h[i].x = fma(f, x[i].x, h[i].x); h[i].y = fma(f, x[i].y, h[i].y); }
+}
+
+// Hop factors in the kernel's precision (FP32 copies are prepared on the host).
+template <typename R> __device__ __forceinline__ R fac_a(const HopArgs& a, int side, int nu, bool fwd);
+template <> __device__ __forceinline__ double fac_a<double>(const HopArgs& a, int side, int nu, bool fwd) { return fwd ? a.a_fwd[side][nu] : a.a_bwd[side][nu]; }
+template <> __device__ __forceinline__ float fac_a<float>(const HopArgs& a, int side, int nu, bool fwd) { return fwd ? a.af_fwd[side][nu] : a.af_bwd[side][nu]; }
+template <typename R> __device__ __forceinline__ R fac_e(const HopArgs& a, int side, int nu, bool fwd);
+template <> __device__ __forceinline__ double fac_e<double>(const HopArgs& a, int side, int nu, bool fwd) { return fwd ? a.e_fwd[side][nu] : a.e_bwd[side][nu]; }
+template <> __device__ __forceinline__ float fac_e<float>(const HopArgs& a, int side, int nu, bool fwd) { return fwd ? a.ef_fwd[side][nu] : a.ef_bwd[side][nu]; }
+template <typename R> __device__ __forceinline__ R fac_diag(const HopArgs& a);
+template <> __device__ __forceinline__ double fac_diag<double>(const HopArgs& a) { return a.diag; }
+template <> __device__ __forceinline__ float fac_diag<float>(const HopArgs& a) { return a.diag_f; }
+
+// Site coordinates (x, y, z, t) from the linear site index (32-bit arithmetic: V < 2^31).
+__device__ __forceinline__ void site_coords(const HopArgs& a, size_t s, int (&x)[4]) {
+    unsigned r = (unsigned)s;
+    const unsigned d0 = (unsigned)a.dims[0], d1 = (unsigned)a.dims[1], d2 = (unsigned)a.dims[2];
+    unsigned q = r / d0; x[0] = (int)(r - q * d0); r = q;
+    q = r / d1; x[1] = (int)(r - q * d1); r = q;
+    q = r / d2; x[2] = (int)(r - q * d2);
+    x[3] = (int)q;
+}
+
+
+// gamma5 [diag * psi + acc]
+template <typename C>
+__device__ __forceinline__ void finish(const C (&psi)[12], decltype(C::x) diag, C (&acc)[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        C v = cmk<C>(fma(diag, psi[c].x, acc[c].x), fma(diag, psi[c].y, acc[c].y));
+        acc[c] = (c < 6) ? v : cmk<C>(-v.x, -v.y);
+    }
+}
+
+}  // namespace lq

@@ -37,7 +37,7 @@ EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_u
             "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
             "lq_profile_read", "lq_newton_sign_noalloc", "lq_error_estimate",
             "lq_upload_deflation", "lq_deflation_derivatives", "lq_sign_bilinear_grad",
-            "lq_dense_eig"]
+            "lq_dense_eig", "lq_compute_deflation"]
 
 
 class LatticeDesc(ctypes.Structure):
@@ -71,6 +71,11 @@ class Profile(ctypes.Structure):
 
     def as_dict(self):
         return {f: getattr(self, f) for f, _ in self._fields_ if f != "reserved"}
+
+
+class EigOpts(ctypes.Structure):
+    _fields_ = [("nev", ctypes.c_int), ("nsub", ctypes.c_int), ("degree", ctypes.c_int), ("max_iter", ctypes.c_int),
+                ("tol", ctypes.c_double)]
 
 
 class Direction(ctypes.Structure):
@@ -113,6 +118,7 @@ def lib():
         L.lq_deflation_derivatives.argtypes = [P, ctypes.POINTER(Direction), ctypes.POINTER(Opts), P, P, P, P]
         L.lq_sign_bilinear_grad.argtypes = [P, P, P, ctypes.POINTER(Opts), P, P, P, P]
         L.lq_dense_eig.argtypes = [I, P, P, P]
+        L.lq_compute_deflation.argtypes = [P, ctypes.POINTER(EigOpts), P, P, P, P]
         L.lq_newton_sign_noalloc.argtypes = [P, P, I, I, I, D, ctypes.POINTER(I), P]
         for name in EXPORTED:
             if name not in ("lq_default_opts", "lq_destroy", "lq_last_error"):
@@ -356,6 +362,17 @@ class Context:
         R, L = _as_c128(R), _as_c128(L)
         self._defl_keep = (lam, R, L)
         self._check(self._L.lq_upload_deflation(self._h, int(lam.shape[0]), _ptr(lam), _ptr(R), _ptr(L), _stream(R)))
+
+    def compute_deflation(self, nev, X0, nsub=0, degree=0, max_iter=0, tol=0.0):
+        """Install the nev eigenpairs of H(mu) closest to zero as the deflation space, from the
+        library's eigensolver started at X0 [nsub][V][4][3]; returns (lambda [nev], residuals [nev])."""
+        X0 = _as_c128(X0)
+        eo = EigOpts(int(nev), int(nsub or X0.shape[0]), int(degree), int(max_iter), float(tol))
+        lam = np.zeros(nev, np.complex128)
+        res = np.zeros(nev, np.float64)
+        self._check(self._L.lq_compute_deflation(self._h, ctypes.byref(eo), _ptr(X0), _ptr(lam), _ptr(res), _stream(X0)))
+        self._defl_keep = (lam,)
+        return lam, res
 
     def deflation_derivatives(self, k, kind=LQ_DIR_MU, field=None, **kw):
         """(dlambda [l], dR [l][V][4][3], dL kets [l][V][4][3]) along the direction (host arrays)."""

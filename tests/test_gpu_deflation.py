@@ -118,3 +118,53 @@ def test_derivative_generalised_deflation(lqlib):
               "%.3g); deriv error vs exact %.3g (undeflated %.3g)" % (k, LD, pd, ps, sens, ed, ed0))
         assert pd < max(1e-10, 30 * sens) and ps < max(1e-10, 30 * sens)
         assert ed < 0.1 * ed0
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-10)])
+def test_compute_deflation_eigensolver(lqlib, prec, tol):
+    """The library's eigensolver (Chebyshev-filtered subspace iteration on H^2 with Rayleigh-Ritz)
+    finds the eigenvalues of H(mu) closest to zero that the oracle's dense eig gives, and the
+    installed space deflates the sign like the oracle's eigenpairs do.  Its stencil is FP64 in
+    both precisions, so both reach the FP64 tolerance."""
+    from paper_1611_00195_gb300 import lq
+    dims, nev, nsub, k = (4, 2, 2, 2), 8, 16, 60
+    lat = od.Lattice(dims)
+    U = syn.gauge_field(dims, 0.4, 3)
+    A = od.dense_H(lat, U, MU)
+    lam_all = np.linalg.eigvals(A)
+    lam_all = lam_all[np.argsort(np.abs(lam_all))]
+    assert np.abs(lam_all[nev]) > 1.01 * np.abs(lam_all[nev - 1])      # a gap at the cut
+    c = lq.Context(dims, mu=MU, precision=prec)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(k, 8, True)
+    X0 = syn.gaussian_source(dims, 41, nsrc=nsub)
+    lam, res = c.compute_deflation(nev, torch.from_numpy(X0).cuda(), nsub=nsub, tol=tol)
+    print("eigensolver prec %d: residuals max %.3g; eigenvalue error max %.3g"
+          % (prec, res.max(), max(np.min(np.abs(lam_all[:nev] - z)) for z in lam)))
+    assert res.max() <= tol
+    for z in lam:
+        assert np.min(np.abs(lam_all[:nev] - z)) < 20 * tol * np.abs(lam_all).max()
+    # deflation with the computed space matches deflation with the oracle's eigenpairs
+    x = torch.from_numpy(syn.gaussian_source(dims, 5, nsrc=2)).cuda()
+    y1, _ = c.sign_apply(x, k, deflate=1)
+    lo, R, L, full = odf.eigenpairs(A, nev)
+    c.upload_deflation(lo, torch.from_numpy(np.ascontiguousarray(R.T.reshape(nev, lat.V, 4, 3))).cuda(),
+                       torch.from_numpy(np.ascontiguousarray(L.conj().reshape(nev, lat.V, 4, 3))).cuda())
+    y2, _ = c.sign_apply(x, k, deflate=1)
+    e = relerr(y1.cpu().numpy(), y2.cpu().numpy())
+    if prec == 0:
+        print("deflated sign with computed vs dense eigenpairs: %.3g" % e)
+        assert e < 1e-7
+    else:
+        # mixed precision: both results carry FP32 rounding of the Krylov vectors; the computed
+        # space must do as well as the dense eigenpairs against the FP64 deflated result
+        c64 = lq.Context(dims, mu=MU, precision=0)
+        c64.upload_gauge(torch.from_numpy(U).cuda())
+        c64.reserve(k, 8, True)
+        c64.upload_deflation(lo, torch.from_numpy(np.ascontiguousarray(R.T.reshape(nev, lat.V, 4, 3))).cuda(),
+                             torch.from_numpy(np.ascontiguousarray(L.conj().reshape(nev, lat.V, 4, 3))).cuda())
+        y64, _ = c64.sign_apply(x, k, deflate=1)
+        e1 = relerr(y1.cpu().numpy(), y64.cpu().numpy())
+        e2 = relerr(y2.cpu().numpy(), y64.cpu().numpy())
+        print("mixed deflated sign vs FP64: computed space %.3g, dense eigenpairs %.3g" % (e1, e2))
+        assert e1 < 3 * e2 + 1e-9

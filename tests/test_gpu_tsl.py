@@ -81,7 +81,7 @@ def test_sign_apply_fp64_parity(lqlib, dims, k, nsrc):
 
 @pytest.mark.parametrize("dims,k,nsrc", CASES)
 @pytest.mark.parametrize("kind", [0, 1])
-@pytest.mark.parametrize("variant", [0, 1])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3])
 def test_sign_derivative_fp64_parity(lqlib, dims, k, nsrc, kind, variant):
     from paper_1611_00195_gb300 import lq
     mu = 0.3
@@ -170,8 +170,8 @@ def test_projected_quadrature_matches_newton(lqlib, prec, dims, k):
 
 
 def test_projected_auto_falls_back_to_newton(lqlib):
-    """With a quadrature too coarse to pass the involution check (2 nodes, tiny tolerance)
-    the automatic choice must finish with the Newton iteration and say so."""
+    """With an involution tolerance no quadrature can meet, the automatic choice must climb
+    the node ladder, then finish with the Newton iteration and say so."""
     from paper_1611_00195_gb300 import lq
     dims, k, mu = (4, 4, 4, 4), 64, 0.3
     U = syn.gauge_field(dims, 0.4, 3)
@@ -180,9 +180,29 @@ def test_projected_auto_falls_back_to_newton(lqlib):
     c.upload_gauge(torch.from_numpy(U).cuda())
     c.reserve(k, 1, False)
     yn, rn = c.sign_apply(x, k, projected=lq.LQ_PROJ_NEWTON)
-    ya, ra = c.sign_apply(x, k, projected=lq.LQ_PROJ_AUTO, quad_nodes=2, proj_tol=1e-14)
+    ya, ra = c.sign_apply(x, k, projected=lq.LQ_PROJ_AUTO, quad_nodes=2, proj_tol=1e-300)
     assert ra[0]["projected"] == lq.LQ_PROJ_NEWTON and ra[0]["status"] == 0
     assert relerr(ya.cpu().numpy(), yn.cpu().numpy()) < 1e-15
+
+
+def test_projected_auto_node_ladder(lqlib):
+    """A quadrature started far too coarse (2 nodes) must be retried with doubled nodes until
+    its involution residual passes, per source, without the Newton fallback, and then agree
+    with the Newton iteration."""
+    from paper_1611_00195_gb300 import lq
+    dims, k, mu = (4, 4, 4, 4), 64, 0.3
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = torch.from_numpy(syn.gaussian_source(dims, 5, nsrc=2)).cuda()
+    c = lq.Context(dims, mu=mu)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(k, 2, False)
+    yn, rn = c.sign_apply(x, k, projected=lq.LQ_PROJ_NEWTON)
+    ya, ra = c.sign_apply(x, k, projected=lq.LQ_PROJ_AUTO, quad_nodes=2, proj_tol=1e-11)
+    for s in range(2):
+        print("ladder: source %d check %.3g" % (s, ra[s]["proj_check"]))
+        assert ra[s]["projected"] == lq.LQ_PROJ_QUAD and ra[s]["status"] == 0
+        assert ra[s]["proj_check"] <= 1e-11
+        assert relerr(ya[s].cpu().numpy(), yn[s].cpu().numpy()) < 1e-10
 
 
 @pytest.mark.parametrize("dims,k", [((3, 2, 2, 2), 40), ((4, 4, 4, 4), 64)])
