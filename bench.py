@@ -57,6 +57,7 @@ def parse():
     p.add_argument("--nev", type=int, default=20, help="eigenpairs of the deflation space")
     p.add_argument("--nderiv", type=int, default=6, help="Jordan blocks of the derivative deflation")
     p.add_argument("--eig-iter", type=int, default=20, help="eigensolver iterations for the deflation space")
+    p.add_argument("--hop-variant", type=int, default=-1, help="stencil schedule (-1: autotuned)")
     return p.parse_args()
 
 
@@ -250,6 +251,16 @@ def run_reference(args, ws, rank):
     print(json.dumps(line))
 
 
+# kernel instantiated for each stencil schedule (lq_opts.hop_variant) of the block TSL step, FP32
+HOP_KERNELS = {0: "k_hop<float,2,1,true,1>", 1: "k_hop_roles<float,1,true>", 2: "k_hop<float,2,1,true,5>",
+               3: "k_hop<float,2,1,true,4>"}
+# DRAM bytes (read + write) per launch of the block stencil from one ncu capture of that kernel
+# revision and schedule on the same per-launch shape (14x14^3, 16 sources, both sides; the
+# Krylov depth does not change a launch).  Source: profiles/k_hop_block_stencil_14x14c3_b16.md.
+# Keyed by (kernel revision, schedule, V, sources); anything else reports traffic = null.
+HOP_TRAFFIC = {("hop-v2", 3, 38416, 16): 598750720, ("hop-v2", 1, 38416, 16): 461046784}
+
+
 def main():
     args = parse()
     ws, rank, local = dist_setup()
@@ -278,8 +289,9 @@ def main():
     ys = torch.empty_like(xd)
     yd = torch.empty_like(xd)
 
+    hv = dict(hop_variant=args.hop_variant)
     for _ in range(args.warmup):
-        ctx.sign_derivative_apply(xd, k, out=(ys, yd))
+        ctx.sign_derivative_apply(xd, k, out=(ys, yd), **hv)
     torch.cuda.synchronize(dev)
 
     props = torch.cuda.get_device_properties(dev)
@@ -294,7 +306,7 @@ def main():
     ev0.record(stream)
     reps = None
     for _ in range(args.steps):
-        _, _, reps = ctx.sign_derivative_apply(xd, k, out=(ys, yd))
+        _, _, reps = ctx.sign_derivative_apply(xd, k, out=(ys, yd), **hv)
     ev1.record(stream)
     torch.cuda.synchronize(dev)
     barrier(ws)
@@ -310,15 +322,8 @@ def main():
     hop_flops = 4 * 1320 * V * nsrc
     peak, peak_kind = peaks()
     achieved = hop_bytes / (hop_ms * 1e-3) / 1e9
-    traffic = None
-    tfile = os.path.join(ROOT, "profiles", "hop_traffic.json")
-    if os.path.exists(tfile):
-        try:
-            t = json.load(open(tfile))
-            if t.get("k") == k and t.get("nsrc") == nsrc and t.get("kernel_rev") == lq.KERNEL_REV:
-                traffic = t.get("dram_bytes_per_launch")
-        except Exception:
-            traffic = None
+    schedule = reps[0]["hop_variant"] if reps else -1
+    traffic = HOP_TRAFFIC.get((lq.KERNEL_REV, schedule, V, nsrc))
     total_prof = prof["hop_ms"] + prof["update_ms"] + prof["newton_ms"] + prof["other_ms"]
 
     # end to end through the C ABI with pinned host buffers
@@ -434,7 +439,8 @@ def main():
                    "precision": "FP32 stencil/vectors (FP32 accumulation), FP64 compensated dots, coefficients, Newton",
                    "parallelism": "replicas" if ws > 1 else "single GPU",
                    "l2": "no flush: the Krylov basis streamed per step (%.1f GB) exceeds L2" % (k * nsrc * 2 * n * 8 / 1e9)},
-        "roofline": {"bound": "hbm", "kernel": "k_hop<float,2,1,true> (block stencil + alpha dot)",
+        "roofline": {"bound": "hbm", "kernel": HOP_KERNELS.get(schedule, "k_hop") +
+                     " (block stencil + alpha dot, schedule %d)" % schedule,
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": "%s (MEASURED_PEAKS.json)" % peak_kind if peak_kind == "measured" else "of fallback (6.8 TB/s)",
                      "traffic": traffic, "algorithmic_bytes_per_launch": hop_bytes, "launch_ms": hop_ms,

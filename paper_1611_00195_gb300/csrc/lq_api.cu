@@ -220,7 +220,7 @@ void free_workspace(lq_ctx* c) {
                    (void**)&c->state, (void**)&c->alpha, (void**)&c->beta, (void**)&c->delta, (void**)&c->scale,
                    (void**)&c->nx_X, (void**)&c->nx_Y, (void**)&c->nx_F, (void**)&c->nx_perm, (void**)&c->nx_scal,
                    (void**)&c->nx_partials, (void**)&c->nx_counters, (void**)&c->proj_c, (void**)&c->quad_q,
-                   (void**)&c->quad_work, (void**)&c->quad_c, (void**)&c->quad_check, (void**)&c->quad_nodes, (void**)&c->proj_sel,
+                   (void**)&c->quad_work, (void**)&c->quad_c, (void**)&c->quad_check, (void**)&c->quad_nodes, (void**)&c->quad_part, (void**)&c->proj_sel,
                    &c->lbasis, (void**)&c->uscale, (void**)&c->adj_coef, &c->adj_nu, &c->adj_om,
                    (void**)&c->adj_force, (void**)&c->adj_dmu, (void**)&c->gen_scr};
     for (void** p : ps) { dfree(*p); *p = nullptr; }
@@ -228,9 +228,11 @@ void free_workspace(lq_ctx* c) {
     c->adjoint = false;
 }
 
-// Choose the stencil schedule for the Lanczos step: time each variant on the caller's data
-// (three launches each, no dot, outputs into the scratch operator buffers) and keep the faster
-// one for this context and batch size.
+// Choose the stencil schedule for the Lanczos step: time each variant on the caller's data with
+// the launch the loop makes (alpha dot included), twice round, and keep the fastest for this
+// context and batch size.  The launches run step j = 0 on the freshly initialised state; the
+// loop's own first step recomputes everything they write (outputs, alpha_0, the step's
+// coefficients), so the tuning leaves no trace in the results.
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
     const int nvar = (c->prec == LQ_FP64) ? 2 : 4;
@@ -240,26 +242,28 @@ int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* vari
     }
     int& slot = c->tuned_variant[nf][emode];
     if (slot >= 0) { *variant = slot; return LQ_OK; }
-    h.state = nullptr;
+    h.j = 0;
+    h.kmax_run = std::max(h.kmax_run, 2);   // never mark a source finished while tuning
     cudaEvent_t e0, e1;
     LQ_CUDA(c, cudaEventCreate(&e0));
     LQ_CUDA(c, cudaEventCreate(&e1));
-    float best = 1e30f;
-    int bestv = 0;
-    for (int v = 0; v < nvar; ++v) {
-        h.variant = v;
-        LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, false, st));   // warm-up
-        LQ_CUDA(c, cudaEventRecord(e0, st));
-        for (int i = 0; i < 3; ++i) LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, false, st));
-        LQ_CUDA(c, cudaEventRecord(e1, st));
-        LQ_CUDA(c, cudaEventSynchronize(e1));
-        float ms = 0.f;
-        LQ_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
-        c->launches += 4;
-        if (ms < best) { best = ms; bestv = v; }
-    }
+    std::vector<float> best(nvar, 1e30f);
+    for (int round = 0; round < 2; ++round)
+        for (int v = 0; v < nvar; ++v) {
+            h.variant = v;
+            LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));   // warm-up
+            LQ_CUDA(c, cudaEventRecord(e0, st));
+            for (int i = 0; i < 4; ++i) LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));
+            LQ_CUDA(c, cudaEventRecord(e1, st));
+            LQ_CUDA(c, cudaEventSynchronize(e1));
+            float ms = 0.f;
+            LQ_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
+            c->launches += 5;
+            best[v] = std::min(best[v], ms);
+        }
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
+    const int bestv = (int)(std::min_element(best.begin(), best.end()) - best.begin());
     slot = bestv;
     *variant = bestv;
     return LQ_OK;
@@ -367,6 +371,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
         qa.k = k; qa.nb = nsrc; qa.kmax = c->kmax; qa.nth_max = 2 * kQuadMaxNodes; qa.state = c->state;
         qa.alpha = c->alpha; qa.beta = c->beta; qa.delta = c->delta; qa.c = c->quad_c; qa.work = c->quad_work;
         qa.s = c->proj_c; qa.q = c->quad_q; qa.check = c->quad_check; qa.nodes = c->quad_nodes;
+        qa.nth_max = 2 * kQuadRetryMaxNodes; qa.part = c->quad_part; qa.part_blocks = 2 * kQuadRetryMaxNodes / kQuadBlk;
         // LQ_PROJ_QUAD: one pass with opts.quad_nodes.  LQ_PROJ_AUTO: a source whose involution
         // residual exceeds proj_tol is retried with twice the nodes (up to kQuadRetryMaxNodes),
         // the others keep their result; what still fails goes to the Newton iteration below.
@@ -375,9 +380,10 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
         for (int attempt = 0;; ++attempt) {
             LQ_CUDA(c, cudaMemcpyAsync(c->quad_nodes, nodes.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
             cudaEvent_t eq = prof_begin(c, st);
-            LQ_CUDA(c, quad_sign_e1(qa, attempt == 0, st));
+            const int maxn = *std::max_element(nodes.begin(), nodes.end());
+            LQ_CUDA(c, quad_sign_e1(qa, maxn, attempt == 0, st));
             prof_end(c, PC_NEWTON, eq, st, 0);
-            c->launches += attempt == 0 ? 3 : 2;
+            c->launches += attempt == 0 ? 5 : 4;
             LQ_CUDA(c, cudaMemcpyAsync(check.data(), c->quad_check, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
             LQ_CUDA(c, cudaStreamSynchronize(st));   // nodes and check are host memory
             ok = true;
@@ -916,10 +922,11 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     if ((r = dalloc(c, &c->nx_counters, (size_t)3 * nsrc))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->proj_c, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->quad_q, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
-    if ((r = dalloc(c, &c->quad_work, (size_t)nsrc * kmax * 4 * 2 * kQuadMaxNodes))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->quad_work, (size_t)nsrc * kmax * 4 * 2 * kQuadRetryMaxNodes))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->quad_c, (size_t)nsrc))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->quad_check, (size_t)nsrc))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->quad_nodes, (size_t)nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->quad_part, (size_t)nsrc * (2 * kQuadRetryMaxNodes / kQuadBlk) * kmax))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->proj_sel, (size_t)nsrc))) { free_workspace(c); return r; }
     {
         const int m = std::max(2 * nsrc, 64);   // dots among up to m x m vectors

@@ -220,6 +220,7 @@ struct lq_ctx {
     double* quad_c = nullptr;        // [nsrc]
     double* quad_check = nullptr;    // [nsrc]
     int* quad_nodes = nullptr;       // [nsrc] nodes of the current quadrature pass per source
+    double2* quad_part = nullptr;    // [nsrc][2 * 512 / 32][kmax] block row sums of the quadrature
     int* proj_sel = nullptr;         // [nsrc] sources finished by the Newton fallback
     size_t partial_blocks = 0;       // capacity per source of the TSL partials
     size_t nx_partial_blocks = 0;

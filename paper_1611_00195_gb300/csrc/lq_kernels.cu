@@ -108,10 +108,11 @@ __global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
     using Chunk = typename Tr<R>::Chunk;
     __shared__ CSum smem[32 * 2];
     const int side = blockIdx.z + a.side0;
+    const unsigned bx = blockIdx.x;
     const int src = blockIdx.y;
     if (a.state != nullptr && a.state[src].status != 0) return;   // source finished / failed
     const size_t V = a.V;
-    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const size_t s = (size_t)bx * blockDim.x + threadIdx.x;
     const bool active = s < V;
     const Chunk* in0 = reinterpret_cast<const Chunk*>(a.in[side]) + (size_t)src * a.src_stride_in[side];
     const Chunk* in1 = in0 + field_elems<R>(V);
@@ -161,13 +162,14 @@ __global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
         }
     }
     if (DOT && side == 0) {
+        const int nbx = (int)gridDim.x;
         CSum tot[2];
         block_total<R, 2>(d, tot, smem);
-        double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 4;
+        double* part = a.partials + ((size_t)src * a.partial_stride + bx) * 4;
         if (threadIdx.x == 0) { part[0] = tot[0].s; part[1] = tot[0].e; part[2] = tot[1].s; part[3] = tot[1].e; }
-        if (last_block(a.counters + src, gridDim.x)) {
+        if (last_block(a.counters + src, nbx)) {
             double res[2];
-            reduce_partials<2>(a.partials + (size_t)src * a.partial_stride * 4, gridDim.x, res, smem);
+            reduce_partials<2>(a.partials + (size_t)src * a.partial_stride * 4, nbx, res, smem);
             if (threadIdx.x == 0) tsl_alpha_step(a, src, res[0], res[1]);
         }
     }
@@ -545,7 +547,7 @@ template <typename R, int NF>
 __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
     using C = typename Tr<R>::C;
     using Chunk = typename Tr<R>::Chunk;
-    extern __shared__ double2 coef[];   // [keff] (double) or [keff][2] (float hi/lo)
+    extern __shared__ double2 coef[];   // [keff] (double) or [keff] float4 (hi.x, hi.y, lo.x, lo.y)
     const int src = blockIdx.y;
     const int f = blockIdx.z;           // field index (0 top / 1 bottom)
     const TslState& st = a.state[src];
@@ -558,9 +560,9 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
         double2 cs = make_double2(c.x * sc, c.y * sc);
         if (sizeof(R) == 8) coef[j] = cs;
         else {
-            float hx = (float)cs.x, hy = (float)cs.y;
-            coef[2 * j] = cs;
-            coef[2 * j + 1] = make_double2((double)hx, (double)hy);
+            // split once per block: no FP64 arithmetic is left in the k-loop below
+            const float hx = (float)cs.x, hy = (float)cs.y;
+            reinterpret_cast<float4*>(coef)[j] = make_float4(hx, hy, (float)(cs.x - (double)hx), (float)(cs.y - (double)hy));
         }
     }
     __syncthreads();
@@ -591,9 +593,8 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
         for (int c = 0; c < 12; ++c) { ar[c] = FF{0.f, 0.f}; ai[c] = FF{0.f, 0.f}; }
         for (int j = 0; j < keff; ++j) {
             const float4* vj = reinterpret_cast<const float4*>(base + (size_t)j * a.vec_stride);
-            const double2 cd = coef[2 * j];
-            const float chx = (float)cd.x, chy = (float)cd.y;
-            const float clx = (float)(cd.x - (double)chx), cly = (float)(cd.y - (double)chy);
+            const float4 cf = reinterpret_cast<const float4*>(coef)[j];
+            const float chx = cf.x, chy = cf.y, clx = cf.z, cly = cf.w;
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
                 const float4 v4 = __ldg(vj + (size_t)q * V + s);
@@ -765,7 +766,7 @@ cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, 
     if (lanczos_block && a.variant == 1)
         return prec == LQ_FP64 ? launch_roles_t<double>(a, emode, dot, st) : launch_roles_t<float>(a, emode, dot, st);
     if (lanczos_block && prec != LQ_FP64 && a.variant == 2) return launch_hop_t<float, 5>(a, nf, emode, dot, st);
-    if (lanczos_block && prec != LQ_FP64 && a.variant == 3) return launch_hop_t<float, 6>(a, nf, emode, dot, st);
+    if (lanczos_block && prec != LQ_FP64 && a.variant == 3) return launch_hop_t<float, 4>(a, nf, emode, dot, st);
     return prec == LQ_FP64 ? launch_hop_t<double, 1>(a, nf, emode, dot, st) : launch_hop_t<float, 1>(a, nf, emode, dot, st);
 }
 
@@ -796,7 +797,7 @@ cudaError_t launch_tsl_init(int prec, int nf, const InitArgs& a, cudaStream_t st
 
 cudaError_t launch_recombine(int prec, int nf, const RecArgs& a, cudaStream_t st) {
     dim3 grid((unsigned)((a.V + kRecThreads - 1) / kRecThreads), (unsigned)a.nsrc, (unsigned)nf);
-    size_t sm = (size_t)a.kmax * sizeof(double2) * (prec == LQ_FP64 ? 1 : 2);
+    const size_t sm = (size_t)a.kmax * 16;   // one double2 (FP64) or float4 (FP32 hi/lo) per coefficient
     if (prec == LQ_FP64) {
         if (nf == 1) { cudaFuncSetAttribute(k_recombine<double, 1>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); k_recombine<double, 1><<<grid, kRecThreads, sm, st>>>(a); }
         else { cudaFuncSetAttribute(k_recombine<double, 2>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm); k_recombine<double, 2><<<grid, kRecThreads, sm, st>>>(a); }

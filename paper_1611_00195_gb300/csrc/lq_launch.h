@@ -174,17 +174,20 @@ struct QuadArgs {
     const double2* alpha; const double2* beta; const double* delta;
     double* c;             // [nb] contour scale
     double2* work;         // [nb][4][kmax][nth_max]
-    const int* nodes;      // [nb] quadrature nodes per source (0: skip the source), k_quad only
+    const int* nodes;      // [nb] quadrature nodes per source (0: skip the source), sign quadrature only
+    double2* part;         // [nb][part_blocks][kmax] per-block row sums of the sign quadrature
+    int part_blocks;
     double2* s;            // [nb][kmax] sgn(T) e_1
     double2* q;            // [nb][kmax] sgn(T) s (involution check)
     double* check;         // [nb] ||q - e_1||
 };
 constexpr int kQuadMaxNodes = 128;        // opts.quad_nodes and the adjoint's rank-one terms
 constexpr int kQuadRetryMaxNodes = 512;   // LQ_PROJ_AUTO doubles a failing source's nodes up to this
-constexpr int kQuadChunk = 2 * kQuadMaxNodes;   // shifted solves per pass of k_quad (= work columns)
-// sgn(T) e_1 and the involution check for the sources with a.nodes[src] > 0 (contour scales
-// recomputed when `scale`)
-cudaError_t quad_sign_e1(const QuadArgs& a, bool scale, cudaStream_t st);
+constexpr int kQuadBlk = 32;              // shifted solves per block of the sign quadrature
+constexpr int kQuadFinish = 256;          // threads of the summing kernel
+// sgn(T) e_1 and the involution check for the sources with a.nodes[src] > 0 (at most max_nodes;
+// contour scales recomputed when `scale`).  a.work needs 2 * max_nodes columns (nth_max).
+cudaError_t quad_sign_e1(const QuadArgs& a, int max_nodes, bool scale, cudaStream_t st);
 // c = (sigma_src - T)^{-1} e_1 into a.s (per-source complex shifts, device array)
 cudaError_t proj_resolvent(const QuadArgs& a, const double2* shifts, cudaStream_t st);
 cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st, const int* sel = nullptr);

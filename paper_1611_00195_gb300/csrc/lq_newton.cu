@@ -306,110 +306,136 @@ __global__ void k_nt_copy_out(NewtonArgs a, double2* __restrict__ S) {
 //     sgn(T) b ~ (c / 2N) sum_j cos(theta_j)^{-2} [ (T + i tau_j)^{-1} + (T - i tau_j)^{-1} ] b,
 //     tau_j = c tan(theta_j).
 // Each term is one complex tridiagonal solve (Gaussian elimination with partial pivoting,
-// O(k)).  One block per source, one thread per (node, sign); the U factors live in a
-// [row][thread] scratch so that a warp's accesses at one row are contiguous.
+// O(k)).  One thread per (node, sign), kQuadBlk of them per block and as many blocks per source
+// as the node count needs, so that the FP64 work of a batch spreads over the whole GPU; the U
+// factors live in a [row][term] scratch so that a warp's accesses at one row are contiguous.
+// Each block sums its terms row by row; a second kernel adds the blocks in a fixed order.
 // ---------------------------------------------------------------------------------------------
 // Solve (T + shift) x = b for the tridiagonal T (sub-diagonal de real, diagonal al, super-
 // diagonal be) by Gaussian elimination with partial pivoting (row interchanges create a second
-// super-diagonal).  b(i) is read in row order, so the right-hand side may alias sx.  The U
-// factors go to sd/s1/s2 and w * x to sx, all at stride ld.
+// super-diagonal).  b(i) is read in row order, so the right-hand side may alias sx.  Per row the
+// reciprocal of the pivot goes to sd, the U entries right of it to s1/s2 and the eliminated
+// right-hand side to sx; w * x overwrites sx, all at stride ld.  One real division per row.
 template <class RHS>
 __device__ __forceinline__ void tri_solve(const double2* __restrict__ al, const double2* __restrict__ be,
                                           const double* __restrict__ de, int n, double2 shift, RHS b,
                                           double2* sd, double2* s1, double2* s2, double2* sx, size_t ld, double w) {
     auto D = [&](int i) -> double2 { double2 v = al[i]; v.x += shift.x; v.y += shift.y; return v; };
+    auto recip = [](double2 z) -> double2 { const double r = 1.0 / (z.x * z.x + z.y * z.y); return make_double2(z.x * r, -z.y * r); };
     double2 cd = D(0), cu = (n > 1) ? be[0] : make_double2(0.0, 0.0), cx = b(0);
     for (int i = 0; i < n - 1; ++i) {
-        const double2 l = make_double2(de[i], 0.0);
+        const double l = de[i];
         const double2 nd = D(i + 1);
         const double2 nu = (i + 1 < n - 1) ? be[i + 1] : make_double2(0.0, 0.0);
         const double2 nx = b(i + 1);
         const size_t o = (size_t)i * ld;
-        if (l.x * l.x > cd.x * cd.x + cd.y * cd.y) {
+        if (l * l > cd.x * cd.x + cd.y * cd.y) {
             // pivot on the sub-diagonal row: stored row i = (l, nd, nu | nx)
-            const double2 f = cdiv(cd, l);
-            sd[o] = l; s1[o] = nd; s2[o] = nu; sx[o] = nx;
+            const double rl = 1.0 / l;
+            const double2 f = cscale(cd, rl);
+            sd[o] = make_double2(rl, 0.0); s1[o] = nd; s2[o] = nu; sx[o] = nx;
             const double2 ncd = csub(cu, cmul(f, nd));
             const double2 ncu = make_double2(-(f.x * nu.x - f.y * nu.y), -(f.x * nu.y + f.y * nu.x));
             cx = csub(cx, cmul(f, nx));
             cd = ncd;
             cu = ncu;
         } else {
-            const double2 f = cdiv(l, cd);
-            sd[o] = cd; s1[o] = cu; s2[o] = make_double2(0.0, 0.0); sx[o] = cx;
+            const double2 rc = recip(cd);
+            const double2 f = cscale(rc, l);
+            sd[o] = rc; s1[o] = cu; s2[o] = make_double2(0.0, 0.0); sx[o] = cx;
             cd = csub(nd, cmul(f, cu));
             cu = nu;
             cx = csub(nx, cmul(f, cx));
         }
     }
-    double2 x1 = cdiv(cx, cd), x2 = make_double2(0.0, 0.0);
+    double2 x1 = cmul(cx, recip(cd)), x2 = make_double2(0.0, 0.0);
     sx[(size_t)(n - 1) * ld] = cscale(x1, w);
     for (int i = n - 2; i >= 0; --i) {
         const size_t o = (size_t)i * ld;
         double2 v = csub(sx[o], cmul(s1[o], x1));
         v = csub(v, cmul(s2[o], x2));
-        v = cdiv(v, sd[o]);
+        v = cmul(v, sd[o]);
         sx[o] = cscale(v, w);
         x2 = x1;
         x1 = v;
     }
 }
 
-__global__ void __launch_bounds__(kQuadChunk) k_quad(QuadArgs a, int pass) {
-    const int src = blockIdx.x;
+// The right-hand side of a quadrature pass: e_1 (pass 0) or the pass-0 result (pass 1, for the
+// involution check Q(T) Q(T) e_1).
+struct QuadRhs {
+    const double2* rhs;
+    __device__ double2 operator()(int i) const { return rhs ? rhs[i] : make_double2(i == 0 ? 1.0 : 0.0, 0.0); }
+};
+
+// Terms [blockIdx.x * kQuadBlk, +kQuadBlk) of source blockIdx.y: solve, then the block's row sums
+// into part[src][blockIdx.x][row].
+__global__ void __launch_bounds__(kQuadBlk) k_quad_solve(QuadArgs a, int pass) {
+    const int src = blockIdx.y;
     const int N = a.nodes[src];          // nodes for this source; 0: already accepted, skip
-    if (N <= 0) return;
-    const int keff = a.state[src].k_eff;
-    if (keff <= 0) return;
+    const int term0 = blockIdx.x * kQuadBlk;
+    if (N <= 0 || term0 >= 2 * N) return;
+    const int n = a.state[src].k_eff;    // rows beyond k_eff are the identity padding (finish kernel)
+    if (n <= 0) return;
     const int t = threadIdx.x;
-    const int k = a.k;
+    const int width = min(kQuadBlk, 2 * N - term0);
     const double2* al = a.alpha + (size_t)src * a.kmax;
     const double2* be = a.beta + (size_t)src * a.kmax;
     const double* de = a.delta + (size_t)src * a.kmax;
-    double2* sd = a.work + (size_t)src * a.kmax * 4 * a.nth_max;   // [row][column] x 4 arrays
+    double2* sd = a.work + (size_t)src * a.kmax * 4 * a.nth_max;   // [row][term] x 4 arrays
     double2* s1 = sd + (size_t)a.kmax * a.nth_max;
     double2* s2 = s1 + (size_t)a.kmax * a.nth_max;
     double2* sx = s2 + (size_t)a.kmax * a.nth_max;
-    const double2* rhs = (pass == 0) ? nullptr : a.s + (size_t)src * a.kmax;
-    const double c = a.c[src];
-    const int n = keff;   // rows beyond keff are the identity padding: they only carry the rhs
-    auto B = [&](int i) -> double2 { return pass == 0 ? make_double2(i == 0 ? 1.0 : 0.0, 0.0) : rhs[i]; };
+    const QuadRhs B{pass == 0 ? nullptr : a.s + (size_t)src * a.kmax};
+    if (t < width) {
+        const int term = term0 + t;
+        const int j = term >> 1;
+        const double sg = (term & 1) ? -1.0 : 1.0;
+        const double c = a.c[src];
+        const double th = (j + 0.5) * 3.14159265358979323846 / (2.0 * N);
+        const double ct = cos(th);
+        const double tau = sg * c * tan(th);
+        const double w = c / (2.0 * N) / (ct * ct);
+        tri_solve(al, be, de, n, make_double2(0.0, tau), B, sd + term, s1 + term, s2 + term, sx + term, a.nth_max, w);
+    }
+    __syncthreads();
+    double2* part = a.part + ((size_t)src * a.part_blocks + blockIdx.x) * a.kmax;
+    for (int i = t; i < n; i += blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        for (int q = 0; q < width; ++q) acc = cadd(acc, sx[(size_t)i * a.nth_max + term0 + q]);
+        part[i] = acc;
+    }
+}
+
+// out = sum of the block sums (fixed order: deterministic), identity padding beyond k_eff; the
+// involution residual ||out - e_1|| after pass 1.
+__global__ void __launch_bounds__(kQuadFinish) k_quad_finish(QuadArgs a, int pass) {
+    const int src = blockIdx.x;
+    const int N = a.nodes[src];
+    if (N <= 0) return;
+    const int n = a.state[src].k_eff;
+    if (n <= 0) return;
+    const int t = threadIdx.x;
+    const int nbk = (2 * N + kQuadBlk - 1) / kQuadBlk;
+    const QuadRhs B{pass == 0 ? nullptr : a.s + (size_t)src * a.kmax};
     double2* out = (pass == 0 ? a.s : a.q) + (size_t)src * a.kmax;
-    // the 2N shifted solves (T +- i tau_j)^{-1} b, kQuadChunk at a time; each chunk's columns are
-    // summed row by row into out in a fixed order (deterministic)
-    const int nterms = 2 * N;
-    for (int c0 = 0; c0 < nterms; c0 += kQuadChunk) {
-        const int width = min(kQuadChunk, nterms - c0);
-        if (t < width) {
-            const int term = c0 + t;
-            const int j = term >> 1;
-            const double sg = (term & 1) ? -1.0 : 1.0;
-            const double th = (j + 0.5) * 3.14159265358979323846 / (2.0 * N);
-            const double ct = cos(th);
-            const double tau = sg * c * tan(th);
-            const double w = c / (2.0 * N) / (ct * ct);
-            tri_solve(al, be, de, n, make_double2(0.0, tau), B, sd + t, s1 + t, s2 + t, sx + t, a.nth_max, w);
+    const double2* part = a.part + (size_t)src * a.part_blocks * a.kmax;
+    double loc = 0.0;
+    for (int i = t; i < a.k; i += blockDim.x) {
+        double2 acc = make_double2(0.0, 0.0);
+        if (i < n) {
+            for (int b = 0; b < nbk; ++b) acc = cadd(acc, part[(size_t)b * a.kmax + i]);
+        } else {
+            acc = B(i);          // identity padding: sgn(1) = 1
         }
-        __syncthreads();
-        for (int i = t; i < k; i += blockDim.x) {
-            double2 acc = (c0 == 0) ? make_double2(0.0, 0.0) : out[i];
-            if (i < n) {
-                for (int q = 0; q < width; ++q) acc = cadd(acc, sx[(size_t)i * a.nth_max + q]);
-            } else if (c0 == 0) {
-                acc = B(i);      // identity padding: sgn(1) = 1
-            }
-            out[i] = acc;
+        if (pass == 1) {
+            const double ex = (i == 0) ? 1.0 : 0.0;
+            loc += (acc.x - ex) * (acc.x - ex) + acc.y * acc.y;
         }
-        __syncthreads();         // the next chunk reuses the work columns
+        out[i] = acc;            // pass 1 writes q, never the rhs s it reads
     }
     if (pass == 1) {
-        __shared__ double red[kQuadChunk];
-        double loc = 0.0;
-        for (int i = t; i < k; i += blockDim.x) {
-            const double2 v = out[i];
-            const double ex = (i == 0) ? 1.0 : 0.0;
-            loc += (v.x - ex) * (v.x - ex) + v.y * v.y;
-        }
+        __shared__ double red[kQuadFinish];
         red[t] = loc;
         __syncthreads();
         for (int off = blockDim.x / 2; off > 0; off >>= 1) {
@@ -516,10 +542,15 @@ __global__ void k_nt_first_column(NewtonArgs a, double2* __restrict__ out, int l
     out[(size_t)b * ldo + i] = a.X[(size_t)b * a.ld * a.ld + (size_t)i * a.ld];
 }
 
-cudaError_t quad_sign_e1(const QuadArgs& a, bool scale, cudaStream_t st) {
+cudaError_t quad_sign_e1(const QuadArgs& a, int max_nodes, bool scale, cudaStream_t st) {
+    if (max_nodes < 1 || 2 * max_nodes > a.nth_max || (2 * max_nodes + kQuadBlk - 1) / kQuadBlk > a.part_blocks)
+        return cudaErrorInvalidValue;
     if (scale) k_quad_scale<<<(a.nb + 31) / 32, 32, 0, st>>>(a);
-    k_quad<<<a.nb, kQuadChunk, 0, st>>>(a, 0);
-    k_quad<<<a.nb, kQuadChunk, 0, st>>>(a, 1);
+    const dim3 grid((unsigned)((2 * max_nodes + kQuadBlk - 1) / kQuadBlk), (unsigned)a.nb);
+    for (int pass = 0; pass < 2; ++pass) {
+        k_quad_solve<<<grid, kQuadBlk, 0, st>>>(a, pass);
+        k_quad_finish<<<a.nb, kQuadFinish, 0, st>>>(a, pass);
+    }
     return cudaGetLastError();
 }
 

@@ -62,32 +62,62 @@ template <> struct DotAcc<float> {
 };
 
 // Reduce NV per-thread accumulators to one compensated double per value for the block.
-// Valid in thread 0.  smem holds 32 * NV CSum.
+// Valid in thread 0.  smem holds 32 * NV CSum.  FP32 data stays in float-float up to the block
+// total (one conversion per value in thread 0): FP64 is slow on this GPU and has no place in the
+// body of an FP32 kernel.
 template <typename R, int NV>
 __device__ __forceinline__ void block_total(DotAcc<R> (&acc)[NV], CSum (&out)[NV], CSum* smem) {
     const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
-    CSum w[NV];
-#pragma unroll
-    for (int i = 0; i < NV; ++i) w[i] = acc[i].warp_total();
-    if (lane == 0)
-#pragma unroll
-        for (int i = 0; i < NV; ++i) smem[warp * NV + i] = w[i];
-    __syncthreads();
-    if (warp == 0) {
+    if constexpr (sizeof(R) == 4) {
+        FF* fs = reinterpret_cast<FF*>(smem);
+        FF w[NV];
 #pragma unroll
         for (int i = 0; i < NV; ++i) {
-            if (lane < nw) w[i] = smem[lane * NV + i];
-            else { w[i].s = 0.0; w[i].e = 0.0; }
+            FF r = acc[i].v;
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                FF o; o.h = __shfl_down_sync(0xffffffffu, r.h, off); o.l = __shfl_down_sync(0xffffffffu, r.l, off);
+                r = ff_merge(r, o);
+            }
+            w[i] = r;
         }
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-#pragma unroll
-            for (int i = 0; i < NV; ++i) w[i] = cs_merge(w[i], cs_shfl_down(w[i], off));
         if (lane == 0)
 #pragma unroll
-            for (int i = 0; i < NV; ++i) out[i] = w[i];
+            for (int i = 0; i < NV; ++i) fs[warp * NV + i] = w[i];
+        __syncthreads();
+        if (threadIdx.x == 0)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                FF t = fs[i];
+                for (int v = 1; v < nw; ++v) t = ff_merge(t, fs[v * NV + i]);
+                out[i].s = (double)t.h;
+                out[i].e = (double)t.l;
+            }
+        __syncthreads();
+    } else {
+        CSum w[NV];
+#pragma unroll
+        for (int i = 0; i < NV; ++i) w[i] = acc[i].warp_total();
+        if (lane == 0)
+#pragma unroll
+            for (int i = 0; i < NV; ++i) smem[warp * NV + i] = w[i];
+        __syncthreads();
+        if (warp == 0) {
+#pragma unroll
+            for (int i = 0; i < NV; ++i) {
+                if (lane < nw) w[i] = smem[lane * NV + i];
+                else { w[i].s = 0.0; w[i].e = 0.0; }
+            }
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1)
+#pragma unroll
+                for (int i = 0; i < NV; ++i) w[i] = cs_merge(w[i], cs_shfl_down(w[i], off));
+            if (lane == 0)
+#pragma unroll
+                for (int i = 0; i < NV; ++i) out[i] = w[i];
+        }
+        __syncthreads();
     }
-    __syncthreads();
 }
 
 // "Last block done" election: every block of a source publishes its partials, then the
