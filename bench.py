@@ -252,8 +252,8 @@ def run_reference(args, ws, rank):
 
 
 # kernel instantiated for each stencil schedule (lq_opts.hop_variant) of the block TSL step, FP32
-HOP_KERNELS = {0: "k_hop<float,2,1,true,1>", 1: "k_hop_roles<float,1,true>", 2: "k_hop<float,2,1,true,5>",
-               3: "k_hop<float,2,1,true,4>"}
+HOP_KERNELS = {0: "k_hop<float,2,1,true,1>", 1: "k_hop_roles<float,1,true,32,1>", 2: "k_hop<float,2,1,true,5>",
+               3: "k_hop<float,2,1,true,4>", 4: "k_hop_roles<float,1,true,64,2>", 5: "k_hop_roles<float,1,true,32,5>"}
 # DRAM bytes (read + write) per launch of the block stencil from one ncu capture of that kernel
 # revision and schedule on the same per-launch shape (14x14^3, 16 sources, both sides; the
 # Krylov depth does not change a launch).  Source: profiles/k_hop_block_stencil_14x14c3_b16.md.

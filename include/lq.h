@@ -88,7 +88,9 @@ typedef struct {
                               (default 1e-11)                                                   */
     int hop_variant;       /* stencil schedule: -1 = autotuned on first use (default), 0 = one
                               thread per (site, side), 1 = one thread per (site, output field),
-                              2 / 3 = as 0 with at least 5 / 4 resident blocks per SM (FP32) */
+                              2 / 3 = as 0 with at least 5 / 4 resident blocks per SM, 4 = as
+                              1 with 64 sites per block, 5 = as 1 with at least 5 resident
+                              blocks per SM (2-5: FP32 only; FP64 runs 0 for them)          */
     int defl_kmax;         /* depth of the shifted solves for the eigenvector derivatives of the
                               generalised deflation (0 = the reserved kmax)                    */
     int defl_nderiv;       /* Jordan blocks of the derivative deflation: the first defl_nderiv

@@ -235,7 +235,7 @@ void free_workspace(lq_ctx* c) {
 // coefficients), so the tuning leaves no trace in the results.
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
-    const int nvar = (c->prec == LQ_FP64) ? 2 : 4;
+    const int nvar = (c->prec == LQ_FP64) ? 2 : 6;
     if (c->tuned_nsrc != h.nsrc) {
         for (auto& row : c->tuned_variant) for (int& v : row) v = -1;
         c->tuned_nsrc = h.nsrc;
@@ -462,7 +462,7 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->projected < LQ_PROJ_AUTO || o->projected > LQ_PROJ_QUAD) return set_err(c, LQ_ERR_ARG, "unknown projected-sign solver");
     if (o->projected != LQ_PROJ_NEWTON && (o->quad_nodes < 1 || o->quad_nodes > kQuadMaxNodes || !(o->proj_tol > 0.0)))
         return set_err(c, LQ_ERR_ARG, "quad_nodes must be in [1, 128] and proj_tol > 0");
-    if (o->hop_variant < -1 || o->hop_variant > 3) return set_err(c, LQ_ERR_ARG, "hop_variant must be in [-1, 3]");
+    if (o->hop_variant < -1 || o->hop_variant > 5) return set_err(c, LQ_ERR_ARG, "hop_variant must be in [-1, 5]");
     if (o->defl_kmax < 0 || o->defl_kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "defl_kmax must be in [0, reserved kmax]");
     if (o->defl_nderiv < 0) return set_err(c, LQ_ERR_ARG, "defl_nderiv must be >= 0");
     return LQ_OK;
@@ -901,7 +901,7 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     if ((r = dalloc(c, &c->io, (size_t)6 * nsrc * c->V * 24))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->norms, (size_t)3 * nsrc))) { free_workspace(c); return r; }
     size_t pb = (c->V + 31) / 32;   // finest stencil grid (32 sites per block)
-    pb = std::max(pb, (size_t)kUpdBlocksPerSrc);   // update grid
+    pb = std::max(pb, (size_t)64);   // update grid (one resident wave over all sources, capped here)
     pb = std::max(pb, (c->V + kUpdThreads - 1) / kUpdThreads);
     c->partial_blocks = pb;
     if ((r = dalloc(c, &c->partials, (size_t)nsrc * pb * 8))) { free_workspace(c); return r; }

@@ -10,6 +10,7 @@
 #include "lq_launch.h"
 #include "lq_stencil.cuh"
 
+#include <algorithm>
 #include <cstdio>
 
 namespace lq {
@@ -107,9 +108,11 @@ __global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
     using C = typename Tr<R>::C;
     using Chunk = typename Tr<R>::Chunk;
     __shared__ CSum smem[32 * 2];
-    const int side = blockIdx.z + a.side0;
+    // grid (site blocks, sides, sources): the two sides of one source run close together in
+    // launch order, so that the right side's alpha dot finds the left vectors in L2
+    const int side = blockIdx.y + a.side0;
     const unsigned bx = blockIdx.x;
-    const int src = blockIdx.y;
+    const int src = blockIdx.z;
     if (a.state != nullptr && a.state[src].status != 0) return;   // source finished / failed
     const size_t V = a.V;
     const size_t s = (size_t)bx * blockDim.x + threadIdx.x;
@@ -180,7 +183,7 @@ __global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
 // of a site for the block operator of Eq. (2.5) are
 //   role 0: A t + E b      role 1: A b          (right side, operator A = H(mu))
 //   role 2: A^dag p        role 3: A^dag q + E^dag p   (left side, A^dag = H(-mu))
-// A block holds kRoleSites sites x 4 roles (one warp per role), so the four warps read the
+// A block holds RS sites x 4 roles (RS / 32 warps per role), so the four roles read the
 // same links and neighbour sites and share them in L1.  The alpha dot is accumulated by the
 // right-side roles: conj(p(x)) . (A t + E b)(x) + conj(q(x)) . (A b)(x).
 // ---------------------------------------------------------------------------------------
@@ -233,18 +236,18 @@ __device__ __forceinline__ void role_dir(const HopArgs& a, int side, bool with_e
     role_hop<R, EMODE, NU, +1>(a, side, with_e, V, sb, sb, bb, fa_in, fe_in, acc);
 }
 
-template <typename R, int EMODE, bool DOT>
-__global__ void __launch_bounds__(4 * kRoleSites) k_hop_roles(HopArgs a) {
+template <typename R, int EMODE, bool DOT, int RS, int MINB>
+__global__ void __launch_bounds__(4 * RS, MINB) k_hop_roles(HopArgs a) {
     using C = typename Tr<R>::C;
     using Chunk = typename Tr<R>::Chunk;
     __shared__ CSum smem[32 * 2];
     const int src = blockIdx.y;
     if (a.state != nullptr && a.state[src].status != 0) return;
-    const int role = threadIdx.x / kRoleSites;       // warp-uniform
+    const int role = threadIdx.x / RS;                // warp-uniform
     const int side = role >> 1;                       // 0 right, 1 left
     const int fld = role & 1;                         // output field within the side
     const size_t V = a.V;
-    const size_t s = (size_t)blockIdx.x * kRoleSites + (threadIdx.x % kRoleSites);
+    const size_t s = (size_t)blockIdx.x * RS + (threadIdx.x % RS);
     const bool active = s < V;
     const size_t F = field_elems<R>(V);
     const Chunk* in0 = reinterpret_cast<const Chunk*>(a.in[side]) + (size_t)src * a.src_stride_in[side];
@@ -730,7 +733,7 @@ __global__ void k_direction(const double2* __restrict__ U, const double* __restr
 // ---------------------------------------------------------------------------------------
 template <typename R, int MINB>
 static cudaError_t launch_hop_t(const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st) {
-    dim3 grid((unsigned)((a.V + kHopThreads - 1) / kHopThreads), (unsigned)a.nsrc, (unsigned)a.nsides);
+    dim3 grid((unsigned)((a.V + kHopThreads - 1) / kHopThreads), (unsigned)a.nsides, (unsigned)a.nsrc);
     dim3 block(kHopThreads);
 #define LQ_HOP(NF, EM, D) k_hop<R, NF, EM, D, MINB><<<grid, block, 0, st>>>(a)
     if (nf == 1) {
@@ -744,11 +747,11 @@ static cudaError_t launch_hop_t(const HopArgs& a, int nf, int emode, bool dot, c
     return cudaGetLastError();
 }
 
-template <typename R>
+template <typename R, int RS, int MINB>
 static cudaError_t launch_roles_t(const HopArgs& a, int emode, bool dot, cudaStream_t st) {
-    dim3 grid((unsigned)((a.V + kRoleSites - 1) / kRoleSites), (unsigned)a.nsrc, 1);
-    dim3 block(4 * kRoleSites);
-#define LQ_ROLE(EM, D) k_hop_roles<R, EM, D><<<grid, block, 0, st>>>(a)
+    dim3 grid((unsigned)((a.V + RS - 1) / RS), (unsigned)a.nsrc, 1);
+    dim3 block(4 * RS);
+#define LQ_ROLE(EM, D) k_hop_roles<R, EM, D, RS, MINB><<<grid, block, 0, st>>>(a)
     if (emode == 0) { if (dot) LQ_ROLE(0, true); else LQ_ROLE(0, false); }
     else if (emode == 1) { if (dot) LQ_ROLE(1, true); else LQ_ROLE(1, false); }
     else { if (dot) LQ_ROLE(2, true); else LQ_ROLE(2, false); }
@@ -758,31 +761,48 @@ static cudaError_t launch_roles_t(const HopArgs& a, int emode, bool dot, cudaStr
 
 // Stencil schedules (chosen by the autotuner in the Lanczos driver):
 //   0: one thread per (site, side), registers unconstrained
-//   1: one thread per (site, output field), four roles of a site per block
+//   1: one thread per (site, output field), four roles of 32 sites per block
 //   2: as 0 with at least 5 resident blocks per SM (register cap ~100)
-//   3: as 0 with at least 6 resident blocks per SM (register cap ~84)
+//   3: as 0 with at least 4 resident blocks per SM (register cap 128)
+//   4: as 1 with 64 sites per block and at least 2 resident blocks per SM (FP32)
+//   5: as 1 with at least 5 resident blocks per SM (FP32)
 cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st) {
     const bool lanczos_block = nf == 2 && a.nsides == 2 && a.side0 == 0;
     if (lanczos_block && a.variant == 1)
-        return prec == LQ_FP64 ? launch_roles_t<double>(a, emode, dot, st) : launch_roles_t<float>(a, emode, dot, st);
+        return prec == LQ_FP64 ? launch_roles_t<double, kRoleSites, 1>(a, emode, dot, st)
+                               : launch_roles_t<float, kRoleSites, 1>(a, emode, dot, st);
     if (lanczos_block && prec != LQ_FP64 && a.variant == 2) return launch_hop_t<float, 5>(a, nf, emode, dot, st);
     if (lanczos_block && prec != LQ_FP64 && a.variant == 3) return launch_hop_t<float, 4>(a, nf, emode, dot, st);
+    if (lanczos_block && prec != LQ_FP64 && a.variant == 4) return launch_roles_t<float, 2 * kRoleSites, 2>(a, emode, dot, st);
+    if (lanczos_block && prec != LQ_FP64 && a.variant == 5) return launch_roles_t<float, kRoleSites, 5>(a, emode, dot, st);
     return prec == LQ_FP64 ? launch_hop_t<double, 1>(a, nf, emode, dot, st) : launch_hop_t<float, 1>(a, nf, emode, dot, st);
 }
 
 size_t hop_blocks(const HopArgs& a, int nf) {
-    if (nf == 2 && a.nsides == 2 && a.side0 == 0 && a.variant == 1) return (a.V + kRoleSites - 1) / kRoleSites;
+    if (nf == 2 && a.nsides == 2 && a.side0 == 0 && (a.variant == 1 || a.variant == 5)) return (a.V + kRoleSites - 1) / kRoleSites;
+    if (nf == 2 && a.nsides == 2 && a.side0 == 0 && a.variant == 4) return (a.V + 2 * kRoleSites - 1) / (2 * kRoleSites);
     return (a.V + kHopThreads - 1) / kHopThreads;
 }
 
-unsigned update_grid(size_t nelem) {
-    size_t b = (nelem + kUpdThreads - 1) / kUpdThreads;
-    size_t cap = kUpdBlocksPerSrc;
-    return (unsigned)(b < cap ? (b > 0 ? b : 1) : cap);
+// Blocks per source of the grid-stride update: enough for exactly one resident wave over all
+// sources (no partial last wave), at most one per 256 chunks and at most `cap` (the partials).
+unsigned update_grid(size_t nelem, int nsrc, size_t cap) {
+    static int resident = 0;   // blocks of k_update<float> resident on the whole GPU
+    if (resident == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        cudaGetDevice(&dev);
+        cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_update<float>, kUpdThreads, 0);
+        resident = std::max(1, sms * std::max(1, per_sm));
+    }
+    size_t b = std::max(1, resident / std::max(1, nsrc));
+    b = std::min(b, std::max<size_t>(1, (nelem + kUpdThreads - 1) / kUpdThreads));
+    b = std::min(b, std::max<size_t>(1, cap));
+    return (unsigned)b;
 }
 
 cudaError_t launch_update(int prec, const UpdArgs& a, cudaStream_t st) {
-    dim3 grid(update_grid(a.nelem), (unsigned)a.nsrc);
+    dim3 grid(update_grid(a.nelem, a.nsrc, a.partial_stride), (unsigned)a.nsrc);
     if (prec == LQ_FP64) k_update<double><<<grid, kUpdThreads, 0, st>>>(a);
     else k_update<float><<<grid, kUpdThreads, 0, st>>>(a);
     return cudaGetLastError();

@@ -10,7 +10,6 @@ namespace lq {
 constexpr int kHopThreads = 128;
 constexpr int kUpdThreads = 256;
 constexpr int kRecThreads = 128;
-constexpr int kUpdBlocksPerSrc = 64;       // grid-stride update kernel: ~30 chunks per thread at 14^4
 
 // Arguments of the stencil kernel k_hop (Eq. (1.1), block operator of Eq. (2.5)).
 struct HopArgs {
@@ -19,7 +18,7 @@ struct HopArgs {
     size_t V;
     int apbc;
     int nsrc, nsides;
-    int side0;             // side of blockIdx.z == 0 (0 = right / A, 1 = left / A^dag)
+    int side0;             // side of blockIdx.y == 0 (0 = right / A, 1 = left / A^dag)
     int variant;           // 0: one thread per (site, side); 1: one thread per (site, output field)
     double diag;           // 4r + m_w
     // hop factors, including the -1/2 of Dw: [side][direction]
@@ -101,7 +100,7 @@ cudaError_t launch_to_internal(int prec, const double* x, void* f, size_t V, int
 cudaError_t launch_to_boundary(int prec, const void* f, double* x, size_t V, int nfields, cudaStream_t st);
 cudaError_t launch_links_internal(int prec, const double* U, void* L, size_t V, cudaStream_t st);
 cudaError_t launch_direction(int prec, const double* U, const double* w, int kind, void* Y, size_t V, cudaStream_t st);
-unsigned update_grid(size_t nelem);
+unsigned update_grid(size_t nelem, int nsrc, size_t cap);
 // Deflation vector algebra on FP64 boundary-layout vectors (lq_deflate.cu).  Sizes and strides
 // are in doubles (2 per complex number).
 cudaError_t launch_bdots(const double* X, size_t xs, int nx, const double* Y, size_t ys, int ny, size_t n,

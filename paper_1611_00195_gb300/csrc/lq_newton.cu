@@ -350,12 +350,18 @@ __device__ __forceinline__ void tri_solve(const double2* __restrict__ al, const 
     }
     double2 x1 = cmul(cx, recip(cd)), x2 = make_double2(0.0, 0.0);
     sx[(size_t)(n - 1) * ld] = cscale(x1, w);
+    if (n < 2) return;
+    // back substitution, the next row's factors loaded one row ahead (they do not depend on x)
+    size_t o = (size_t)(n - 2) * ld;
+    double2 px = sx[o], p1 = s1[o], p2 = s2[o], pd = sd[o];
     for (int i = n - 2; i >= 0; --i) {
-        const size_t o = (size_t)i * ld;
-        double2 v = csub(sx[o], cmul(s1[o], x1));
-        v = csub(v, cmul(s2[o], x2));
-        v = cmul(v, sd[o]);
-        sx[o] = cscale(v, w);
+        const double2 cxr = px, c1 = p1, c2 = p2, cdr = pd;
+        const size_t oi = o;
+        if (i > 0) { o -= ld; px = sx[o]; p1 = s1[o]; p2 = s2[o]; pd = sd[o]; }
+        double2 v = csub(cxr, cmul(c1, x1));
+        v = csub(v, cmul(c2, x2));
+        v = cmul(v, cdr);
+        sx[oi] = cscale(v, w);
         x2 = x1;
         x1 = v;
     }
@@ -450,10 +456,11 @@ __global__ void __launch_bounds__(kQuadFinish) k_quad_finish(QuadArgs a, int pas
 // decays like exp(-4 N atanh(min(|lambda|/c, c/|lambda|))), so c is placed at the geometric
 // centre of the spectrum.  lambda_hi: ||T x|| after six power-iteration steps; lambda_lo:
 // 1 / ||T^{-1} x|| after six inverse-iteration steps (tridiagonal solves).  Only the scale
-// matters (a factor 2 costs little), so a few steps suffice.  One thread per source, in the
+// matters (a factor 2 costs little), so a few steps suffice.  One block (one working thread) per source, in the
 // first column of the quadrature workspace.
 __global__ void k_quad_scale(QuadArgs a) {
-    const int src = blockIdx.x * blockDim.x + threadIdx.x;
+    const int src = blockIdx.x;              // one source per block (spread over the SMs)
+    if (threadIdx.x != 0) return;
     if (src >= a.nb) return;
     const int n = a.state[src].k_eff;
     if (n <= 0) { a.c[src] = 1.0; return; }
@@ -508,7 +515,8 @@ __global__ void k_quad_scale(QuadArgs a) {
 // approximation of (sigma - A)^{-1} b (Sec. 2 applied to f(a) = 1/(sigma - a)).  One thread per
 // source; rows beyond k_eff are zero.
 __global__ void k_proj_resolvent(QuadArgs a, const double2* __restrict__ shifts) {
-    const int src = blockIdx.x * blockDim.x + threadIdx.x;
+    const int src = blockIdx.x;              // one source per block (spread over the SMs)
+    if (threadIdx.x != 0) return;
     if (src >= a.nb) return;
     const int n = a.state[src].k_eff;
     double2* out = a.s + (size_t)src * a.kmax;
@@ -530,7 +538,7 @@ __global__ void k_proj_resolvent(QuadArgs a, const double2* __restrict__ shifts)
 }
 
 cudaError_t proj_resolvent(const QuadArgs& a, const double2* shifts, cudaStream_t st) {
-    k_proj_resolvent<<<(a.nb + 31) / 32, 32, 0, st>>>(a, shifts);
+    k_proj_resolvent<<<a.nb, 32, 0, st>>>(a, shifts);
     return cudaGetLastError();
 }
 
@@ -545,7 +553,7 @@ __global__ void k_nt_first_column(NewtonArgs a, double2* __restrict__ out, int l
 cudaError_t quad_sign_e1(const QuadArgs& a, int max_nodes, bool scale, cudaStream_t st) {
     if (max_nodes < 1 || 2 * max_nodes > a.nth_max || (2 * max_nodes + kQuadBlk - 1) / kQuadBlk > a.part_blocks)
         return cudaErrorInvalidValue;
-    if (scale) k_quad_scale<<<(a.nb + 31) / 32, 32, 0, st>>>(a);
+    if (scale) k_quad_scale<<<a.nb, 32, 0, st>>>(a);
     const dim3 grid((unsigned)((2 * max_nodes + kQuadBlk - 1) / kQuadBlk), (unsigned)a.nb);
     for (int pass = 0; pass < 2; ++pass) {
         k_quad_solve<<<grid, kQuadBlk, 0, st>>>(a, pass);

@@ -83,16 +83,19 @@ def test_eigen_derivatives_parity(lqlib):
 def test_derivative_generalised_deflation(lqlib):
     """Eqs. (3.2)-(3.4) on the GPU against the oracle's generalised deflation driven by the same
     eigenvector derivatives (those the GPU computed), so that the comparison isolates the
-    deflation and the block Lanczos process; the tolerance scales with the oracle's own
-    rounding sensitivity at this depth.  Deflation must also beat no deflation against the
-    exact derivative."""
+    deflation and the block Lanczos process.  Parity is taken at k = 60, where the process is
+    still far from the dimension of the problem (768) and the oracle's own rounding
+    sensitivity is small; the tolerance scales with that sensitivity (the largest of three
+    1e-16 input perturbations).  At k = 300 deflation must beat no deflation against the exact
+    derivative."""
     from paper_1611_00195_gb300 import lq
-    dims, k = (4, 2, 2, 2), 300
+    dims, k, kp = (4, 2, 2, 2), 300, 60
     c, U, lat, A, lam, R, L, x = _setup(lq, dims, LP, k)
     xs_d = torch.from_numpy(x).cuda()
+    ysp, ydp, _ = c.sign_derivative_apply(xs_d, kp, deflate=1, defl_nderiv=LD)
     ys, yd, rep = c.sign_derivative_apply(xs_d, k, deflate=1, defl_nderiv=LD)
     ys0, yd0, _ = c.sign_derivative_apply(xs_d, k, deflate=0)
-    ys, yd, ys0, yd0 = (t.cpu().numpy() for t in (ys, yd, ys0, yd0))
+    ysp, ydp, ys, yd, ys0, yd0 = (t.cpu().numpy() for t in (ysp, ydp, ys, yd, ys0, yd0))
     dlam, dR, dLk = c.deflation_derivatives(k, kind=lq.LQ_DIR_MU, defl_nderiv=LD)
     gR = dR.reshape(LP, -1).T[:, :LD]
     gL = dLk.reshape(LP, -1).conj()[:LD]
@@ -103,19 +106,20 @@ def test_derivative_generalised_deflation(lqlib):
     rng = np.random.default_rng(7)
 
     def blk(v):
-        t, b, _ = ot.tsl_sign_block(Ao, Aho, Eo, Eho, v[:n], v[n:], k)
+        t, b, _ = ot.tsl_sign_block(Ao, Aho, Eo, Eho, v[:n], v[n:], kp)
         return np.concatenate([t, b])
     for s in range(x.shape[0]):
         psi = np.concatenate([np.zeros(n), x[s].ravel()])
         ref = odf.sign_block_deflated(blk, lam[:LD], R[:, :LD], L[:LD], gR, gL, psi)
-        psip = psi * (1 + 1e-16 * rng.standard_normal(psi.shape))
-        refp = odf.sign_block_deflated(blk, lam[:LD], R[:, :LD], L[:LD], gR, gL, psip)
-        sens = relerr(refp, ref)
+        sens = 0.0
+        for _ in range(3):
+            psip = psi * (1 + 1e-16 * rng.standard_normal(psi.shape))
+            sens = max(sens, relerr(odf.sign_block_deflated(blk, lam[:LD], R[:, :LD], L[:LD], gR, gL, psip), ref))
+        pd, ps = relerr(ydp[s], ref[:n]), relerr(ysp[s], ref[n:])
         ex = SB @ psi
-        pd, ps = relerr(yd[s], ref[:n]), relerr(ys[s], ref[n:])
         ed, ed0 = relerr(yd[s], ex[:n]), relerr(yd0[s], ex[:n])
-        print("deflated derivative k=%d (%d Jordan blocks): parity deriv %.3g sign %.3g (oracle self-sensitivity "
-              "%.3g); deriv error vs exact %.3g (undeflated %.3g)" % (k, LD, pd, ps, sens, ed, ed0))
+        print("deflated derivative (%d Jordan blocks): parity at k=%d deriv %.3g sign %.3g (oracle self-sensitivity "
+              "%.3g); at k=%d deriv error vs exact %.3g (undeflated %.3g)" % (LD, kp, pd, ps, sens, k, ed, ed0))
         assert pd < max(1e-10, 30 * sens) and ps < max(1e-10, 30 * sens)
         assert ed < 0.1 * ed0
 

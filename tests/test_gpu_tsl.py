@@ -110,6 +110,44 @@ def test_sign_derivative_fp64_parity(lqlib, dims, k, nsrc, kind, variant):
         assert ed < _parity_tol(sens)
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5])
+def test_sign_derivative_mixed_schedules(lqlib, variant):
+    """Every FP32 stencil schedule of the block TSL step (lq_opts.hop_variant) against the FP64
+    oracle at the same depth.  FP32 arithmetic and storage perturb every step by about 6e-8
+    (relative), so the bound scales with the oracle's own response to a 6e-8 relative random
+    perturbation of every operator application (the FP32 analogue of the FP64 bound above).
+    All schedules must also agree with each other to FP32 rounding."""
+    from paper_1611_00195_gb300 import lq
+    dims, k, mu = (6, 3, 5, 2), 40, 0.3
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = syn.gaussian_source(dims, 5, nsrc=2)
+    c = lq.Context(dims, mu=mu, precision=lq.LQ_MIXED)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(k, 2, True)
+    ys, yd, rep = c.sign_derivative_apply(torch.from_numpy(x).cuda(), k, hop_variant=variant)
+    ys, yd = ys.cpu().numpy(), yd.cpu().numpy()
+    lat, A, Ah, E, Eh = oracle_ops(dims, U, mu)
+    rng = np.random.default_rng(11)
+
+    def pert(op):
+        return lambda v: (lambda y: y * (1 + 6e-8 * (rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape))
+                                         / np.sqrt(2)))(op(v))
+    for s in range(2):
+        assert rep[s]["status"] == 0 and rep[s]["hop_variant"] == variant
+        rd, rs, _ = ot.tsl_sign_derivative(A, Ah, E, Eh, x[s], k)
+        sens = 0.0
+        for _ in range(2):
+            rdp, rsp, _ = ot.tsl_sign_derivative(pert(A), pert(Ah), pert(E), pert(Eh), x[s], k)
+            sens = max(sens, relerr(rdp, rd), relerr(rsp, rs))
+        es, ed = relerr(ys[s], rs), relerr(yd[s], rd)
+        print("schedule %d mixed vs oracle k=%d: sign %.3g deriv %.3g (oracle FP32-size sensitivity %.3g)"
+              % (variant, k, es, ed, sens))
+        assert es < max(1e-6, 30 * sens) and ed < max(1e-6, 30 * sens)
+    if variant > 0:
+        y0s, y0d, _ = c.sign_derivative_apply(torch.from_numpy(x).cuda(), k, hop_variant=0)
+        assert relerr(ys, y0s.cpu().numpy()) < 1e-5 and relerr(yd, y0d.cpu().numpy()) < 1e-4
+
+
 def test_mixed_converges_to_exact(lqlib):
     """Mixed path (FP32 stencil and vectors; FP64 dots, coefficients and Newton) against the
     exact dense sign and Frechet derivative of the oracle, at a depth where the FP64 method
