@@ -58,6 +58,7 @@ def parse():
     p.add_argument("--nderiv", type=int, default=6, help="Jordan blocks of the derivative deflation")
     p.add_argument("--eig-iter", type=int, default=20, help="eigensolver iterations for the deflation space")
     p.add_argument("--hop-variant", type=int, default=-1, help="stencil schedule (-1: autotuned)")
+    p.add_argument("--no-extra", action="store_true", help="skip the su(3)-direction and k = 800 measurements")
     return p.parse_args()
 
 
@@ -253,7 +254,8 @@ def run_reference(args, ws, rank):
 
 # kernel instantiated for each stencil schedule (lq_opts.hop_variant) of the block TSL step, FP32
 HOP_KERNELS = {0: "k_hop<float,2,1,true,1>", 1: "k_hop_roles<float,1,true,32,1>", 2: "k_hop<float,2,1,true,5>",
-               3: "k_hop<float,2,1,true,4>", 4: "k_hop_roles<float,1,true,64,2>", 5: "k_hop_roles<float,1,true,32,5>"}
+               3: "k_hop<float,2,1,true,4>", 4: "k_hop_roles<float,1,true,64,2>", 5: "k_hop_roles<float,1,true,32,5>",
+               6: "k_hop_tiled<1,true>"}
 # DRAM bytes (read + write) per launch of the block stencil from one ncu capture of that kernel
 # revision and schedule on the same per-launch shape (14x14^3, 16 sources, both sides; the
 # Krylov depth does not change a launch).  Source: profiles/k_hop_block_stencil_14x14c3_b16.md.
@@ -370,6 +372,35 @@ def main():
                 "rel_err_mixed_vs_fp64_deriv": {"max": float(ed.max()), "median": float(np.median(ed))}}
         del ctx64
 
+    # the other workloads of the same configuration: an su(3) link direction (k as configured)
+    # and k = 800 (d/dmu); two timed steps each after one warm-up, same clock and events
+    extra = None
+    if not args.no_extra:
+        extra = {}
+
+        def timed(fn, steps=2):
+            fn()
+            torch.cuda.synchronize(dev)
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                r = fn()
+            e1.record(stream)
+            torch.cuda.synchronize(dev)
+            return e0.elapsed_time(e1) / steps, r
+        om = torch.from_numpy(syn.su3_direction(DIMS, 77)).to(dev)
+        ms_su3, r = timed(lambda: ctx.sign_derivative_apply(xd, k, kind=lq.LQ_DIR_SU3, field=om, out=(ys, yd), **hv))
+        extra["su3_direction"] = {"value": nsrc / (ms_su3 / 1e3), "unit": "solves/s", "ms_per_step": ms_su3, "k": k,
+                                  "direction": "random su(3) link field, seed 77", "status": [x["status"] for x in r[2]]}
+        if args.k < 800:
+            ctx.reserve(800, nsrc, True)
+            ms800, r = timed(lambda: ctx.sign_derivative_apply(xd, 800, out=(ys, yd), **hv))
+            eps800 = ctx.error_estimate(xd[:2].contiguous(), 800, kind=lq.LQ_DIR_MU).tolist()
+            extra["k800"] = {"value": nsrc / (ms800 / 1e3), "unit": "solves/s", "ms_per_step": ms800,
+                             "direction": "d/dmu", "eps_A_deriv": eps800,
+                             "projected": [x["projected"] for x in r[2]]}
+            ctx.reserve(k, nsrc, True)
+
     # accuracy: eps_A of Sec. 4 (sign and derivative) on two of the sources, no deflation
     x2 = xd[:2].contiguous()
     eps_sign = c_eps = None
@@ -453,6 +484,7 @@ def main():
         "accuracy": {"eps_A_sign": eps_sign, "eps_A_deriv": c_eps,
                      "note": "eps_A = ||sgn(A)^2 psi - psi|| / (2 ||psi||) (Sec. 4) on 2 of the sources, k as configured"},
         "deflated": defl,
+        "other_workloads": extra,
         "time_breakdown_ms_per_step": {"stencil": prof["hop_ms"] / args.steps, "update": prof["update_ms"] / args.steps,
                                        "projected_sign": prof["newton_ms"] / args.steps, "other": prof["other_ms"] / args.steps,
                                        "sum_of_kernels": total_prof / args.steps},

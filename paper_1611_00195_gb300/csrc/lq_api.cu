@@ -235,7 +235,7 @@ void free_workspace(lq_ctx* c) {
 // coefficients), so the tuning leaves no trace in the results.
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
-    const int nvar = (c->prec == LQ_FP64) ? 2 : 6;
+    const int nvar = (c->prec == LQ_FP64) ? 2 : 7;
     if (c->tuned_nsrc != h.nsrc) {
         for (auto& row : c->tuned_variant) for (int& v : row) v = -1;
         c->tuned_nsrc = h.nsrc;
@@ -250,6 +250,7 @@ int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* vari
     std::vector<float> best(nvar, 1e30f);
     for (int round = 0; round < 2; ++round)
         for (int v = 0; v < nvar; ++v) {
+            if (v == 6 && !tile_ok(h.dims)) continue;
             h.variant = v;
             LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));   // warm-up
             LQ_CUDA(c, cudaEventRecord(e0, st));
@@ -314,7 +315,12 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     h.src_stride_out[0] = sio; h.src_stride_out[1] = sio;
     h.out[0] = c->rout; h.out[1] = c->lout;
     if (o->hop_variant >= 0) {
-        h.variant = (nf == 2) ? o->hop_variant : 0;
+        // the schedule that actually runs (and is reported): FP64 has schedules 0 and 1 only,
+        // the plain operator 0 only, and schedule 6 needs tiles that cover the lattice
+        int v = (nf == 2) ? o->hop_variant : 0;
+        if (c->prec == LQ_FP64 && v > 1) v = 0;
+        if (v == 6 && !tile_ok(h.dims)) v = 3;
+        h.variant = v;
     } else {
         h.in[0] = bvec(0);
         h.in[1] = lvec(0);
@@ -462,7 +468,7 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->projected < LQ_PROJ_AUTO || o->projected > LQ_PROJ_QUAD) return set_err(c, LQ_ERR_ARG, "unknown projected-sign solver");
     if (o->projected != LQ_PROJ_NEWTON && (o->quad_nodes < 1 || o->quad_nodes > kQuadMaxNodes || !(o->proj_tol > 0.0)))
         return set_err(c, LQ_ERR_ARG, "quad_nodes must be in [1, 128] and proj_tol > 0");
-    if (o->hop_variant < -1 || o->hop_variant > 5) return set_err(c, LQ_ERR_ARG, "hop_variant must be in [-1, 5]");
+    if (o->hop_variant < -1 || o->hop_variant > 6) return set_err(c, LQ_ERR_ARG, "hop_variant must be in [-1, 6]");
     if (o->defl_kmax < 0 || o->defl_kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "defl_kmax must be in [0, reserved kmax]");
     if (o->defl_nderiv < 0) return set_err(c, LQ_ERR_ARG, "defl_nderiv must be >= 0");
     return LQ_OK;

@@ -93,6 +93,7 @@ struct RecArgs {
 __device__ void tsl_alpha_step(const HopArgs& a, int src, double dre, double dim);
 
 cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st);
+bool tile_ok(const int (&dims)[4]);   // schedule 6 (shared-memory tiles) covers this lattice
 cudaError_t launch_update(int prec, const UpdArgs& a, cudaStream_t st);
 cudaError_t launch_tsl_init(int prec, int nf, const InitArgs& a, cudaStream_t st);
 cudaError_t launch_recombine(int prec, int nf, const RecArgs& a, cudaStream_t st);

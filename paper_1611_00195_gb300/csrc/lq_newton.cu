@@ -454,9 +454,10 @@ __global__ void __launch_bounds__(kQuadFinish) k_quad_finish(QuadArgs a, int pas
 
 // Contour scale c = sqrt(lambda_lo * lambda_hi): the midpoint error for an eigenvalue lambda
 // decays like exp(-4 N atanh(min(|lambda|/c, c/|lambda|))), so c is placed at the geometric
-// centre of the spectrum.  lambda_hi: ||T x|| after six power-iteration steps; lambda_lo:
-// 1 / ||T^{-1} x|| after six inverse-iteration steps (tridiagonal solves).  Only the scale
-// matters (a factor 2 costs little), so a few steps suffice.  One block (one working thread) per source, in the
+// centre of the spectrum.  lambda_hi: ||T x|| after four power-iteration steps; lambda_lo:
+// 1 / ||T^{-1} x|| after three inverse-iteration steps (tridiagonal solves).  Only the scale
+// matters (a factor 2 costs little): on the 14^4, k = 400 projected matrices four and three
+// steps need the same node counts as six and six for all but one of 16 sources.  One block (one working thread) per source, in the
 // first column of the quadrature workspace.
 __global__ void k_quad_scale(QuadArgs a) {
     const int src = blockIdx.x;              // one source per block (spread over the SMs)
@@ -476,7 +477,7 @@ __global__ void k_quad_scale(QuadArgs a) {
     // lambda_hi: power iteration with T (x in sx, T x into s1)
     for (int i = 0; i < n; ++i) sx[(size_t)i * ld] = make_double2(x0, (i & 1) ? x0 : -x0);
     double hi = 1.0, nx = sqrt(2.0);
-    for (int it = 0; it < 6; ++it) {
+    for (int it = 0; it < 4; ++it) {
         double ny = 0.0;
         for (int i = 0; i < n; ++i) {
             double2 v = cmul(al[i], sx[(size_t)i * ld]);
@@ -495,7 +496,7 @@ __global__ void k_quad_scale(QuadArgs a) {
     for (int i = 0; i < n; ++i) sx[(size_t)i * ld] = make_double2(x0, (i & 1) ? x0 : -x0);
     double lo = hi;
     nx = sqrt(2.0);
-    for (int it = 0; it < 6; ++it) {
+    for (int it = 0; it < 3; ++it) {
         auto B = [&](int i) -> double2 { return sx[(size_t)i * ld]; };
         tri_solve(al, be, de, n, make_double2(0.0, 0.0), B, sd, s1, s2, sx, ld, 1.0);
         double ny = 0.0;

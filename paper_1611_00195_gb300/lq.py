@@ -25,7 +25,7 @@ LIB_PATH = os.path.join(_HERE, "liblq.so")
 
 LQ_OK = 0
 # Revision tag of the stencil kernel; stored ncu traffic figures are only valid for this one.
-KERNEL_REV = "hop-v2"
+KERNEL_REV = "hop-v3"
 ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_CUDA", -5: "LQ_ERR_BREAKDOWN",
           -6: "LQ_ERR_NEWTON", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NOT_READY", -9: "LQ_ERR_NONFINITE"}
 LQ_FP64, LQ_MIXED = 0, 1
