@@ -260,7 +260,7 @@ HOP_KERNELS = {0: "k_hop<float,2,1,true,1>", 1: "k_hop_roles<float,1,true,32,1>"
 # revision and schedule on the same per-launch shape (14x14^3, 16 sources, both sides; the
 # Krylov depth does not change a launch).  Source: profiles/k_hop_block_stencil_14x14c3_b16.md.
 # Keyed by (kernel revision, schedule, V, sources); anything else reports traffic = null.
-HOP_TRAFFIC = {("hop-v2", 3, 38416, 16): 598750720, ("hop-v2", 1, 38416, 16): 461046784}
+HOP_TRAFFIC = {("hop-v3", 3, 38416, 16): 467833856}
 
 
 def main():

@@ -106,8 +106,8 @@ typedef struct {
  *  LQ_PROJ_QUAD    midpoint quadrature of sgn(T) = (2/pi) T int_0^inf (t^2 + T^2)^{-1} dt
  *                  with t = c tan(theta): 2N complex tridiagonal solves (FP64, O(N k));
  *  LQ_PROJ_AUTO    the quadrature, accepted per source only if its involution residual
- *                  ||Q(T) Q(T) e_1 - e_1|| <= proj_tol; a failing source is retried with
- *                  twice the nodes, up to 512, and only what still fails goes to Newton.  */
+ *                  ||Q(T) Q(T) e_1 - e_1|| <= proj_tol; a failing source is retried once
+ *                  with 512 nodes, and only what still fails goes to Newton.             */
 #define LQ_PROJ_AUTO    0
 #define LQ_PROJ_NEWTON  1
 #define LQ_PROJ_QUAD    2

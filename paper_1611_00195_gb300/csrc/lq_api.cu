@@ -379,8 +379,10 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
         qa.s = c->proj_c; qa.q = c->quad_q; qa.check = c->quad_check; qa.nodes = c->quad_nodes;
         qa.nth_max = 2 * kQuadRetryMaxNodes; qa.part = c->quad_part; qa.part_blocks = 2 * kQuadRetryMaxNodes / kQuadBlk;
         // LQ_PROJ_QUAD: one pass with opts.quad_nodes.  LQ_PROJ_AUTO: a source whose involution
-        // residual exceeds proj_tol is retried with twice the nodes (up to kQuadRetryMaxNodes),
-        // the others keep their result; what still fails goes to the Newton iteration below.
+        // residual exceeds proj_tol is retried once with kQuadRetryMaxNodes nodes (a pass costs
+        // the latency of one sequential tridiagonal solve whatever the node count, so one large
+        // retry beats a ladder of doublings); the others keep their result; what still fails
+        // goes to the Newton iteration below.
         std::vector<int> nodes(nsrc, o->quad_nodes);
         bool ok = false;
         for (int attempt = 0;; ++attempt) {
@@ -398,7 +400,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
                 const bool pass = std::isfinite(check[s]) && check[s] <= o->proj_tol;
                 ok = ok && pass;
                 if (pass || nodes[s] == 0) { nodes[s] = 0; continue; }
-                if (o->projected == LQ_PROJ_AUTO && 2 * nodes[s] <= kQuadRetryMaxNodes) { nodes[s] *= 2; retry = true; }
+                if (o->projected == LQ_PROJ_AUTO && nodes[s] < kQuadRetryMaxNodes) { nodes[s] = kQuadRetryMaxNodes; retry = true; }
                 else nodes[s] = 0;
             }
             if (ok || !retry) break;

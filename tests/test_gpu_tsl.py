@@ -229,9 +229,9 @@ def test_projected_auto_falls_back_to_newton(lqlib):
 
 
 def test_projected_auto_node_ladder(lqlib):
-    """A quadrature started far too coarse (2 nodes) must be retried with doubled nodes until
-    its involution residual passes, per source, without the Newton fallback, and then agree
-    with the Newton iteration."""
+    """A quadrature started far too coarse (2 nodes) must be retried with the large node count
+    until its involution residual passes, per source, without the Newton fallback, and then
+    agree with the Newton iteration."""
     from paper_1611_00195_gb300 import lq
     dims, k, mu = (4, 4, 4, 4), 64, 0.3
     U = syn.gauge_field(dims, 0.4, 3)
