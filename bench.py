@@ -223,6 +223,17 @@ def allmax(ws, v):
     return float(t.item())
 
 
+def whole_job_rate(nsrc_per_rank, steps, ws, ms_max):
+    """Solves per second of the whole job: every rank solves nsrc_per_rank sources per step
+    (replicas, weak scaling) and the job takes the slowest rank's time ms_max."""
+    return nsrc_per_rank * steps * ws / (ms_max / 1e3)
+
+
+def rank_sources(rank):
+    """Seed of each rank's batch of sources: replicas solve different sources."""
+    return SOURCE_SEED + rank
+
+
 def run_reference(args, ws, rank):
     """The CPU oracle as it stands on the host cores: each step is a bounded sample (a few
     block-TSL iterations of one source), scaled to one derivative solve at depth k."""
@@ -283,7 +294,7 @@ def main():
     n = 12 * V
 
     U = syn.gauge_field(DIMS, EPS, GAUGE_SEED)
-    x = syn.gaussian_source(DIMS, SOURCE_SEED + rank, nsrc=nsrc)
+    x = syn.gaussian_source(DIMS, rank_sources(rank), nsrc=nsrc)
     xd = torch.from_numpy(x).to(dev)
     ctx = lq.Context(DIMS, m_w=M_W, mu=MU, precision=lq.LQ_MIXED)
     ctx.upload_gauge(torch.from_numpy(U).to(dev))
@@ -316,7 +327,7 @@ def main():
     prof = ctx.profile()
     ms_local = ev0.elapsed_time(ev1)
     ms = allmax(ws, ms_local)
-    value = nsrc * args.steps * ws / (ms / 1e3)
+    value = whole_job_rate(nsrc, args.steps, ws, ms)
 
     # roofline of the dominant kernel: the fused block stencil (right: B v, left: B^dag w)
     hop_ms = prof["hop_ms"] / max(1, prof["hop_launches"])
