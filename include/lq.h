@@ -99,6 +99,12 @@ typedef struct {
                               uploaded pairs (0 = all); the shifted solves still project out all
                               uploaded pairs (the paper deflates the derivative with fewer pairs
                               than the sign, Sec. 4)                                           */
+    int two_pass;          /* 1: two passes over the Krylov process with O(n) memory instead of
+                              O(k n): the first keeps a ring of basis vectors and yields T_k,
+                              the second reruns the (deterministic) process and recombines
+                              windows of 16 vectors as they appear; twice the operator work.
+                              Required for kmax beyond the ring of a LQ_RESERVE_TWO_PASS
+                              workspace; not available to lq_sign_bilinear_grad (default 0) */
 } lq_opts;
 
 /* Projected step sgn(T_k) e_1 (Sec. 2):
@@ -149,9 +155,12 @@ int  lq_set_mu(lq_ctx* ctx, double mu);
 /* Reserve all workspace for Krylov depth <= kmax and <= nsrc sources per call.  flags:
  * LQ_RESERVE_BLOCK for the derivative path (2n-dimensional block vectors of Eq. (2.6)),
  * LQ_RESERVE_ADJOINT for lq_sign_bilinear_grad (stored left basis, nsrc >= 2); 0 for the sign
- * path only.  No later solve call allocates device memory.  LQ_ERR_OOM on failure. */
+ * path only.  LQ_RESERVE_TWO_PASS keeps a ring of 32 basis vectors per source instead of kmax
+ * (runs deeper than 32 then need lq_opts.two_pass = 1; not with LQ_RESERVE_ADJOINT).  No later
+ * solve call allocates device memory.  LQ_ERR_OOM on failure. */
 #define LQ_RESERVE_BLOCK    1
 #define LQ_RESERVE_ADJOINT  2
+#define LQ_RESERVE_TWO_PASS 4
 int  lq_reserve(lq_ctx* ctx, int kmax, int nsrc, int flags);
 
 /* y = H(mu) x (dagger = 0) or y = H(mu)^dag x = H(-mu) x (dagger = 1) for nsrc fields

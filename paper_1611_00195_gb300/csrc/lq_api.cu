@@ -224,7 +224,7 @@ void free_workspace(lq_ctx* c) {
                    &c->lbasis, (void**)&c->uscale, (void**)&c->adj_coef, &c->adj_nu, &c->adj_om,
                    (void**)&c->adj_force, (void**)&c->adj_dmu, (void**)&c->gen_scr};
     for (void** p : ps) { dfree(*p); *p = nullptr; }
-    c->kmax = c->nsrc = c->block = 0;
+    c->kmax = c->nsrc = c->block = c->ring = 0;
     c->adjoint = false;
 }
 
@@ -282,13 +282,19 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     const int k = o->kmax;
     const size_t F = fe(c);
     const size_t vstride = (size_t)nf * F;        // Chunk elements per Krylov vector
-    const size_t sb = (size_t)c->kmax * vstride;  // per source: basis
+    const int slots = c->ring > 0 ? c->ring : c->kmax;   // basis vectors held per source
+    const size_t sb = (size_t)slots * vstride;    // per source: basis
     const size_t sl = 3 * vstride;                // per source: left ring
     const size_t sio = vstride;                   // per source: operator outputs
     const size_t cb = chunk_bytes(c);
+    // Two-pass run (lq_opts.two_pass): the first pass keeps only a ring of basis vectors and
+    // yields T_k; the second reruns the same (deterministic) process and recombines windows of
+    // kTwoPassWindow vectors into y while they are still in the ring.
+    const bool two = o->two_pass != 0 && k > 1;
+    const int ring = two ? std::min(slots, kTwoPassRing) : 0;
     char* basis = reinterpret_cast<char*>(c->basis);
     char* left = reinterpret_cast<char*>(c->left);
-    auto bvec = [&](int j) -> void* { return basis + (size_t)j * vstride * cb; };
+    auto bvec = [&](int j) -> void* { return basis + (size_t)(ring ? j % ring : j) * vstride * cb; };
     auto lvec = [&](int j) -> void* { return left + (size_t)(j % 3) * vstride * cb; };
 
     InitArgs ia;
@@ -299,10 +305,15 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     ia.breakdown_tol = o->breakdown_tol;
     const size_t sst = (size_t)c->kmax * F;   // per source: stored left basis (NF = 1)
     if (store_left) { ia.w1_store = c->lbasis; ia.src_stride_store = sst; }
-    cudaEvent_t e0 = prof_begin(c, st);
-    LQ_CUDA(c, launch_tsl_init(c->prec, nf, ia, st));
-    prof_end(c, PC_OTHER, e0, st);
-    c->launches += 1;
+    auto init = [&]() -> int {
+        cudaEvent_t e0 = prof_begin(c, st);
+        LQ_CUDA(c, launch_tsl_init(c->prec, nf, ia, st));
+        prof_end(c, PC_OTHER, e0, st);
+        c->launches += 1;
+        return LQ_OK;
+    };
+    int r0 = init();
+    if (r0) return r0;
 
     HopArgs h = base_hop(c);
     h.nsrc = nsrc; h.nsides = 2; h.side0 = 0;
@@ -337,25 +348,52 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     u.state = c->state; u.partials = c->partials; u.partial_stride = c->partial_blocks; u.counters = c->counters;
     u.beta = c->beta; u.delta = c->delta; u.kmax = c->kmax;
 
-    for (int j = 0; j < k; ++j) {
-        h.j = j;
-        h.in[0] = bvec(j);
-        h.in[1] = lvec(j);
-        cudaEvent_t eh = prof_begin(c, st);
-        LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));
-        prof_end(c, PC_HOP, eh, st);
+    RecArgs ra;
+    std::memset(&ra, 0, sizeof(ra));
+    ra.V = c->V; ra.nsrc = nsrc; ra.basis = c->basis; ra.src_stride_basis = sb; ra.vec_stride = vstride;
+    ra.state = c->state; ra.scale = c->scale; ra.kmax = c->kmax; ra.coef = c->proj_c;
+    ra.y0 = y0; ra.y1 = y1; ra.ring = ring;
+    auto recombine = [&](int j0, int j1) -> int {   // y (+)= |x| sum_{j0 <= j < j1} c_j s_j vh_j
+        ra.j0 = j0; ra.j1 = j1; ra.accumulate = j0 > 0 ? 1 : 0;
+        cudaEvent_t er = prof_begin(c, st);
+        LQ_CUDA(c, launch_recombine(c->prec, nf, ra, st));
+        prof_end(c, PC_OTHER, er, st);
         c->launches += 1;
-        if (j < k - 1) {
-            u.j = j;
-            u.v_cur = bvec(j); u.v_prev = bvec(j > 0 ? j - 1 : j); u.v_next = bvec(j + 1);
-            u.w_cur = lvec(j); u.w_prev = lvec(j > 0 ? j - 1 : j); u.w_next = lvec(j + 1);
-            if (store_left) { u.w_store = reinterpret_cast<char*>(c->lbasis) + (size_t)(j + 1) * F * cb; u.src_stride_store = sst; }
-            cudaEvent_t eu = prof_begin(c, st);
-            LQ_CUDA(c, launch_update(c->prec, u, st));
-            prof_end(c, PC_UPDATE, eu, st);
+        return LQ_OK;
+    };
+
+    // the Lanczos loop; with `windows` the second pass of a two-pass run
+    auto lanczos = [&](bool windows) -> int {
+        int j0 = 0;
+        for (int j = 0; j < k; ++j) {
+            h.j = j;
+            h.in[0] = bvec(j);
+            h.in[1] = lvec(j);
+            cudaEvent_t eh = prof_begin(c, st);
+            LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));
+            prof_end(c, PC_HOP, eh, st);
             c->launches += 1;
+            // vh_0 .. vh_j are in the ring and the update below overwrites slot j + 1
+            if (windows && (j + 1 - j0 == kTwoPassWindow || j == k - 1)) {
+                int rr = recombine(j0, j + 1);
+                if (rr) return rr;
+                j0 = j + 1;
+            }
+            if (j < k - 1) {
+                u.j = j;
+                u.v_cur = bvec(j); u.v_prev = bvec(j > 0 ? j - 1 : j); u.v_next = bvec(j + 1);
+                u.w_cur = lvec(j); u.w_prev = lvec(j > 0 ? j - 1 : j); u.w_next = lvec(j + 1);
+                if (store_left) { u.w_store = reinterpret_cast<char*>(c->lbasis) + (size_t)(j + 1) * F * cb; u.src_stride_store = sst; }
+                cudaEvent_t eu = prof_begin(c, st);
+                LQ_CUDA(c, launch_update(c->prec, u, st));
+                prof_end(c, PC_UPDATE, eu, st);
+                c->launches += 1;
+            }
         }
-    }
+        return LQ_OK;
+    };
+    int rl = lanczos(false);
+    if (rl) return rl;
 
     std::vector<double> scal((size_t)nsrc * 16, 0.0);
     std::vector<double> check(nsrc, 0.0);   // stays 0 when the quadrature is not attempted
@@ -427,15 +465,13 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
         LQ_CUDA(c, cudaStreamSynchronize(st));   // sel is host memory
     }
 
-    RecArgs ra;
-    std::memset(&ra, 0, sizeof(ra));
-    ra.V = c->V; ra.nsrc = nsrc; ra.basis = c->basis; ra.src_stride_basis = sb; ra.vec_stride = vstride;
-    ra.state = c->state; ra.scale = c->scale; ra.kmax = c->kmax; ra.coef = c->proj_c;
-    ra.y0 = y0; ra.y1 = y1;
-    cudaEvent_t er = prof_begin(c, st);
-    LQ_CUDA(c, launch_recombine(c->prec, nf, ra, st));
-    prof_end(c, PC_OTHER, er, st);
-    c->launches += 1;
+    if (two) {
+        // second pass: the same process from the same start, recombining as it goes
+        if ((rl = init())) return rl;
+        if ((rl = lanczos(true))) return rl;
+    } else if ((rl = recombine(0, 0))) {
+        return rl;
+    }
 
     std::vector<TslState> hs(nsrc);
     LQ_CUDA(c, cudaMemcpyAsync(hs.data(), c->state, sizeof(TslState) * nsrc, cudaMemcpyDeviceToHost, st));
@@ -473,6 +509,9 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->hop_variant < -1 || o->hop_variant > 6) return set_err(c, LQ_ERR_ARG, "hop_variant must be in [-1, 6]");
     if (o->defl_kmax < 0 || o->defl_kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "defl_kmax must be in [0, reserved kmax]");
     if (o->defl_nderiv < 0) return set_err(c, LQ_ERR_ARG, "defl_nderiv must be >= 0");
+    if (o->two_pass != 0 && o->two_pass != 1) return set_err(c, LQ_ERR_ARG, "two_pass must be 0 or 1");
+    if (c->ring > 0 && !o->two_pass && o->kmax > c->ring)
+        return set_err(c, LQ_ERR_ARG, "workspace reserved for two-pass runs: set opts.two_pass = 1 or kmax <= " + std::to_string(c->ring));
     return LQ_OK;
 }
 
@@ -823,6 +862,7 @@ void lq_default_opts(lq_opts* o) {
     o->hop_variant = -1;
     o->defl_kmax = 0;
     o->defl_nderiv = 0;
+    o->two_pass = 0;
 }
 
 int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
@@ -886,8 +926,10 @@ int lq_set_mu(lq_ctx* c, double mu) {
 }
 
 int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
-    if (!c || kmax < 1 || nsrc < 1 || (flags & ~(LQ_RESERVE_BLOCK | LQ_RESERVE_ADJOINT)))
+    if (!c || kmax < 1 || nsrc < 1 || (flags & ~(LQ_RESERVE_BLOCK | LQ_RESERVE_ADJOINT | LQ_RESERVE_TWO_PASS)))
         return set_err(c, LQ_ERR_ARG, "invalid reserve arguments");
+    if ((flags & LQ_RESERVE_TWO_PASS) && (flags & LQ_RESERVE_ADJOINT))
+        return set_err(c, LQ_ERR_ARG, "the adjoint keeps the whole left basis: no two-pass reserve");
     free_workspace(c);
     const int block = (flags & LQ_RESERVE_BLOCK) ? 1 : 0;
     const int nf = block ? 2 : 1;
@@ -902,7 +944,9 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
         }
         return LQ_OK;
     };
-    if ((r = alloc_fields(&c->basis, (size_t)nsrc * kmax * nf))) { free_workspace(c); return r; }
+    // the Krylov basis: kmax vectors per source, or a ring of kTwoPassRing for two-pass runs
+    const int ring = ((flags & LQ_RESERVE_TWO_PASS) && kmax > kTwoPassRing) ? kTwoPassRing : 0;
+    if ((r = alloc_fields(&c->basis, (size_t)nsrc * (ring ? ring : kmax) * nf))) { free_workspace(c); return r; }
     if ((r = alloc_fields(&c->left, (size_t)nsrc * 3 * nf))) { free_workspace(c); return r; }
     if ((r = alloc_fields(&c->rout, (size_t)nsrc * nf))) { free_workspace(c); return r; }
     if ((r = alloc_fields(&c->lout, (size_t)nsrc * nf))) { free_workspace(c); return r; }
@@ -959,6 +1003,7 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     c->kmax = kmax;
     c->nsrc = nsrc;
     c->block = block;
+    c->ring = ring;
     return LQ_OK;
 }
 
@@ -1296,6 +1341,7 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
     if (!c->adjoint) return set_err(c, LQ_ERR_NOT_READY, "workspace reserved without LQ_RESERVE_ADJOINT");
     int r = check_ready(c, 2, 0);
     if (r || (r = check_opts(c, o))) return r;
+    if (o->two_pass) return set_err(c, LQ_ERR_ARG, "the adjoint keeps the whole left basis: two_pass is not available");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nv = nvec(c);
     const size_t reg = (size_t)c->nsrc * nv;

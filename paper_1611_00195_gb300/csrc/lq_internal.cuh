@@ -192,6 +192,7 @@ struct lq_ctx {
 
     // workspace (lq_reserve)
     int kmax = 0, nsrc = 0, block = 0;
+    int ring = 0;                    // basis slots per source when reserved for two-pass runs only
     void* basis = nullptr;           // [nsrc][kmax][NF] fields
     void* left = nullptr;            // [nsrc][3][NF] fields (ring)
     void* rout = nullptr;            // [nsrc][NF] fields: B vh_j

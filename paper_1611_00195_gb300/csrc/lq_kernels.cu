@@ -869,46 +869,49 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
     const int keff = st.k_eff;
     const size_t V = a.V;
     const double xn = st.xnorm;
-    for (int j = threadIdx.x; j < keff; j += blockDim.x) {
+    const int j0 = a.j0, j1 = (a.j1 > 0 && a.j1 < keff) ? a.j1 : keff;   // window [j0, j1)
+    for (int j = j0 + threadIdx.x; j < j1; j += blockDim.x) {
         double2 c = a.coef[(size_t)src * a.kmax + j];
         double sc = a.scale[(size_t)src * a.kmax + j] * xn;
         double2 cs = make_double2(c.x * sc, c.y * sc);
-        if (sizeof(R) == 8) coef[j] = cs;
+        if (sizeof(R) == 8) coef[j - j0] = cs;
         else {
             // split once per block: no FP64 arithmetic is left in the k-loop below
             const float hx = (float)cs.x, hy = (float)cs.y;
-            reinterpret_cast<float4*>(coef)[j] = make_float4(hx, hy, (float)(cs.x - (double)hx), (float)(cs.y - (double)hy));
+            reinterpret_cast<float4*>(coef)[j - j0] = make_float4(hx, hy, (float)(cs.x - (double)hx), (float)(cs.y - (double)hy));
         }
     }
     __syncthreads();
     const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (s >= V) return;
     double2* y = reinterpret_cast<double2*>(f == 0 ? a.y0 : a.y1) + ((size_t)src * V + s) * 12;
-    if (keff <= 0) {
+    if (j1 <= j0) {
+        if (!a.accumulate)
 #pragma unroll
-        for (int c = 0; c < 12; ++c) y[c] = make_double2(0.0, 0.0);
+            for (int c = 0; c < 12; ++c) y[c] = make_double2(0.0, 0.0);
         return;
     }
+    auto slot = [&](int j) -> size_t { return (size_t)(a.ring > 0 ? j % a.ring : j); };
     const Chunk* base = reinterpret_cast<const Chunk*>(a.basis) + (size_t)src * a.src_stride_basis + (size_t)f * field_elems<R>(V);
     if (sizeof(R) == 8) {
         double2 acc[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) acc[c] = make_double2(0.0, 0.0);
-        for (int j = 0; j < keff; ++j) {
-            const double2* vj = reinterpret_cast<const double2*>(base + (size_t)j * a.vec_stride);
-            const double2 cj = coef[j];
+        for (int j = j0; j < j1; ++j) {
+            const double2* vj = reinterpret_cast<const double2*>(base + slot(j) * a.vec_stride);
+            const double2 cj = coef[j - j0];
 #pragma unroll
             for (int c = 0; c < 12; ++c) acc[c] = cfma(cj, __ldg(vj + (size_t)c * V + s), acc[c]);
         }
 #pragma unroll
-        for (int c = 0; c < 12; ++c) y[c] = acc[c];
+        for (int c = 0; c < 12; ++c) y[c] = a.accumulate ? cadd(y[c], acc[c]) : acc[c];
     } else {
         FF ar[12], ai[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) { ar[c] = FF{0.f, 0.f}; ai[c] = FF{0.f, 0.f}; }
-        for (int j = 0; j < keff; ++j) {
-            const float4* vj = reinterpret_cast<const float4*>(base + (size_t)j * a.vec_stride);
-            const float4 cf = reinterpret_cast<const float4*>(coef)[j];
+        for (int j = j0; j < j1; ++j) {
+            const float4* vj = reinterpret_cast<const float4*>(base + slot(j) * a.vec_stride);
+            const float4 cf = reinterpret_cast<const float4*>(coef)[j - j0];
             const float chx = cf.x, chy = cf.y, clx = cf.z, cly = cf.w;
 #pragma unroll
             for (int q = 0; q < 6; ++q) {
@@ -926,7 +929,10 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
             }
         }
 #pragma unroll
-        for (int c = 0; c < 12; ++c) y[c] = make_double2((double)ar[c].h + (double)ar[c].l, (double)ai[c].h + (double)ai[c].l);
+        for (int c = 0; c < 12; ++c) {
+            const double2 w = make_double2((double)ar[c].h + (double)ar[c].l, (double)ai[c].h + (double)ai[c].l);
+            y[c] = a.accumulate ? cadd(y[c], w) : w;
+        }
     }
 }
 

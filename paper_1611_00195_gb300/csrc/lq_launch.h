@@ -10,6 +10,8 @@ namespace lq {
 constexpr int kHopThreads = 128;
 constexpr int kUpdThreads = 256;
 constexpr int kRecThreads = 128;
+constexpr int kTwoPassRing = 32;     // basis slots per source of a two-pass run
+constexpr int kTwoPassWindow = 16;   // Krylov vectors recombined at a time in the second pass
 
 // Arguments of the stencil kernel k_hop (Eq. (1.1), block operator of Eq. (2.5)).
 struct HopArgs {
@@ -88,6 +90,9 @@ struct RecArgs {
     int kmax;
     const double2* coef;       // [nsrc][kmax] sgn(T_k) e_1
     double* y0; double* y1;    // boundary layout outputs (device), field 0 / field 1
+    int j0, j1;                // window of Krylov indices [j0, j1) (j1 = 0: up to k_eff)
+    int ring;                  // basis slots of a ring (two-pass runs), 0: vector j in slot j
+    int accumulate;            // 1: y += window sum; 0: y = window sum
 };
 
 __device__ void tsl_alpha_step(const HopArgs& a, int src, double dre, double dim);
