@@ -363,6 +363,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     };
 
     // the Lanczos loop; with `windows` the second pass of a two-pass run
+    // the Lanczos loop; with `windows` the second pass of a two-pass run
     auto lanczos = [&](bool windows) -> int {
         int j0 = 0;
         for (int j = 0; j < k; ++j) {

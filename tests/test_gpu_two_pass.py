@@ -66,3 +66,4 @@ def test_two_pass_on_full_basis_and_short_runs(lqlib):
         c2.sign_apply(x, 60)                       # deeper than the ring without two_pass
     with pytest.raises(lq.LQError):
         lq.Context(DIMS, mu=MU).reserve(60, 2, False, adjoint=True, two_pass=True)
+
