@@ -227,6 +227,15 @@ typedef struct {
 int  lq_compute_deflation(lq_ctx* ctx, const lq_eig_opts* eo, const double* X0, double* lambda,
                           double* resid, void* stream);
 
+/* The massless overlap operator at finite density, Eq. (1.1) with lattice spacing 1:
+ *   y = D_ov x = x + gamma5 sgn(H(mu)) x,   dy = d D_ov x = gamma5 d_t sgn(H(mu)) x,
+ * the sign (and its derivative along `dir`, Eqs. (2.5)-(2.6)) by the two-sided Lanczos process
+ * with the options and reports of lq_sign_apply / lq_sign_derivative_apply (deflation included).
+ * dy may be NULL (then dir may be NULL and only y is computed; the workspace needs no
+ * LQ_RESERVE_BLOCK).  x, y, dy: double[nsrc][V][4][3][2], host or device.  Synchronises. */
+int  lq_overlap_apply(lq_ctx* ctx, const lq_direction* dir, const double* x, double* y, double* dy, int nsrc,
+                      const lq_opts* opts, lq_report* rep, void* stream);
+
 /* The derivatives of the uploaded eigenpairs along `dir` (end of Sec. 3), as used by the
  * generalised deflation: dlambda_i = L_i E R_i; dR_j = sum_{i != j} R_i (L_i E R_j)/(lambda_j -
  * lambda_i) + Pbar (lambda_j - A)^{-1} Pbar E R_j and its left analogue, with the shifted solves on

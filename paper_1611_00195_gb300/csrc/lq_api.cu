@@ -1089,11 +1089,15 @@ int lq_apply_block(lq_ctx* c, const double* xt, const double* xb, double* yt, do
     return LQ_OK;
 }
 
-int lq_sign_apply(lq_ctx* c, const double* x, double* y, int nsrc, const lq_opts* o, lq_report* rep, void* stream) {
-    if (!c || !x || !y) return set_err(c, LQ_ERR_ARG, "null argument");
+}  // extern "C"
+
+namespace {
+
+// sgn(H) x (Eq. (3.1) deflation when opts ask for it) into staging region 1; x is staged into
+// region 0 (and deflated there).
+int sign_core(lq_ctx* c, const double* x, int nsrc, const lq_opts* o, lq_report* rep, cudaStream_t st) {
     int r = check_ready(c, nsrc, 0);
     if (r || (r = check_opts(c, o, true))) return r;
-    cudaStream_t st = (cudaStream_t)stream;
     const size_t n = (size_t)nsrc * c->V * 24;
     double* y0 = c->io + (size_t)c->nsrc * c->V * 24;
     if ((r = stage_in(c, c->io, x, n, st))) return r;
@@ -1115,18 +1119,16 @@ int lq_sign_apply(lq_ctx* c, const double* x, double* y, int nsrc, const lq_opts
         }
         if ((r = bcombine_host(c, y0, y0, nsrc, c->defl_V, l, coef, st))) return r;
     }
-    if ((r = stage_out(c, y, y0, n, st))) return r;
-    LQ_CUDA(c, cudaStreamSynchronize(st));
     return LQ_OK;
 }
 
-int lq_sign_derivative_apply(lq_ctx* c, const lq_direction* dir, const double* x, double* ys, double* yd, int nsrc,
-                              const lq_opts* o, lq_report* rep, void* stream) {
-    if (!c || !dir || !x || !ys || !yd) return set_err(c, LQ_ERR_ARG, "null argument");
+// (d sgn(H) x, sgn(H) x) into staging regions 1 and 2 (generalised deflation, Eqs. (3.2)-(3.4),
+// when opts ask for it); x is staged into region 0.
+int sign_derivative_core(lq_ctx* c, const lq_direction* dir, const double* x, int nsrc, const lq_opts* o,
+                         lq_report* rep, cudaStream_t st) {
     int r = check_ready(c, nsrc, 1);
     if (r || (r = check_opts(c, o, true))) return r;
-    cudaStream_t st = (cudaStream_t)stream;
-    if ((r = lq_set_direction(c, dir, stream))) return r;
+    if ((r = lq_set_direction(c, dir, st))) return r;
     const size_t n = (size_t)nsrc * c->V * 24;
     const size_t reg = (size_t)c->nsrc * c->V * 24;
     double* y0 = c->io + reg;
@@ -1172,8 +1174,57 @@ int lq_sign_derivative_apply(lq_ctx* c, const lq_direction* dir, const double* x
         if ((r = bcombine_host(c, y0, y0, nsrc, c->defl_V, 2 * l, ct, st))) return r;
         if ((r = bcombine_host(c, y1, y1, nsrc, c->defl_V, 2 * l, cb, st))) return r;
     }
-    if ((r = stage_out(c, yd, y0, n, st))) return r;
-    if ((r = stage_out(c, ys, y1, n, st))) return r;
+    return LQ_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+int lq_sign_apply(lq_ctx* c, const double* x, double* y, int nsrc, const lq_opts* o, lq_report* rep, void* stream) {
+    if (!c || !x || !y) return set_err(c, LQ_ERR_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = sign_core(c, x, nsrc, o, rep, st);
+    if (r) return r;
+    if ((r = stage_out(c, y, c->io + (size_t)c->nsrc * c->V * 24, (size_t)nsrc * c->V * 24, st))) return r;
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_sign_derivative_apply(lq_ctx* c, const lq_direction* dir, const double* x, double* ys, double* yd, int nsrc,
+                              const lq_opts* o, lq_report* rep, void* stream) {
+    if (!c || !dir || !x || !ys || !yd) return set_err(c, LQ_ERR_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = sign_derivative_core(c, dir, x, nsrc, o, rep, st);
+    if (r) return r;
+    const size_t reg = (size_t)c->nsrc * c->V * 24, n = (size_t)nsrc * c->V * 24;
+    if ((r = stage_out(c, yd, c->io + reg, n, st))) return r;
+    if ((r = stage_out(c, ys, c->io + 2 * reg, n, st))) return r;
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_overlap_apply(lq_ctx* c, const lq_direction* dir, const double* x, double* y, double* dy, int nsrc,
+                     const lq_opts* o, lq_report* rep, void* stream) {
+    if (!c || !x || !y || (dy && !dir)) return set_err(c, LQ_ERR_ARG, "null argument");
+    cudaStream_t st = (cudaStream_t)stream;
+    int r = check_ready(c, nsrc, dy ? 1 : 0);
+    if (r) return r;
+    const size_t reg = (size_t)c->nsrc * c->V * 24, n = (size_t)nsrc * c->V * 24;
+    double* xk = c->io + 5 * reg;   // the undeflated source, kept for the "1" of Eq. (1.1)
+    if ((r = stage_in(c, xk, x, n, st))) return r;
+    if (dy) {
+        if ((r = sign_derivative_core(c, dir, xk, nsrc, o, rep, st))) return r;
+        LQ_CUDA(c, launch_overlap(xk, c->io + 2 * reg, c->io + reg, (size_t)nsrc * c->V, st));
+        c->launches += 1;
+        if ((r = stage_out(c, dy, c->io + reg, n, st))) return r;
+        if ((r = stage_out(c, y, c->io + 2 * reg, n, st))) return r;
+    } else {
+        if ((r = sign_core(c, xk, nsrc, o, rep, st))) return r;
+        LQ_CUDA(c, launch_overlap(xk, c->io + reg, nullptr, (size_t)nsrc * c->V, st));
+        c->launches += 1;
+        if ((r = stage_out(c, y, c->io + reg, n, st))) return r;
+    }
     LQ_CUDA(c, cudaStreamSynchronize(st));
     return LQ_OK;
 }

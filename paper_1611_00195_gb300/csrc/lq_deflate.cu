@@ -96,4 +96,22 @@ cudaError_t launch_bcombine(double* Z, const double* W, size_t zs, int nz, const
 
 size_t bdots_partial_doubles(int npairs) { return (size_t)npairs * kDotBlocks * 4; }
 
+// Overlap operator of Eq. (1.1) from the sign and its derivative, in place on boundary-layout
+// FP64 fields: s <- x + gamma5 s (D_ov x), d <- gamma5 d (d D_ov x; d may be null).  gamma5 =
+// diag(1, 1, -1, -1) on spin: the first six of a site's twelve components keep their sign.
+__global__ void k_overlap(const double2* __restrict__ x, double2* __restrict__ s, double2* __restrict__ d, size_t ncomp) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncomp; i += (size_t)gridDim.x * blockDim.x) {
+        const double g = (i % 12 < 6) ? 1.0 : -1.0;
+        const double2 v = s[i], xv = x[i];
+        s[i] = make_double2(xv.x + g * v.x, xv.y + g * v.y);
+        if (d) { const double2 w = d[i]; d[i] = make_double2(g * w.x, g * w.y); }
+    }
+}
+
+cudaError_t launch_overlap(const double* x, double* s, double* d, size_t nsites, cudaStream_t st) {
+    k_overlap<<<1216, 256, 0, st>>>(reinterpret_cast<const double2*>(x), reinterpret_cast<double2*>(s),
+                                    reinterpret_cast<double2*>(d), nsites * 12);
+    return cudaGetLastError();
+}
+
 }  // namespace lq

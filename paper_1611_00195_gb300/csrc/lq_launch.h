@@ -117,6 +117,8 @@ size_t bdots_partial_doubles(int npairs);
 cudaError_t launch_axpby3(double* Z, double a1, const double* X1, double a2, const double* X2, double a3, const double* X3,
                           size_t n, cudaStream_t st);
 cudaError_t launch_norm2(const double* a, const double* b, double sigma, size_t n, int nsrc, double* out, cudaStream_t st);
+// s <- x + gamma5 s, d <- gamma5 d (d may be null) over nsites boundary-layout sites (Eq. (1.1))
+cudaError_t launch_overlap(const double* x, double* s, double* d, size_t nsites, cudaStream_t st);
 size_t hop_blocks(const HopArgs& a, int nf);
 
 // Newton sign iteration (lq_newton.cu)

@@ -37,7 +37,7 @@ EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_u
             "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
             "lq_profile_read", "lq_newton_sign_noalloc", "lq_error_estimate",
             "lq_upload_deflation", "lq_deflation_derivatives", "lq_sign_bilinear_grad",
-            "lq_dense_eig", "lq_compute_deflation"]
+            "lq_dense_eig", "lq_compute_deflation", "lq_overlap_apply"]
 
 
 class LatticeDesc(ctypes.Structure):
@@ -109,6 +109,8 @@ def lib():
         L.lq_sign_apply.argtypes = [P, P, P, I, ctypes.POINTER(Opts), ctypes.POINTER(Report), P]
         L.lq_sign_derivative_apply.argtypes = [P, ctypes.POINTER(Direction), P, P, P, I, ctypes.POINTER(Opts),
                                                ctypes.POINTER(Report), P]
+        L.lq_overlap_apply.argtypes = [P, ctypes.POINTER(Direction), P, P, P, I, ctypes.POINTER(Opts),
+                                       ctypes.POINTER(Report), P]
         L.lq_tsl_coefficients.argtypes = [P, I, I, P, P, P]
         L.lq_profile_enable.argtypes = [P, I]
         L.lq_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
@@ -338,6 +340,20 @@ class Context:
                                                      ctypes.byref(o), rep, _stream(x)))
         del keep
         return ys, yd, [r.as_dict() for r in rep]
+
+    def overlap_apply(self, x, k, kind=LQ_DIR_MU, field=None, derivative=True, out=None, **kw):
+        """Eq. (1.1): returns (D_ov x, d_t D_ov x or None, reports), D_ov = 1 + gamma5 sgn(H(mu)),
+        the derivative along the direction (kind, field) when `derivative`."""
+        x = _as_c128(x)
+        nsrc = x.shape[0]
+        y, dy = (_empty_like(x), _empty_like(x) if derivative else None) if out is None else out
+        d, keep = self._direction(kind, field) if derivative else (None, None)
+        o = self.opts(k, **kw)
+        rep = (Report * nsrc)()
+        self._check(self._L.lq_overlap_apply(self._h, ctypes.byref(d) if d is not None else None, _ptr(x), _ptr(y),
+                                             _ptr(dy), int(nsrc), ctypes.byref(o), rep, _stream(x)))
+        del keep
+        return y, dy, [r.as_dict() for r in rep]
 
     def profile_enable(self, enable=True):
         """Reset the kernel-time totals and launch count; enable CUDA-event timing."""
