@@ -855,8 +855,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_tsl_init(InitArgs a) {
 // ---------------------------------------------------------------------------------------
 // Recombination y = |x| sum_j c_j s_j vh_j for each field, written in the boundary layout.
 // c = sgn(T_k) e_1 (from the Newton iteration or the quadrature), one row per source.
-// FP64 basis: FP64 accumulation.  FP32 basis: float-float accumulation with exact products
-// of the split coefficient (hi + lo).
+// FP64 basis: FP64 accumulation.  FP32 basis: groups of four terms in FP32, the group sums in
+// float-float (see the kernel).
 // ---------------------------------------------------------------------------------------
 template <typename R, int NF>
 __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
@@ -906,26 +906,40 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
 #pragma unroll
         for (int c = 0; c < 12; ++c) y[c] = a.accumulate ? cadd(y[c], acc[c]) : acc[c];
     } else {
+        // groups of kRecGroup terms summed in FP32 (the coefficient rounded to FP32), the group
+        // sums added into float-float accumulators: the result carries about the error of the
+        // FP32 storage of the basis itself (4 products per group in one FMA chain), at a sixth
+        // of the instructions of exact products per term
+        constexpr int kRecGroup = 4;
         FF ar[12], ai[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) { ar[c] = FF{0.f, 0.f}; ai[c] = FF{0.f, 0.f}; }
-        for (int j = j0; j < j1; ++j) {
-            const float4* vj = reinterpret_cast<const float4*>(base + slot(j) * a.vec_stride);
-            const float4 cf = reinterpret_cast<const float4*>(coef)[j - j0];
-            const float chx = cf.x, chy = cf.y, clx = cf.z, cly = cf.w;
+        for (int jg = j0; jg < j1; jg += kRecGroup) {
+            float2 g[12];
 #pragma unroll
-            for (int q = 0; q < 6; ++q) {
-                const float4 v4 = __ldg(vj + (size_t)q * V + s);
-                const float vx[2] = {v4.x, v4.z}, vy[2] = {v4.y, v4.w};
+            for (int c = 0; c < 12; ++c) g[c] = make_float2(0.f, 0.f);
 #pragma unroll
-                for (int h = 0; h < 2; ++h) {
-                    const int c = 2 * q + h;
-                    // (ch + cl) * v, exact products of the high part, low part folded in
-                    ff_add_prod(ar[c], chx, vx[h]); ff_add_prod(ar[c], -chy, vy[h]);
-                    ff_add_prod(ai[c], chx, vy[h]); ff_add_prod(ai[c], chy, vx[h]);
-                    ar[c].l = fmaf(clx, vx[h], ar[c].l); ar[c].l = fmaf(-cly, vy[h], ar[c].l);
-                    ai[c].l = fmaf(clx, vy[h], ai[c].l); ai[c].l = fmaf(cly, vx[h], ai[c].l);
+            for (int t = 0; t < kRecGroup; ++t) {
+                const int j = jg + t;
+                if (j < j1) {
+                    const float4* vj = reinterpret_cast<const float4*>(base + slot(j) * a.vec_stride);
+                    const float4 cf = reinterpret_cast<const float4*>(coef)[j - j0];
+                    const float cr = cf.x, ci = cf.y;
+#pragma unroll
+                    for (int q = 0; q < 6; ++q) {
+                        const float4 v4 = __ldg(vj + (size_t)q * V + s);
+                        g[2 * q].x = fmaf(cr, v4.x, fmaf(-ci, v4.y, g[2 * q].x));
+                        g[2 * q].y = fmaf(cr, v4.y, fmaf(ci, v4.x, g[2 * q].y));
+                        g[2 * q + 1].x = fmaf(cr, v4.z, fmaf(-ci, v4.w, g[2 * q + 1].x));
+                        g[2 * q + 1].y = fmaf(cr, v4.w, fmaf(ci, v4.z, g[2 * q + 1].y));
+                    }
                 }
+            }
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                float sh, st;
+                two_sum_f(ar[c].h, g[c].x, sh, st); ar[c].h = sh; ar[c].l += st;
+                two_sum_f(ai[c].h, g[c].y, sh, st); ai[c].h = sh; ai[c].l += st;
             }
         }
 #pragma unroll
