@@ -497,7 +497,7 @@ def main():
         "roofline": {"bound": "hbm", "kernel": HOP_KERNELS.get(schedule, "k_hop") +
                      " (block stencil + alpha dot, schedule %d)" % schedule,
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
-                     "peak_source": "%s (MEASURED_PEAKS.json)" % peak_kind if peak_kind == "measured" else "of fallback (6.8 TB/s)",
+                     "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)" if peak_kind == "measured" else "of fallback (6.8 TB/s)",
                      "traffic": traffic, "algorithmic_bytes_per_launch": hop_bytes, "launch_ms": hop_ms,
                      "achieved_tflops": hop_flops / (hop_ms * 1e-3) / 1e12},
         "cpu_baseline": cpu,
