@@ -58,7 +58,7 @@ def parse():
     p.add_argument("--nderiv", type=int, default=6, help="Jordan blocks of the derivative deflation")
     p.add_argument("--eig-iter", type=int, default=20, help="eigensolver iterations for the deflation space")
     p.add_argument("--hop-variant", type=int, default=-1, help="stencil schedule (-1: autotuned)")
-    p.add_argument("--no-extra", action="store_true", help="skip the su(3)-direction, k = 800 and two-pass measurements")
+    p.add_argument("--no-extra", action="store_true", help="skip the su(3)-direction, k = 800, two-pass and 10^4 batch measurements")
     return p.parse_args()
 
 
@@ -424,6 +424,21 @@ def main():
                              "basis_gb": basis_gb(32), "basis_gb_one_pass": basis_gb(k),
                              "rel_diff_vs_one_pass": {"sign": relmax(ys, ys_ref), "deriv": relmax(yd, yd_ref)}}
         ctx.reserve(k, nsrc, True)
+        # the batching workload: 32 Z2-noise sources on 10^4, k = 150, mu = 0.2 (d/dmu), with the
+        # Krylov loop replayed from a CUDA graph and with plain launches
+        d3, k3, n3 = (10, 10, 10, 10), 150, 32
+        c3 = lq.Context(d3, m_w=M_W, mu=0.2, precision=lq.LQ_MIXED)
+        c3.upload_gauge(torch.from_numpy(syn.gauge_field(d3, EPS, GAUGE_SEED)).to(dev))
+        c3.reserve(k3, n3, True)
+        x3 = torch.from_numpy(syn.z2_source(d3, SOURCE_SEED, nsrc=n3)).to(dev)
+        y3s, y3d = torch.empty_like(x3), torch.empty_like(x3)
+        ms_g, r = timed(lambda: c3.sign_derivative_apply(x3, k3, out=(y3s, y3d), graph=-1), steps=3)
+        ms_p, _ = timed(lambda: c3.sign_derivative_apply(x3, k3, out=(y3s, y3d), graph=0), steps=3)
+        extra["batch_10x10c3_z2"] = {"value": n3 / (ms_g / 1e3), "unit": "solves/s", "ms_per_step": ms_g, "k": k3,
+                                     "sources": "32 Z2 noise", "mu": 0.2, "graph": True,
+                                     "plain_launches": {"value": n3 / (ms_p / 1e3), "ms_per_step": ms_p},
+                                     "status": [x["status"] for x in r[2]]}
+        del c3
 
     # accuracy: eps_A of Sec. 4 (sign and derivative) on two of the sources, no deflation
     x2 = xd[:2].contiguous()

@@ -105,6 +105,11 @@ typedef struct {
                               windows of 16 vectors as they appear; twice the operator work.
                               Required for kmax beyond the ring of a LQ_RESERVE_TWO_PASS
                               workspace; not available to lq_sign_bilinear_grad (default 0) */
+    int graph;             /* -1 / 1: the Krylov loop (2k - 1 launches) is captured once per
+                              configuration into a CUDA graph and replayed (default -1); 0:
+                              plain launches.  Off while lq_profile_enable times kernels.  The
+                              first call of a configuration captures: make it outside any stream
+                              capture of the caller's own                                    */
 } lq_opts;
 
 /* Projected step sgn(T_k) e_1 (Sec. 2):

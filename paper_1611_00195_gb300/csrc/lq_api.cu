@@ -215,7 +215,13 @@ NewtonArgs newton_args(lq_ctx* c, int k, int nb, int max_iter, double tol) {
     return a;
 }
 
+void clear_graphs(lq_ctx* c) {
+    for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
+    c->graphs.clear();
+}
+
 void free_workspace(lq_ctx* c) {
+    clear_graphs(c);
     void** ps[] = {&c->basis, &c->left, &c->rout, &c->lout, (void**)&c->io, (void**)&c->norms, (void**)&c->partials, (void**)&c->counters,
                    (void**)&c->state, (void**)&c->alpha, (void**)&c->beta, (void**)&c->delta, (void**)&c->scale,
                    (void**)&c->nx_X, (void**)&c->nx_Y, (void**)&c->nx_F, (void**)&c->nx_perm, (void**)&c->nx_scal,
@@ -363,16 +369,16 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     };
 
     // the Lanczos loop; with `windows` the second pass of a two-pass run
-    // the Lanczos loop; with `windows` the second pass of a two-pass run
-    auto lanczos = [&](bool windows) -> int {
+    // the Lanczos loop on stream ls; with `windows` the second pass of a two-pass run
+    auto lanczos = [&](bool windows, cudaStream_t ls) -> int {
         int j0 = 0;
         for (int j = 0; j < k; ++j) {
             h.j = j;
             h.in[0] = bvec(j);
             h.in[1] = lvec(j);
-            cudaEvent_t eh = prof_begin(c, st);
-            LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));
-            prof_end(c, PC_HOP, eh, st);
+            cudaEvent_t eh = prof_begin(c, ls);
+            LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, ls));
+            prof_end(c, PC_HOP, eh, ls);
             c->launches += 1;
             // vh_0 .. vh_j are in the ring and the update below overwrites slot j + 1
             if (windows && (j + 1 - j0 == kTwoPassWindow || j == k - 1)) {
@@ -385,15 +391,53 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
                 u.v_cur = bvec(j); u.v_prev = bvec(j > 0 ? j - 1 : j); u.v_next = bvec(j + 1);
                 u.w_cur = lvec(j); u.w_prev = lvec(j > 0 ? j - 1 : j); u.w_next = lvec(j + 1);
                 if (store_left) { u.w_store = reinterpret_cast<char*>(c->lbasis) + (size_t)(j + 1) * F * cb; u.src_stride_store = sst; }
-                cudaEvent_t eu = prof_begin(c, st);
-                LQ_CUDA(c, launch_update(c->prec, u, st));
-                prof_end(c, PC_UPDATE, eu, st);
+                cudaEvent_t eu = prof_begin(c, ls);
+                LQ_CUDA(c, launch_update(c->prec, u, ls));
+                prof_end(c, PC_UPDATE, eu, ls);
                 c->launches += 1;
             }
         }
         return LQ_OK;
     };
-    int rl = lanczos(false);
+    // First pass (or the only one): replayed from a CUDA graph of the whole loop when graphs are
+    // on and the kernels are not being timed one by one (lq_profile_enable); the graph is
+    // captured on the first call with this configuration.  Any capture failure falls back to
+    // plain launches.
+    auto lanczos_graph = [&]() -> int {
+        lq_ctx::GraphKey key{k, nsrc, nf, emode, h.variant, store_left ? 1 : 0, ring, c->desc.mu};
+        cudaGraphExec_t exec = nullptr;
+        for (auto& g : c->graphs) if (g.key == key) exec = g.exec;
+        if (!exec) {
+            if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+                cudaGetLastError();
+                return lanczos(false, st);
+            }
+            (void)update_grid(u.nelem, u.nsrc, u.partial_stride);   // its one-time device query, before capture
+            const long long launches0 = c->launches;
+            cudaGraph_t g = nullptr;
+            if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+                cudaGetLastError();
+                return lanczos(false, st);
+            }
+            const int rr = lanczos(false, c->cap_stream);
+            const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+            c->launches = launches0;
+            cudaError_t ei = cudaErrorUnknown;
+            if (!rr && e == cudaSuccess && g) ei = cudaGraphInstantiate(&exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+            if (ei != cudaSuccess) {
+                cudaGetLastError();
+                c->err.clear();
+                return lanczos(false, st);
+            }
+            if (c->graphs.size() >= 8) { cudaGraphExecDestroy(c->graphs.front().exec); c->graphs.erase(c->graphs.begin()); }
+            c->graphs.push_back({key, exec});
+        }
+        LQ_CUDA(c, cudaGraphLaunch(exec, st));
+        c->launches += 2 * (long long)k - 1;
+        return LQ_OK;
+    };
+    int rl = (o->graph != 0 && !c->prof_on) ? lanczos_graph() : lanczos(false, st);
     if (rl) return rl;
 
     std::vector<double> scal((size_t)nsrc * 16, 0.0);
@@ -469,7 +513,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     if (two) {
         // second pass: the same process from the same start, recombining as it goes
         if ((rl = init())) return rl;
-        if ((rl = lanczos(true))) return rl;
+        if ((rl = lanczos(true, st))) return rl;
     } else if ((rl = recombine(0, 0))) {
         return rl;
     }
@@ -511,6 +555,7 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->defl_kmax < 0 || o->defl_kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "defl_kmax must be in [0, reserved kmax]");
     if (o->defl_nderiv < 0) return set_err(c, LQ_ERR_ARG, "defl_nderiv must be >= 0");
     if (o->two_pass != 0 && o->two_pass != 1) return set_err(c, LQ_ERR_ARG, "two_pass must be 0 or 1");
+    if (o->graph < -1 || o->graph > 1) return set_err(c, LQ_ERR_ARG, "graph must be -1, 0 or 1");
     if (c->ring > 0 && !o->two_pass && o->kmax > c->ring)
         return set_err(c, LQ_ERR_ARG, "workspace reserved for two-pass runs: set opts.two_pass = 1 or kmax <= " + std::to_string(c->ring));
     return LQ_OK;
@@ -864,6 +909,7 @@ void lq_default_opts(lq_opts* o) {
     o->defl_kmax = 0;
     o->defl_nderiv = 0;
     o->two_pass = 0;
+    o->graph = -1;
 }
 
 int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
@@ -889,6 +935,7 @@ int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
 void lq_destroy(lq_ctx* c) {
     if (!c) return;
     free_workspace(c);
+    if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
     dfree(c->U);
     dfree(c->Ub);
     dfree(c->Y);

@@ -254,6 +254,20 @@ struct lq_ctx {
     int tuned_variant[3][3] = {{-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}};
     int tuned_nsrc = -1;
 
+    // CUDA graphs of the Krylov loop, one per configuration (cleared when the workspace is
+    // reserved again); captured on cap_stream, launched on the caller's stream
+    struct GraphKey {
+        int k, nsrc, nf, emode, variant, store_left, ring;
+        double mu;
+        bool operator==(const GraphKey& o) const {
+            return k == o.k && nsrc == o.nsrc && nf == o.nf && emode == o.emode && variant == o.variant &&
+                   store_left == o.store_left && ring == o.ring && mu == o.mu;
+        }
+    };
+    struct GraphEntry { GraphKey key; cudaGraphExec_t exec; };
+    std::vector<GraphEntry> graphs;
+    cudaStream_t cap_stream = nullptr;
+
     // profiling (lq_profile_enable): event pairs per kernel class, summed at sync points
     int prof_on = 0;
     long long launches = 0;
