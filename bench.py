@@ -450,6 +450,24 @@ def main():
                                      "plain_launches": {"value": n3 / (ms_p / 1e3), "ms_per_step": ms_p},
                                      "status": [x["status"] for x in r[2]]}
         del c3
+        # the ragged batch of the same workload: 6^4, 8^4, 8x12^3, 10^4 (k = 100-300), 8 Z2
+        # sources each, d/dmu: one graph launch for all four Krylov loops (lq_batch_apply)
+        # against the four single-lattice calls one after another
+        nr = 8
+        members = []
+        for d4, eps4, k4, seed4 in syn.RAGGED_BATCH:
+            c4 = lq.Context(d4, m_w=M_W, mu=syn.RAGGED_MU, precision=lq.LQ_MIXED)
+            c4.upload_gauge(torch.from_numpy(syn.gauge_field(d4, eps4, seed4)).to(dev))
+            c4.reserve(k4, nr, True)
+            members.append({"ctx": c4, "k": k4, "x": torch.from_numpy(syn.z2_source(d4, seed4 + 100, nsrc=nr)).to(dev)})
+        ms_seq, _ = timed(lambda: [m["ctx"].sign_derivative_apply(m["x"], m["k"]) for m in members], steps=3)
+        ms_b, rb = timed(lambda: lq.batch_apply(members), steps=3)
+        extra["ragged_batch"] = {"value": len(members) * nr / (ms_b / 1e3), "unit": "solves/s", "ms_per_step": ms_b,
+                                 "lattices": ["%dx%dx%dx%d eps %.1f k %d" % (d4 + (e4, k4)) for d4, e4, k4, _ in syn.RAGGED_BATCH],
+                                 "sources": "%d Z2 noise per lattice" % nr, "mu": syn.RAGGED_MU, "graph_launches": 1,
+                                 "sequential_calls": {"value": len(members) * nr / (ms_seq / 1e3), "ms_per_step": ms_seq},
+                                 "status": [[x["status"] for x in m_out[2]] for m_out in rb]}
+        del members
 
     # accuracy: eps_A of Sec. 4 (sign and derivative) on two of the sources, no deflation
     x2 = xd[:2].contiguous()

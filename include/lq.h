@@ -202,7 +202,7 @@ int  lq_sign_derivative_apply(lq_ctx* ctx, const lq_direction* dir, const double
  * double[l][V][4][3][2]; L: the left eigenvectors as kets, Lk_i = L_i^dag (so L_i A = lambda_i L_i
  * and <Lk_i|R_j> = delta_ij), same layout.  Host or device memory; copied (FP64).  l = 0 removes
  * the space.  Used by lq_sign_apply and lq_sign_derivative_apply when opts->deflate = 1.  Must
- * follow lq_reserve; the library's own Arnoldi is not part of this version. */
+ * follow lq_reserve; lq_compute_deflation below computes such a space itself. */
 int  lq_upload_deflation(lq_ctx* ctx, int l, const double* lambda, const double* R, const double* L,
                          void* stream);
 
@@ -240,6 +240,41 @@ int  lq_compute_deflation(lq_ctx* ctx, const lq_eig_opts* eo, const double* X0, 
  * LQ_RESERVE_BLOCK).  x, y, dy: double[nsrc][V][4][3][2], host or device.  Synchronises. */
 int  lq_overlap_apply(lq_ctx* ctx, const lq_direction* dir, const double* x, double* y, double* dy, int nsrc,
                       const lq_opts* opts, lq_report* rep, void* stream);
+
+/* One member of a ragged batch (lq_batch_apply). */
+typedef struct {
+    lq_ctx* ctx;               /* the member's own context: lattice, links, mu, precision and
+                                  workspace; each context at most once per batch               */
+    const lq_direction* dir;   /* direction of d_t (Eq. (2.6)), or NULL for sgn(H) x alone     */
+    const double* x;           /* double[nsrc][V][4][3][2] sources, host or device            */
+    double* y_sign;            /* sgn(H(mu)) x, same layout, host or device                   */
+    double* y_deriv;           /* d_t sgn(H(mu)) x when dir != NULL (else unused)             */
+    int nsrc;                  /* sources of this member, 1 <= nsrc <= its reserved nsrc      */
+    const lq_opts* opts;       /* opts->kmax is this member's Krylov depth; deflate and two_pass
+                                  must be 0                                                     */
+    lq_report* report;         /* host array of nsrc reports, or NULL                         */
+} lq_batch_item;
+
+/* Up to LQ_BATCH_MAX independent two-sided Lanczos problems (Sec. 2) at once: lattices of
+ * different extents and parameters, with their own sources and Krylov depths.  Member i gives
+ * exactly (bit for bit) what lq_sign_derivative_apply (dir != NULL) or lq_sign_apply (dir ==
+ * NULL) gives with the same context and options: the same kernels, stencil schedule and
+ * reduction order.  The Krylov loops of all members (2k_i - 1 launches each) are one CUDA graph
+ * with one branch per member, captured the first time the batch configuration is met (the
+ * contexts, and per member k, nsrc, direction kind, stencil schedule and mu) and replayed with a
+ * single launch on `stream`; the branches are independent, so the GPU runs the members' kernels
+ * side by side and small lattices fill it together.  With opts->graph = 0 for some member, or
+ * kernel timing on for some context (lq_profile_enable), the loops run as plain launches on
+ * per-context streams forked from and joined into `stream`.  The projected signs and the
+ * recombinations follow on the same per-context streams.  No device allocation beyond
+ * lq_reserve's, except the first capture of a configuration (the CUDA graph; at most 8 batch
+ * configurations are kept, dropped when a member context is reserved again or destroyed).
+ * Errors: LQ_ERR_ARG for n outside [1, LQ_BATCH_MAX], a null member context or buffer, a
+ * context named twice, members on different devices, or deflate / two_pass set; a member's
+ * own errors as in the single-problem calls, stored on that context (lq_last_error).
+ * Synchronises `stream`. */
+#define LQ_BATCH_MAX 16
+int  lq_batch_apply(const lq_batch_item* items, int n, void* stream);
 
 /* The derivatives of the uploaded eigenpairs along `dir` (end of Sec. 3), as used by the
  * generalised deflation: dlambda_i = L_i E R_i; dR_j = sum_{i != j} R_i (L_i E R_j)/(lambda_j -

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <complex>
 #include <cstring>
+#include <mutex>
 #include <numeric>
 #include <new>
 #include <string>
@@ -215,9 +216,34 @@ NewtonArgs newton_args(lq_ctx* c, int k, int nb, int max_iter, double tol) {
     return a;
 }
 
+// CUDA graphs of ragged batches (lq_batch_apply): one per batch configuration, keyed by each
+// member context and the configuration of its run; shared by all contexts of the process.
+struct BatchGraph {
+    std::vector<std::pair<lq_ctx*, lq_ctx::GraphKey>> key;
+    cudaGraphExec_t exec;
+};
+std::mutex g_batch_mu;
+std::vector<BatchGraph> g_batch_graphs;
+
+// Drop every batch graph that launches kernels on c's workspace.
+void clear_batch_graphs(const lq_ctx* c) {
+    std::lock_guard<std::mutex> lk(g_batch_mu);
+    for (size_t i = 0; i < g_batch_graphs.size();) {
+        bool hit = false;
+        for (auto& kv : g_batch_graphs[i].key) hit = hit || kv.first == c;
+        if (hit) {
+            cudaGraphExecDestroy(g_batch_graphs[i].exec);
+            g_batch_graphs.erase(g_batch_graphs.begin() + (long)i);
+        } else {
+            ++i;
+        }
+    }
+}
+
 void clear_graphs(lq_ctx* c) {
     for (auto& g : c->graphs) cudaGraphExecDestroy(g.exec);
     c->graphs.clear();
+    clear_batch_graphs(c);
 }
 
 void free_workspace(lq_ctx* c) {
@@ -276,101 +302,131 @@ int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* vari
     return LQ_OK;
 }
 
-// The Lanczos driver shared by lq_sign_apply (nf = 1) and lq_sign_derivative_apply (nf = 2).
-// The source is already staged in c->io (region 0, boundary layout); results go to the device
-// boundary-layout buffers y0 (field 0: sign, or top = derivative) and y1 (field 1: bottom = sign).
+// The Lanczos driver shared by lq_sign_apply (nf = 1), lq_sign_derivative_apply (nf = 2) and
+// lq_batch_apply.  The source is staged in c->io (region 0, boundary layout) unless x_dev names
+// another device buffer; results go to the device boundary-layout buffers y0 (field 0: sign, or
+// top = derivative) and y1 (field 1: bottom = sign).  A run goes through phases so that a batch
+// of contexts can interleave them on separate streams: setup (launch arguments, start vectors,
+// stencil schedule), the Krylov loop, the projected sign (enqueued, then completed on the host),
+// and the recombination with the reports (enqueued, then completed).
 enum { FN_SIGN = 0, FN_RESOLVENT = 1 };
 
-int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report* rep,
-            double* y0, double* y1, cudaStream_t st, const double* x_dev = nullptr,
-            const double* x_top = nullptr, int fn = FN_SIGN, const double2* shifts = nullptr,
-            bool store_left = false) {
-    const int k = o->kmax;
-    const size_t F = fe(c);
-    const size_t vstride = (size_t)nf * F;        // Chunk elements per Krylov vector
-    const int slots = c->ring > 0 ? c->ring : c->kmax;   // basis vectors held per source
-    const size_t sb = (size_t)slots * vstride;    // per source: basis
-    const size_t sl = 3 * vstride;                // per source: left ring
-    const size_t sio = vstride;                   // per source: operator outputs
-    const size_t cb = chunk_bytes(c);
-    // Two-pass run (lq_opts.two_pass): the first pass keeps only a ring of basis vectors and
-    // yields T_k; the second reruns the same (deterministic) process and recombines windows of
-    // kTwoPassWindow vectors into y while they are still in the ring.
-    const bool two = o->two_pass != 0 && k > 1;
-    const int ring = two ? std::min(slots, kTwoPassRing) : 0;
-    char* basis = reinterpret_cast<char*>(c->basis);
-    char* left = reinterpret_cast<char*>(c->left);
-    auto bvec = [&](int j) -> void* { return basis + (size_t)(ring ? j % ring : j) * vstride * cb; };
-    auto lvec = [&](int j) -> void* { return left + (size_t)(j % 3) * vstride * cb; };
+struct TslRun {
+    lq_ctx* c = nullptr;
+    int nf = 1, emode = 0, nsrc = 0, fn = FN_SIGN;
+    const lq_opts* o = nullptr;
+    lq_report* rep = nullptr;
+    double* y0 = nullptr;
+    double* y1 = nullptr;
+    const double2* shifts = nullptr;
+    bool store_left = false;
 
+    int k = 0, ring = 0;
+    bool two = false;
+    size_t F = 0, vstride = 0, sst = 0, cb = 0;
     InitArgs ia;
-    std::memset(&ia, 0, sizeof(ia));
-    ia.V = c->V; ia.nsrc = nsrc; ia.x = x_dev ? x_dev : c->io; ia.xt = x_top; ia.v1 = bvec(0); ia.w1 = lvec(0);
-    ia.src_stride_basis = sb; ia.src_stride_left = sl; ia.state = c->state;
-    ia.partials = c->partials; ia.partial_stride = c->partial_blocks; ia.counters = c->counters;
-    ia.breakdown_tol = o->breakdown_tol;
-    const size_t sst = (size_t)c->kmax * F;   // per source: stored left basis (NF = 1)
-    if (store_left) { ia.w1_store = c->lbasis; ia.src_stride_store = sst; }
-    auto init = [&]() -> int {
+    HopArgs h;
+    UpdArgs u;
+    RecArgs ra;
+    QuadArgs qa;
+    std::vector<double> scal, check;
+    std::vector<int> used, nodes;
+    int quad_attempt = -1;   // quadrature passes enqueued so far - 1; -1: no quadrature
+
+    void* bvec(int j) const {
+        return reinterpret_cast<char*>(c->basis) + (size_t)(ring ? j % ring : j) * vstride * cb;
+    }
+    void* lvec(int j) const { return reinterpret_cast<char*>(c->left) + (size_t)(j % 3) * vstride * cb; }
+
+    int init(cudaStream_t st) {
         cudaEvent_t e0 = prof_begin(c, st);
         LQ_CUDA(c, launch_tsl_init(c->prec, nf, ia, st));
         prof_end(c, PC_OTHER, e0, st);
         c->launches += 1;
         return LQ_OK;
-    };
-    int r0 = init();
-    if (r0) return r0;
-
-    HopArgs h = base_hop(c);
-    h.nsrc = nsrc; h.nsides = 2; h.side0 = 0;
-    set_side(h, 0, c, 0, emode);
-    set_side(h, 1, c, 1, emode);
-    h.state = c->state; h.partials = c->partials; h.partial_stride = c->partial_blocks; h.counters = c->counters;
-    h.alpha = c->alpha; h.scale = c->scale; h.kmax = c->kmax; h.kmax_run = k;
-    h.uscale = store_left ? c->uscale : nullptr;
-    h.src_stride_in[0] = sb; h.src_stride_in[1] = sl;
-    h.src_stride_out[0] = sio; h.src_stride_out[1] = sio;
-    h.out[0] = c->rout; h.out[1] = c->lout;
-    if (o->hop_variant >= 0) {
-        // the schedule that actually runs (and is reported): FP64 has schedules 0 and 1 only,
-        // the plain operator 0 only, and schedule 6 needs tiles that cover the lattice
-        int v = (nf == 2) ? o->hop_variant : 0;
-        if (c->prec == LQ_FP64 && v > 1) v = 0;
-        if (v == 6 && !tile_ok(h.dims)) v = 3;
-        h.variant = v;
-    } else {
-        h.in[0] = bvec(0);
-        h.in[1] = lvec(0);
-        int v = 0;
-        int rr = tune_hop(c, h, nf, emode, st, &v);
-        if (rr) return rr;
-        h.variant = v;
     }
 
-    UpdArgs u;
-    std::memset(&u, 0, sizeof(u));
-    u.nelem = vstride; u.nsrc = nsrc; u.rout = c->rout; u.lout = c->lout;
-    u.src_stride_io = sio; u.src_stride_basis = sb; u.src_stride_left = sl;
-    u.state = c->state; u.partials = c->partials; u.partial_stride = c->partial_blocks; u.counters = c->counters;
-    u.beta = c->beta; u.delta = c->delta; u.kmax = c->kmax;
+    // Launch arguments and start vectors (on st); the stencil schedule (the autotuner launches
+    // on st and synchronises it the first time a configuration is met).
+    int setup(cudaStream_t st, const double* x_dev, const double* x_top) {
+        k = o->kmax;
+        F = fe(c);
+        vstride = (size_t)nf * F;                    // Chunk elements per Krylov vector
+        const int slots = c->ring > 0 ? c->ring : c->kmax;   // basis vectors held per source
+        const size_t sb = (size_t)slots * vstride;   // per source: basis
+        const size_t sl = 3 * vstride;               // per source: left ring
+        const size_t sio = vstride;                  // per source: operator outputs
+        cb = chunk_bytes(c);
+        // Two-pass run (lq_opts.two_pass): the first pass keeps only a ring of basis vectors and
+        // yields T_k; the second reruns the same (deterministic) process and recombines windows
+        // of kTwoPassWindow vectors into y while they are still in the ring.
+        two = o->two_pass != 0 && k > 1;
+        ring = two ? std::min(slots, kTwoPassRing) : 0;
+        sst = (size_t)c->kmax * F;                   // per source: stored left basis (NF = 1)
 
-    RecArgs ra;
-    std::memset(&ra, 0, sizeof(ra));
-    ra.V = c->V; ra.nsrc = nsrc; ra.basis = c->basis; ra.src_stride_basis = sb; ra.vec_stride = vstride;
-    ra.state = c->state; ra.scale = c->scale; ra.kmax = c->kmax; ra.coef = c->proj_c;
-    ra.y0 = y0; ra.y1 = y1; ra.ring = ring;
-    auto recombine = [&](int j0, int j1) -> int {   // y (+)= |x| sum_{j0 <= j < j1} c_j s_j vh_j
+        std::memset(&ia, 0, sizeof(ia));
+        ia.V = c->V; ia.nsrc = nsrc; ia.x = x_dev ? x_dev : c->io; ia.xt = x_top; ia.v1 = bvec(0); ia.w1 = lvec(0);
+        ia.src_stride_basis = sb; ia.src_stride_left = sl; ia.state = c->state;
+        ia.partials = c->partials; ia.partial_stride = c->partial_blocks; ia.counters = c->counters;
+        ia.breakdown_tol = o->breakdown_tol;
+        if (store_left) { ia.w1_store = c->lbasis; ia.src_stride_store = sst; }
+        int r = init(st);
+        if (r) return r;
+
+        h = base_hop(c);
+        h.nsrc = nsrc; h.nsides = 2; h.side0 = 0;
+        set_side(h, 0, c, 0, emode);
+        set_side(h, 1, c, 1, emode);
+        h.state = c->state; h.partials = c->partials; h.partial_stride = c->partial_blocks; h.counters = c->counters;
+        h.alpha = c->alpha; h.scale = c->scale; h.kmax = c->kmax; h.kmax_run = k;
+        h.uscale = store_left ? c->uscale : nullptr;
+        h.src_stride_in[0] = sb; h.src_stride_in[1] = sl;
+        h.src_stride_out[0] = sio; h.src_stride_out[1] = sio;
+        h.out[0] = c->rout; h.out[1] = c->lout;
+        if (o->hop_variant >= 0) {
+            // the schedule that actually runs (and is reported): FP64 has schedules 0 and 1 only,
+            // the plain operator 0 only, and schedule 6 needs tiles that cover the lattice
+            int v = (nf == 2) ? o->hop_variant : 0;
+            if (c->prec == LQ_FP64 && v > 1) v = 0;
+            if (v == 6 && !tile_ok(h.dims)) v = 3;
+            h.variant = v;
+        } else {
+            h.in[0] = bvec(0);
+            h.in[1] = lvec(0);
+            int v = 0;
+            if ((r = tune_hop(c, h, nf, emode, st, &v))) return r;
+            h.variant = v;
+        }
+
+        std::memset(&u, 0, sizeof(u));
+        u.nelem = vstride; u.nsrc = nsrc; u.rout = c->rout; u.lout = c->lout;
+        u.src_stride_io = sio; u.src_stride_basis = sb; u.src_stride_left = sl;
+        u.state = c->state; u.partials = c->partials; u.partial_stride = c->partial_blocks; u.counters = c->counters;
+        u.beta = c->beta; u.delta = c->delta; u.kmax = c->kmax;
+
+        std::memset(&ra, 0, sizeof(ra));
+        ra.V = c->V; ra.nsrc = nsrc; ra.basis = c->basis; ra.src_stride_basis = sb; ra.vec_stride = vstride;
+        ra.state = c->state; ra.scale = c->scale; ra.kmax = c->kmax; ra.coef = c->proj_c;
+        ra.y0 = y0; ra.y1 = y1; ra.ring = ring;
+
+        scal.assign((size_t)nsrc * 16, 0.0);
+        check.assign(nsrc, 0.0);   // stays 0 when the quadrature is not attempted
+        used.assign(nsrc, LQ_PROJ_NEWTON);
+        quad_attempt = -1;
+        return LQ_OK;
+    }
+
+    int recombine(int j0, int j1, cudaStream_t st) {   // y (+)= |x| sum_{j0 <= j < j1} c_j s_j vh_j
         ra.j0 = j0; ra.j1 = j1; ra.accumulate = j0 > 0 ? 1 : 0;
         cudaEvent_t er = prof_begin(c, st);
         LQ_CUDA(c, launch_recombine(c->prec, nf, ra, st));
         prof_end(c, PC_OTHER, er, st);
         c->launches += 1;
         return LQ_OK;
-    };
+    }
 
-    // the Lanczos loop; with `windows` the second pass of a two-pass run
-    // the Lanczos loop on stream ls; with `windows` the second pass of a two-pass run
-    auto lanczos = [&](bool windows, cudaStream_t ls) -> int {
+    // The Lanczos loop on stream ls; with `windows` the second pass of a two-pass run.
+    int lanczos(bool windows, cudaStream_t ls) {
         int j0 = 0;
         for (int j = 0; j < k; ++j) {
             h.j = j;
@@ -382,7 +438,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
             c->launches += 1;
             // vh_0 .. vh_j are in the ring and the update below overwrites slot j + 1
             if (windows && (j + 1 - j0 == kTwoPassWindow || j == k - 1)) {
-                int rr = recombine(j0, j + 1);
+                int rr = recombine(j0, j + 1, ls);
                 if (rr) return rr;
                 j0 = j + 1;
             }
@@ -398,131 +454,113 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
             }
         }
         return LQ_OK;
-    };
-    // First pass (or the only one): replayed from a CUDA graph of the whole loop when graphs are
-    // on and the kernels are not being timed one by one (lq_profile_enable); the graph is
-    // captured on the first call with this configuration.  Any capture failure falls back to
-    // plain launches.
-    auto lanczos_graph = [&]() -> int {
-        lq_ctx::GraphKey key{k, nsrc, nf, emode, h.variant, store_left ? 1 : 0, ring, c->desc.mu};
-        cudaGraphExec_t exec = nullptr;
-        for (auto& g : c->graphs) if (g.key == key) exec = g.exec;
-        if (!exec) {
-            if (!c->cap_stream && cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
-                cudaGetLastError();
-                return lanczos(false, st);
-            }
-            (void)update_grid(u.nelem, u.nsrc, u.partial_stride);   // its one-time device query, before capture
-            const long long launches0 = c->launches;
-            cudaGraph_t g = nullptr;
-            if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
-                cudaGetLastError();
-                return lanczos(false, st);
-            }
-            const int rr = lanczos(false, c->cap_stream);
-            const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
-            c->launches = launches0;
-            cudaError_t ei = cudaErrorUnknown;
-            if (!rr && e == cudaSuccess && g) ei = cudaGraphInstantiate(&exec, g, 0);
-            if (g) cudaGraphDestroy(g);
-            if (ei != cudaSuccess) {
-                cudaGetLastError();
-                c->err.clear();
-                return lanczos(false, st);
-            }
-            if (c->graphs.size() >= 8) { cudaGraphExecDestroy(c->graphs.front().exec); c->graphs.erase(c->graphs.begin()); }
-            c->graphs.push_back({key, exec});
-        }
-        LQ_CUDA(c, cudaGraphLaunch(exec, st));
-        c->launches += 2 * (long long)k - 1;
-        return LQ_OK;
-    };
-    int rl = (o->graph != 0 && !c->prof_on) ? lanczos_graph() : lanczos(false, st);
-    if (rl) return rl;
+    }
 
-    std::vector<double> scal((size_t)nsrc * 16, 0.0);
-    std::vector<double> check(nsrc, 0.0);   // stays 0 when the quadrature is not attempted
-    std::vector<int> used(nsrc, LQ_PROJ_NEWTON);
-    int r;
-    bool need_newton = o->projected == LQ_PROJ_NEWTON && fn == FN_SIGN;
-    if (fn == FN_RESOLVENT) {
-        QuadArgs qa;
+    lq_ctx::GraphKey key() const { return {k, nsrc, nf, emode, h.variant, store_left ? 1 : 0, ring, c->desc.mu}; }
+    bool graphed() const { return o->graph != 0 && !c->prof_on; }
+    long long loop_launches() const { return 2 * (long long)k - 1; }
+
+    int quad_pass(cudaStream_t st) {
+        LQ_CUDA(c, cudaMemcpyAsync(c->quad_nodes, nodes.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
+        cudaEvent_t eq = prof_begin(c, st);
+        const int maxn = *std::max_element(nodes.begin(), nodes.end());
+        LQ_CUDA(c, quad_sign_e1(qa, maxn, quad_attempt == 0, st));
+        prof_end(c, PC_NEWTON, eq, st, 0);
+        c->launches += quad_attempt == 0 ? 5 : 4;
+        return LQ_OK;
+    }
+
+    // Projected step, the part that needs no host decision: the resolvent, or the first
+    // quadrature pass (the Newton iteration of LQ_PROJ_NEWTON runs in proj_complete).
+    int proj_enqueue(cudaStream_t st) {
+        if (fn == FN_RESOLVENT) {
+            QuadArgs q;
+            std::memset(&q, 0, sizeof(q));
+            q.k = k; q.nb = nsrc; q.kmax = c->kmax; q.nth_max = 2 * kQuadMaxNodes; q.state = c->state;
+            q.alpha = c->alpha; q.beta = c->beta; q.delta = c->delta; q.work = c->quad_work;
+            q.s = c->proj_c; q.check = c->quad_check;
+            LQ_CUDA(c, proj_resolvent(q, shifts, st));
+            c->launches += 1;
+            for (int s = 0; s < nsrc; ++s) used[s] = 3;
+            return LQ_OK;
+        }
+        if (o->projected == LQ_PROJ_NEWTON) return LQ_OK;
         std::memset(&qa, 0, sizeof(qa));
-        qa.k = k; qa.nb = nsrc; qa.kmax = c->kmax; qa.nth_max = 2 * kQuadMaxNodes; qa.state = c->state;
-        qa.alpha = c->alpha; qa.beta = c->beta; qa.delta = c->delta; qa.work = c->quad_work;
-        qa.s = c->proj_c; qa.check = c->quad_check;
-        LQ_CUDA(c, proj_resolvent(qa, shifts, st));
-        c->launches += 1;
-        for (int s = 0; s < nsrc; ++s) used[s] = 3;
-    } else if (o->projected != LQ_PROJ_NEWTON) {
-        QuadArgs qa;
-        std::memset(&qa, 0, sizeof(qa));
-        qa.k = k; qa.nb = nsrc; qa.kmax = c->kmax; qa.nth_max = 2 * kQuadMaxNodes; qa.state = c->state;
+        qa.k = k; qa.nb = nsrc; qa.kmax = c->kmax; qa.state = c->state;
         qa.alpha = c->alpha; qa.beta = c->beta; qa.delta = c->delta; qa.c = c->quad_c; qa.work = c->quad_work;
         qa.s = c->proj_c; qa.q = c->quad_q; qa.check = c->quad_check; qa.nodes = c->quad_nodes;
         qa.nth_max = 2 * kQuadRetryMaxNodes; qa.part = c->quad_part; qa.part_blocks = 2 * kQuadRetryMaxNodes / kQuadBlk;
-        // LQ_PROJ_QUAD: one pass with opts.quad_nodes.  LQ_PROJ_AUTO: a source whose involution
-        // residual exceeds proj_tol is retried once with kQuadRetryMaxNodes nodes (a pass costs
-        // the latency of one sequential tridiagonal solve whatever the node count, so one large
-        // retry beats a ladder of doublings); the others keep their result; what still fails
-        // goes to the Newton iteration below.
-        std::vector<int> nodes(nsrc, o->quad_nodes);
-        bool ok = false;
-        for (int attempt = 0;; ++attempt) {
-            LQ_CUDA(c, cudaMemcpyAsync(c->quad_nodes, nodes.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
-            cudaEvent_t eq = prof_begin(c, st);
-            const int maxn = *std::max_element(nodes.begin(), nodes.end());
-            LQ_CUDA(c, quad_sign_e1(qa, maxn, attempt == 0, st));
-            prof_end(c, PC_NEWTON, eq, st, 0);
-            c->launches += attempt == 0 ? 5 : 4;
-            LQ_CUDA(c, cudaMemcpyAsync(check.data(), c->quad_check, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
-            LQ_CUDA(c, cudaStreamSynchronize(st));   // nodes and check are host memory
-            ok = true;
-            bool retry = false;
-            for (int s = 0; s < nsrc; ++s) {
-                const bool pass = std::isfinite(check[s]) && check[s] <= o->proj_tol;
-                ok = ok && pass;
-                if (pass || nodes[s] == 0) { nodes[s] = 0; continue; }
-                if (o->projected == LQ_PROJ_AUTO && nodes[s] < kQuadRetryMaxNodes) { nodes[s] = kQuadRetryMaxNodes; retry = true; }
-                else nodes[s] = 0;
+        nodes.assign(nsrc, o->quad_nodes);
+        quad_attempt = 0;
+        return quad_pass(st);
+    }
+
+    // LQ_PROJ_QUAD: one pass with opts.quad_nodes.  LQ_PROJ_AUTO: a source whose involution
+    // residual exceeds proj_tol is retried once with kQuadRetryMaxNodes nodes (a pass costs the
+    // latency of one sequential tridiagonal solve whatever the node count, so one large retry
+    // beats a ladder of doublings); the others keep their result; what still fails goes to the
+    // Newton iteration.  Synchronises st.
+    int proj_complete(cudaStream_t st) {
+        bool need_newton = o->projected == LQ_PROJ_NEWTON && fn == FN_SIGN;
+        if (quad_attempt >= 0) {
+            bool ok = false;
+            for (;;) {
+                LQ_CUDA(c, cudaMemcpyAsync(check.data(), c->quad_check, sizeof(double) * nsrc, cudaMemcpyDeviceToHost, st));
+                LQ_CUDA(c, cudaStreamSynchronize(st));   // nodes and check are host memory
+                ok = true;
+                bool retry = false;
+                for (int s = 0; s < nsrc; ++s) {
+                    const bool pass = std::isfinite(check[s]) && check[s] <= o->proj_tol;
+                    ok = ok && pass;
+                    if (pass || nodes[s] == 0) { nodes[s] = 0; continue; }
+                    if (o->projected == LQ_PROJ_AUTO && nodes[s] < kQuadRetryMaxNodes) { nodes[s] = kQuadRetryMaxNodes; retry = true; }
+                    else nodes[s] = 0;
+                }
+                if (ok || !retry) break;
+                ++quad_attempt;
+                int r = quad_pass(st);
+                if (r) return r;
             }
-            if (ok || !retry) break;
+            need_newton = !ok && o->projected == LQ_PROJ_AUTO;
+            for (int s = 0; s < nsrc; ++s) used[s] = LQ_PROJ_QUAD;
         }
-        need_newton = !ok && o->projected == LQ_PROJ_AUTO;
-        for (int s = 0; s < nsrc; ++s) used[s] = LQ_PROJ_QUAD;
-    }
-    if (need_newton) {
-        // Newton for every source (LQ_PROJ_NEWTON) or only for those whose quadrature failed
-        std::vector<int> sel(nsrc, 1);
-        if (o->projected == LQ_PROJ_AUTO)
-            for (int s = 0; s < nsrc; ++s) sel[s] = !(std::isfinite(check[s]) && check[s] <= o->proj_tol);
-        NewtonArgs na = newton_args(c, k, nsrc, o->newton_max_iter, o->newton_tol);
-        LQ_CUDA(c, newton_init_tridiag(na, st));
-        c->launches += 1;
-        const double one = 1.0;
-        for (int s = 0; s < nsrc; ++s)
-            if (!sel[s]) LQ_CUDA(c, cudaMemcpyAsync(c->nx_scal + (size_t)s * 16 + NS_DONE, &one, sizeof(double), cudaMemcpyHostToDevice, st));
-        LQ_CUDA(c, cudaMemcpyAsync(c->proj_sel, sel.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
-        if ((r = run_newton(c, na, st, scal))) return r;
-        LQ_CUDA(c, newton_first_column(na, c->proj_c, c->kmax, st, c->proj_sel));
-        c->launches += 1;
-        for (int s = 0; s < nsrc; ++s) if (sel[s]) used[s] = LQ_PROJ_NEWTON;
-        LQ_CUDA(c, cudaStreamSynchronize(st));   // sel is host memory
-    }
-
-    if (two) {
-        // second pass: the same process from the same start, recombining as it goes
-        if ((rl = init())) return rl;
-        if ((rl = lanczos(true, st))) return rl;
-    } else if ((rl = recombine(0, 0))) {
-        return rl;
+        if (need_newton) {
+            // Newton for every source (LQ_PROJ_NEWTON) or only for those whose quadrature failed
+            std::vector<int> sel(nsrc, 1);
+            if (o->projected == LQ_PROJ_AUTO)
+                for (int s = 0; s < nsrc; ++s) sel[s] = !(std::isfinite(check[s]) && check[s] <= o->proj_tol);
+            NewtonArgs na = newton_args(c, k, nsrc, o->newton_max_iter, o->newton_tol);
+            LQ_CUDA(c, newton_init_tridiag(na, st));
+            c->launches += 1;
+            const double one = 1.0;
+            for (int s = 0; s < nsrc; ++s)
+                if (!sel[s]) LQ_CUDA(c, cudaMemcpyAsync(c->nx_scal + (size_t)s * 16 + NS_DONE, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+            LQ_CUDA(c, cudaMemcpyAsync(c->proj_sel, sel.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
+            int r = run_newton(c, na, st, scal);
+            if (r) return r;
+            LQ_CUDA(c, newton_first_column(na, c->proj_c, c->kmax, st, c->proj_sel));
+            c->launches += 1;
+            for (int s = 0; s < nsrc; ++s) if (sel[s]) used[s] = LQ_PROJ_NEWTON;
+            LQ_CUDA(c, cudaStreamSynchronize(st));   // sel is host memory
+        }
+        return LQ_OK;
     }
 
-    std::vector<TslState> hs(nsrc);
-    LQ_CUDA(c, cudaMemcpyAsync(hs.data(), c->state, sizeof(TslState) * nsrc, cudaMemcpyDeviceToHost, st));
-    LQ_CUDA(c, cudaStreamSynchronize(st));
-    prof_collect(c);
-    if (rep) {
+    // y = |x| V_k sgn(T_k) e_1, or the second pass of a two-pass run (the same process from the
+    // same start, recombining as it goes).
+    int finish_enqueue(cudaStream_t st) {
+        if (!two) return recombine(0, 0, st);
+        int r = init(st);
+        return r ? r : lanczos(true, st);
+    }
+
+    // Reports (host); synchronises st.
+    int finish_complete(cudaStream_t st) {
+        std::vector<TslState> hs(nsrc);
+        LQ_CUDA(c, cudaMemcpyAsync(hs.data(), c->state, sizeof(TslState) * nsrc, cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(c, cudaStreamSynchronize(st));
+        prof_collect(c);
+        if (!rep) return LQ_OK;
         for (int s = 0; s < nsrc; ++s) {
             lq_report& R = rep[s];
             std::memset(&R, 0, sizeof(R));
@@ -538,7 +576,161 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
             if (used[s] == LQ_PROJ_QUAD && !(std::isfinite(check[s]) && check[s] <= o->proj_tol)) ns = LQ_ERR_NEWTON;
             R.status = ts < 0 ? ts : (ns != 0 ? ns : LQ_OK);
         }
+        return LQ_OK;
     }
+};
+
+bool ensure_cap_stream(lq_ctx* c) {
+    if (c->cap_stream) return true;
+    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess) return true;
+    cudaGetLastError();
+    c->cap_stream = nullptr;
+    return false;
+}
+
+// First pass (or the only one): replayed from a CUDA graph of the whole loop when graphs are on
+// and the kernels are not being timed one by one (lq_profile_enable); the graph is captured on
+// the first call with this configuration.  Any capture failure falls back to plain launches.
+int lanczos_graph(TslRun& t, cudaStream_t st) {
+    lq_ctx* c = t.c;
+    const lq_ctx::GraphKey key = t.key();
+    cudaGraphExec_t exec = nullptr;
+    for (auto& g : c->graphs) if (g.key == key) exec = g.exec;
+    if (!exec) {
+        if (!ensure_cap_stream(c)) return t.lanczos(false, st);
+        (void)update_grid(t.u.nelem, t.u.nsrc, t.u.partial_stride);   // its one-time device query, before capture
+        const long long launches0 = c->launches;
+        cudaGraph_t g = nullptr;
+        if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
+            cudaGetLastError();
+            return t.lanczos(false, st);
+        }
+        const int rr = t.lanczos(false, c->cap_stream);
+        const cudaError_t e = cudaStreamEndCapture(c->cap_stream, &g);
+        c->launches = launches0;
+        cudaError_t ei = cudaErrorUnknown;
+        if (!rr && e == cudaSuccess && g) ei = cudaGraphInstantiate(&exec, g, 0);
+        if (g) cudaGraphDestroy(g);
+        if (ei != cudaSuccess) {
+            cudaGetLastError();
+            c->err.clear();
+            return t.lanczos(false, st);
+        }
+        if (c->graphs.size() >= 8) { cudaGraphExecDestroy(c->graphs.front().exec); c->graphs.erase(c->graphs.begin()); }
+        c->graphs.push_back({key, exec});
+    }
+    LQ_CUDA(c, cudaGraphLaunch(exec, st));
+    c->launches += t.loop_launches();
+    return LQ_OK;
+}
+
+int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report* rep,
+            double* y0, double* y1, cudaStream_t st, const double* x_dev = nullptr,
+            const double* x_top = nullptr, int fn = FN_SIGN, const double2* shifts = nullptr,
+            bool store_left = false) {
+    TslRun t;
+    t.c = c; t.nf = nf; t.emode = emode; t.nsrc = nsrc; t.o = o; t.rep = rep;
+    t.y0 = y0; t.y1 = y1; t.fn = fn; t.shifts = shifts; t.store_left = store_left;
+    int r = t.setup(st, x_dev, x_top);
+    if (r) return r;
+    if ((r = t.graphed() ? lanczos_graph(t, st) : t.lanczos(false, st))) return r;
+    if ((r = t.proj_enqueue(st)) || (r = t.proj_complete(st))) return r;
+    if ((r = t.finish_enqueue(st))) return r;
+    return t.finish_complete(st);
+}
+
+// ---- ragged batches (lq_batch_apply) --------------------------------------------------------
+// Every member of a batch runs on its own context; the branch of member i is its context's
+// capture stream.  fork: each branch waits for the work enqueued on `from` so far; join: `into`
+// waits for the work enqueued on each branch so far.
+int fork_streams(lq_ctx* c0, cudaStream_t from, const std::vector<cudaStream_t>& to) {
+    cudaEvent_t e = nullptr;
+    LQ_CUDA(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t err = cudaEventRecord(e, from);
+    for (cudaStream_t s : to) if (err == cudaSuccess) err = cudaStreamWaitEvent(s, e, 0);
+    cudaEventDestroy(e);
+    LQ_CUDA(c0, err);
+    return LQ_OK;
+}
+int join_streams(lq_ctx* c0, const std::vector<cudaStream_t>& from, cudaStream_t into) {
+    for (cudaStream_t s : from) {
+        cudaEvent_t e = nullptr;
+        LQ_CUDA(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaError_t err = cudaEventRecord(e, s);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(into, e, 0);
+        cudaEventDestroy(e);
+        LQ_CUDA(c0, err);
+    }
+    return LQ_OK;
+}
+
+// The Krylov loops of all members as plain launches, each on its branch, between a fork from
+// and a join into st.
+int batch_lanczos_plain(std::vector<TslRun>& runs, cudaStream_t st) {
+    std::vector<cudaStream_t> br;
+    for (auto& t : runs) br.push_back(t.c->cap_stream);
+    int r = fork_streams(runs[0].c, st, br);
+    if (r) return r;
+    for (size_t i = 0; i < runs.size() && !r; ++i) r = runs[i].lanczos(false, br[i]);
+    const int rj = join_streams(runs[0].c, br, st);
+    return r ? r : rj;
+}
+
+// The Krylov loops of all members as one CUDA graph with one branch per member, captured the
+// first time this batch configuration is met and replayed with a single launch on st; the
+// branches are independent, so the GPU runs the members' kernels side by side.  Any capture
+// failure falls back to batch_lanczos_plain.
+int batch_lanczos_graph(std::vector<TslRun>& runs, cudaStream_t st) {
+    const size_t n = runs.size();
+    lq_ctx* c0 = runs[0].c;
+    std::vector<std::pair<lq_ctx*, lq_ctx::GraphKey>> key;
+    for (auto& t : runs) key.push_back({t.c, t.key()});
+    cudaGraphExec_t exec = nullptr;
+    {
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        for (auto& g : g_batch_graphs) if (g.key == key) exec = g.exec;
+    }
+    if (!exec) {
+        for (auto& t : runs) (void)update_grid(t.u.nelem, t.u.nsrc, t.u.partial_stride);   // device queries, before capture
+        std::vector<long long> launches0;
+        for (auto& t : runs) launches0.push_back(t.c->launches);
+        std::vector<cudaEvent_t> ev(n, nullptr);   // ev[0]: the fork; ev[i], i > 0: the join of member i
+        bool ok = true;
+        for (auto& e : ev) ok = ok && cudaEventCreateWithFlags(&e, cudaEventDisableTiming) == cudaSuccess;
+        const cudaStream_t origin = c0->cap_stream;
+        cudaError_t ei = cudaErrorUnknown;
+        if (ok && cudaStreamBeginCapture(origin, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            int rr = cudaEventRecord(ev[0], origin) == cudaSuccess ? LQ_OK : LQ_ERR_CUDA;
+            if (!rr) rr = runs[0].lanczos(false, origin);
+            for (size_t i = 1; i < n && !rr; ++i) {
+                const cudaStream_t b = runs[i].c->cap_stream;
+                if (cudaStreamWaitEvent(b, ev[0], 0) != cudaSuccess) { rr = LQ_ERR_CUDA; break; }
+                rr = runs[i].lanczos(false, b);
+                // join even after a failed launch, so that the capture ends on the origin stream
+                if (cudaEventRecord(ev[i], b) != cudaSuccess || cudaStreamWaitEvent(origin, ev[i], 0) != cudaSuccess)
+                    rr = rr ? rr : LQ_ERR_CUDA;
+            }
+            cudaGraph_t g = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(origin, &g);
+            if (!rr && e == cudaSuccess && g) ei = cudaGraphInstantiate(&exec, g, 0);
+            if (g) cudaGraphDestroy(g);
+        }
+        for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
+        for (size_t i = 0; i < n; ++i) runs[i].c->launches = launches0[i];
+        if (ei != cudaSuccess) {
+            cudaGetLastError();
+            for (auto& t : runs) t.c->err.clear();
+            return batch_lanczos_plain(runs, st);
+        }
+        std::lock_guard<std::mutex> lk(g_batch_mu);
+        if (g_batch_graphs.size() >= 8) {
+            cudaGraphExecDestroy(g_batch_graphs.front().exec);
+            g_batch_graphs.erase(g_batch_graphs.begin());
+        }
+        g_batch_graphs.push_back({key, exec});
+    }
+    LQ_CUDA(c0, cudaGraphLaunch(exec, st));
+    for (auto& t : runs) t.c->launches += t.loop_launches();
     return LQ_OK;
 }
 
@@ -1273,6 +1465,70 @@ int lq_overlap_apply(lq_ctx* c, const lq_direction* dir, const double* x, double
         if ((r = stage_out(c, y, c->io + reg, n, st))) return r;
     }
     LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_batch_apply(const lq_batch_item* items, int n, void* stream) {
+    if (!items || n < 1 || n > LQ_BATCH_MAX) return LQ_ERR_ARG;
+    lq_ctx* c0 = items[0].ctx;
+    if (!c0) return LQ_ERR_ARG;
+    for (int i = 0; i < n; ++i) {
+        const lq_batch_item& it = items[i];
+        lq_ctx* c = it.ctx;
+        if (!c) return set_err(c0, LQ_ERR_ARG, "batch member " + std::to_string(i) + ": null context");
+        for (int j = 0; j < i; ++j)
+            if (items[j].ctx == c) return set_err(c, LQ_ERR_ARG, "a context appears twice in the batch");
+        if (c->device != c0->device) return set_err(c, LQ_ERR_ARG, "batch members on different devices");
+        if (!it.x || !it.y_sign || (it.dir && !it.y_deriv)) return set_err(c, LQ_ERR_ARG, "null argument");
+        int r = check_ready(c, it.nsrc, it.dir ? 1 : 0);
+        if (r || (r = check_opts(c, it.opts))) return r;
+        if (it.opts->two_pass) return set_err(c, LQ_ERR_ARG, "two-pass runs are not batched");
+        if (!ensure_cap_stream(c)) return set_err(c, LQ_ERR_CUDA, "cannot create the member's stream");
+    }
+    cudaStream_t st = (cudaStream_t)stream;
+    std::vector<TslRun> runs((size_t)n);
+    std::vector<cudaStream_t> br((size_t)n);
+    int r = LQ_OK;
+    // direction, source and start vectors of every member on st (and its schedule, tuned there
+    // on first use)
+    for (int i = 0; i < n; ++i) {
+        const lq_batch_item& it = items[i];
+        lq_ctx* c = it.ctx;
+        const size_t reg = (size_t)c->nsrc * c->V * 24;
+        if (it.dir && (r = lq_set_direction(c, it.dir, st))) return r;
+        if ((r = stage_in(c, c->io, it.x, (size_t)it.nsrc * c->V * 24, st))) return r;
+        TslRun& t = runs[(size_t)i];
+        t.c = c; t.nsrc = it.nsrc; t.o = it.opts; t.rep = it.report;
+        t.nf = it.dir ? 2 : 1;
+        t.emode = it.dir ? emode_of(c) : 0;
+        t.y0 = c->io + reg;
+        t.y1 = it.dir ? c->io + 2 * reg : nullptr;
+        if ((r = t.setup(st, c->io, nullptr))) return r;
+        br[(size_t)i] = c->cap_stream;
+    }
+    bool graphed = true;
+    for (auto& t : runs) graphed = graphed && t.graphed();
+    if ((r = graphed ? batch_lanczos_graph(runs, st) : batch_lanczos_plain(runs, st))) return r;
+    // projected signs, recombinations and outputs on the members' branches
+    if ((r = fork_streams(c0, st, br))) return r;
+    for (int i = 0; i < n && !r; ++i) r = runs[(size_t)i].proj_enqueue(br[(size_t)i]);
+    for (int i = 0; i < n && !r; ++i) r = runs[(size_t)i].proj_complete(br[(size_t)i]);
+    for (int i = 0; i < n && !r; ++i) r = runs[(size_t)i].finish_enqueue(br[(size_t)i]);
+    for (int i = 0; i < n && !r; ++i) {
+        const lq_batch_item& it = items[i];
+        lq_ctx* c = it.ctx;
+        const size_t reg = (size_t)c->nsrc * c->V * 24, cnt = (size_t)it.nsrc * c->V * 24;
+        if (it.dir) {
+            if ((r = stage_out(c, it.y_deriv, c->io + reg, cnt, br[(size_t)i]))) break;
+            r = stage_out(c, it.y_sign, c->io + 2 * reg, cnt, br[(size_t)i]);
+        } else {
+            r = stage_out(c, it.y_sign, c->io + reg, cnt, br[(size_t)i]);
+        }
+    }
+    for (int i = 0; i < n && !r; ++i) r = runs[(size_t)i].finish_complete(br[(size_t)i]);
+    const int rj = join_streams(c0, br, st);
+    if (r || (r = rj)) return r;
+    LQ_CUDA(c0, cudaStreamSynchronize(st));
     return LQ_OK;
 }
 

@@ -37,7 +37,7 @@ EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_u
             "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
             "lq_profile_read", "lq_newton_sign_noalloc", "lq_error_estimate",
             "lq_upload_deflation", "lq_deflation_derivatives", "lq_sign_bilinear_grad",
-            "lq_dense_eig", "lq_compute_deflation", "lq_overlap_apply"]
+            "lq_dense_eig", "lq_compute_deflation", "lq_overlap_apply", "lq_batch_apply"]
 
 
 class LatticeDesc(ctypes.Structure):
@@ -86,6 +86,12 @@ class Direction(ctypes.Structure):
 _lib = None
 
 
+class BatchItem(ctypes.Structure):
+    _fields_ = [("ctx", ctypes.c_void_p), ("dir", ctypes.POINTER(Direction)), ("x", ctypes.c_void_p),
+                ("y_sign", ctypes.c_void_p), ("y_deriv", ctypes.c_void_p), ("nsrc", ctypes.c_int),
+                ("opts", ctypes.POINTER(Opts)), ("report", ctypes.POINTER(Report))]
+
+
 def lib():
     """Load liblq.so (built in-tree by paper_1611_00195_gb300.build); raise if it is missing."""
     global _lib
@@ -123,6 +129,7 @@ def lib():
         L.lq_dense_eig.argtypes = [I, P, P, P]
         L.lq_compute_deflation.argtypes = [P, ctypes.POINTER(EigOpts), P, P, P, P]
         L.lq_newton_sign_noalloc.argtypes = [P, P, I, I, I, D, ctypes.POINTER(I), P]
+        L.lq_batch_apply.argtypes = [ctypes.POINTER(BatchItem), I, P]
         for name in EXPORTED:
             if name not in ("lq_default_opts", "lq_destroy", "lq_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -218,6 +225,42 @@ def newton_sign_noalloc(X, max_iter=50, tol=1e-13):
     if code != LQ_OK:
         raise LQError(code, "lq_newton_sign_noalloc (k <= 128, nb <= 8)")
     return S, list(iters)
+
+
+def batch_apply(members):
+    """Ragged batch through lq_batch_apply: the Krylov loops of all members in one CUDA graph
+    launch.  `members` is a list of dicts with keys ctx (a Context, each at most once), x
+    ([nsrc][V][4][3]), k, and optionally kind / field (a derivative along that direction, as in
+    Context.sign_derivative_apply; kind=None for the sign alone) and any option of Context.opts.
+    Returns one (y_sign, y_deriv or None, reports) per member."""
+    n = len(members)
+    items = (BatchItem * n)()
+    keep, outs = [], []
+    for i, m in enumerate(members):
+        c = m["ctx"]
+        x = _as_c128(m["x"])
+        nsrc = x.shape[0]
+        kind = m.get("kind", LQ_DIR_MU)
+        ys = _empty_like(x)
+        yd = _empty_like(x) if kind is not None else None
+        o = Context.opts(m["k"], **{key: v for key, v in m.items() if key not in ("ctx", "x", "k", "kind", "field")})
+        rep = (Report * nsrc)()
+        d, f = c._direction(kind, m.get("field")) if kind is not None else (None, None)
+        keep += [x, o, rep, d, f]
+        items[i] = BatchItem(c._h, ctypes.pointer(d) if d is not None else None, _ptr(x), _ptr(ys), _ptr(yd),
+                             int(nsrc), ctypes.pointer(o), rep)
+        outs.append((ys, yd, rep))
+    code = lib().lq_batch_apply(items, n, _stream(keep[0]))
+    if code != LQ_OK:
+        msg = ""   # from the first member context that holds one
+        for m in members:
+            e = lib().lq_last_error(m["ctx"]._h)
+            if e:
+                msg = e.decode()
+                break
+        raise LQError(code, msg)
+    del keep
+    return [(ys, yd, [r.as_dict() for r in rep]) for ys, yd, rep in outs]
 
 
 class Context:

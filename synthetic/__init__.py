@@ -17,7 +17,13 @@ Conventions (shared by every consumer):
 import numpy as np
 
 __all__ = ["volume", "gauge_field", "gaussian_source", "z2_source",
-           "su3_direction", "u1_direction"]
+           "su3_direction", "u1_direction", "RAGGED_BATCH", "RAGGED_MU"]
+
+# The ragged batch of the batching workload: four lattices of uneven size, link spread eps
+# and Krylov depth k, as (dims, eps, k, gauge seed); Z2-noise sources; mu = RAGGED_MU.
+RAGGED_BATCH = [((6, 6, 6, 6), 0.3, 100, 31), ((8, 8, 8, 8), 0.5, 200, 32),
+                ((8, 12, 12, 12), 0.3, 250, 33), ((10, 10, 10, 10), 0.5, 300, 34)]
+RAGGED_MU = 0.2
 
 
 def volume(dims):

@@ -59,6 +59,17 @@ def test_create_rejects_bad_descriptors_without_gpu(built_lib):
     assert L.lq_create(None, ctypes.byref(h)) == -1
 
 
+def test_batch_rejects_bad_arguments_without_gpu(built_lib):
+    """lq_batch_apply validates the batch size and member contexts on the host first."""
+    from paper_1611_00195_gb300 import lq
+    L = lq.lib()
+    items = (lq.BatchItem * 17)()
+    assert L.lq_batch_apply(None, 1, None) == -1
+    assert L.lq_batch_apply(items, 0, None) == -1
+    assert L.lq_batch_apply(items, 17, None) == -1      # more than LQ_BATCH_MAX
+    assert L.lq_batch_apply(items, 1, None) == -1       # null member context
+
+
 @pytest.mark.parametrize("n", [1, 2, 5, 30, 64])
 def test_dense_eig_host_utility(built_lib, n):
     """The host eigensolver used by the deflation-space Rayleigh-Ritz steps, against numpy."""
