@@ -468,6 +468,48 @@ def main():
                                  "sequential_calls": {"value": len(members) * nr / (ms_seq / 1e3), "ms_per_step": ms_seq},
                                  "status": [[x["status"] for x in m_out[2]] for m_out in rb]}
         del members
+        # the precision workload: 8^4, one Gaussian source, k = 200, mu in {0, 0.1, 0.2}; the
+        # plain FP64 GPU path against the mixed path (their relative difference per mu; the
+        # FP64 path's parity with the oracle is a GPU test)
+        d2, k2 = (8, 8, 8, 8), 200
+        x2p = torch.from_numpy(syn.gaussian_source(d2, SOURCE_SEED, nsrc=1)).to(dev)
+        U2 = torch.from_numpy(syn.gauge_field(d2, EPS, GAUGE_SEED)).to(dev)
+        prec_rows = []
+        for mu2 in (0.0, 0.1, 0.2):
+            row = {"mu": mu2}
+            res2 = {}
+            for pname, pcode in (("fp64", lq.LQ_FP64), ("mixed", lq.LQ_MIXED)):
+                c2 = lq.Context(d2, m_w=M_W, mu=mu2, precision=pcode)
+                c2.upload_gauge(U2)
+                c2.reserve(k2, 1, True)
+                ms2, r2 = timed(lambda: c2.sign_derivative_apply(x2p, k2), steps=3)
+                res2[pname] = r2
+                row[pname] = {"solves_per_s": 1 / (ms2 / 1e3), "ms": ms2, "status": r2[2][0]["status"]}
+                del c2
+            rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+            row["mixed_vs_fp64_rel_diff"] = {"sign": rel(res2["mixed"][0], res2["fp64"][0]),
+                                             "deriv": rel(res2["mixed"][1], res2["fp64"][1])}
+            prec_rows.append(row)
+        extra["precision_8x8c3"] = {"k": k2, "source": "1 Gaussian", "eps": EPS, "per_mu": prec_rows}
+        # the differentiation workload: 12x12^3, k = 300, mu = 0.3, S = Re <y|sgn(H)|x> with the
+        # force on all 4 V links x 8 generators and dS/dmu from the adjoint (one call = two TSL
+        # runs, the projected block sign and the per-link contraction)
+        d5, k5 = (12, 12, 12, 12), 300
+        U5 = torch.from_numpy(syn.gauge_field(d5, EPS, GAUGE_SEED)).to(dev)
+        x5 = torch.from_numpy(syn.gaussian_source(d5, SOURCE_SEED)).to(dev)
+        y5 = torch.from_numpy(syn.gaussian_source(d5, SOURCE_SEED + 1)).to(dev)
+        force = {"k": k5, "mu": MU, "outputs": "S, dS/domega [4][V][8], dS/dmu"}
+        F5 = {}
+        for pname, pcode in (("mixed", lq.LQ_MIXED), ("fp64", lq.LQ_FP64)):
+            c5 = lq.Context(d5, m_w=M_W, mu=MU, precision=pcode)
+            c5.upload_gauge(U5)
+            c5.reserve(k5, 2, block=False, adjoint=True)
+            ms5, r5 = timed(lambda: c5.bilinear_grad(x5, y5, k5), steps=3)
+            F5[pname] = r5[1]
+            force[pname] = {"value": 1 / (ms5 / 1e3), "unit": "forces/s", "ms": ms5}
+            del c5
+        force["mixed_vs_fp64_rel_diff"] = float(torch.linalg.vector_norm(F5["mixed"] - F5["fp64"]) / torch.linalg.vector_norm(F5["fp64"]))
+        extra["force_12x12c3"] = force
 
     # accuracy: eps_A of Sec. 4 (sign and derivative) on two of the sources, no deflation
     x2 = xd[:2].contiguous()

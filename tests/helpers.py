@@ -36,3 +36,29 @@ def oracle_ops(dims, U, mu, kind=0, field=None, m_w=-2.0):
         def Eh(v):
             return od.apply_dH_dir_dag(lat, U, Y, v, mu).ravel()
     return lat, A, Ah, E, Eh
+
+
+def oracle_block_tsl_run(job):
+    """One oracle block-TSL run (Eq. (2.6), d/dmu) for a process pool, built from seeds so that
+    nothing but plain data crosses the process boundary.  job = (dims, eps, gauge_seed,
+    source_seed, mu, k, perturbation, perturbation_seed); perturbation None, "input" (1e-16
+    relative noise on the source: the FP64 rounding sensitivity) or "step" (6e-8 relative noise
+    on every operator application: the FP32 sensitivity).  Returns (d sgn(H) x, sgn(H) x)."""
+    import synthetic as syn
+    from oracle import tsl as ot
+    dims, eps, gseed, sseed, mu, k, pert, pseed = job
+    U = syn.gauge_field(dims, eps, gseed)
+    x = syn.gaussian_source(dims, sseed, nsrc=1)[0].ravel()
+    lat, A, Ah, E, Eh = oracle_ops(dims, U, mu)
+    rng = np.random.default_rng(pseed)
+    if pert == "input":
+        x = x * (1 + 1e-16 * rng.standard_normal(x.shape))
+    elif pert == "step":
+        def wrap(op):
+            def f(v):
+                y = op(v)
+                return y * (1 + 6e-8 * (rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape)) / np.sqrt(2))
+            return f
+        A, Ah, E, Eh = wrap(A), wrap(Ah), wrap(E), wrap(Eh)
+    rd, rs, _ = ot.tsl_sign_derivative(A, Ah, E, Eh, x, k)
+    return rd, rs

@@ -111,3 +111,78 @@ def test_force_mixed_precision(lqlib):
     e = np.linalg.norm(F32 - F64) / np.linalg.norm(F64)
     print("force mixed vs fp64 k=%d: %.3g" % (k, e))
     assert e < 1e-3
+
+
+def _exp_direction(U, omega, t):
+    """Links exp(i t Omega_nu(x)) U_nu(x) for the su(3) field omega [4][V][8] (batched
+    eigendecomposition of the Hermitian Omega; test infrastructure only)."""
+    w, Q = np.linalg.eigh(od.su3_tangent(omega))
+    E = np.einsum("dsij,dsj,dskj->dsik", Q, np.exp(1j * t * w), Q.conj())
+    return np.einsum("dsij,dsjk->dsik", E, U)
+
+
+def test_force_workload_12x12c3(lqlib):
+    """The differentiation workload at full size: 12x12^3 (n = 248832), eps = 0.4, mu = 0.3,
+    Gaussian x and y.  (a) At the workload's depth k = 300, the torch.autograd.Function (mixed
+    and FP64) gives the force for all 4 V links x 8 generators and dS/dmu within 10 eps_A of
+    the converged force (eps_A of Sec. 4 for x and y at that depth).  (b) At a depth where the
+    process has converged (k = 1800, eps_A <= 1e-10), central differences with step 1e-4 of
+    S = Re <y|sgn(H)|x> (each S one FP64 solve on the GPU) along 16 random su(3) link
+    directions and in mu agree with the force.  Below convergence the finite differences
+    measure the change of the Krylov truncation error with the links, not the derivative."""
+    from paper_1611_00195_gb300 import lq
+    dims, h = (12, 12, 12, 12), 1e-4
+    V = int(np.prod(dims))
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = torch.from_numpy(syn.gaussian_source(dims, 5)).cuda()
+    y = torch.from_numpy(syn.gaussian_source(dims, 6)).cuda()
+    kc = 1800
+    c = _ctx(lq, dims, U, kc)
+    S, F, dmu = c.bilinear_grad(x, y, kc)
+    F = F.cpu().numpy()
+    x1 = x.reshape(1, V, 4, 3)
+    eps_c = max(c.error_estimate(x1, kc)[0], c.error_estimate(y.reshape(1, V, 4, 3), kc)[0])
+    assert eps_c <= 1e-10, eps_c
+
+    def S_of():
+        z, rep = c.sign_apply(x1, kc)
+        assert rep[0]["status"] == 0
+        return float(torch.real(torch.vdot(y.reshape(-1), z.reshape(-1))))
+    worst = 0.0
+    for seed in range(16):
+        om = syn.su3_direction(dims, 100 + seed)
+        Sp = []
+        for t in (h, -h):
+            c.upload_gauge(torch.from_numpy(_exp_direction(U, om, t)).cuda())
+            Sp.append(S_of())
+        d = float(np.sum(om * F))
+        fd = (Sp[0] - Sp[1]) / (2 * h)
+        worst = max(worst, abs(fd - d) / abs(d))
+        assert abs(fd - d) <= 1e-4 * abs(d) + 1e-12, (seed, fd, d)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    Sm = []
+    for m in (MU + h, MU - h):
+        c.set_mu(m)
+        Sm.append(S_of())
+    c.set_mu(MU)
+    fdm = (Sm[0] - Sm[1]) / (2 * h)
+    print("12^4 k=%d (eps_A %.2g): force vs central differences on 16 directions, worst rel %.3g; dS/dmu %.3g"
+          % (kc, eps_c, worst, abs(fdm - dmu) / abs(dmu)))
+    assert abs(fdm - dmu) <= 1e-6 * abs(dmu)
+    del c
+
+    k = 300
+    for prec in (1, 0):
+        cw = _ctx(lq, dims, U, k, prec)
+        omega = torch.zeros((4, V, 8), dtype=torch.float64, device="cuda", requires_grad=True)
+        mu = torch.tensor(MU, dtype=torch.float64, requires_grad=True)
+        Sw = lq.SignBilinearForce.apply(omega, mu, cw, x, y, k)
+        Sw.backward()
+        eps_k = max(cw.error_estimate(x1, k)[0], cw.error_estimate(y.reshape(1, V, 4, 3), k)[0])
+        eF = float(np.linalg.norm(omega.grad.cpu().numpy() - F) / np.linalg.norm(F))
+        emu = abs(mu.grad.item() - dmu) / abs(dmu)
+        eS = abs(Sw.item() - S) / abs(S)
+        print("12^4 k=%d prec %d via autograd: S %.3g force %.3g dS/dmu %.3g against the converged values (eps_A %.3g)"
+              % (k, prec, eS, eF, emu, eps_k))
+        assert max(eS, eF, emu) <= 10 * eps_k
+        del cw
