@@ -510,6 +510,24 @@ def main():
             del c5
         force["mixed_vs_fp64_rel_diff"] = float(torch.linalg.vector_norm(F5["mixed"] - F5["fp64"]) / torch.linalg.vector_norm(F5["fp64"]))
         extra["force_12x12c3"] = force
+        # accuracy at a converged depth on this workload: 2 sources, k = 2400, FP64 and mixed, with
+        # eps_A of the derivative (Sec. 4) for each path and their relative difference
+        kc, nc = 2400, 2
+        xc = xd[:nc].contiguous()
+        conv = {"k": kc, "sources": nc}
+        resc = {}
+        for pname, pcode in (("fp64", lq.LQ_FP64), ("mixed", lq.LQ_MIXED)):
+            cc = lq.Context(DIMS, m_w=M_W, mu=MU, precision=pcode)
+            cc.upload_gauge(torch.from_numpy(U).to(dev))
+            cc.reserve(kc, nc, True)
+            msc, rc = timed(lambda: cc.sign_derivative_apply(xc, kc), steps=1)
+            resc[pname] = rc
+            conv[pname] = {"ms": msc, "eps_A_deriv": cc.error_estimate(xc, kc, kind=lq.LQ_DIR_MU).tolist(),
+                           "status": [x["status"] for x in rc[2]], "projected": [x["projected"] for x in rc[2]]}
+            del cc
+        relv = lambda a, b: (torch.linalg.vector_norm((a - b).reshape(nc, -1), dim=1) / torch.linalg.vector_norm(b.reshape(nc, -1), dim=1)).tolist()
+        conv["mixed_vs_fp64_rel_diff"] = {"sign": relv(resc["mixed"][0], resc["fp64"][0]), "deriv": relv(resc["mixed"][1], resc["fp64"][1])}
+        extra["converged_depth_accuracy"] = conv
 
     # accuracy: eps_A of Sec. 4 (sign and derivative) on two of the sources, no deflation
     x2 = xd[:2].contiguous()
