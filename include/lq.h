@@ -110,6 +110,13 @@ typedef struct {
                               plain launches.  Off while lq_profile_enable times kernels.  The
                               first call of a configuration captures: make it outside any stream
                               capture of the caller's own                                    */
+    int split;             /* -1 / 1: a derivative solve in FP32 with an even nsrc >= 8 runs the
+                              Krylov loops of its two source halves as concurrent branches, so
+                              that the bandwidth-bound update of one half overlaps the
+                              issue-bound stencil of the other (default -1); 0: one batch.  Off
+                              while lq_profile_enable times kernels, for two-pass runs and for
+                              the adjoint.  Results differ from the unsplit run by FP32
+                              rounding only (each half has its own reduction grids)           */
 } lq_opts;
 
 /* Projected step sgn(T_k) e_1 (Sec. 2):

@@ -268,12 +268,8 @@ void free_workspace(lq_ctx* c) {
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
     const int nvar = (c->prec == LQ_FP64) ? 2 : 7;
-    if (c->tuned_nsrc != h.nsrc) {
-        for (auto& row : c->tuned_variant) for (int& v : row) v = -1;
-        c->tuned_nsrc = h.nsrc;
-    }
-    int& slot = c->tuned_variant[nf][emode];
-    if (slot >= 0) { *variant = slot; return LQ_OK; }
+    for (const auto& t : c->tuned)
+        if (t.nsrc == h.nsrc && t.nf == nf && t.emode == emode) { *variant = t.variant; return LQ_OK; }
     h.j = 0;
     h.kmax_run = std::max(h.kmax_run, 2);   // never mark a source finished while tuning
     cudaEvent_t e0, e1;
@@ -297,7 +293,7 @@ int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* vari
     cudaEventDestroy(e0);
     cudaEventDestroy(e1);
     const int bestv = (int)(std::min_element(best.begin(), best.end()) - best.begin());
-    slot = bestv;
+    c->tuned.push_back({h.nsrc, nf, emode, bestv});
     *variant = bestv;
     return LQ_OK;
 }
@@ -320,10 +316,12 @@ struct TslRun {
     double* y1 = nullptr;
     const double2* shifts = nullptr;
     bool store_left = false;
+    int s0 = 0;                // first source of this run in the context's per-source arrays
+    bool args_only = false;    // build the launch arguments only (no start vectors, no tuning)
 
     int k = 0, ring = 0;
     bool two = false;
-    size_t F = 0, vstride = 0, sst = 0, cb = 0;
+    size_t F = 0, vstride = 0, sst = 0, cb = 0, sb = 0, sl = 0, sio = 0;
     InitArgs ia;
     HopArgs h;
     UpdArgs u;
@@ -334,9 +332,10 @@ struct TslRun {
     int quad_attempt = -1;   // quadrature passes enqueued so far - 1; -1: no quadrature
 
     void* bvec(int j) const {
-        return reinterpret_cast<char*>(c->basis) + (size_t)(ring ? j % ring : j) * vstride * cb;
+        return reinterpret_cast<char*>(c->basis) + ((size_t)s0 * sb + (size_t)(ring ? j % ring : j) * vstride) * cb;
     }
-    void* lvec(int j) const { return reinterpret_cast<char*>(c->left) + (size_t)(j % 3) * vstride * cb; }
+    void* lvec(int j) const { return reinterpret_cast<char*>(c->left) + ((size_t)s0 * sl + (size_t)(j % 3) * vstride) * cb; }
+    void* ofs(void* base, size_t chunks) const { return reinterpret_cast<char*>(base) + (size_t)s0 * chunks * cb; }
 
     int init(cudaStream_t st) {
         cudaEvent_t e0 = prof_begin(c, st);
@@ -353,9 +352,9 @@ struct TslRun {
         F = fe(c);
         vstride = (size_t)nf * F;                    // Chunk elements per Krylov vector
         const int slots = c->ring > 0 ? c->ring : c->kmax;   // basis vectors held per source
-        const size_t sb = (size_t)slots * vstride;   // per source: basis
-        const size_t sl = 3 * vstride;               // per source: left ring
-        const size_t sio = vstride;                  // per source: operator outputs
+        sb = (size_t)slots * vstride;                // per source: basis
+        sl = 3 * vstride;                            // per source: left ring
+        sio = vstride;                               // per source: operator outputs
         cb = chunk_bytes(c);
         // Two-pass run (lq_opts.two_pass): the first pass keeps only a ring of basis vectors and
         // yields T_k; the second reruns the same (deterministic) process and recombines windows
@@ -364,26 +363,36 @@ struct TslRun {
         ring = two ? std::min(slots, kTwoPassRing) : 0;
         sst = (size_t)c->kmax * F;                   // per source: stored left basis (NF = 1)
 
+        // per-source arrays from source s0 on (a source group of a split run); the group's
+        // last-block counters are a block of 3 nsrc from 3 s0 on
+        const size_t xs = (size_t)s0 * c->V * 24;
+        TslState* state = c->state + s0;
+        double* partials = c->partials + (size_t)s0 * c->partial_blocks * 8;
+        int* counters = c->counters + (size_t)3 * s0;
+        const size_t ks = (size_t)s0 * c->kmax;
         std::memset(&ia, 0, sizeof(ia));
-        ia.V = c->V; ia.nsrc = nsrc; ia.x = x_dev ? x_dev : c->io; ia.xt = x_top; ia.v1 = bvec(0); ia.w1 = lvec(0);
-        ia.src_stride_basis = sb; ia.src_stride_left = sl; ia.state = c->state;
-        ia.partials = c->partials; ia.partial_stride = c->partial_blocks; ia.counters = c->counters;
+        ia.V = c->V; ia.nsrc = nsrc; ia.x = (x_dev ? x_dev : c->io) + xs; ia.xt = x_top ? x_top + xs : nullptr;
+        ia.v1 = bvec(0); ia.w1 = lvec(0);
+        ia.src_stride_basis = sb; ia.src_stride_left = sl; ia.state = state;
+        ia.partials = partials; ia.partial_stride = c->partial_blocks; ia.counters = counters;
         ia.breakdown_tol = o->breakdown_tol;
         if (store_left) { ia.w1_store = c->lbasis; ia.src_stride_store = sst; }
-        int r = init(st);
+        int r = args_only ? LQ_OK : init(st);
         if (r) return r;
 
         h = base_hop(c);
         h.nsrc = nsrc; h.nsides = 2; h.side0 = 0;
         set_side(h, 0, c, 0, emode);
         set_side(h, 1, c, 1, emode);
-        h.state = c->state; h.partials = c->partials; h.partial_stride = c->partial_blocks; h.counters = c->counters;
-        h.alpha = c->alpha; h.scale = c->scale; h.kmax = c->kmax; h.kmax_run = k;
+        h.state = state; h.partials = partials; h.partial_stride = c->partial_blocks; h.counters = counters;
+        h.alpha = c->alpha + ks; h.scale = c->scale + ks; h.kmax = c->kmax; h.kmax_run = k;
         h.uscale = store_left ? c->uscale : nullptr;
         h.src_stride_in[0] = sb; h.src_stride_in[1] = sl;
         h.src_stride_out[0] = sio; h.src_stride_out[1] = sio;
-        h.out[0] = c->rout; h.out[1] = c->lout;
-        if (o->hop_variant >= 0) {
+        h.out[0] = ofs(c->rout, sio); h.out[1] = ofs(c->lout, sio);
+        if (args_only) {
+            h.variant = 0;
+        } else if (o->hop_variant >= 0) {
             // the schedule that actually runs (and is reported): FP64 has schedules 0 and 1 only,
             // the plain operator 0 only, and schedule 6 needs tiles that cover the lattice
             int v = (nf == 2) ? o->hop_variant : 0;
@@ -399,10 +408,10 @@ struct TslRun {
         }
 
         std::memset(&u, 0, sizeof(u));
-        u.nelem = vstride; u.nsrc = nsrc; u.rout = c->rout; u.lout = c->lout;
+        u.nelem = vstride; u.nsrc = nsrc; u.rout = ofs(c->rout, sio); u.lout = ofs(c->lout, sio);
         u.src_stride_io = sio; u.src_stride_basis = sb; u.src_stride_left = sl;
-        u.state = c->state; u.partials = c->partials; u.partial_stride = c->partial_blocks; u.counters = c->counters;
-        u.beta = c->beta; u.delta = c->delta; u.kmax = c->kmax;
+        u.state = state; u.partials = partials; u.partial_stride = c->partial_blocks; u.counters = counters;
+        u.beta = c->beta + ks; u.delta = c->delta + ks; u.kmax = c->kmax;
 
         std::memset(&ra, 0, sizeof(ra));
         ra.V = c->V; ra.nsrc = nsrc; ra.basis = c->basis; ra.src_stride_basis = sb; ra.vec_stride = vstride;
@@ -456,7 +465,7 @@ struct TslRun {
         return LQ_OK;
     }
 
-    lq_ctx::GraphKey key() const { return {k, nsrc, nf, emode, h.variant, store_left ? 1 : 0, ring, c->desc.mu}; }
+    lq_ctx::GraphKey key(int groups = 1) const { return {k, nsrc, nf, emode, h.variant, store_left ? 1 : 0, ring, c->desc.mu, groups}; }
     bool graphed() const { return o->graph != 0 && !c->prof_on; }
     long long loop_launches() const { return 2 * (long long)k - 1; }
 
@@ -580,13 +589,38 @@ struct TslRun {
     }
 };
 
-bool ensure_cap_stream(lq_ctx* c) {
-    if (c->cap_stream) return true;
-    if (cudaStreamCreateWithFlags(&c->cap_stream, cudaStreamNonBlocking) == cudaSuccess) return true;
+bool ensure_cap_stream(lq_ctx* c, bool second = false) {
+    cudaStream_t& s = second ? c->cap_stream2 : c->cap_stream;
+    if (s) return true;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) == cudaSuccess) return true;
     cudaGetLastError();
-    c->cap_stream = nullptr;
+    s = nullptr;
     return false;
 }
+
+// fork: each stream of `to` waits for the work enqueued on `from` so far; join: `into` waits for
+// the work enqueued on each stream of `from` so far.
+int fork_streams(lq_ctx* c0, cudaStream_t from, const std::vector<cudaStream_t>& to) {
+    cudaEvent_t e = nullptr;
+    LQ_CUDA(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+    cudaError_t err = cudaEventRecord(e, from);
+    for (cudaStream_t s : to) if (err == cudaSuccess) err = cudaStreamWaitEvent(s, e, 0);
+    cudaEventDestroy(e);
+    LQ_CUDA(c0, err);
+    return LQ_OK;
+}
+int join_streams(lq_ctx* c0, const std::vector<cudaStream_t>& from, cudaStream_t into) {
+    for (cudaStream_t s : from) {
+        cudaEvent_t e = nullptr;
+        LQ_CUDA(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
+        cudaError_t err = cudaEventRecord(e, s);
+        if (err == cudaSuccess) err = cudaStreamWaitEvent(into, e, 0);
+        cudaEventDestroy(e);
+        LQ_CUDA(c0, err);
+    }
+    return LQ_OK;
+}
+
 
 // First pass (or the only one): replayed from a CUDA graph of the whole loop when graphs are on
 // and the kernels are not being timed one by one (lq_profile_enable); the graph is captured on
@@ -624,6 +658,62 @@ int lanczos_graph(TslRun& t, cudaStream_t st) {
     return LQ_OK;
 }
 
+// The Krylov loops of the two source halves g[0], g[1] of a split run as concurrent branches on
+// the context's two capture streams, forked from and joined into st: replayed from one CUDA graph
+// when graphs are on (captured on the first call of the configuration), else plain launches.
+int lanczos_split(TslRun (&g)[2], cudaStream_t st, bool graphed) {
+    lq_ctx* c = g[0].c;
+    const std::vector<cudaStream_t> br{c->cap_stream, c->cap_stream2};
+    auto plain = [&]() -> int {
+        int r = fork_streams(c, st, br);
+        if (r) return r;
+        r = g[0].lanczos(false, br[0]);
+        if (!r) r = g[1].lanczos(false, br[1]);
+        const int rj = join_streams(c, br, st);
+        return r ? r : rj;
+    };
+    if (!graphed) return plain();
+    const lq_ctx::GraphKey key = g[0].key(2);
+    cudaGraphExec_t exec = nullptr;
+    for (auto& e : c->graphs) if (e.key == key) exec = e.exec;
+    if (!exec) {
+        for (auto& t : g) (void)update_grid(t.u.nelem, t.u.nsrc, t.u.partial_stride);   // device queries, before capture
+        const long long launches0 = c->launches;
+        cudaEvent_t ev[2] = {nullptr, nullptr};   // fork, join
+        bool ok = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) == cudaSuccess &&
+                  cudaEventCreateWithFlags(&ev[1], cudaEventDisableTiming) == cudaSuccess;
+        cudaError_t ei = cudaErrorUnknown;
+        if (ok && cudaStreamBeginCapture(br[0], cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+            int rr = (cudaEventRecord(ev[0], br[0]) == cudaSuccess && cudaStreamWaitEvent(br[1], ev[0], 0) == cudaSuccess)
+                         ? LQ_OK : LQ_ERR_CUDA;
+            if (!rr) {
+                rr = g[0].lanczos(false, br[0]);
+                const int r1 = g[1].lanczos(false, br[1]);
+                rr = rr ? rr : r1;
+                // join even after a failed launch, so that the capture ends on the origin stream
+                if (cudaEventRecord(ev[1], br[1]) != cudaSuccess || cudaStreamWaitEvent(br[0], ev[1], 0) != cudaSuccess)
+                    rr = rr ? rr : LQ_ERR_CUDA;
+            }
+            cudaGraph_t gr = nullptr;
+            const cudaError_t e = cudaStreamEndCapture(br[0], &gr);
+            if (!rr && e == cudaSuccess && gr) ei = cudaGraphInstantiate(&exec, gr, 0);
+            if (gr) cudaGraphDestroy(gr);
+        }
+        for (cudaEvent_t e : ev) if (e) cudaEventDestroy(e);
+        c->launches = launches0;
+        if (ei != cudaSuccess) {
+            cudaGetLastError();
+            c->err.clear();
+            return plain();
+        }
+        if (c->graphs.size() >= 8) { cudaGraphExecDestroy(c->graphs.front().exec); c->graphs.erase(c->graphs.begin()); }
+        c->graphs.push_back({key, exec});
+    }
+    LQ_CUDA(c, cudaGraphLaunch(exec, st));
+    c->launches += g[0].loop_launches() + g[1].loop_launches();
+    return LQ_OK;
+}
+
 int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report* rep,
             double* y0, double* y1, cudaStream_t st, const double* x_dev = nullptr,
             const double* x_top = nullptr, int fn = FN_SIGN, const double2* shifts = nullptr,
@@ -631,9 +721,28 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     TslRun t;
     t.c = c; t.nf = nf; t.emode = emode; t.nsrc = nsrc; t.o = o; t.rep = rep;
     t.y0 = y0; t.y1 = y1; t.fn = fn; t.shifts = shifts; t.store_left = store_left;
-    int r = t.setup(st, x_dev, x_top);
-    if (r) return r;
-    if ((r = t.graphed() ? lanczos_graph(t, st) : t.lanczos(false, st))) return r;
+    // lq_opts.split: the two source halves' Krylov loops as concurrent branches (the update of one
+    // half, bandwidth-bound, overlaps the stencil of the other, issue-bound)
+    const bool split = o->split != 0 && !c->prof_on && c->prec != LQ_FP64 && nf == 2 && fn == FN_SIGN && !store_left &&
+                       !(o->two_pass != 0 && o->kmax > 1) && nsrc >= 8 && nsrc % 2 == 0 &&
+                       ensure_cap_stream(c) && ensure_cap_stream(c, true);
+    int r;
+    if (!split) {
+        if ((r = t.setup(st, x_dev, x_top))) return r;
+        if ((r = t.graphed() ? lanczos_graph(t, st) : t.lanczos(false, st))) return r;
+    } else {
+        TslRun g[2] = {t, t};
+        for (int i = 0; i < 2; ++i) {
+            g[i].nsrc = nsrc / 2;
+            g[i].s0 = i * (nsrc / 2);
+            g[i].rep = nullptr;
+            if ((r = g[i].setup(st, x_dev, x_top))) return r;
+        }
+        t.args_only = true;
+        if ((r = t.setup(st, x_dev, x_top))) return r;
+        t.h.variant = g[0].h.variant;   // reported schedule
+        if ((r = lanczos_split(g, st, t.graphed()))) return r;
+    }
     if ((r = t.proj_enqueue(st)) || (r = t.proj_complete(st))) return r;
     if ((r = t.finish_enqueue(st))) return r;
     return t.finish_complete(st);
@@ -641,29 +750,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
 
 // ---- ragged batches (lq_batch_apply) --------------------------------------------------------
 // Every member of a batch runs on its own context; the branch of member i is its context's
-// capture stream.  fork: each branch waits for the work enqueued on `from` so far; join: `into`
-// waits for the work enqueued on each branch so far.
-int fork_streams(lq_ctx* c0, cudaStream_t from, const std::vector<cudaStream_t>& to) {
-    cudaEvent_t e = nullptr;
-    LQ_CUDA(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-    cudaError_t err = cudaEventRecord(e, from);
-    for (cudaStream_t s : to) if (err == cudaSuccess) err = cudaStreamWaitEvent(s, e, 0);
-    cudaEventDestroy(e);
-    LQ_CUDA(c0, err);
-    return LQ_OK;
-}
-int join_streams(lq_ctx* c0, const std::vector<cudaStream_t>& from, cudaStream_t into) {
-    for (cudaStream_t s : from) {
-        cudaEvent_t e = nullptr;
-        LQ_CUDA(c0, cudaEventCreateWithFlags(&e, cudaEventDisableTiming));
-        cudaError_t err = cudaEventRecord(e, s);
-        if (err == cudaSuccess) err = cudaStreamWaitEvent(into, e, 0);
-        cudaEventDestroy(e);
-        LQ_CUDA(c0, err);
-    }
-    return LQ_OK;
-}
-
+// capture stream.
 // The Krylov loops of all members as plain launches, each on its branch, between a fork from
 // and a join into st.
 int batch_lanczos_plain(std::vector<TslRun>& runs, cudaStream_t st) {
@@ -748,6 +835,7 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->defl_nderiv < 0) return set_err(c, LQ_ERR_ARG, "defl_nderiv must be >= 0");
     if (o->two_pass != 0 && o->two_pass != 1) return set_err(c, LQ_ERR_ARG, "two_pass must be 0 or 1");
     if (o->graph < -1 || o->graph > 1) return set_err(c, LQ_ERR_ARG, "graph must be -1, 0 or 1");
+    if (o->split < -1 || o->split > 1) return set_err(c, LQ_ERR_ARG, "split must be -1, 0 or 1");
     if (c->ring > 0 && !o->two_pass && o->kmax > c->ring)
         return set_err(c, LQ_ERR_ARG, "workspace reserved for two-pass runs: set opts.two_pass = 1 or kmax <= " + std::to_string(c->ring));
     return LQ_OK;
@@ -1102,6 +1190,7 @@ void lq_default_opts(lq_opts* o) {
     o->defl_nderiv = 0;
     o->two_pass = 0;
     o->graph = -1;
+    o->split = -1;
 }
 
 int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
@@ -1128,6 +1217,7 @@ void lq_destroy(lq_ctx* c) {
     if (!c) return;
     free_workspace(c);
     if (c->cap_stream) cudaStreamDestroy(c->cap_stream);
+    if (c->cap_stream2) cudaStreamDestroy(c->cap_stream2);
     dfree(c->U);
     dfree(c->Ub);
     dfree(c->Y);

@@ -250,23 +250,25 @@ struct lq_ctx {
     double2* defl_shift = nullptr;   // [nsrc] resolvent shifts
     double defl_resid = 0.0;         // largest relative residual of the last shifted solves
 
-    // stencil autotuning: chosen variant per (nf, emode) of the Lanczos step, -1 = not tuned
-    int tuned_variant[3][3] = {{-1, -1, -1}, {-1, -1, -1}, {-1, -1, -1}};
-    int tuned_nsrc = -1;
+    // stencil autotuning: chosen variant per (batch size, nf, emode) of the Lanczos step
+    struct Tuned { int nsrc, nf, emode, variant; };
+    std::vector<Tuned> tuned;
 
     // CUDA graphs of the Krylov loop, one per configuration (cleared when the workspace is
     // reserved again); captured on cap_stream, launched on the caller's stream
     struct GraphKey {
         int k, nsrc, nf, emode, variant, store_left, ring;
         double mu;
+        int groups;        // source groups run as concurrent branches (1: none)
         bool operator==(const GraphKey& o) const {
             return k == o.k && nsrc == o.nsrc && nf == o.nf && emode == o.emode && variant == o.variant &&
-                   store_left == o.store_left && ring == o.ring && mu == o.mu;
+                   store_left == o.store_left && ring == o.ring && mu == o.mu && groups == o.groups;
         }
     };
     struct GraphEntry { GraphKey key; cudaGraphExec_t exec; };
     std::vector<GraphEntry> graphs;
     cudaStream_t cap_stream = nullptr;
+    cudaStream_t cap_stream2 = nullptr;   // the second source group's branch
 
     // profiling (lq_profile_enable): event pairs per kernel class, summed at sync points
     int prof_on = 0;

@@ -51,7 +51,7 @@ class Opts(ctypes.Structure):
                 ("newton_tol", ctypes.c_double), ("deflate", ctypes.c_int), ("projected", ctypes.c_int),
                 ("quad_nodes", ctypes.c_int), ("proj_tol", ctypes.c_double), ("hop_variant", ctypes.c_int),
                 ("defl_kmax", ctypes.c_int), ("defl_nderiv", ctypes.c_int), ("two_pass", ctypes.c_int),
-                ("graph", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("split", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -344,7 +344,7 @@ class Context:
 
     @staticmethod
     def opts(k, breakdown_tol=1e-14, newton_max_iter=50, newton_tol=1e-13, projected=LQ_PROJ_AUTO, quad_nodes=64,
-             proj_tol=1e-11, hop_variant=-1, deflate=0, defl_kmax=0, defl_nderiv=0, two_pass=0, graph=-1):
+             proj_tol=1e-11, hop_variant=-1, deflate=0, defl_kmax=0, defl_nderiv=0, two_pass=0, graph=-1, split=-1):
         o = Opts()
         lib().lq_default_opts(ctypes.byref(o))
         o.kmax = int(k)
@@ -360,6 +360,7 @@ class Context:
         o.defl_nderiv = int(defl_nderiv)
         o.two_pass = int(two_pass)
         o.graph = int(graph)
+        o.split = int(split)
         return o
 
     def sign_apply(self, x, k, out=None, **kw):
