@@ -56,3 +56,33 @@ def test_apply_matches_matrix():
     y, dy = oo.overlap_apply(lat, U, 0.3, x, E)
     assert np.allclose(y, D @ x.ravel(), rtol=0, atol=1e-13)
     assert np.allclose(dy, oo.overlap_derivative_dense(lat, U, 0.3, E) @ x.ravel(), rtol=0, atol=1e-12)
+
+
+def test_axial_current_pins():
+    """The conserved axial current Tr(D^{-1} dD gamma5) and its estimates, pinned by consequences
+    of the Ginsparg-Wilson relation (m = 0: D^{-1} gamma5 + gamma5 D^{-1} = gamma5), the special
+    mass m = 2 (D = 2, dD = 0) and the unit-vector sum of the estimator; a U(1) link direction."""
+    mu = 0.3
+    lat, U, D, g5 = _setup(mu)
+    theta = syn.u1_direction(DIMS, 9)
+    E = od.dense_dH_dir(lat, U, od.link_derivative(U, theta=theta), mu)
+    dD = oo.overlap_derivative_dense(lat, U, mu, E)
+    # Tr(gamma5 dD_ov) = d Tr sgn(H) = 0: the index does not change along a smooth direction
+    assert abs(np.trace(g5 @ dD)) < 1e-10 * np.abs(dD).sum()
+    J = oo.axial_current_trace(lat, U, mu, E)
+    Di = np.linalg.inv(D)
+    # GW: Tr(D^{-1} dD g5) = Tr(dD g5) - Tr(dD D^{-1} g5) = -Tr(D^{-1} g5 dD)
+    Jr = np.trace(Di @ g5 @ dD)
+    assert abs(J + Jr) < 1e-9 * max(abs(J), 1e-3)
+    # a planted mistake (the gamma5 of dD_ov = gamma5 d sgn(H) dropped) breaks it
+    dS = g5 @ dD
+    Jb, Jrb = np.trace(Di @ dS @ g5), np.trace(Di @ g5 @ dS)
+    assert abs(Jb + Jrb) > 1e-3 * abs(Jb)
+    # m = 2: D(2) = 2 and dD(2) = 0
+    assert np.allclose(oo.massive_overlap_dense(lat, U, mu, 2.0), 2 * np.eye(lat.n), atol=1e-12)
+    assert abs(oo.axial_current_trace(lat, U, mu, E, 2.0)) < 1e-14
+    # the estimator over all unit vectors sums to the trace (m = 0 and m = 0.2)
+    for m in (0.0, 0.2):
+        I = np.eye(lat.n).reshape(lat.n, lat.V, 4, 3)
+        est = oo.axial_current_estimates(lat, U, mu, E, I, m)
+        assert abs(est.sum() - oo.axial_current_trace(lat, U, mu, E, m)) < 1e-9 * np.abs(est).sum()
