@@ -50,6 +50,7 @@ extern "C" {
 #define LQ_ERR_TIMEOUT     -7   /* a bounded device-side wait gave up                        */
 #define LQ_ERR_NOT_READY   -8   /* gauge / workspace / direction / deflation not set         */
 #define LQ_ERR_NONFINITE   -9   /* (status) NaN or Inf met in a reduction                    */
+#define LQ_ERR_NOT_CONVERGED -10 /* (status) an iterative solve stopped at its iteration cap  */
 
 /* ---- internal precision ------------------------------------------------------------- */
 #define LQ_FP64   0   /* stencil, vectors, dots, scalars and Newton all in FP64                */
@@ -173,6 +174,8 @@ int  lq_set_mu(lq_ctx* ctx, double mu);
 #define LQ_RESERVE_BLOCK    1
 #define LQ_RESERVE_ADJOINT  2
 #define LQ_RESERVE_TWO_PASS 4
+#define LQ_RESERVE_SOLVE    8   /* nine more FP64 fields per source for lq_overlap_solve and
+                                   lq_axial_current */
 int  lq_reserve(lq_ctx* ctx, int kmax, int nsrc, int flags);
 
 /* y = H(mu) x (dagger = 0) or y = H(mu)^dag x = H(-mu) x (dagger = 1) for nsrc fields
@@ -247,6 +250,38 @@ int  lq_compute_deflation(lq_ctx* ctx, const lq_eig_opts* eo, const double* X0, 
  * LQ_RESERVE_BLOCK).  x, y, dy: double[nsrc][V][4][3][2], host or device.  Synchronises. */
 int  lq_overlap_apply(lq_ctx* ctx, const lq_direction* dir, const double* x, double* y, double* dy, int nsrc,
                       const lq_opts* opts, lq_report* rep, void* stream);
+
+/* Per-source outcome of an overlap solve. */
+typedef struct {
+    int iterations;        /* BiCGStab iterations (two operator applications each)            */
+    int status;            /* LQ_OK, LQ_ERR_NOT_CONVERGED, LQ_ERR_BREAKDOWN or a status of the
+                              inner sign solves                                                */
+    double residual;       /* ||b - D(m) z|| / ||b|| recomputed with one more application      */
+} lq_solve_report;
+
+/* z = D(m)^{-1} b for nsrc sources: the overlap operator with a bare mass,
+ *   D(m) = (1 - m/2) D_ov + m,   D_ov = 1 + gamma5 sgn(H(mu))   (Eq. (1.1), lattice spacing 1),
+ * mass = 0 giving the paper's massless operator.  BiCGStab with per-source scalars; every
+ * application of D(m) is one batched two-sided Lanczos solve for sgn(H) x with opts (deflated with
+ * the installed eigenpairs when opts->deflate = 1).  The Lanczos approximation at a fixed depth
+ * is not linear in x, so the solve converges only down to the accuracy of that approximation:
+ * choose opts->kmax (or deflation) so that sgn(H) is as accurate as tol asks.  Stops for a source
+ * when ||r|| <= tol ||b|| or after max_iter iterations.  b, z: double[nsrc][V][4][3][2], host or
+ * device.  Needs lq_reserve(..., LQ_RESERVE_SOLVE).  rep: nsrc entries (may be NULL).
+ * Synchronises `stream`. */
+int  lq_overlap_solve(lq_ctx* ctx, const double* b, double* z, int nsrc, double mass, double tol, int max_iter,
+                      const lq_opts* opts, lq_solve_report* rep, void* stream);
+
+/* Stochastic estimates of the conserved axial current of the paper's conclusion,
+ *   J = Tr(D(m)^{-1} dD(m)/dt gamma5),   dD(m)/dt = (1 - m/2) gamma5 d_t sgn(H(mu)),
+ * along the direction `dir` (for the current through the links that a U(1) field theta moves,
+ * LQ_DIR_U1): out[s] = eta_s^dag D(m)^{-1} dD(m) gamma5 eta_s for each noise vector eta_s (Z2 noise
+ * gives an unbiased estimate of J; the random numbers are the caller's).  Per source: one
+ * derivative solve (Eq. (2.6)) for d sgn(H) gamma5 eta, then lq_overlap_solve's BiCGStab.  eta:
+ * double[nsrc][V][4][3][2], host or device; out: host double[nsrc][2] (complex).  Needs
+ * lq_reserve(..., LQ_RESERVE_BLOCK | LQ_RESERVE_SOLVE).  Synchronises `stream`. */
+int  lq_axial_current(lq_ctx* ctx, const lq_direction* dir, const double* eta, int nsrc, double mass, double tol,
+                      int max_iter, const lq_opts* opts, double* out, lq_solve_report* rep, void* stream);
 
 /* One member of a ragged batch (lq_batch_apply). */
 typedef struct {

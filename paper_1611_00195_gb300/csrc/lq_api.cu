@@ -254,7 +254,7 @@ void free_workspace(lq_ctx* c) {
                    (void**)&c->nx_partials, (void**)&c->nx_counters, (void**)&c->proj_c, (void**)&c->quad_q,
                    (void**)&c->quad_work, (void**)&c->quad_c, (void**)&c->quad_check, (void**)&c->quad_nodes, (void**)&c->quad_part, (void**)&c->proj_sel,
                    &c->lbasis, (void**)&c->uscale, (void**)&c->adj_coef, &c->adj_nu, &c->adj_om,
-                   (void**)&c->adj_force, (void**)&c->adj_dmu, (void**)&c->gen_scr};
+                   (void**)&c->adj_force, (void**)&c->adj_dmu, (void**)&c->gen_scr, (void**)&c->solve_ws};
     for (void** p : ps) { dfree(*p); *p = nullptr; }
     c->kmax = c->nsrc = c->block = c->ring = 0;
     c->adjoint = false;
@@ -1256,7 +1256,7 @@ int lq_set_mu(lq_ctx* c, double mu) {
 }
 
 int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
-    if (!c || kmax < 1 || nsrc < 1 || (flags & ~(LQ_RESERVE_BLOCK | LQ_RESERVE_ADJOINT | LQ_RESERVE_TWO_PASS)))
+    if (!c || kmax < 1 || nsrc < 1 || (flags & ~(LQ_RESERVE_BLOCK | LQ_RESERVE_ADJOINT | LQ_RESERVE_TWO_PASS | LQ_RESERVE_SOLVE)))
         return set_err(c, LQ_ERR_ARG, "invalid reserve arguments");
     if ((flags & LQ_RESERVE_TWO_PASS) && (flags & LQ_RESERVE_ADJOINT))
         return set_err(c, LQ_ERR_ARG, "the adjoint keeps the whole left basis: no two-pass reserve");
@@ -1315,6 +1315,7 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
         c->gen_scr_doubles = bdots_partial_doubles(m * m) + (size_t)2 * m * m;
         if ((r = dalloc(c, &c->gen_scr, c->gen_scr_doubles))) { free_workspace(c); return r; }
     }
+    if ((flags & LQ_RESERVE_SOLVE) && (r = dalloc(c, &c->solve_ws, (size_t)9 * nsrc * c->V * 24))) { free_workspace(c); return r; }
     if (flags & LQ_RESERVE_ADJOINT) {
         const int np = 2 * kQuadMaxNodes;
         if ((r = alloc_fields(&c->lbasis, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
@@ -1506,6 +1507,157 @@ int sign_derivative_core(lq_ctx* c, const lq_direction* dir, const double* x, in
     return LQ_OK;
 }
 
+
+// ---- overlap solver (lq_overlap_solve, lq_axial_current) -----------------------------------
+// Per-source inner products <X_s|Y_s> over the first nsrc fields of two device sets.
+int sdots_host(lq_ctx* c, const double* X, const double* Y, int nsrc, std::vector<cplx>& out, cudaStream_t st) {
+    const size_t nv = nvec(c);
+    double* part = c->gen_scr;
+    double* res = part + bdots_partial_doubles(nsrc);
+    LQ_CUDA(c, launch_sdots(X, Y, nv, nv, nsrc, part, res, st));
+    std::vector<double2> h(nsrc);
+    LQ_CUDA(c, cudaMemcpyAsync(h.data(), res, sizeof(double2) * nsrc, cudaMemcpyDeviceToHost, st));
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    c->launches += 2;
+    out.resize(nsrc);
+    for (int s = 0; s < nsrc; ++s) out[s] = cplx(h[s].x, h[s].y);
+    return LQ_OK;
+}
+
+// Z_s = a_s X0_s + b_s X1_s + c_s X2_s with per-source complex coefficients (host values)
+int scomb_host(lq_ctx* c, double* Z, const double* X0, const double* X1, const double* X2, const std::vector<cplx>& a,
+               const std::vector<cplx>& b, const std::vector<cplx>& cc, int nsrc, cudaStream_t st) {
+    const size_t nv = nvec(c);
+    std::vector<double2> coef((size_t)3 * nsrc);
+    for (int s = 0; s < nsrc; ++s) {
+        coef[3 * s] = make_double2(a[s].real(), a[s].imag());
+        coef[3 * s + 1] = make_double2(b.empty() ? 0.0 : b[s].real(), b.empty() ? 0.0 : b[s].imag());
+        coef[3 * s + 2] = make_double2(cc.empty() ? 0.0 : cc[s].real(), cc.empty() ? 0.0 : cc[s].imag());
+    }
+    double* dcoef = c->gen_scr + bdots_partial_doubles(nsrc) + 2 * (size_t)nsrc;
+    LQ_CUDA(c, cudaMemcpyAsync(dcoef, coef.data(), sizeof(double2) * coef.size(), cudaMemcpyHostToDevice, st));
+    LQ_CUDA(c, launch_scomb(Z, X0, X1, X2, dcoef, nv, nv, nsrc, st));
+    c->launches += 1;
+    return LQ_OK;
+}
+
+// out = D(m) x = (1 - m/2)(x + gamma5 sgn(H) x) + m x = (1 + m/2) x + (1 - m/2) gamma5 sgn(H) x for
+// nsrc device fields; sgn(H) x by the two-sided Lanczos process with opts (into staging region 1).
+// worst[s] keeps the worst status of the sign solves of a source still running (done[s] == 0: a
+// finished source is applied to a zero vector, whose solve reports an empty source).
+int apply_Dm(lq_ctx* c, const double* x, double* out, int nsrc, double mass, const lq_opts* o, std::vector<int>& worst,
+             const std::vector<int>& done, cudaStream_t st) {
+    std::vector<lq_report> rep(nsrc);
+    int r = sign_core(c, x, nsrc, o, rep.data(), st);
+    if (r) return r;
+    for (int s = 0; s < nsrc; ++s) if (!done[s] && rep[s].status < 0 && worst[s] == LQ_OK) worst[s] = rep[s].status;
+    LQ_CUDA(c, launch_g5axpy(out, x, 1.0 + 0.5 * mass, c->io + (size_t)c->nsrc * c->V * 24, 1.0 - 0.5 * mass,
+                             (size_t)nsrc * c->V, st));
+    c->launches += 1;
+    return LQ_OK;
+}
+
+// BiCGStab for D(m) Z = B, nsrc sources at once with their own scalars (van der Vorst, SIAM J.
+// Sci. Stat. Comput. 13 (1992)).  B and Z are fields of the solver workspace (device); the six
+// others hold the recurrence vectors.  A source stops when its recursive residual is below
+// tol ||b||; its scalars are then zero, so its vectors no longer change.  The reported residual
+// is recomputed as ||B - D(m) Z|| at the end.
+int overlap_bicgstab(lq_ctx* c, const double* B, double* Z, int nsrc, double mass, double tol, int max_iter,
+                     const lq_opts* o, lq_solve_report* rep, cudaStream_t st) {
+    const size_t nv = nvec(c), reg = (size_t)c->nsrc * nv;
+    double* R = c->solve_ws;
+    double* RH = R + reg;
+    double* P = RH + reg;
+    double* Vv = P + reg;
+    double* S = Vv + reg;
+    double* T = S + reg;
+    const size_t bytes = sizeof(double) * nv * nsrc;
+    LQ_CUDA(c, cudaMemsetAsync(Z, 0, bytes, st));
+    LQ_CUDA(c, cudaMemcpyAsync(R, B, bytes, cudaMemcpyDeviceToDevice, st));
+    LQ_CUDA(c, cudaMemcpyAsync(RH, B, bytes, cudaMemcpyDeviceToDevice, st));
+    LQ_CUDA(c, cudaMemsetAsync(P, 0, bytes, st));
+    LQ_CUDA(c, cudaMemsetAsync(Vv, 0, bytes, st));
+    std::vector<cplx> bb, rho1, d, ts, tt, rr;
+    int r = sdots_host(c, B, B, nsrc, bb, st);
+    if (r) return r;
+    std::vector<double> bn(nsrc);
+    std::vector<cplx> rho(nsrc, 1.0), alpha(nsrc, 1.0), omega(nsrc, 1.0), one(nsrc, 1.0);
+    std::vector<int> done(nsrc, 0), conv(nsrc, 0), status(nsrc, LQ_OK), iters(nsrc, 0), worst(nsrc, LQ_OK);
+    for (int s = 0; s < nsrc; ++s) {
+        bn[s] = std::sqrt(std::max(bb[s].real(), 0.0));
+        if (!(bn[s] > 0.0)) done[s] = conv[s] = 1;
+    }
+    auto all_done = [&]() { return std::all_of(done.begin(), done.end(), [](int v) { return v != 0; }); };
+    auto tiny = [](cplx v, double scale) { return !(std::abs(v) > 1e-300 * scale) || !std::isfinite(std::abs(v)); };
+    for (int it = 0; it < max_iter && !all_done(); ++it) {
+        if ((r = sdots_host(c, RH, R, nsrc, rho1, st))) return r;
+        std::vector<cplx> beta(nsrc, 0.0), mbo(nsrc, 0.0);
+        for (int s = 0; s < nsrc; ++s) {
+            if (done[s]) continue;
+            if (tiny(rho1[s], bn[s] * bn[s] * 1e-30) || tiny(omega[s], 1.0)) { status[s] = LQ_ERR_BREAKDOWN; done[s] = 1; continue; }
+            beta[s] = (rho1[s] / rho[s]) * (alpha[s] / omega[s]);
+            mbo[s] = -beta[s] * omega[s];
+        }
+        std::vector<cplx> keep(nsrc);
+        for (int s = 0; s < nsrc; ++s) keep[s] = done[s] ? cplx(0.0) : cplx(1.0);
+        // P = R + beta (P - omega V) for running sources; a finished source keeps P = 0
+        if ((r = scomb_host(c, P, R, P, Vv, keep, beta, mbo, nsrc, st))) return r;
+        if ((r = apply_Dm(c, P, Vv, nsrc, mass, o, worst, done, st))) return r;
+        if ((r = sdots_host(c, RH, Vv, nsrc, d, st))) return r;
+        std::vector<cplx> malpha(nsrc, 0.0);
+        for (int s = 0; s < nsrc; ++s) {
+            if (done[s]) { alpha[s] = 0.0; continue; }
+            if (tiny(d[s], bn[s] * bn[s] * 1e-30)) { status[s] = LQ_ERR_BREAKDOWN; done[s] = 1; alpha[s] = 0.0; continue; }
+            alpha[s] = rho1[s] / d[s];
+            malpha[s] = -alpha[s];
+        }
+        if ((r = scomb_host(c, S, R, Vv, nullptr, one, malpha, {}, nsrc, st))) return r;   // S = R - alpha V
+        if ((r = apply_Dm(c, S, T, nsrc, mass, o, worst, done, st))) return r;
+        if ((r = sdots_host(c, T, S, nsrc, ts, st))) return r;
+        if ((r = sdots_host(c, T, T, nsrc, tt, st))) return r;
+        std::vector<cplx> momega(nsrc, 0.0);
+        for (int s = 0; s < nsrc; ++s) {
+            if (done[s]) { omega[s] = 0.0; continue; }
+            omega[s] = tt[s].real() > 0.0 ? ts[s] / tt[s].real() : cplx(0.0);
+            momega[s] = -omega[s];
+        }
+        if ((r = scomb_host(c, Z, Z, P, S, one, alpha, omega, nsrc, st))) return r;         // Z += alpha P + omega S
+        if ((r = scomb_host(c, R, S, T, nullptr, one, momega, {}, nsrc, st))) return r;     // R = S - omega T
+        if ((r = sdots_host(c, R, R, nsrc, rr, st))) return r;
+        for (int s = 0; s < nsrc; ++s) {
+            if (done[s]) continue;
+            iters[s] = it + 1;
+            rho[s] = rho1[s];
+            if (std::sqrt(std::max(rr[s].real(), 0.0)) <= tol * bn[s]) done[s] = conv[s] = 1;
+            else if (tiny(omega[s], 1.0)) { status[s] = LQ_ERR_BREAKDOWN; done[s] = 1; }
+        }
+    }
+    // true residual
+    const std::vector<int> none(nsrc, 0);
+    if ((r = apply_Dm(c, Z, T, nsrc, mass, o, worst, none, st))) return r;
+    std::vector<cplx> mone(nsrc, -1.0);
+    if ((r = scomb_host(c, R, B, T, nullptr, one, mone, {}, nsrc, st))) return r;
+    if ((r = sdots_host(c, R, R, nsrc, rr, st))) return r;
+    if (rep) {
+        for (int s = 0; s < nsrc; ++s) {
+            lq_solve_report& q = rep[s];
+            q.iterations = iters[s];
+            q.residual = bn[s] > 0.0 ? std::sqrt(std::max(rr[s].real(), 0.0)) / bn[s] : 0.0;
+            // converged: the recursive residual met tol (the recomputed one is reported as is)
+            q.status = status[s] != LQ_OK ? status[s] : worst[s] != LQ_OK ? worst[s] : conv[s] ? LQ_OK : LQ_ERR_NOT_CONVERGED;
+        }
+    }
+    return LQ_OK;
+}
+
+int solve_ready(lq_ctx* c, int nsrc, int need_block, double mass, double tol, int max_iter, const lq_opts* o) {
+    int r = check_ready(c, nsrc, need_block);
+    if (r || (r = check_opts(c, o, true))) return r;
+    if (!c->solve_ws) return set_err(c, LQ_ERR_NOT_READY, "workspace reserved without LQ_RESERVE_SOLVE");
+    if (!(tol > 0.0) || max_iter < 1 || !std::isfinite(mass)) return set_err(c, LQ_ERR_ARG, "need tol > 0, max_iter >= 1, finite mass");
+    return LQ_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1619,6 +1771,51 @@ int lq_batch_apply(const lq_batch_item* items, int n, void* stream) {
     const int rj = join_streams(c0, br, st);
     if (r || (r = rj)) return r;
     LQ_CUDA(c0, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_overlap_solve(lq_ctx* c, const double* b, double* z, int nsrc, double mass, double tol, int max_iter,
+                     const lq_opts* o, lq_solve_report* rep, void* stream) {
+    if (!c || !b || !z) return set_err(c, LQ_ERR_ARG, "null argument");
+    int r = solve_ready(c, nsrc, 0, mass, tol, max_iter, o);
+    if (r) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t reg = (size_t)c->nsrc * nvec(c), n = (size_t)nsrc * nvec(c);
+    double* B = c->solve_ws + 6 * reg;
+    double* Z = c->solve_ws + 7 * reg;
+    if ((r = stage_in(c, B, b, n, st))) return r;
+    if ((r = overlap_bicgstab(c, B, Z, nsrc, mass, tol, max_iter, o, rep, st))) return r;
+    if ((r = stage_out(c, z, Z, n, st))) return r;
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    return LQ_OK;
+}
+
+int lq_axial_current(lq_ctx* c, const lq_direction* dir, const double* eta, int nsrc, double mass, double tol,
+                     int max_iter, const lq_opts* o, double* out, lq_solve_report* rep, void* stream) {
+    if (!c || !dir || !eta || !out) return set_err(c, LQ_ERR_ARG, "null argument");
+    int r = solve_ready(c, nsrc, 1, mass, tol, max_iter, o);
+    if (r) return r;
+    cudaStream_t st = (cudaStream_t)stream;
+    const size_t reg = (size_t)c->nsrc * nvec(c), n = (size_t)nsrc * nvec(c);
+    double* B = c->solve_ws + 6 * reg;
+    double* Z = c->solve_ws + 7 * reg;
+    double* E = c->solve_ws + 8 * reg;
+    double* A = c->solve_ws + 2 * reg;   // gamma5 eta (the recurrence vectors are not in use yet)
+    if ((r = stage_in(c, E, eta, n, st))) return r;
+    LQ_CUDA(c, launch_g5axpy(A, nullptr, 0.0, E, 1.0, (size_t)nsrc * c->V, st));
+    std::vector<lq_report> drep(nsrc);
+    if ((r = sign_derivative_core(c, dir, A, nsrc, o, drep.data(), st))) return r;
+    // B = dD(m) gamma5 eta = (1 - m/2) gamma5 d sgn(H) gamma5 eta (the derivative is staging region 1)
+    LQ_CUDA(c, launch_g5axpy(B, nullptr, 0.0, c->io + reg, 1.0 - 0.5 * mass, (size_t)nsrc * c->V, st));
+    c->launches += 2;
+    if ((r = overlap_bicgstab(c, B, Z, nsrc, mass, tol, max_iter, o, rep, st))) return r;
+    std::vector<cplx> j;
+    if ((r = sdots_host(c, E, Z, nsrc, j, st))) return r;
+    for (int s = 0; s < nsrc; ++s) {
+        out[2 * s] = j[s].real();
+        out[2 * s + 1] = j[s].imag();
+        if (rep && drep[s].status < 0 && rep[s].status == LQ_OK) rep[s].status = drep[s].status;
+    }
     return LQ_OK;
 }
 

@@ -96,6 +96,79 @@ cudaError_t launch_bcombine(double* Z, const double* W, size_t zs, int nz, const
 
 size_t bdots_partial_doubles(int npairs) { return (size_t)npairs * kDotBlocks * 4; }
 
+// Per-source inner products <X_s | Y_s> (compensated FP64), partial[s][blockIdx.x]; summed by
+// k_bdots_finish.  Source s of a set starts at s * xs (or s * ys) complex numbers.
+__global__ void __launch_bounds__(kDotThreads) k_sdots(const double2* __restrict__ X, size_t xs,
+                                                       const double2* __restrict__ Y, size_t ys, size_t n,
+                                                       double* __restrict__ partial) {
+    __shared__ CSum smem[32 * 2];
+    const int src = blockIdx.y;
+    const double2* x = X + (size_t)src * xs;
+    const double2* y = Y + (size_t)src * ys;
+    CSum acc[2] = {{0.0, 0.0}, {0.0, 0.0}};
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        const double2 u = x[i], v = y[i];
+        cs_add_prod(acc[0], u.x, v.x); cs_add_prod(acc[0], u.y, v.y);
+        cs_add_prod(acc[1], u.x, v.y); cs_add_prod(acc[1], -u.y, v.x);
+    }
+    block_reduce_cs<2>(acc, smem);
+    if (threadIdx.x == 0) {
+        double* p = partial + ((size_t)src * gridDim.x + blockIdx.x) * 4;
+        p[0] = acc[0].s; p[1] = acc[0].e; p[2] = acc[1].s; p[3] = acc[1].e;
+    }
+}
+
+cudaError_t launch_sdots(const double* X, const double* Y, size_t stride, size_t n, int nsrc, double* partial, double* out,
+                         cudaStream_t st) {
+    if (nsrc <= 0) return cudaSuccess;
+    k_sdots<<<dim3(kDotBlocks, (unsigned)nsrc), kDotThreads, 0, st>>>(reinterpret_cast<const double2*>(X), stride / 2,
+                                                                      reinterpret_cast<const double2*>(Y), stride / 2, n / 2, partial);
+    k_bdots_finish<<<(nsrc + 127) / 128, 128, 0, st>>>(partial, kDotBlocks, nsrc, reinterpret_cast<double2*>(out));
+    return cudaGetLastError();
+}
+
+// Per-source combinations Z_s = c[s][0] X0_s + c[s][1] X1_s + c[s][2] X2_s (complex coefficients;
+// X1, X2 may be null; Z may alias any X: element i is read before it is written)
+__global__ void k_scomb(double2* Z, const double2* X0, const double2* X1, const double2* X2, const double2* __restrict__ coef,
+                        size_t stride, size_t n) {
+    const int src = blockIdx.y;
+    const double2 c0 = coef[src * 3], c1 = coef[src * 3 + 1], c2 = coef[src * 3 + 2];
+    const size_t o = (size_t)src * stride;
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+        double2 v = cmul(c0, X0[o + i]);
+        if (X1) v = cfma(c1, X1[o + i], v);
+        if (X2) v = cfma(c2, X2[o + i], v);
+        Z[o + i] = v;
+    }
+}
+
+cudaError_t launch_scomb(double* Z, const double* X0, const double* X1, const double* X2, const double* coef, size_t stride,
+                         size_t n, int nsrc, cudaStream_t st) {
+    if (nsrc <= 0) return cudaSuccess;
+    k_scomb<<<dim3(256, (unsigned)nsrc), 256, 0, st>>>(reinterpret_cast<double2*>(Z), reinterpret_cast<const double2*>(X0),
+                                                       reinterpret_cast<const double2*>(X1), reinterpret_cast<const double2*>(X2),
+                                                       reinterpret_cast<const double2*>(coef), stride / 2, n / 2);
+    return cudaGetLastError();
+}
+
+// out = cx x + cs gamma5 s on boundary-layout FP64 fields (x may be null); gamma5 = diag(1, 1, -1, -1)
+// on spin.  With cx = 1 + m/2, cs = 1 - m/2 and s = sgn(H) x: the massive overlap operator D(m) x.
+__global__ void k_g5axpy(double2* out, const double2* x, double cx, const double2* s, double cs, size_t ncomp) {
+    for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < ncomp; i += (size_t)gridDim.x * blockDim.x) {
+        const double g = (i % 12 < 6) ? cs : -cs;
+        const double2 v = s[i];
+        double2 r = make_double2(g * v.x, g * v.y);
+        if (x) { const double2 xv = x[i]; r.x += cx * xv.x; r.y += cx * xv.y; }
+        out[i] = r;
+    }
+}
+
+cudaError_t launch_g5axpy(double* out, const double* x, double cx, const double* s, double cs, size_t nsites, cudaStream_t st) {
+    k_g5axpy<<<1216, 256, 0, st>>>(reinterpret_cast<double2*>(out), reinterpret_cast<const double2*>(x), cx,
+                                   reinterpret_cast<const double2*>(s), cs, nsites * 12);
+    return cudaGetLastError();
+}
+
 // Overlap operator of Eq. (1.1) from the sign and its derivative, in place on boundary-layout
 // FP64 fields: s <- x + gamma5 s (D_ov x), d <- gamma5 d (d D_ov x; d may be null).  gamma5 =
 // diag(1, 1, -1, -1) on spin: the first six of a site's twelve components keep their sign.

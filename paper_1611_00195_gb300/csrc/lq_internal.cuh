@@ -246,6 +246,7 @@ struct lq_ctx {
     double* defl_scr = nullptr;      // dot partials and coefficient matrices
     size_t defl_scr_doubles = 0;
     double* gen_scr = nullptr;       // general dot / combine scratch (lq_reserve)
+    double* solve_ws = nullptr;      // overlap solver: [9][nsrc][V][12] complex (LQ_RESERVE_SOLVE)
     size_t gen_scr_doubles = 0;
     double2* defl_shift = nullptr;   // [nsrc] resolvent shifts
     double defl_resid = 0.0;         // largest relative residual of the last shifted solves

@@ -119,6 +119,15 @@ cudaError_t launch_axpby3(double* Z, double a1, const double* X1, double a2, con
 cudaError_t launch_norm2(const double* a, const double* b, double sigma, size_t n, int nsrc, double* out, cudaStream_t st);
 // s <- x + gamma5 s, d <- gamma5 d (d may be null) over nsites boundary-layout sites (Eq. (1.1))
 cudaError_t launch_overlap(const double* x, double* s, double* d, size_t nsites, cudaStream_t st);
+// Overlap solver (lq_deflate.cu).  Sizes and strides in doubles.
+// out[s] = <X_s|Y_s> for nsrc sources; partial: bdots_partial_doubles(nsrc)
+cudaError_t launch_sdots(const double* X, const double* Y, size_t stride, size_t n, int nsrc, double* partial, double* out,
+                         cudaStream_t st);
+// Z_s = c[s][0] X0_s + c[s][1] X1_s + c[s][2] X2_s (complex coef [nsrc][3] on the device)
+cudaError_t launch_scomb(double* Z, const double* X0, const double* X1, const double* X2, const double* coef, size_t stride,
+                         size_t n, int nsrc, cudaStream_t st);
+// out = cx x + cs gamma5 s over nsites boundary-layout sites (x may be null)
+cudaError_t launch_g5axpy(double* out, const double* x, double cx, const double* s, double cs, size_t nsites, cudaStream_t st);
 size_t hop_blocks(const HopArgs& a, int nf);
 
 // Newton sign iteration (lq_newton.cu)

@@ -27,7 +27,8 @@ LQ_OK = 0
 # Revision tag of the stencil kernel; stored ncu traffic figures are only valid for this one.
 KERNEL_REV = "hop-v3"
 ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_CUDA", -5: "LQ_ERR_BREAKDOWN",
-          -6: "LQ_ERR_NEWTON", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NOT_READY", -9: "LQ_ERR_NONFINITE"}
+          -6: "LQ_ERR_NEWTON", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NOT_READY", -9: "LQ_ERR_NONFINITE",
+          -10: "LQ_ERR_NOT_CONVERGED"}
 LQ_FP64, LQ_MIXED = 0, 1
 LQ_DIR_MU, LQ_DIR_SU3, LQ_DIR_U1 = 0, 1, 2
 LQ_PROJ_AUTO, LQ_PROJ_NEWTON, LQ_PROJ_QUAD = 0, 1, 2
@@ -37,7 +38,8 @@ EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_u
             "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
             "lq_profile_read", "lq_newton_sign_noalloc", "lq_error_estimate",
             "lq_upload_deflation", "lq_deflation_derivatives", "lq_sign_bilinear_grad",
-            "lq_dense_eig", "lq_compute_deflation", "lq_overlap_apply", "lq_batch_apply"]
+            "lq_dense_eig", "lq_compute_deflation", "lq_overlap_apply", "lq_batch_apply", "lq_overlap_solve",
+            "lq_axial_current"]
 
 
 class LatticeDesc(ctypes.Structure):
@@ -86,6 +88,13 @@ class Direction(ctypes.Structure):
 _lib = None
 
 
+class SolveReport(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int), ("status", ctypes.c_int), ("residual", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
+
+
 class BatchItem(ctypes.Structure):
     _fields_ = [("ctx", ctypes.c_void_p), ("dir", ctypes.POINTER(Direction)), ("x", ctypes.c_void_p),
                 ("y_sign", ctypes.c_void_p), ("y_deriv", ctypes.c_void_p), ("nsrc", ctypes.c_int),
@@ -130,6 +139,9 @@ def lib():
         L.lq_compute_deflation.argtypes = [P, ctypes.POINTER(EigOpts), P, P, P, P]
         L.lq_newton_sign_noalloc.argtypes = [P, P, I, I, I, D, ctypes.POINTER(I), P]
         L.lq_batch_apply.argtypes = [ctypes.POINTER(BatchItem), I, P]
+        L.lq_overlap_solve.argtypes = [P, P, P, I, D, D, I, ctypes.POINTER(Opts), ctypes.POINTER(SolveReport), P]
+        L.lq_axial_current.argtypes = [P, ctypes.POINTER(Direction), P, I, D, D, I, ctypes.POINTER(Opts), P,
+                                       ctypes.POINTER(SolveReport), P]
         for name in EXPORTED:
             if name not in ("lq_default_opts", "lq_destroy", "lq_last_error"):
                 getattr(L, name).restype = ctypes.c_int
@@ -310,8 +322,8 @@ class Context:
         self._check(self._L.lq_set_mu(self._h, float(mu)))
         self.mu = float(mu)
 
-    def reserve(self, kmax, nsrc, block=True, adjoint=False, two_pass=False):
-        flags = (1 if block else 0) | (2 if adjoint else 0) | (4 if two_pass else 0)
+    def reserve(self, kmax, nsrc, block=True, adjoint=False, two_pass=False, solve=False):
+        flags = (1 if block else 0) | (2 if adjoint else 0) | (4 if two_pass else 0) | (8 if solve else 0)
         self._check(self._L.lq_reserve(self._h, int(kmax), int(nsrc), int(flags)))
 
     def _direction(self, kind, field):
@@ -400,6 +412,32 @@ class Context:
                                              _ptr(dy), int(nsrc), ctypes.byref(o), rep, _stream(x)))
         del keep
         return y, dy, [r.as_dict() for r in rep]
+
+    def overlap_solve(self, b, k, mass=0.0, tol=1e-10, max_iter=100, **kw):
+        """z = D(m)^{-1} b, D(m) = (1 - m/2) D_ov + m (include/lq.h: lq_overlap_solve); returns
+        (z, per-source solve reports)."""
+        b = _as_c128(b)
+        nsrc = b.shape[0]
+        z = _empty_like(b)
+        o = self.opts(k, **kw)
+        rep = (SolveReport * nsrc)()
+        self._check(self._L.lq_overlap_solve(self._h, _ptr(b), _ptr(z), int(nsrc), float(mass), float(tol), int(max_iter),
+                                             ctypes.byref(o), rep, _stream(b)))
+        return z, [r.as_dict() for r in rep]
+
+    def axial_current(self, eta, k, kind=LQ_DIR_U1, field=None, mass=0.0, tol=1e-10, max_iter=100, **kw):
+        """Per noise vector eta_s: eta_s^dag D(m)^{-1} dD(m) gamma5 eta_s along the direction (kind,
+        field) (include/lq.h: lq_axial_current); returns (complex array [nsrc], solve reports)."""
+        eta = _as_c128(eta)
+        nsrc = eta.shape[0]
+        d, keep = self._direction(kind, field)
+        o = self.opts(k, **kw)
+        out = np.zeros(2 * nsrc, np.float64)
+        rep = (SolveReport * nsrc)()
+        self._check(self._L.lq_axial_current(self._h, ctypes.byref(d), _ptr(eta), int(nsrc), float(mass), float(tol),
+                                             int(max_iter), ctypes.byref(o), _ptr(out), rep, _stream(eta)))
+        del keep
+        return out[0::2] + 1j * out[1::2], [r.as_dict() for r in rep]
 
     def profile_enable(self, enable=True):
         """Reset the kernel-time totals and launch count; enable CUDA-event timing."""
