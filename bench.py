@@ -528,6 +528,27 @@ def main():
         relv = lambda a, b: (torch.linalg.vector_norm((a - b).reshape(nc, -1), dim=1) / torch.linalg.vector_norm(b.reshape(nc, -1), dim=1)).tolist()
         conv["mixed_vs_fp64_rel_diff"] = {"sign": relv(resc["mixed"][0], resc["fp64"][0]), "deriv": relv(resc["mixed"][1], resc["fp64"][1])}
         extra["converged_depth_accuracy"] = conv
+        # the axial-current workload on the paper's lattice shape for it: 6x18^3, mu = 0.04, the
+        # massless overlap operator, 8 Z2 noise vectors, the current through all z links (a U(1)
+        # direction theta_z = const); one derivative solve and a BiCGStab solve of D_ov per vector
+        da, ka, na = (6, 18, 18, 18), 200, 8
+        ca = lq.Context(da, m_w=M_W, mu=0.04, precision=lq.LQ_MIXED)
+        ca.upload_gauge(torch.from_numpy(syn.gauge_field(da, EPS, GAUGE_SEED)).to(dev))
+        ca.reserve(ka, na, True, solve=True)
+        Va = int(np.prod(da))
+        th = np.zeros((4, Va))
+        th[2] = 1.0 / np.sqrt(Va)
+        tha = torch.from_numpy(th).to(dev)
+        eta = torch.from_numpy(syn.z2_source(da, SOURCE_SEED + 7, nsrc=na)).to(dev)
+        msa, ra = timed(lambda: ca.axial_current(eta, ka, kind=lq.LQ_DIR_U1, field=tha, mass=0.0, tol=1e-5, max_iter=60), steps=1)
+        ja = ra[0] * np.sqrt(Va)   # per unit theta on every z link
+        extra["axial_current_6x18c3"] = {"ms": msa, "noise_vectors": na, "k": ka, "mu": 0.04, "mass": 0.0,
+                                         "J_mean": [float(ja.mean().real), float(ja.mean().imag)],
+                                         "J_stderr": float(ja.real.std(ddof=1) / np.sqrt(na)),
+                                         "bicgstab_iterations": [x["iterations"] for x in ra[1]],
+                                         "residual_max": float(max(x["residual"] for x in ra[1])),
+                                         "status": [x["status"] for x in ra[1]]}
+        del ca
 
     # accuracy: eps_A of Sec. 4 (sign and derivative) on two of the sources, no deflation
     x2 = xd[:2].contiguous()
