@@ -55,3 +55,47 @@ def test_krylov_route_converges():
         errs.append(np.linalg.norm(Ft - F) / np.linalg.norm(F))
     assert errs[1] < 0.01 * errs[0]
     assert errs[1] < 1e-3
+
+
+def test_deflated_adjoint_blocks():
+    """The deflated adjoint: the four-block assembly of G = L_sgn(H, x y^H) from l eigenpairs
+    (divided differences on the deflated space, the two mixed blocks through the functions
+    (sgn z - sgn lambda) / (z - lambda), the Krylov route on the deflated sources) equals the plain
+    Sylvester Frechet derivative, exactly with dense functions and in the limit with the Krylov
+    ones; S deflated by Eq. (3.1) equals the bilinear.  A planted mistake (the left functions
+    taken without the conjugate shift) breaks the identity."""
+    from oracle import deflation as odf
+    dims, mu, l = (2, 2, 2, 2), 0.3, 6
+    lat = od.Lattice(dims)
+    U = syn.gauge_field(dims, 0.4, 3)
+    H = od.dense_H(lat, U, mu)
+    x = syn.gaussian_source(dims, 5).ravel()
+    y = syn.gaussian_source(dims, 6).ravel()
+    G0 = osg.frechet_sylvester(H, np.outer(x, y.conj()))
+    lam, R, L, _ = odf.eigenpairs(H, l)
+    Gd = oad.G_deflated_dense(H, lam, R, L, x, y)
+    assert np.abs(Gd - G0).max() < 1e-11 * np.abs(G0).max()
+    # planted mistake: g_i with lambda_i instead of conj(lambda_i)
+    c, d, F, xp, yp = oad.G_deflated_parts(lam, R, L, x, y)
+    S = osg.sign_schur(H)
+    bad = R @ (F * np.outer(c, d)) @ L + osg.frechet_sylvester(H, np.outer(xp, yp.conj()))
+    for i in range(l):
+        si = np.sign(lam[i].real)
+        u = np.linalg.solve(lam[i] * np.eye(lat.n) - H.conj().T, si * yp - S.conj().T @ yp)
+        v = np.linalg.solve(H - lam[i] * np.eye(lat.n), S @ xp - si * xp)
+        u, v = u - L.conj().T @ (R.conj().T @ u), v - R @ (L @ v)
+        bad += np.outer(R[:, i] * c[i], u.conj()) + np.outer(v * d[i], L[i])
+    assert np.abs(bad - G0).max() > 1e-6 * np.abs(G0).max()
+    # the Krylov blocks converge to it; S and the force follow
+    A = lambda v: od.apply_H(lat, U, v, mu).ravel()        # noqa: E731
+    Ah = lambda v: od.apply_Hdag(lat, U, v, mu).ravel()    # noqa: E731
+    errs = []
+    for k in (60, 120, 180):
+        Gk, Sk = oad.G_deflated_tsl(A, Ah, lam, R, L, x, y, k)
+        errs.append(np.abs(Gk - G0).max() / np.abs(G0).max())
+    Sd, Fd, dmud = oad.grad_dense(lat, U, x, y, mu)
+    assert errs[-1] < 1e-6 and errs[-1] < errs[0]
+    assert abs(Sk - Sd) < 1e-8 * abs(Sd)
+    Fk = oad.force_from_G(lat, U, Gk, mu)
+    assert np.linalg.norm(Fk - Fd) < 1e-6 * np.linalg.norm(Fd)
+    assert abs(oad.dmu_from_G(lat, U, Gk, mu) - dmud) < 1e-6 * abs(dmud)
