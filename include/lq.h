@@ -354,7 +354,12 @@ int  lq_profile_read(lq_ctx* ctx, lq_profile* out);
  * approximation L ~ |x||y| V_1 X W_2^H: V_1, T_1 from the Lanczos process started at x, W_2, T_2
  * from the process started at y, X the top-right block of sgn([[T_1, e_1 e_1^T], [0, T_2]]) by
  * Mathias' identity (Eq. (2.5)), evaluated by the quadrature of the projected sign (2 quad_nodes
- * rank-one terms).  x, y: one field each (host or device); S, dS_dmu: host double*; force:
+ * rank-one terms).  With opts->deflate = 1 the installed eigenpairs (Sec. 3) split
+ * L_sgn(H, x y^H) by the spectral projectors Pi = sum_j R_j L_j, Pbar = 1 - Pi: the deflated block
+ * exactly (divided differences of sgn at the eigenvalues), the two mixed blocks through
+ * (sgn z - sgn lambda_j) / (z - lambda_j) of the two Lanczos runs, and the rest by the Krylov route
+ * on the deflated sources Pbar x, Pbar^H y; S is deflated by Eq. (3.1).  This needs
+ * 2 quad_nodes + 3 l <= 256.  x, y: one field each (host or device); S, dS_dmu: host double*; force:
  * double[4][V][8] (host or device, may be NULL).  Needs lq_reserve(kmax, nsrc >= 2,
  * LQ_RESERVE_ADJOINT).  Synchronises `stream`. */
 int  lq_sign_bilinear_grad(lq_ctx* ctx, const double* x, const double* y, const lq_opts* opts,

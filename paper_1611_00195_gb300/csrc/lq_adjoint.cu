@@ -115,6 +115,99 @@ __global__ void k_adj_pairs(AdjArgs a) {
     }
 }
 
+// Deflated adjoint (the eigenpairs of Sec. 3 applied to G = L_sgn(H, x y^H)): with spectral
+// projectors Pi = sum_j R_j L_j and Pbar = 1 - Pi, the blocks Pi G Pbar and Pbar G Pi are
+//   sum_j R_j c_j u_j^H,  u_j = h_{conj lambda_j}(A^H) y',     sum_j v_j d_j L_j,  v_j = h_{lambda_j}(A) x',
+// h_l(z) = (sgn z - sgn l) / (z - l), x' = Pbar x, y' = Pbar^H y, c_j = L_j x, d_j = y^H R_j.  With the
+// quadrature sgn(z) ~ Q(z) = sum_q w_q (z + i tau_q)^{-1} of k_adj_pairs and the resolvent identity,
+//   h_l(T) e_1 = -sum_q w_q (l + i tau_q)^{-1} (T + i tau_q)^{-1} e_1 + (Q(l) - sgn l) (T - l)^{-1} e_1,
+// so v_j and u_j are combinations of the node solves a_q, b_q already in cnu / com plus one shifted
+// tridiagonal solve.  Thread (j, side) writes the basis coefficients of d_j v_j (side 0, right basis
+// of source 0) or conj(c_j) u_j (side 1, left basis of source 1).
+__global__ void k_defl_coef(AdjArgs a) {
+    const int nd = a.ndefl;
+    const int t = threadIdx.x;
+    if (t >= 2 * nd) return;
+    const int side = t / nd, j = t % nd;
+    const int nq = a.npairs, N = nq / 2;
+    const int src = side;
+    const int n = a.state[src].k_eff;
+    const double2 lj = a.dlam[j];
+    const double sl = lj.x > 0.0 ? 1.0 : -1.0;                    // sgn(lambda_j) = sign of Re
+    const double2 l = side == 0 ? lj : make_double2(lj.x, -lj.y);  // lambda_j or its conjugate
+    const double c = a.c;
+    // per node: g_q = 1 / (l + i s tau_q) with s = +1 for v (T_1 + i tau_q) and s = -1 for u, whose
+    // left solves b_q belong to T_2^H - i tau_q; the scalar quadrature Q(l) over all nodes
+    double2 Q = make_double2(0.0, 0.0);
+    for (int q = 0; q < nq; ++q) {
+        const int jj = q >> 1;
+        const double sg = (q & 1) ? -1.0 : 1.0;
+        const double th = (jj + 0.5) * 3.14159265358979323846 / (2.0 * N);
+        const double ct = cos(th);
+        const double w = c / (2.0 * N) / (ct * ct);
+        const double2 g = cdiv(make_double2(1.0, 0.0), make_double2(l.x, l.y + sg * c * tan(th)));
+        Q = make_double2(Q.x + w * g.x, Q.y + w * g.y);
+    }
+    const double2 corr = make_double2(Q.x - sl, Q.y);   // Q(l) - sgn l
+    // (T_1 - lambda_j)^{-1} e_1, or (T_2^T - lambda_j)^{-1} e_1 whose conjugate is (T_2^H - conj lambda_j)^{-1} e_1
+    const double2* al = a.alpha + (size_t)src * a.kmax;
+    const double2* be = a.beta + (size_t)src * a.kmax;
+    const double* de = a.delta + (size_t)src * a.kmax;
+    double2* base = a.work + (size_t)src * a.kmax * 4 * a.nth_max;
+    const int col = nq + j;
+    double2* sd = base + col;
+    double2* s1 = base + (size_t)a.kmax * a.nth_max + col;
+    double2* s2 = base + (size_t)2 * a.kmax * a.nth_max + col;
+    double2* sx = base + (size_t)3 * a.kmax * a.nth_max + col;
+    auto B = [&](int i) -> double2 { return make_double2(i == 0 ? 1.0 : 0.0, 0.0); };
+    auto D = [&](int i) -> double2 { return csub(al[i], lj); };
+    if (n > 0) {
+        if (side == 0) {
+            auto Up = [&](int i) -> double2 { return be[i]; };
+            auto Lo = [&](int i) -> double2 { return make_double2(de[i], 0.0); };
+            tri_solve_gen(n, D, Up, Lo, B, sd, s1, s2, sx, a.nth_max, make_double2(1.0, 0.0));
+        } else {
+            auto Up = [&](int i) -> double2 { return make_double2(de[i], 0.0); };
+            auto Lo = [&](int i) -> double2 { return be[i]; };
+            tri_solve_gen(n, D, Up, Lo, B, sd, s1, s2, sx, a.nth_max, make_double2(1.0, 0.0));
+        }
+    }
+    const double nx = a.state[0].xnorm, ny = a.state[1].xnorm;
+    const double2 fold = side == 0 ? a.ddy[j] : make_double2(a.dcx[j].x, -a.dcx[j].y);   // d_j or conj(c_j)
+    double2* out = (side == 0 ? a.cnu + (size_t)(nq + 2 * nd + j) * a.kmax : a.com + (size_t)(nq + nd + j) * a.kmax);
+    for (int i = 0; i < a.kmax; ++i) {
+        double2 v = make_double2(0.0, 0.0);
+        if (i < n) {
+            for (int q = 0; q < nq; ++q) {
+                const int jj = q >> 1;
+                const double sg = (q & 1) ? -1.0 : 1.0;
+                const double th = (jj + 0.5) * 3.14159265358979323846 / (2.0 * N);
+                const double ct = cos(th);
+                const double w = c / (2.0 * N) / (ct * ct);
+                const double tau = sg * c * tan(th);
+                if (side == 0) {
+                    // cnu[q][i] = -w_q |x'||y'| a_q[i] s_i, so |x'| (-w_q g_q) a_q[i] s_i = cnu[q][i] g_q / |y'|
+                    const double2 g = cdiv(make_double2(1.0, 0.0), make_double2(l.x, l.y + tau));
+                    v = cfma(a.cnu[(size_t)q * a.kmax + i], make_double2(g.x / ny, g.y / ny), v);
+                } else {
+                    // com[q][i] = conj(b_q[i]) u_i and W_2 conj(b_q) = W_2 (T_2^H - i tau_q)^{-1} e_1
+                    const double2 g = cdiv(make_double2(1.0, 0.0), make_double2(l.x, l.y - tau));
+                    v = cfma(a.com[(size_t)q * a.kmax + i], make_double2(-w * ny * g.x, -w * ny * g.y), v);
+                }
+            }
+            const double2 z = sx[(size_t)i * a.nth_max];
+            if (side == 0) {
+                const double2 r = cmul(corr, z);
+                v = make_double2(v.x + nx * a.scale[i] * r.x, v.y + nx * a.scale[i] * r.y);
+            } else {
+                const double2 r = cmul(cmul(corr, make_double2(z.x, -z.y)), a.uscale[(size_t)a.kmax + i]);
+                v = make_double2(v.x + ny * r.x, v.y + ny * r.y);
+            }
+        }
+        out[i] = cmul(fold, v);
+    }
+}
+
 // out[q] = sum_{j < k} coef[q][j] basis_j for QB outputs per thread (internal layout).
 constexpr int kQB = 8;
 template <typename R>
@@ -231,7 +324,8 @@ __device__ __forceinline__ void force_dir(const AdjArgs& a, size_t s, const int 
     double2 Pf[9], Pb[9];
 #pragma unroll
     for (int i = 0; i < 9; ++i) { Pf[i] = make_double2(0.0, 0.0); Pb[i] = make_double2(0.0, 0.0); }
-    for (int q = 0; q < a.npairs; ++q) {
+    const int np = a.npairs_force > 0 ? a.npairs_force : a.npairs;
+    for (int q = 0; q < np; ++q) {
         double2 w[12], v[12], g[12];
         // forward hop: conj(omega(x)) . gamma5 (1 - gamma) nu(x + nu)
         load_d(om + (size_t)q * F, V, s, w);
@@ -331,6 +425,17 @@ cudaError_t launch_adjoint(int prec, const AdjArgs& a, const void* basis, size_t
                                                      a.npairs, reinterpret_cast<double2*>(a.nu), F);
         k_recomb_multi<double><<<grid, 128, sm, st>>>(reinterpret_cast<const double2*>(lbasis), lbasis_vec_stride, k, a.com, a.kmax,
                                                      a.npairs, reinterpret_cast<double2*>(a.om), F);
+        if (a.ndefl > 0) {
+            const int nq = a.npairs, nd = a.ndefl;
+            dim3 gd((unsigned)((F + 127) / 128), (unsigned)((nd + kQB - 1) / kQB));
+            k_defl_coef<<<1, 2 * nd, 0, st>>>(a);
+            k_recomb_multi<double><<<gd, 128, sm, st>>>(reinterpret_cast<const double2*>(basis), basis_vec_stride, k,
+                                                       a.cnu + (size_t)(nq + 2 * nd) * a.kmax, a.kmax, nd,
+                                                       reinterpret_cast<double2*>(a.nu) + (size_t)(nq + 2 * nd) * F, F);
+            k_recomb_multi<double><<<gd, 128, sm, st>>>(reinterpret_cast<const double2*>(lbasis), lbasis_vec_stride, k,
+                                                       a.com + (size_t)(nq + nd) * a.kmax, a.kmax, nd,
+                                                       reinterpret_cast<double2*>(a.om) + (size_t)(nq + nd) * F, F);
+        }
         k_force<double><<<(unsigned)((a.V + 127) / 128), 128, 0, st>>>(a);
     } else {
         cudaFuncSetAttribute(k_recomb_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
@@ -338,6 +443,17 @@ cudaError_t launch_adjoint(int prec, const AdjArgs& a, const void* basis, size_t
                                                     a.npairs, reinterpret_cast<float4*>(a.nu), F);
         k_recomb_multi<float><<<grid, 128, sm, st>>>(reinterpret_cast<const float4*>(lbasis), lbasis_vec_stride, k, a.com, a.kmax,
                                                     a.npairs, reinterpret_cast<float4*>(a.om), F);
+        if (a.ndefl > 0) {
+            const int nq = a.npairs, nd = a.ndefl;
+            dim3 gd((unsigned)((F + 127) / 128), (unsigned)((nd + kQB - 1) / kQB));
+            k_defl_coef<<<1, 2 * nd, 0, st>>>(a);
+            k_recomb_multi<float><<<gd, 128, sm, st>>>(reinterpret_cast<const float4*>(basis), basis_vec_stride, k,
+                                                      a.cnu + (size_t)(nq + 2 * nd) * a.kmax, a.kmax, nd,
+                                                      reinterpret_cast<float4*>(a.nu) + (size_t)(nq + 2 * nd) * F, F);
+            k_recomb_multi<float><<<gd, 128, sm, st>>>(reinterpret_cast<const float4*>(lbasis), lbasis_vec_stride, k,
+                                                      a.com + (size_t)(nq + nd) * a.kmax, a.kmax, nd,
+                                                      reinterpret_cast<float4*>(a.om) + (size_t)(nq + nd) * F, F);
+        }
         k_force<float><<<(unsigned)((a.V + 127) / 128), 128, 0, st>>>(a);
     }
     return cudaGetLastError();

@@ -1982,24 +1982,45 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
     if (!c || !x || !y) return set_err(c, LQ_ERR_ARG, "null argument");
     if (!c->adjoint) return set_err(c, LQ_ERR_NOT_READY, "workspace reserved without LQ_RESERVE_ADJOINT");
     int r = check_ready(c, 2, 0);
-    if (r || (r = check_opts(c, o))) return r;
+    if (r || (r = check_opts(c, o, true))) return r;
     if (o->two_pass) return set_err(c, LQ_ERR_ARG, "the adjoint keeps the whole left basis: two_pass is not available");
+    const int l = o->deflate ? c->defl_l : 0;
+    if (l > 0 && 2 * o->quad_nodes + 3 * l > 2 * kQuadMaxNodes)
+        return set_err(c, LQ_ERR_ARG, "deflated adjoint: 2 quad_nodes + 3 l must not exceed " + std::to_string(2 * kQuadMaxNodes));
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nv = nvec(c);
     const size_t reg = (size_t)c->nsrc * nv;
-    double* io0 = c->io;            // sources: 0 = x, 1 = y
-    double* io1 = c->io + reg;      // results: 0 = sgn(H) x
-    if ((r = stage_in(c, io0, x, nv, st))) return r;
-    if ((r = stage_in(c, io0 + nv, y, nv, st))) return r;
+    double* io0 = c->io;            // sources: 0 = x, 1 = y (deflated: x' = Pbar x, y' = Pbar^H y)
+    double* io1 = c->io + reg;      // results: 0 = sgn(H) x'
+    double* io2 = c->io + 2 * reg;  // the caller's x and y
+    if ((r = stage_in(c, io2, x, nv, st))) return r;
+    if ((r = stage_in(c, io2 + nv, y, nv, st))) return r;
+    LQ_CUDA(c, cudaMemcpyAsync(io0, io2, sizeof(double) * 2 * nv, cudaMemcpyDeviceToDevice, st));
+    // deflation (Sec. 3): c_j = <Lk_j|x>, d_j = y^H R_j = conj(<R_j|y>); x' = x - sum_j R_j c_j,
+    // y' = y - sum_j Lk_j <R_j|y>
+    std::vector<double2> cx, ry;
+    if (l > 0) {
+        if ((r = bdots_host(c, c->defl_W, l, io2, 1, cx, st))) return r;
+        if ((r = bdots_host(c, c->defl_V, l, io2 + nv, 1, ry, st))) return r;
+        std::vector<double2> m1(l), m2(l);
+        for (int j = 0; j < l; ++j) { m1[j] = make_double2(-cx[j].x, -cx[j].y); m2[j] = make_double2(-ry[j].x, -ry[j].y); }
+        if ((r = bcombine_host(c, io0, io0, 1, c->defl_V, l, m1, st))) return r;
+        if ((r = bcombine_host(c, io0 + nv, io0 + nv, 1, c->defl_W, l, m2, st))) return r;
+    }
     lq_opts so = *o;
     if (so.projected == LQ_PROJ_NEWTON) so.projected = LQ_PROJ_AUTO;   // the adjoint uses the quadrature
     std::vector<lq_report> rep(2);
     if ((r = run_tsl(c, 1, 0, 2, &so, rep.data(), io1, nullptr, st, io0, nullptr, FN_SIGN, nullptr, true))) return r;
     for (int s = 0; s < 2; ++s)
         if (rep[s].status != LQ_OK) return set_err(c, rep[s].status, "Lanczos process failed for the bilinear");
-    // S = Re <y | sgn(H) x>
+    // S = Re <y | sgn(H) x'> (+ Re sum_j sgn(lambda_j) c_j d_j with deflation)
     std::vector<double2> d;
-    if ((r = bdots_host(c, io0 + nv, 1, io1, 1, d, st))) return r;
+    if ((r = bdots_host(c, io2 + nv, 1, io1, 1, d, st))) return r;
+    double Sdefl = 0.0;
+    for (int j = 0; j < l; ++j) {
+        const cplx cj(cx[j].x, cx[j].y), dj(ry[j].x, -ry[j].y);
+        Sdefl += sgn_re(c->defl_lam[j]) * (cj * dj).real();
+    }
     // gradient from 2N quadrature pairs
     double cscale = 1.0;
     LQ_CUDA(c, cudaMemcpy(&cscale, c->quad_c, sizeof(double), cudaMemcpyDeviceToHost));
@@ -2030,6 +2051,44 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
     a.force = c->adj_force;
     a.dmu_part = c->adj_dmu;
     const size_t F = fe(c);
+    if (l > 0) {
+        // the 3 l deflation pairs after the 2N Krylov pairs, from the four-block split of G by the
+        // spectral projectors (lq_adjoint.cu, k_defl_coef): (R_i, b_i) with b_i = sum_j conj(F_ij c_i
+        // d_j) Lk_j and the divided differences F_ij = (sgn l_i - sgn l_j) / (l_i - l_j) (the
+        // deflated block); (R_i, conj(c_i) u_i) and (d_j v_j, Lk_j) (the two mixed blocks)
+        const int nq = a.npairs;
+        std::vector<double2> bc((size_t)l * l);
+        for (int i = 0; i < l; ++i)
+            for (int j = 0; j < l; ++j) {
+                const cplx li(c->defl_lam[i].x, c->defl_lam[i].y), lj(c->defl_lam[j].x, c->defl_lam[j].y);
+                const double si = sgn_re(c->defl_lam[i]), sj = sgn_re(c->defl_lam[j]);
+                const cplx F_ij = si != sj ? cplx(si - sj) / (li - lj) : cplx(0.0);
+                const cplx m = std::conj(F_ij * cplx(cx[i].x, cx[i].y) * cplx(ry[j].x, -ry[j].y));
+                bc[(size_t)i * l + j] = make_double2(m.real(), m.imag());
+            }
+        double* bvec = c->defl_work;   // l FP64 fields
+        if ((r = bcombine_host(c, bvec, nullptr, l, c->defl_W, l, bc, st))) return r;
+        const size_t fbytes = fb(c);
+        auto slot = [&](void* base, int q) { return reinterpret_cast<char*>(base) + (size_t)q * fbytes; };
+        LQ_CUDA(c, launch_to_internal(c->prec, c->defl_V, slot(c->adj_nu, nq), c->V, l, st));
+        LQ_CUDA(c, launch_to_internal(c->prec, bvec, slot(c->adj_om, nq), c->V, l, st));
+        LQ_CUDA(c, launch_to_internal(c->prec, c->defl_V, slot(c->adj_nu, nq + l), c->V, l, st));
+        LQ_CUDA(c, launch_to_internal(c->prec, c->defl_W, slot(c->adj_om, nq + 2 * l), c->V, l, st));
+        c->launches += 4;
+        std::vector<double2> small((size_t)3 * l);
+        for (int j = 0; j < l; ++j) {
+            small[j] = c->defl_lam[j];
+            small[(size_t)l + j] = cx[j];
+            small[(size_t)2 * l + j] = make_double2(ry[j].x, -ry[j].y);
+        }
+        double2* dsmall = reinterpret_cast<double2*>(c->gen_scr + c->gen_scr_doubles) - 3 * (size_t)l;
+        LQ_CUDA(c, cudaMemcpyAsync(dsmall, small.data(), sizeof(double2) * small.size(), cudaMemcpyHostToDevice, st));
+        a.ndefl = l;
+        a.npairs_force = nq + 3 * l;
+        a.dlam = dsmall;
+        a.dcx = dsmall + l;
+        a.ddy = dsmall + 2 * l;
+    }
     // right basis of source 0 (x) and stored left basis of source 1 (y)
     const void* lb1 = reinterpret_cast<const char*>(c->lbasis) + (size_t)c->kmax * F * chunk_bytes(c);
     LQ_CUDA(c, launch_adjoint(c->prec, a, c->basis, F, lb1, F, std::max(k, 1), st));
@@ -2039,7 +2098,7 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
     LQ_CUDA(c, cudaMemcpyAsync(dmu.data(), c->adj_dmu, sizeof(double) * nblk, cudaMemcpyDeviceToHost, st));
     if (force && (r = stage_out(c, force, c->adj_force, c->V * 32, st))) return r;
     LQ_CUDA(c, cudaStreamSynchronize(st));
-    if (S) *S = d[0].x;
+    if (S) *S = d[0].x + Sdefl;
     if (dS_dmu) { double t = 0.0; for (double v : dmu) t += v; *dS_dmu = t; }
     return LQ_OK;
 }

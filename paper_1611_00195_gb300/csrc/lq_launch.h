@@ -176,6 +176,14 @@ struct AdjArgs {
     const double2* Ub;     // FP64 links, boundary layout [4][V][9]
     double* force;         // [4][V][8]
     double* dmu_part;      // [blocks]
+    // deflated adjoint (ndefl = 0 without deflation): the mixed-block vectors d_j v_j and
+    // conj(c_j) u_j (coefficient rows 2N + 2l + j of cnu and 2N + l + j of com) and the pairs
+    // contracted by k_force (npairs_force, 2N + 3l; 0 means npairs)
+    int ndefl;
+    int npairs_force;
+    const double2* dlam;   // [l] eigenvalues lambda_j
+    const double2* dcx;    // [l] c_j = L_j x'  (before deflation: L_j x)
+    const double2* ddy;    // [l] d_j = y^H R_j
 };
 cudaError_t launch_adjoint(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,
                            size_t lbasis_vec_stride, int k, cudaStream_t st);

@@ -186,3 +186,70 @@ def test_force_workload_12x12c3(lqlib):
               % (k, prec, eS, eF, emu, eps_k))
         assert max(eS, eF, emu) <= 10 * eps_k
         del cw
+
+
+def _upload_eigenpairs(c, lat, U, l):
+    from oracle import deflation as odf
+    H = od.dense_H(lat, U, MU)
+    lam, R, L, _ = odf.eigenpairs(H, l)
+    c.upload_deflation(lam, torch.from_numpy(np.ascontiguousarray(R.T.reshape(l, lat.V, 4, 3))).cuda(),
+                       torch.from_numpy(np.ascontiguousarray(L.conj().reshape(l, lat.V, 4, 3))).cuda())
+    return lam, R, L
+
+
+@pytest.mark.parametrize("dims,k,l", [((4, 2, 2, 2), 80, 6), ((2, 2, 2, 2), 60, 8)])
+def test_deflated_force_parity_same_depth(lqlib, dims, k, l):
+    """The deflated adjoint (opts.deflate = 1) against the oracle's deflated Krylov route at the
+    same depth, with the oracle's eigenpairs installed: S, the force on every link and dS/dmu,
+    within 30 times the oracle's own rounding sensitivity."""
+    from paper_1611_00195_gb300 import lq
+    lat = od.Lattice(dims)
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = syn.gaussian_source(dims, 5)
+    y = syn.gaussian_source(dims, 6)
+    c = _ctx(lq, dims, U, k)
+    lam, R, L = _upload_eigenpairs(c, lat, U, l)
+    S, F, dmu = c.bilinear_grad(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), k, deflate=1)
+    F = F.cpu().numpy()
+    A = lambda v: od.apply_H(lat, U, v, MU).ravel()        # noqa: E731
+    Ah = lambda v: od.apply_Hdag(lat, U, v, MU).ravel()    # noqa: E731
+
+    def oracle(xx, yy):
+        G, So = oad.G_deflated_tsl(A, Ah, lam, R, L, xx.ravel(), yy.ravel(), k)
+        return So, oad.force_from_G(lat, U, G, MU), oad.dmu_from_G(lat, U, G, MU)
+    So, Fo, dmuo = oracle(x, y)
+    rng = np.random.default_rng(1)
+    sens = 0.0
+    for xp, yp in ((x * (1 + 1e-16 * rng.standard_normal(x.shape)), y), (x, y * (1 + 1e-16 * rng.standard_normal(y.shape)))):
+        Sp, Fp, dmup = oracle(xp, yp)
+        sens = max(sens, np.linalg.norm(Fp - Fo) / np.linalg.norm(Fo))
+    eF = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
+    print("deflated force parity %s k=%d l=%d: S %.3g F %.3g dmu %.3g (oracle self-sensitivity %.3g)"
+          % (dims, k, l, abs(S - So) / abs(So), eF, abs(dmu - dmuo) / abs(dmuo), sens))
+    tol = max(1e-10, 30 * sens)
+    assert eF < tol
+    assert abs(S - So) < tol * abs(So) and abs(dmu - dmuo) < tol * max(abs(dmuo), 1e-3)
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_deflated_force_converges(lqlib, prec):
+    """At a converged depth on 2^4 the deflated force equals the dense one (and the undeflated
+    GPU force); in mixed precision it matches the FP64 deflated force to FP32 accuracy."""
+    from paper_1611_00195_gb300 import lq
+    dims, k, l = (2, 2, 2, 2), 150, 8
+    lat = od.Lattice(dims)
+    U = syn.gauge_field(dims, 0.3, 3)
+    x = syn.gaussian_source(dims, 5)
+    y = syn.gaussian_source(dims, 6)
+    c = _ctx(lq, dims, U, k, prec)
+    _upload_eigenpairs(c, lat, U, l)
+    xt, yt = torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda()
+    S, F, dmu = c.bilinear_grad(xt, yt, k, deflate=1)
+    S0, F0, dmu0 = c.bilinear_grad(xt, yt, k)
+    F, F0 = F.cpu().numpy(), F0.cpu().numpy()
+    Sd, Fd, dmud = oad.grad_dense(lat, U, x, y, MU)
+    eF, eF0 = np.linalg.norm(F - Fd) / np.linalg.norm(Fd), np.linalg.norm(F0 - Fd) / np.linalg.norm(Fd)
+    print("prec %d k=%d: deflated force vs dense %.3g (undeflated %.3g); S %.3g dmu %.3g"
+          % (prec, k, eF, eF0, abs(S - Sd) / abs(Sd), abs(dmu - dmud) / abs(dmud)))
+    tol = 1e-6 if prec == 0 else 1e-3
+    assert eF < tol and abs(S - Sd) < tol * abs(Sd) and abs(dmu - dmud) < tol * abs(dmud)
