@@ -668,12 +668,14 @@ __device__ __forceinline__ float4 axpy3<float>(float4 r, float4 v, float4 p, con
 
 template <typename R>
 __device__ __forceinline__ void dot_chunk(DotAcc<R> (&d)[4], typename Tr<R>::Chunk w, typename Tr<R>::Chunk v);
+// omega = <w, v> compensated (it becomes delta_j and beta_j); the norms |v|^2, |w|^2 only set
+// the breakdown threshold and are summed plainly in FP64
 template <>
 __device__ __forceinline__ void dot_chunk<double>(DotAcc<double> (&d)[4], double2 w, double2 v) {
     d[0].add_prod(w.x, v.x); d[0].add_prod(w.y, v.y);
     d[1].add_prod(w.x, v.y); d[1].add_prod(-w.y, v.x);
-    d[2].add_prod(v.x, v.x); d[2].add_prod(v.y, v.y);
-    d[3].add_prod(w.x, w.x); d[3].add_prod(w.y, w.y);
+    d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y);
+    d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y);
 }
 template <>
 __device__ __forceinline__ void dot_chunk<float>(DotAcc<float> (&d)[4], float4 w, float4 v) {

@@ -36,6 +36,9 @@ template <> struct DotAcc<double> {
     CSum v;
     __device__ __forceinline__ void zero() { v.s = 0.0; v.e = 0.0; }
     __device__ __forceinline__ void add_prod(double a, double b) { cs_add_prod(v, a, b); }
+    // a plain FMA term (for sums that only feed a threshold: the compensation, several FP64
+    // operations per term, is what bounds the FP64 update on this GPU)
+    __device__ __forceinline__ void add_plain(double a, double b) { v.s = fma(a, b, v.s); }
     // warp-level reduction then conversion to a double compensated sum (valid in lane 0)
     __device__ __forceinline__ CSum warp_total() {
         CSum r = v;
