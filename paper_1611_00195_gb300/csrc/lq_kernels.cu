@@ -151,15 +151,13 @@ __global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
             load_spinor(l0, V, s, w);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                d[0].add_prod(w[c].x, acc0[c].x); d[0].add_prod(w[c].y, acc0[c].y);
-                d[1].add_prod(w[c].x, acc0[c].y); d[1].add_prod(-w[c].y, acc0[c].x);
+                add_cdot(d[0], d[1], w[c], acc0[c]);
             }
             if (NF == 2) {
                 load_spinor(l0 + field_elems<R>(V), V, s, w);
 #pragma unroll
                 for (int c = 0; c < 12; ++c) {
-                    d[0].add_prod(w[c].x, acc1[c].x); d[0].add_prod(w[c].y, acc1[c].y);
-                    d[1].add_prod(w[c].x, acc1[c].y); d[1].add_prod(-w[c].y, acc1[c].x);
+                    add_cdot(d[0], d[1], w[c], acc1[c]);
                 }
             }
         }
@@ -277,8 +275,7 @@ __global__ void __launch_bounds__(4 * RS, MINB) k_hop_roles(HopArgs a) {
             load_spinor(w, V, s, psi);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                d[0].add_prod(psi[c].x, acc[c].x); d[0].add_prod(psi[c].y, acc[c].y);
-                d[1].add_prod(psi[c].x, acc[c].y); d[1].add_prod(-psi[c].y, acc[c].x);
+                add_cdot(d[0], d[1], psi[c], acc[c]);
             }
         }
     }
@@ -574,8 +571,7 @@ __global__ void __launch_bounds__(kTileThreadsMax) k_hop_tiled(HopArgs a) {
             load_spinor(wl + (size_t)f * F, V, s, psi);
 #pragma unroll
             for (int c = 0; c < 12; ++c) {
-                d[0].add_prod(psi[c].x, acc[c].x); d[0].add_prod(psi[c].y, acc[c].y);
-                d[1].add_prod(psi[c].x, acc[c].y); d[1].add_prod(-psi[c].y, acc[c].x);
+                add_cdot(d[0], d[1], psi[c], acc[c]);
             }
         }
     };
@@ -668,12 +664,11 @@ __device__ __forceinline__ float4 axpy3<float>(float4 r, float4 v, float4 p, con
 
 template <typename R>
 __device__ __forceinline__ void dot_chunk(DotAcc<R> (&d)[4], typename Tr<R>::Chunk w, typename Tr<R>::Chunk v);
-// omega = <w, v> compensated (it becomes delta_j and beta_j); the norms |v|^2, |w|^2 only set
-// the breakdown threshold and are summed plainly in FP64
+// omega = <w, v> compensated over the elements (it becomes delta_j and beta_j); the norms
+// |v|^2, |w|^2 only set the breakdown threshold and are summed plainly in FP64
 template <>
 __device__ __forceinline__ void dot_chunk<double>(DotAcc<double> (&d)[4], double2 w, double2 v) {
-    d[0].add_prod(w.x, v.x); d[0].add_prod(w.y, v.y);
-    d[1].add_prod(w.x, v.y); d[1].add_prod(-w.y, v.x);
+    add_cdot(d[0], d[1], w, v);
     d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y);
     d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y);
 }

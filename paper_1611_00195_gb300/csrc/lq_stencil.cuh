@@ -64,6 +64,19 @@ template <> struct DotAcc<float> {
     }
 };
 
+// re += Re conj(w) a, im += Im conj(w) a.  FP64: each complex term is formed with one product
+// and one FMA and then added by a compensated two-sum, so the long sums over sites and elements
+// stay compensated while a term costs a few FP64 operations instead of two exact products (FP64
+// is slow on this GPU).  FP32: exact products in float-float.
+__device__ __forceinline__ void add_cdot(DotAcc<double>& re, DotAcc<double>& im, double2 w, double2 a) {
+    cs_add(re.v, fma(w.x, a.x, w.y * a.y));
+    cs_add(im.v, fma(w.x, a.y, -(w.y * a.x)));
+}
+__device__ __forceinline__ void add_cdot(DotAcc<float>& re, DotAcc<float>& im, float2 w, float2 a) {
+    re.add_prod(w.x, a.x); re.add_prod(w.y, a.y);
+    im.add_prod(w.x, a.y); im.add_prod(-w.y, a.x);
+}
+
 // Reduce NV per-thread accumulators to one compensated double per value for the block.
 // Valid in thread 0.  smem holds 32 * NV CSum.  FP32 data stays in float-float up to the block
 // total (one conversion per value in thread 0): FP64 is slow on this GPU and has no place in the
