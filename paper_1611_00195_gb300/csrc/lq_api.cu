@@ -920,7 +920,6 @@ double2 cdivh(double2 a, double2 b) {
     const double d = b.x * b.x + b.y * b.y;
     return make_double2((a.x * b.x + a.y * b.y) / d, (a.y * b.x - a.x * b.y) / d);
 }
-double2 cmulh(double2 a, double2 b) { return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x); }
 double2 conjh(double2 a) { return make_double2(a.x, -a.y); }
 
 // dlambda_i, dR_i, dL_i for the current direction (end of Sec. 3):
@@ -1587,6 +1586,7 @@ int overlap_bicgstab(lq_ctx* c, const double* B, double* Z, int nsrc, double mas
         bn[s] = std::sqrt(std::max(bb[s].real(), 0.0));
         if (!(bn[s] > 0.0)) done[s] = conv[s] = 1;
     }
+    const std::vector<cplx> nocoef;   // an absent third term of scomb_host
     auto all_done = [&]() { return std::all_of(done.begin(), done.end(), [](int v) { return v != 0; }); };
     auto tiny = [](cplx v, double scale) { return !(std::abs(v) > 1e-300 * scale) || !std::isfinite(std::abs(v)); };
     for (int it = 0; it < max_iter && !all_done(); ++it) {
@@ -1611,7 +1611,7 @@ int overlap_bicgstab(lq_ctx* c, const double* B, double* Z, int nsrc, double mas
             alpha[s] = rho1[s] / d[s];
             malpha[s] = -alpha[s];
         }
-        if ((r = scomb_host(c, S, R, Vv, nullptr, one, malpha, {}, nsrc, st))) return r;   // S = R - alpha V
+        if ((r = scomb_host(c, S, R, Vv, nullptr, one, malpha, nocoef, nsrc, st))) return r;   // S = R - alpha V
         if ((r = apply_Dm(c, S, T, nsrc, mass, o, worst, done, st))) return r;
         if ((r = sdots_host(c, T, S, nsrc, ts, st))) return r;
         if ((r = sdots_host(c, T, T, nsrc, tt, st))) return r;
@@ -1622,7 +1622,7 @@ int overlap_bicgstab(lq_ctx* c, const double* B, double* Z, int nsrc, double mas
             momega[s] = -omega[s];
         }
         if ((r = scomb_host(c, Z, Z, P, S, one, alpha, omega, nsrc, st))) return r;         // Z += alpha P + omega S
-        if ((r = scomb_host(c, R, S, T, nullptr, one, momega, {}, nsrc, st))) return r;     // R = S - omega T
+        if ((r = scomb_host(c, R, S, T, nullptr, one, momega, nocoef, nsrc, st))) return r;     // R = S - omega T
         if ((r = sdots_host(c, R, R, nsrc, rr, st))) return r;
         for (int s = 0; s < nsrc; ++s) {
             if (done[s]) continue;
@@ -1636,7 +1636,7 @@ int overlap_bicgstab(lq_ctx* c, const double* B, double* Z, int nsrc, double mas
     const std::vector<int> none(nsrc, 0);
     if ((r = apply_Dm(c, Z, T, nsrc, mass, o, worst, none, st))) return r;
     std::vector<cplx> mone(nsrc, -1.0);
-    if ((r = scomb_host(c, R, B, T, nullptr, one, mone, {}, nsrc, st))) return r;
+    if ((r = scomb_host(c, R, B, T, nullptr, one, mone, nocoef, nsrc, st))) return r;
     if ((r = sdots_host(c, R, R, nsrc, rr, st))) return r;
     if (rep) {
         for (int s = 0; s < nsrc; ++s) {
