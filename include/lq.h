@@ -414,8 +414,8 @@ int  lq_newton_sign(lq_ctx* ctx, const double* X, double* S, int k, int nb,
  *     host threads or on several streams at once -- race on it and give wrong results:
  *     serialise them.
  * X, S: device double[nb][k][k][2] row-major; iters: host int[nb] or NULL.  Returns LQ_OK,
- * LQ_ERR_ARG, LQ_ERR_CUDA, or LQ_ERR_NEWTON if a matrix did not converge.  Synchronises
- * `stream`. */
+ * LQ_ERR_ARG, LQ_ERR_LAYOUT if X or S is not device memory (checked before any launch),
+ * LQ_ERR_CUDA, or LQ_ERR_NEWTON if a matrix did not converge.  Synchronises `stream`. */
 int  lq_newton_sign_noalloc(const double* X, double* S, int k, int nb, int max_iter, double tol,
                             int* iters, void* stream);
 

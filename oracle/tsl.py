@@ -19,14 +19,18 @@ tridiagonal projection T = W^H A V:
 
 The projected sign sgn(T_k) is evaluated by the ordered-Schur method (oracle.sign),
 a different algorithm from the Newton iteration of the CUDA path.  A serious
-breakdown |omega| < tol |wh| |vh| stops the process early (k_eff < k).
+breakdown |omega| < tol |wh| |vh| stops the process early (k_eff < k), and so does an
+invariant subspace (the paper is silent on both): |vh| <= invariant_tol |A v_j| or
+|wh| <= invariant_tol |A^H w_j|, where the recurrence has cancelled to rounding.  On an
+invariant right subspace A V_j = V_j T_j holds exactly, so f(A)x = |x| V_j f(T_j) e_1 is
+then the exact result (a free-field plane wave stops at k_eff = 2).
 """
 import numpy as np
 
 from .sign import sign_schur
 
 
-def tsl(apply_A, apply_Ah, v1, w1, k, breakdown_tol=1e-14, rebiorth=False):
+def tsl(apply_A, apply_Ah, v1, w1, k, breakdown_tol=1e-14, rebiorth=False, invariant_tol=1e-10):
     """Run k steps; returns dict(T, V [k_eff][n], W [k_eff][n], k_eff, alpha, beta, delta)."""
     V = [np.asarray(v1, dtype=complex)]
     W = [np.asarray(w1, dtype=complex)]
@@ -38,8 +42,9 @@ def tsl(apply_A, apply_Ah, v1, w1, k, breakdown_tol=1e-14, rebiorth=False):
         alpha.append(a)
         if j == k - 1:
             break
+        Aw = apply_Ah(W[j])
         vh = Av - a * V[j]
-        wh = apply_Ah(W[j]) - np.conj(a) * W[j]
+        wh = Aw - np.conj(a) * W[j]
         if j > 0:
             vh = vh - beta[j - 1] * V[j - 1]
             wh = wh - np.conj(delta[j - 1]) * W[j - 1]
@@ -47,6 +52,10 @@ def tsl(apply_A, apply_Ah, v1, w1, k, breakdown_tol=1e-14, rebiorth=False):
             Vm, Wm = np.array(V), np.array(W)
             vh = vh - Vm.T @ (Wm.conj() @ vh)
             wh = wh - Wm.T @ (Vm.conj() @ wh)
+        if (np.linalg.norm(vh) <= invariant_tol * np.linalg.norm(Av)
+                or np.linalg.norm(wh) <= invariant_tol * np.linalg.norm(Aw)):
+            k_eff = j + 1          # invariant subspace
+            break
         om = np.vdot(wh, vh)
         if abs(om) < breakdown_tol * np.linalg.norm(wh) * np.linalg.norm(vh):
             k_eff = j + 1

@@ -367,7 +367,7 @@ struct TslRun {
         // last-block counters are a block of 3 nsrc from 3 s0 on
         const size_t xs = (size_t)s0 * c->V * 24;
         TslState* state = c->state + s0;
-        double* partials = c->partials + (size_t)s0 * c->partial_blocks * 8;
+        double* partials = c->partials + (size_t)s0 * c->partial_blocks * 12;   // 12 doubles per block and source
         int* counters = c->counters + (size_t)3 * s0;
         const size_t ks = (size_t)s0 * c->kmax;
         std::memset(&ia, 0, sizeof(ia));
@@ -1285,7 +1285,7 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     pb = std::max(pb, (size_t)64);   // update grid (one resident wave over all sources, capped here)
     pb = std::max(pb, (c->V + kUpdThreads - 1) / kUpdThreads);
     c->partial_blocks = pb;
-    if ((r = dalloc(c, &c->partials, (size_t)nsrc * pb * 8))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->partials, (size_t)nsrc * pb * 12))) { free_workspace(c); return r; }   // 6 sums per block
     if ((r = dalloc(c, &c->counters, (size_t)4 * nsrc))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->state, (size_t)nsrc))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->alpha, (size_t)nsrc * kmax))) { free_workspace(c); return r; }

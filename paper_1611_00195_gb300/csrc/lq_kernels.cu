@@ -663,28 +663,45 @@ __device__ __forceinline__ float4 axpy3<float>(float4 r, float4 v, float4 p, con
 }
 
 template <typename R>
-__device__ __forceinline__ void dot_chunk(DotAcc<R> (&d)[4], typename Tr<R>::Chunk w, typename Tr<R>::Chunk v);
+__device__ __forceinline__ void dot_chunk(DotAcc<R> (&d)[6], typename Tr<R>::Chunk w, typename Tr<R>::Chunk v);
 // omega = <w, v> compensated over the elements (it becomes delta_j and beta_j); the norms
-// |v|^2, |w|^2 only set the breakdown threshold and are summed plainly in FP64
+// |v|^2, |w|^2 only set the breakdown thresholds and are summed plainly
 template <>
-__device__ __forceinline__ void dot_chunk<double>(DotAcc<double> (&d)[4], double2 w, double2 v) {
+__device__ __forceinline__ void dot_chunk<double>(DotAcc<double> (&d)[6], double2 w, double2 v) {
     add_cdot(d[0], d[1], w, v);
     d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y);
     d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y);
 }
 template <>
-__device__ __forceinline__ void dot_chunk<float>(DotAcc<float> (&d)[4], float4 w, float4 v) {
+__device__ __forceinline__ void dot_chunk<float>(DotAcc<float> (&d)[6], float4 w, float4 v) {
     d[0].add_prod(w.x, v.x); d[0].add_prod(w.y, v.y); d[0].add_prod(w.z, v.z); d[0].add_prod(w.w, v.w);
     d[1].add_prod(w.x, v.y); d[1].add_prod(-w.y, v.x); d[1].add_prod(w.z, v.w); d[1].add_prod(-w.w, v.z);
-    d[2].add_prod(v.x, v.x); d[2].add_prod(v.y, v.y); d[2].add_prod(v.z, v.z); d[2].add_prod(v.w, v.w);
-    d[3].add_prod(w.x, w.x); d[3].add_prod(w.y, w.y); d[3].add_prod(w.z, w.z); d[3].add_prod(w.w, w.w);
+    d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y); d[2].add_plain(v.z, v.z); d[2].add_plain(v.w, v.w);
+    d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y); d[3].add_plain(w.z, w.z); d[3].add_plain(w.w, w.w);
 }
+// |B vh_j|^2 (d[4]) and |B^dag wh_j|^2 (d[5]): the scale against which an invariant subspace is
+// detected (plain sums, thresholds only)
+__device__ __forceinline__ void norm_chunk(DotAcc<double> (&d)[6], double2 r, double2 l) {
+    d[4].add_plain(r.x, r.x); d[4].add_plain(r.y, r.y);
+    d[5].add_plain(l.x, l.x); d[5].add_plain(l.y, l.y);
+}
+__device__ __forceinline__ void norm_chunk(DotAcc<float> (&d)[6], float4 r, float4 l) {
+    d[4].add_plain(r.x, r.x); d[4].add_plain(r.y, r.y); d[4].add_plain(r.z, r.z); d[4].add_plain(r.w, r.w);
+    d[5].add_plain(l.x, l.x); d[5].add_plain(l.y, l.y); d[5].add_plain(l.z, l.z); d[5].add_plain(l.w, l.w);
+}
+
+// An invariant subspace: the new vector has cancelled to this fraction of |B v_j| (right) or
+// |B^dag w_j| (left), a few hundred times the rounding level of the vectors' precision.  A
+// regular step of these processes keeps the ratio of order one.
+template <typename R> __host__ __device__ constexpr double invariant_tol();
+template <> __host__ __device__ constexpr double invariant_tol<double>() { return 1e-10; }
+template <> __host__ __device__ constexpr double invariant_tol<float>() { return 1e-5; }
 
 template <typename R>
 __global__ void __launch_bounds__(kUpdThreads, 3) k_update(UpdArgs a) {
     using C = typename Tr<R>::C;
     using Chunk = typename Tr<R>::Chunk;
-    __shared__ CSum smem[32 * 4];
+    __shared__ CSum smem[32 * 6];
     const int src = blockIdx.y;
     TslState& st = a.state[src];
     if (st.status != 0) return;
@@ -705,9 +722,9 @@ __global__ void __launch_bounds__(kUpdThreads, 3) k_update(UpdArgs a) {
     const Chunk* wp = reinterpret_cast<const Chunk*>(a.w_prev) + (size_t)src * a.src_stride_left;
     Chunk* wn = reinterpret_cast<Chunk*>(a.w_next) + (size_t)src * a.src_stride_left;
     Chunk* ws = a.w_store ? reinterpret_cast<Chunk*>(a.w_store) + (size_t)src * a.src_stride_store : nullptr;
-    DotAcc<R> d[4];
+    DotAcc<R> d[6];
 #pragma unroll
-    for (int i = 0; i < 4; ++i) d[i].zero();
+    for (int i = 0; i < 6; ++i) d[i].zero();
     const size_t stride = (size_t)gridDim.x * blockDim.x;
     const Chunk zero{};
     size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -724,23 +741,27 @@ __global__ void __launch_bounds__(kUpdThreads, 3) k_update(UpdArgs a) {
         if (ws) { ws[e] = nw0; ws[e2] = nw1; }
         dot_chunk<R>(d, nw0, nv0);
         dot_chunk<R>(d, nw1, nv1);
+        norm_chunk(d, r0, l0);
+        norm_chunk(d, r1, l1);
     }
     if (e < N) {
-        const Chunk nv = axpy3<R>(__ldg(r + e), __ldg(v + e), has_prev ? __ldg(vp + e) : zero, cv, has_prev);
-        const Chunk nw = axpy3<R>(__ldg(l + e), __ldg(w + e), has_prev ? __ldg(wp + e) : zero, cw, has_prev);
+        const Chunk re = __ldg(r + e), le = __ldg(l + e);
+        const Chunk nv = axpy3<R>(re, __ldg(v + e), has_prev ? __ldg(vp + e) : zero, cv, has_prev);
+        const Chunk nw = axpy3<R>(le, __ldg(w + e), has_prev ? __ldg(wp + e) : zero, cw, has_prev);
         vn[e] = nv;
         wn[e] = nw;
         if (ws) ws[e] = nw;
         dot_chunk<R>(d, nw, nv);
+        norm_chunk(d, re, le);
     }
-    CSum tot[4];
-    block_total<R, 4>(d, tot, smem);
-    double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 8;
+    CSum tot[6];
+    block_total<R, 6>(d, tot, smem);
+    double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 12;
     if (threadIdx.x == 0)
-        for (int i = 0; i < 4; ++i) { part[2 * i] = tot[i].s; part[2 * i + 1] = tot[i].e; }
+        for (int i = 0; i < 6; ++i) { part[2 * i] = tot[i].s; part[2 * i + 1] = tot[i].e; }
     if (last_block(a.counters + a.nsrc + src, gridDim.x)) {
-        double res[4];
-        reduce_partials<4>(a.partials + (size_t)src * a.partial_stride * 8, gridDim.x, res, smem);
+        double res[6];
+        reduce_partials<6>(a.partials + (size_t)src * a.partial_stride * 12, gridDim.x, res, smem);
         if (threadIdx.x == 0) {
             // omega = <wh_{j+1}, vh_{j+1}>; delta_j = sqrt|omega|; beta_j = omega / delta_j
             const double om_re = res[0], om_im = res[1];
@@ -748,6 +769,12 @@ __global__ void __launch_bounds__(kUpdThreads, 3) k_update(UpdArgs a) {
             const double om = hypot(om_re, om_im);
             const int j = a.j;
             if (!isfinite(om) || !isfinite(nv2) || !isfinite(nw2)) { st.status = LQ_ERR_NONFINITE; return; }
+            // |B v_j|^2 = |s_j|^2 |B vh_j|^2 and |B^dag w_j|^2 = |u_j|^2 |B^dag wh_j|^2 (cv[0] = s_j, cw[0] = u_j)
+            const double tol2 = invariant_tol<R>() * invariant_tol<R>();
+            const double rr = (st.cv[0].x * st.cv[0].x + st.cv[0].y * st.cv[0].y) * res[4];
+            const double ll = (st.cw[0].x * st.cw[0].x + st.cw[0].y * st.cw[0].y) * res[5];
+            // vh_{j+1} = s_j B vh_j - ... is in the units of B v_j already (likewise wh_{j+1})
+            if (nv2 <= tol2 * rr || nw2 <= tol2 * ll) { st.status = LQ_ERR_BREAKDOWN; return; }
             if (om < st.breakdown_tol * sqrt(nv2) * sqrt(nw2) || om == 0.0) { st.status = LQ_ERR_BREAKDOWN; return; }
             const double dl = sqrt(om);
             const double2 be = make_double2(om_re / dl, om_im / dl);
@@ -829,7 +856,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_tsl_init(InitArgs a) {
             st.xnorm = vn;
             st.k_eff = 0;
             st.breakdown_tol = a.breakdown_tol;
-            if (!(vn > 0.0) || !isfinite(vn)) { st.status = LQ_ERR_ARG; return; }
+            if (!isfinite(vn)) { st.status = LQ_ERR_NONFINITE; return; }   // NaN / Inf in the source
+            if (!(vn > 0.0)) { st.status = LQ_ERR_ARG; return; }              // zero source
             const double s1 = 1.0 / vn;
             double2 wv = make_double2(nb, 0.0);                  // <wh_1, vh_1>
             if (NF == 2) { wv.x += res[2]; wv.y += res[3]; }

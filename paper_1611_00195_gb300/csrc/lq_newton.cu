@@ -647,6 +647,14 @@ cudaError_t na_scratch(NaLayout** out) {
     return cudaSuccess;
 }
 
+// True when p is device (or managed) memory that kernels on the current device can address.
+// cudaPointerGetAttributes allocates nothing.
+bool na_device_ptr(const void* p) {
+    cudaPointerAttributes at;
+    if (cudaPointerGetAttributes(&at, p) != cudaSuccess) { cudaGetLastError(); return false; }
+    return at.type == cudaMemoryTypeDevice || at.type == cudaMemoryTypeManaged;
+}
+
 }  // namespace
 }  // namespace lq
 
@@ -655,6 +663,8 @@ extern "C" int lq_newton_sign_noalloc(const double* X, double* S, int k, int nb,
     using namespace lq;
     if (!X || !S || k < 1 || nb < 1 || max_iter < 1 || !(tol > 0.0)) return LQ_ERR_ARG;
     if (k > kNaMaxK || nb > kNaMaxNb) return LQ_ERR_ARG;   // beyond the static workspace
+    // a host or stale pointer must come back as an error code, never reach a kernel
+    if (!na_device_ptr(X) || !na_device_ptr(S)) return LQ_ERR_LAYOUT;
     cudaStream_t st = (cudaStream_t)stream;
     NaLayout* w = nullptr;
     if (na_scratch(&w) != cudaSuccess) { cudaGetLastError(); return LQ_ERR_CUDA; }

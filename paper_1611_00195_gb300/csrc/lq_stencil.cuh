@@ -51,6 +51,8 @@ template <> struct DotAcc<float> {
     FF v;
     __device__ __forceinline__ void zero() { v.h = 0.f; v.l = 0.f; }
     __device__ __forceinline__ void add_prod(float a, float b) { ff_add_prod(v, a, b); }
+    // a plain FMA term (sums that only feed a threshold)
+    __device__ __forceinline__ void add_plain(float a, float b) { v.h = fmaf(a, b, v.h); }
     __device__ __forceinline__ CSum warp_total() {   // valid in lane 0 only
         FF r = v;
 #pragma unroll

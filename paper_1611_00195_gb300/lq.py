@@ -24,6 +24,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(_HERE, "liblq.so")
 
 LQ_OK = 0
+LQ_ERR_ARG, LQ_ERR_LAYOUT, LQ_ERR_BREAKDOWN, LQ_ERR_NEWTON, LQ_ERR_NONFINITE = -1, -2, -5, -6, -9
 # Revision tag of the stencil kernel; stored ncu traffic figures are only valid for this one.
 KERNEL_REV = "hop-v3"
 ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_CUDA", -5: "LQ_ERR_BREAKDOWN",
@@ -228,12 +229,17 @@ class SignBilinearForce(torch.autograd.Function if torch is not None else object
 def newton_sign_noalloc(X, max_iter=50, tol=1e-13):
     """Batched dense sign of complex k x k matrices X [nb][k][k] (CUDA tensor, k <= 128, nb <= 8)
     through the allocation-free entry point: no context and no device allocation by the library
-    (the output tensor is allocated here, by the caller's allocator)."""
+    (the output tensor is allocated here, by the caller's allocator).  The call runs on X's
+    device and current stream."""
+    if not (_is_tensor(X) and X.is_cuda):
+        raise TypeError("newton_sign_noalloc takes a CUDA tensor (the entry point reads device memory only)")
     X = _as_c128(X)
     nb, k = X.shape[0], X.shape[1]
-    S = _empty_like(X)
-    iters = (ctypes.c_int * nb)()
-    code = lib().lq_newton_sign_noalloc(_ptr(X), _ptr(S), int(k), int(nb), int(max_iter), float(tol), iters, _stream(X))
+    with torch.cuda.device(X.device):
+        S = _empty_like(X)
+        iters = (ctypes.c_int * nb)()
+        code = lib().lq_newton_sign_noalloc(_ptr(X), _ptr(S), int(k), int(nb), int(max_iter), float(tol), iters,
+                                            _stream(X))
     if code != LQ_OK:
         raise LQError(code, "lq_newton_sign_noalloc (k <= 128, nb <= 8)")
     return S, list(iters)

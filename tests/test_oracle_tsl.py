@@ -70,6 +70,31 @@ def test_plane_wave_derivative_is_exact_at_k4(mu):
     assert relerr(yd, ff.free_sign_dmu(lat, x, mu).ravel()) < 1e-11
 
 
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_plane_wave_stops_at_its_invariant_subspace(mu):
+    """Asked for k = 8 on a plane wave, the process stops when the recurrence cancels to
+    rounding (an invariant subspace): k_eff = 2 for the sign and 4 for the derivative (the two
+    2x2 Jordan blocks of Eq. (3.2)), and the results still equal the closed forms.  Without
+    the stop the process would go on from rounding noise."""
+    lat, U = _free((4, 4, 2, 2))
+    A = lambda v: od.apply_H(lat, U, v, mu).ravel()                # noqa: E731
+    Ah = lambda v: od.apply_Hdag(lat, U, v, mu).ravel()            # noqa: E731
+    E = lambda v: od.apply_dH_dmu(lat, U, v, mu).ravel()           # noqa: E731
+    Eh = lambda v: od.apply_dH_dmu_dag(lat, U, v, mu).ravel()      # noqa: E731
+    x = _plane_wave(lat, 4)
+    y, r = ot.tsl_sign(A, Ah, x, 8)
+    assert r["k_eff"] == 2
+    assert relerr(y, ff.free_sign(lat, x, mu).ravel()) < 1e-13
+    if mu > 0:
+        yd, ys, r = ot.tsl_sign_derivative(A, Ah, E, Eh, x, 8)
+        assert r["k_eff"] == 4
+        assert relerr(ys, ff.free_sign(lat, x, mu).ravel()) < 1e-12
+        assert relerr(yd, ff.free_sign_dmu(lat, x, mu).ravel()) < 1e-11
+    # a planted mistake: no stop (tolerance 0) lets rounding noise through
+    y0, r0 = ot.tsl_sign(A, Ah, x, 8, invariant_tol=0.0)
+    assert r0["k_eff"] > 2
+
+
 def test_two_plane_waves_need_k4():
     lat, U = _free((4, 4, 2, 2))
     mu = 0.3

@@ -53,3 +53,24 @@ def test_noalloc_rejects_sizes_beyond_its_workspace(lqlib):
     code = L.lq_newton_sign_noalloc(ctypes.c_void_p(X9.data_ptr()), ctypes.c_void_p(X9.data_ptr()), 4, 9, 50, 1e-13,
                                     it, None)
     assert code == -1
+
+
+def test_noalloc_rejects_host_pointers(lqlib):
+    # a host buffer in either argument comes back as LQ_ERR_LAYOUT before any kernel runs;
+    # the device context stays usable afterwards
+    from paper_1611_00195_gb300 import lq
+    L = lq.lib()
+    k = 4
+    Xh = np.eye(k, dtype=np.complex128)[None].copy()
+    Sh = np.zeros_like(Xh)
+    Xd = torch.from_numpy(Xh).cuda()
+    Sd = torch.zeros_like(Xd)
+    it = (ctypes.c_int * 1)()
+    for xp, sp in [(Xh.ctypes.data, Sd.data_ptr()), (Xd.data_ptr(), Sh.ctypes.data), (Xh.ctypes.data, Sh.ctypes.data)]:
+        code = L.lq_newton_sign_noalloc(ctypes.c_void_p(xp), ctypes.c_void_p(sp), k, 1, 50, 1e-13, it, None)
+        assert code == lq.LQ_ERR_LAYOUT
+    with pytest.raises(TypeError):
+        lq.newton_sign_noalloc(Xh)
+    torch.cuda.synchronize()
+    S, _ = lq.newton_sign_noalloc(Xd)
+    assert np.abs(S.cpu().numpy()[0] - np.eye(k)).max() < 1e-14
