@@ -52,6 +52,8 @@ def parse():
     p.add_argument("--nsrc", type=int, default=NSRC)
     p.add_argument("--no-fp64", action="store_true", help="skip the FP64 GPU comparison")
     p.add_argument("--no-cpu", action="store_true", help="skip the CPU-oracle baseline")
+    p.add_argument("--cpu-iters", type=int, default=6,
+                   help="block-TSL iterations each host core times for the CPU-oracle baseline (k: the full depth)")
     p.add_argument("--no-e2e", action="store_true", help="skip the host-buffer measurement")
     p.add_argument("--no-deflation", action="store_true", help="skip the deflated run")
     p.add_argument("--nev", type=int, default=20, help="eigenpairs of the deflation space")
@@ -63,12 +65,14 @@ def parse():
 
 
 # ------------------------------------------------------------------------------------------
-# CPU oracle sample (runs in a spawned child with one BLAS/OpenMP thread)
+# CPU oracle sample: one spawned process per host core, each with one BLAS/OpenMP thread
 # ------------------------------------------------------------------------------------------
-def _oracle_sample(iters, k, seconds_cap=None):
-    """Time `iters` iterations of the oracle's block two-sided Lanczos (Eq. (2.6)) for one
-    source of the workload, plus the k x k projected sign by the oracle's Schur method, and
-    scale to one derivative solve at depth k.  Returns (seconds per solve, description)."""
+def _oracle_sample(iters, k, seed):
+    """Time `iters` iterations of the oracle's block two-sided Lanczos (Eq. (2.6)) for the source
+    of seed `seed` of the workload, plus the k x k projected sign by the oracle's Schur method
+    (of the process's own T_k when iters == k, else of a k x k tridiagonal of the same kind),
+    and scale to one derivative solve at depth k.  Returns (seconds per solve, s/iteration,
+    seconds of the projected sign)."""
     import numpy as np
     import synthetic as syn
     from oracle import dirac as od
@@ -76,7 +80,7 @@ def _oracle_sample(iters, k, seconds_cap=None):
     from oracle import sign as osg
     lat = od.Lattice(DIMS, m_w=M_W)
     U = syn.gauge_field(DIMS, EPS, GAUGE_SEED)
-    x = syn.gaussian_source(DIMS, SOURCE_SEED, nsrc=1)[0].ravel()
+    x = syn.gaussian_source(DIMS, seed, nsrc=1)[0].ravel()
     A = lambda v: od.apply_H(lat, U, v, MU).ravel()              # noqa: E731
     Ah = lambda v: od.apply_Hdag(lat, U, v, MU).ravel()          # noqa: E731
     E = lambda v: od.apply_dH_dmu(lat, U, v, MU).ravel()         # noqa: E731
@@ -88,48 +92,66 @@ def _oracle_sample(iters, k, seconds_cap=None):
     w1 = np.concatenate([x, x]) / nx
     t0 = time.perf_counter()
     r = ot.tsl(B, Bh, v1, w1, iters)
-    t_iter = (time.perf_counter() - t0) / iters
-    # projected step at the full depth: Schur sign of a k x k tridiagonal of the same kind
+    t_loop = time.perf_counter() - t0
+    t_iter = t_loop / iters
     T = r["T"]
-    rng = np.random.default_rng(0)
-    Tk = np.diag(np.resize(np.diag(T), k)) + np.diag(np.resize(np.diag(T, 1), k - 1), 1) + np.diag(np.resize(np.diag(T, -1), k - 1), -1)
-    Tk = Tk + 1e-3 * np.diag(rng.standard_normal(k))
+    if T.shape[0] < k:
+        # projected step at the full depth: Schur sign of a k x k tridiagonal of the same kind
+        rng = np.random.default_rng(0)
+        Tk = np.diag(np.resize(np.diag(T), k)) + np.diag(np.resize(np.diag(T, 1), k - 1), 1) \
+            + np.diag(np.resize(np.diag(T, -1), k - 1), -1)
+        T = Tk + 1e-3 * np.diag(rng.standard_normal(k))
     t1 = time.perf_counter()
-    osg.sign_schur(Tk)
+    c = osg.sign_schur(T)[:, 0]
+    y = nx * (r["V"].T @ c) if T.shape[0] == r["V"].shape[0] else None
     t_proj = time.perf_counter() - t1
-    per_solve = t_iter * k + t_proj
-    desc = ("oracle block TSL (FP64 numpy), 1 source of 16, %d of %d iterations at 14x14^3 timed "
-            "(%.3f s/iteration) and scaled to k=%d, plus one k x k Schur sign (%.2f s)" % (iters, k, t_iter, k, t_proj))
-    return per_solve, desc
+    del y
+    return t_iter * k + t_proj, t_iter, t_proj
 
 
-def _oracle_child(q, iters, k):
+def _oracle_worker(job):
+    iters, k, seed = job
     try:
-        q.put(_oracle_sample(iters, k))
+        return _oracle_sample(iters, k, seed)
     except Exception as e:  # report, never hang the parent
-        q.put((None, repr(e)))
+        return (None, repr(e), None)
 
 
-def cpu_baseline(iters, k):
+def cpu_baseline(iters, k, workers=None):
+    """The oracle as it stands on all host cores: `workers` spawned processes (default: one per
+    core, at most one per source of the batch), each timing the same bounded sample on its own
+    source with one BLAS/OpenMP thread.  The host's rate is workers / (the slowest worker's time
+    per solve).  Returns (solves/s, workers, description) or (None, 0, error)."""
     import multiprocessing as mp
+    P = workers or max(1, min(os.cpu_count() or 1, NSRC))
     env_keys = ("OMP_NUM_THREADS", "OPENBLAS_NUM_THREADS", "MKL_NUM_THREADS")
     saved = {e: os.environ.get(e) for e in env_keys}
     for e in env_keys:
         os.environ[e] = "1"
     try:
         ctx = mp.get_context("spawn")
-        q = ctx.Queue()
-        p = ctx.Process(target=_oracle_child, args=(q, iters, k))
-        p.start()
-        res = q.get(timeout=900)
-        p.join(timeout=60)
+        with ctx.Pool(P) as pool:
+            res = pool.map(_oracle_worker, [(iters, k, SOURCE_SEED + i) for i in range(P)])
     finally:
         for e, v in saved.items():
             if v is None:
                 os.environ.pop(e, None)
             else:
                 os.environ[e] = v
-    return res
+    bad = [r for r in res if r[0] is None]
+    if bad:
+        return None, 0, bad[0][1]
+    per_solve = max(r[0] for r in res)
+    t_iter = max(r[1] for r in res)
+    t_proj = max(r[2] for r in res)
+    if iters >= k:
+        what = "the full depth k=%d timed (no scaling)" % k
+    else:
+        what = "%d of %d iterations timed and scaled to k=%d" % (iters, k, k)
+    desc = ("oracle block TSL (FP64 numpy) on %d host cores at once, one source each (%d of the batch of %d), "
+            "%s: %.3f s/iteration (slowest core), plus one k x k Schur sign (%.2f s)"
+            % (P, P, NSRC, what, t_iter, t_proj))
+    return P / per_solve, P, desc
 
 
 # ------------------------------------------------------------------------------------------
@@ -239,26 +261,26 @@ def run_reference(args, ws, rank):
     block-TSL iterations of one source), scaled to one derivative solve at depth k."""
     if rank != 0:
         return
-    iters = 3
-    times, walls = [], []
-    desc = ""
+    iters = min(3, args.k)      # a short sample per step: the whole run stays within a few minutes
+    rates, walls = [], []
+    desc, cores = "", 1
     for _ in range(args.steps):
         t0 = time.perf_counter()
-        per_solve, desc = cpu_baseline(iters, args.k)
+        rate, cores, desc = cpu_baseline(iters, args.k)
         walls.append(time.perf_counter() - t0)
-        if per_solve is None:
+        if rate is None:
             print(json.dumps({"impl": "reference", "unavailable": "oracle sample failed: %s" % desc}))
             return
-        times.append(per_solve)
-    per_solve = statistics.median(times)
-    value = 1.0 / per_solve
+        rates.append(rate)
+    value = statistics.median(rates)
+    per_solve = cores / value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "solves/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": statistics.median(walls) * 1e3,
             "ms_per_solve_extrapolated": per_solve * 1e3, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
             "config": {"workload": "14x14^3 derivative solves (d/dmu), k=%d, Gaussian sources, CPU FP64 oracle" % args.k,
                        "lattice": "14x14^3", "k": args.k, "mu": MU, "m_w": M_W, "eps": EPS},
-            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc},
+            "cpu_baseline": {"value": value, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": desc},
             "e2e": {"value": value, "unit": "solves/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line))
 
@@ -266,7 +288,8 @@ def run_reference(args, ws, rank):
 # kernel instantiated for each stencil schedule (lq_opts.hop_variant) of the block TSL step, FP32
 HOP_KERNELS = {0: "k_hop<float,2,1,true,1>", 1: "k_hop_roles<float,1,true,32,1>", 2: "k_hop<float,2,1,true,5>",
                3: "k_hop<float,2,1,true,4>", 4: "k_hop_roles<float,1,true,64,2>", 5: "k_hop_roles<float,1,true,32,5>",
-               6: "k_hop_tiled<1,true>"}
+               6: "k_hop_tiled<1,true>", 7: "k_hop_x2<1,true,false> (packed FP32 pairs)",
+               8: "k_hop_x2<1,true,true> (packed FP32 pairs, prefetched neighbours)"}
 # DRAM bytes (read + write) per launch of the block stencil from one ncu capture of that kernel
 # revision and schedule on the same per-launch shape (14x14^3, 16 sources, both sides; the
 # Krylov depth does not change a launch).  Source: profiles/k_hop_block_stencil_14x14c3_b16.md.
@@ -606,11 +629,11 @@ def main():
 
     cpu = None
     if not args.no_cpu and rank == 0:
-        per_solve, desc = cpu_baseline(8, k)
-        if per_solve is not None:
-            cpu = {"value": 1.0 / per_solve, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": desc}
+        rate, cores, desc = cpu_baseline(min(args.cpu_iters, k), k)
+        if rate is not None:
+            cpu = {"value": rate, "unit": "solves/s", "cores": cores, "kind": "oracle", "sample": desc}
         else:
-            cpu = {"value": None, "unit": "solves/s", "cores": 1, "kind": "oracle", "sample": "failed: " + desc}
+            cpu = {"value": None, "unit": "solves/s", "cores": 0, "kind": "oracle", "sample": "failed: " + desc}
 
     if rank != 0:
         return

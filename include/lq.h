@@ -92,8 +92,11 @@ typedef struct {
                               2 / 3 = as 0 with at least 5 / 4 resident blocks per SM, 4 = as
                               1 with 64 sites per block, 5 = as 1 with at least 5 resident
                               blocks per SM, 6 = shared-memory tiles of whole x rows x 2x2x2
-                              (needs even y, z, t extents; else 3).  2-6 are FP32 only (FP64
-                              runs 0); lq_report.hop_variant gives the schedule that ran     */
+                              (needs even y, z, t extents; else 3), 7 = as 3 in packed FP32
+                              pair arithmetic (identical results), 8 = as 7 with the next
+                              hop's neighbour spinors prefetched into shared memory.  2-8 are
+                              FP32 only (FP64 runs 0); lq_report.hop_variant gives the
+                              schedule that ran                                               */
     int defl_kmax;         /* depth of the shifted solves for the eigenvector derivatives of the
                               generalised deflation (0 = the reserved kmax)                    */
     int defl_nderiv;       /* Jordan blocks of the derivative deflation: the first defl_nderiv

@@ -146,6 +146,8 @@ HopArgs base_hop(const lq_ctx* c) {
     a.diag_f = (float)a.diag;
     a.U = c->U;
     a.Y = c->Y;
+    a.Up = c->Up;
+    a.Yp = c->Yp;
     return a;
 }
 
@@ -267,7 +269,7 @@ void free_workspace(lq_ctx* c) {
 // coefficients), so the tuning leaves no trace in the results.
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
-    const int nvar = (c->prec == LQ_FP64) ? 2 : 7;
+    const int nvar = (c->prec == LQ_FP64) ? 2 : kHopSchedules;
     for (const auto& t : c->tuned)
         if (t.nsrc == h.nsrc && t.nf == nf && t.emode == emode) { *variant = t.variant; return LQ_OK; }
     h.j = 0;
@@ -830,7 +832,8 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->projected < LQ_PROJ_AUTO || o->projected > LQ_PROJ_QUAD) return set_err(c, LQ_ERR_ARG, "unknown projected-sign solver");
     if (o->projected != LQ_PROJ_NEWTON && (o->quad_nodes < 1 || o->quad_nodes > kQuadMaxNodes || !(o->proj_tol > 0.0)))
         return set_err(c, LQ_ERR_ARG, "quad_nodes must be in [1, 128] and proj_tol > 0");
-    if (o->hop_variant < -1 || o->hop_variant > 6) return set_err(c, LQ_ERR_ARG, "hop_variant must be in [-1, 6]");
+    if (o->hop_variant < -1 || o->hop_variant >= kHopSchedules)
+        return set_err(c, LQ_ERR_ARG, "hop_variant must be in [-1, " + std::to_string(kHopSchedules - 1) + "]");
     if (o->defl_kmax < 0 || o->defl_kmax > c->kmax) return set_err(c, LQ_ERR_ARG, "defl_kmax must be in [0, reserved kmax]");
     if (o->defl_nderiv < 0) return set_err(c, LQ_ERR_ARG, "defl_nderiv must be >= 0");
     if (o->two_pass != 0 && o->two_pass != 1) return set_err(c, LQ_ERR_ARG, "two_pass must be 0 or 1");
@@ -1220,6 +1223,8 @@ void lq_destroy(lq_ctx* c) {
     dfree(c->U);
     dfree(c->Ub);
     dfree(c->Y);
+    dfree(c->Up);
+    dfree(c->Yp);
     dfree(c->dir_scratch);
     dfree(c->defl_V); dfree(c->defl_W); dfree(c->defl_work); dfree(c->defl_scr); dfree(c->defl_shift);
     for (cudaEvent_t e : c->ev_pool) cudaEventDestroy(e);
@@ -1243,6 +1248,15 @@ int lq_upload_gauge(lq_ctx* c, const double* U, void* stream) {
     if (r) return r;
     LQ_CUDA(c, launch_links_internal(c->prec, c->Ub, c->U, c->V, st));
     c->launches += 1;
+    if (c->prec != LQ_FP64) {   // the packed stencil's copy of the FP32 links
+        if (!c->Up && cudaMalloc(&c->Up, sizeof(float4) * c->V * 36) != cudaSuccess) {
+            cudaGetLastError();
+            c->Up = nullptr;
+            return set_err(c, LQ_ERR_OOM, "packed gauge allocation failed");
+        }
+        LQ_CUDA(c, launch_links_packed(c->U, c->Up, c->V, st));
+        c->launches += 1;
+    }
     c->gauge_ready = true;
     if (c->dir_kind == LQ_DIR_SU3 || c->dir_kind == LQ_DIR_U1) c->dir_kind = -1;   // Y is stale
     return LQ_OK;
@@ -1380,6 +1394,15 @@ int lq_set_direction(lq_ctx* c, const lq_direction* d, void* stream) {
     if ((r = stage_in(c, c->dir_scratch, d->field, n, st))) return r;
     LQ_CUDA(c, launch_direction(c->prec, c->Ub, c->dir_scratch, d->kind, c->Y, c->V, st));
     c->launches += 1;
+    if (c->prec != LQ_FP64) {
+        if (!c->Yp && cudaMalloc(&c->Yp, sizeof(float4) * c->V * 36) != cudaSuccess) {
+            cudaGetLastError();
+            c->Yp = nullptr;
+            return set_err(c, LQ_ERR_OOM, "packed direction allocation failed");
+        }
+        LQ_CUDA(c, launch_links_packed(c->Y, c->Yp, c->V, st));
+        c->launches += 1;
+    }
     c->dir_kind = d->kind;
     return LQ_OK;
 }

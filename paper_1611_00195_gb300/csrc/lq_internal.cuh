@@ -187,6 +187,8 @@ struct lq_ctx {
     bool gauge_ready = false;
     // derivative direction: dU/dt = Y (internal layout/precision); kind of the current one
     void* Y = nullptr;
+    void* Up = nullptr;              // FP32 contexts: links as float4 (ux, ux, -uy, uy), packed stencil
+    void* Yp = nullptr;              // the same for Y
     double* dir_scratch = nullptr;   // staging for the direction coefficients
     int dir_kind = -1;
 

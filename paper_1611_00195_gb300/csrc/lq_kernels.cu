@@ -603,38 +603,6 @@ __global__ void __launch_bounds__(kTileThreadsMax) k_hop_tiled(HopArgs a) {
     }
 }
 
-// Lanczos scalar step after alpha_j: record alpha_j and prepare the update coefficients
-//   vh_{j+1} = s_j B vh_j - alpha_j s_j vh_j - beta_{j-1} s_{j-1} vh_{j-1}
-//   wh_{j+1} = u_j B^dag wh_j - conj(alpha_j) u_j wh_j - delta_{j-1} u_{j-1} wh_{j-1}
-__device__ void tsl_alpha_step(const HopArgs& a, int src, double dre, double dim) {
-    TslState& st = a.state[src];
-    const int j = a.j;
-    const double2 uj = st.u_cur;
-    const double sj = st.s_cur;
-    // alpha = conj(u_j) s_j <wh_j, B vh_j>
-    double2 al;
-    al.x = sj * (uj.x * dre + uj.y * dim);
-    al.y = sj * (uj.x * dim - uj.y * dre);
-    a.alpha[(size_t)src * a.kmax + j] = al;
-    a.scale[(size_t)src * a.kmax + j] = sj;
-    if (a.uscale) a.uscale[(size_t)src * a.kmax + j] = uj;
-    st.k_eff = j + 1;
-    if (!isfinite(al.x) || !isfinite(al.y)) { st.status = LQ_ERR_NONFINITE; return; }
-    st.cv[0] = make_double2(sj, 0.0);
-    st.cv[1] = make_double2(-al.x * sj, -al.y * sj);
-    st.cw[0] = uj;
-    // -conj(alpha) u_j
-    st.cw[1] = make_double2(-(al.x * uj.x + al.y * uj.y), -(al.x * uj.y - al.y * uj.x));
-    if (j > 0) {
-        st.cv[2] = make_double2(-st.beta_prev.x * st.s_prev, -st.beta_prev.y * st.s_prev);
-        st.cw[2] = make_double2(-st.delta_prev * st.u_prev.x, -st.delta_prev * st.u_prev.y);
-    } else {
-        st.cv[2] = make_double2(0.0, 0.0);
-        st.cw[2] = make_double2(0.0, 0.0);
-    }
-    if (j == a.kmax_run - 1) st.status = 1;   // k reached
-}
-
 // ---------------------------------------------------------------------------------------
 // Update: new right/left vectors and the omega dot, |vh|^2, |wh|^2.
 // ---------------------------------------------------------------------------------------
@@ -1146,8 +1114,12 @@ static cudaError_t launch_tiled_t(const HopArgs& a, int emode, bool dot, cudaStr
 //   5: as 1 with at least 5 resident blocks per SM (FP32)
 //   6: shared-memory tiles of whole x rows x 2 x 2 x 2 (FP32; lattices with even y, z, t extents;
 //      schedule 3 otherwise)
+//   7: as 3 with packed FP32 pair arithmetic (lq_hop_x2.cu; identical results)
+//   8: as 7 with the next hop's neighbour spinors prefetched into shared memory
 cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st) {
     const bool lanczos_block = nf == 2 && a.nsides == 2 && a.side0 == 0;
+    if (lanczos_block && prec != LQ_FP64 && (a.variant == 7 || a.variant == 8))
+        return launch_hop_x2(a, emode, dot, a.variant == 8, st);
     if (lanczos_block && prec != LQ_FP64 && a.variant == 6) {
         if (tile_ok(a.dims)) return launch_tiled_t(a, emode, dot, st);
         return launch_hop_t<float, 4>(a, nf, emode, dot, st);

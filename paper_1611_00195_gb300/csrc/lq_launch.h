@@ -30,6 +30,8 @@ struct HopArgs {
     float diag_f;
     const void* U;         // links (internal)
     const void* Y;         // dU/dt (internal), EMODE 2
+    const void* Up;        // FP32 links pre-broadcast as float4 (ux, ux, -uy, uy) (schedules 7, 8)
+    const void* Yp;        // the same for dU/dt
     const void* in[2];     // per side: NF consecutive fields of source 0
     void* out[2];
     size_t src_stride_in[2], src_stride_out[2];   // Chunk units between sources
@@ -95,9 +97,12 @@ struct RecArgs {
     int accumulate;            // 1: y += window sum; 0: y = window sum
 };
 
-__device__ void tsl_alpha_step(const HopArgs& a, int src, double dre, double dim);
 
 cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st);
+// packed-FP32 block stencil (lq_hop_x2.cu): schedule 7, or 8 with the neighbour prefetch
+cudaError_t launch_hop_x2(const HopArgs& a, int emode, bool dot, bool prefetch, cudaStream_t st);
+cudaError_t launch_links_packed(const void* L, void* P, size_t V, cudaStream_t st);   // float2 -> (ux, ux, -uy, uy)
+constexpr int kHopSchedules = 9;     // FP32 block-stencil schedules 0..8 (FP64: 0, 1)
 bool tile_ok(const int (&dims)[4]);   // schedule 6 (shared-memory tiles) covers this lattice
 cudaError_t launch_update(int prec, const UpdArgs& a, cudaStream_t st);
 cudaError_t launch_tsl_init(int prec, int nf, const InitArgs& a, cudaStream_t st);

@@ -276,4 +276,36 @@ __device__ __forceinline__ void finish(const C (&psi)[12], decltype(C::x) diag, 
     }
 }
 
+// Lanczos scalar step after alpha_j: record alpha_j and prepare the update coefficients
+//   vh_{j+1} = s_j B vh_j - alpha_j s_j vh_j - beta_{j-1} s_{j-1} vh_{j-1}
+//   wh_{j+1} = u_j B^dag wh_j - conj(alpha_j) u_j wh_j - delta_{j-1} u_{j-1} wh_{j-1}
+__device__ inline void tsl_alpha_step(const HopArgs& a, int src, double dre, double dim) {
+    TslState& st = a.state[src];
+    const int j = a.j;
+    const double2 uj = st.u_cur;
+    const double sj = st.s_cur;
+    // alpha = conj(u_j) s_j <wh_j, B vh_j>
+    double2 al;
+    al.x = sj * (uj.x * dre + uj.y * dim);
+    al.y = sj * (uj.x * dim - uj.y * dre);
+    a.alpha[(size_t)src * a.kmax + j] = al;
+    a.scale[(size_t)src * a.kmax + j] = sj;
+    if (a.uscale) a.uscale[(size_t)src * a.kmax + j] = uj;
+    st.k_eff = j + 1;
+    if (!isfinite(al.x) || !isfinite(al.y)) { st.status = LQ_ERR_NONFINITE; return; }
+    st.cv[0] = make_double2(sj, 0.0);
+    st.cv[1] = make_double2(-al.x * sj, -al.y * sj);
+    st.cw[0] = uj;
+    // -conj(alpha) u_j
+    st.cw[1] = make_double2(-(al.x * uj.x + al.y * uj.y), -(al.x * uj.y - al.y * uj.x));
+    if (j > 0) {
+        st.cv[2] = make_double2(-st.beta_prev.x * st.s_prev, -st.beta_prev.y * st.s_prev);
+        st.cw[2] = make_double2(-st.delta_prev * st.u_prev.x, -st.delta_prev * st.u_prev.y);
+    } else {
+        st.cv[2] = make_double2(0.0, 0.0);
+        st.cw[2] = make_double2(0.0, 0.0);
+    }
+    if (j == a.kmax_run - 1) st.status = 1;   // k reached
+}
+
 }  // namespace lq

@@ -4,6 +4,19 @@ import numpy as np
 from oracle import dirac as od
 
 
+# Parity bounds in units of the oracle's own rounding sensitivity at the same Krylov depth.  The
+# non-symmetric Lanczos process amplifies rounding, so two correct implementations differ by about
+# the change of the oracle's result under a perturbation of rounding size: 1e-16 relative on the
+# input for FP64, 6e-8 relative on every operator application for FP32.  Each factor is about
+# 2.7 times the largest ratio (GPU error / that sensitivity) seen on the GB300 over every case of
+# the suite: 1.87 for FP64 (a ragged-batch member), 7.3 for the FP32 stencil schedules at k = 40
+# (one FP32 rounding per operation against a 6e-8 model of the whole step), 6.7 for the scalar S
+# of the adjoint, whose sensitivity is measured on the force.
+FP64_SENS_FACTOR = 5.0
+FP32_SENS_FACTOR = 20.0
+ADJ_SENS_FACTOR = 18.0
+
+
 def relerr(a, b):
     a = np.asarray(a).ravel()
     b = np.asarray(b).ravel()

@@ -44,7 +44,7 @@ def test_force_parity_same_depth(lqlib, dims, k):
     eF = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
     print("force parity %s k=%d: S %.3g F %.3g dmu %.3g (oracle self-sensitivity %.3g)"
           % (dims, k, abs(S - So) / abs(So), eF, abs(dmu - dmuo) / abs(dmuo), sens))
-    tol = max(1e-10, 30 * sens)
+    tol = max(1e-10, ADJ_SENS_FACTOR * sens)
     assert eF < tol
     assert abs(S - So) < tol * abs(So) and abs(dmu - dmuo) < tol * max(abs(dmuo), 1e-3)
 
@@ -201,7 +201,7 @@ def _upload_eigenpairs(c, lat, U, l):
 def test_deflated_force_parity_same_depth(lqlib, dims, k, l):
     """The deflated adjoint (opts.deflate = 1) against the oracle's deflated Krylov route at the
     same depth, with the oracle's eigenpairs installed: S, the force on every link and dS/dmu,
-    within 30 times the oracle's own rounding sensitivity."""
+    within ADJ_SENS_FACTOR times the oracle's own rounding sensitivity."""
     from paper_1611_00195_gb300 import lq
     lat = od.Lattice(dims)
     U = syn.gauge_field(dims, 0.4, 3)
@@ -226,7 +226,7 @@ def test_deflated_force_parity_same_depth(lqlib, dims, k, l):
     eF = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
     print("deflated force parity %s k=%d l=%d: S %.3g F %.3g dmu %.3g (oracle self-sensitivity %.3g)"
           % (dims, k, l, abs(S - So) / abs(So), eF, abs(dmu - dmuo) / abs(dmuo), sens))
-    tol = max(1e-10, 30 * sens)
+    tol = max(1e-10, ADJ_SENS_FACTOR * sens)
     assert eF < tol
     assert abs(S - So) < tol * abs(So) and abs(dmu - dmuo) < tol * max(abs(dmuo), 1e-3)
 

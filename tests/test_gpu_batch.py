@@ -8,7 +8,7 @@ import torch
 
 import synthetic as syn
 from oracle import tsl as ot
-from tests.helpers import oracle_ops, relerr
+from tests.helpers import FP64_SENS_FACTOR, oracle_ops, relerr
 
 pytestmark = pytest.mark.gpu
 
@@ -91,7 +91,7 @@ def test_batch_fp64_parity_with_oracle(lqlib):
             got = [ys[s].cpu().numpy()] if kind is None else [yd[s].cpu().numpy(), ys[s].cpu().numpy()]
             errs = [relerr(g, r) for g, r in zip(got, ref)]
             print("batch member %s k=%d src %d: rel err %s, sensitivity %.3g" % (d, k, s, errs, sens))
-            assert max(errs) < max(1e-11, 30 * sens)
+            assert max(errs) < max(1e-11, FP64_SENS_FACTOR * sens)
 
 
 @pytest.mark.parametrize("prec", [0, 1])
@@ -118,7 +118,7 @@ def test_ragged_workload(lqlib, prec):
         sens = max(relerr(pd, rd), relerr(ps, rs))
         es, ed = relerr(out[0][0][0].cpu().numpy(), rs), relerr(out[0][1][0].cpu().numpy(), rd)
         print("ragged 6^4 k=%d vs oracle: sign %.3g deriv %.3g (sensitivity %.3g)" % (k, es, ed, sens))
-        assert max(es, ed) < max(1e-11, 30 * sens)
+        assert max(es, ed) < max(1e-11, FP64_SENS_FACTOR * sens)
 
 
 def test_batch_argument_errors(lqlib):

@@ -11,7 +11,7 @@ from oracle import deflation as odf
 from oracle import dirac as od
 from oracle import sign as osg
 from oracle import tsl as ot
-from tests.helpers import oracle_ops, relerr
+from tests.helpers import FP64_SENS_FACTOR, oracle_ops, relerr
 
 pytestmark = pytest.mark.gpu
 
@@ -33,8 +33,12 @@ def _setup(lq, dims, l, k, nsrc=2, prec=0, seed=3):
     return c, U, lat, A, lam, R, L, x
 
 
-@pytest.mark.parametrize("dims,l,k", [((4, 4, 2, 2), 8, 120), ((4, 2, 2, 2), 6, 60)])
-def test_sign_deflated_parity(lqlib, dims, l, k):
+# Required deflation gain (error against the exact sign, deflated / undeflated) per case.  The
+# paper (Sec. 4) finds little gain where the spectrum keeps a large gap around zero; on 4x2^3 with
+# 6 of 384 eigenvalues deflated at k = 60 the measured ratio is 0.65-0.85, on 4x4x2x2 with 8 of 768
+# at k = 120 it is 0.31-0.40.
+@pytest.mark.parametrize("dims,l,k,gain", [((4, 4, 2, 2), 8, 120, 0.5), ((4, 2, 2, 2), 6, 60, 0.9)])
+def test_sign_deflated_parity(lqlib, dims, l, k, gain):
     from paper_1611_00195_gb300 import lq
     c, U, lat, A, lam, R, L, x = _setup(lq, dims, l, k)
     y, rep = c.sign_apply(torch.from_numpy(x).cuda(), k, deflate=1)
@@ -52,8 +56,8 @@ def test_sign_deflated_parity(lqlib, dims, l, k):
         ex, ex0 = relerr(y[s], S @ xs), relerr(y0[s], S @ xs)
         print("deflated sign k=%d l=%d: parity %.3g (oracle self-sensitivity %.3g); error vs exact %.3g (undeflated %.3g)"
               % (k, l, err, sens, ex, ex0))
-        assert err < max(1e-11, 30 * sens)
-        assert ex < ex0
+        assert err < max(1e-11, FP64_SENS_FACTOR * sens)
+        assert ex < gain * ex0
 
 
 # The shifted solves project out all l uploaded pairs; derivatives are built for the first
@@ -88,10 +92,12 @@ def test_derivative_generalised_deflation(lqlib):
     k = 60, where the process is still far from the dimension of the problem (768).  The
     tolerance scales with the oracle's own rounding sensitivity: the largest change of the
     reference over three 1e-16 relative perturbations of the source and of the eigenvectors
-    (which move the eigenvector derivatives as well).  At k = 300, with the derivatives at full
-    depth, deflation must beat no deflation against the exact derivative."""
+    (which move the eigenvector derivatives as well).  The shifted solves run at depth KD = 60,
+    a sixth of the deflated complement (360): at depth 120 the rounding sensitivity of the
+    resolvent process is already 1e-3, at 60 it is 1e-11.  At k = 300, with the derivatives at
+    full depth, deflation must beat no deflation against the exact derivative."""
     from paper_1611_00195_gb300 import lq
-    dims, k, kp, KD = (4, 2, 2, 2), 300, 60, 120
+    dims, k, kp, KD = (4, 2, 2, 2), 300, 60, 60
     c, U, lat, A, lam, R, L, x = _setup(lq, dims, LP, k)
     xs_d = torch.from_numpy(x).cuda()
     ysp, ydp, _ = c.sign_derivative_apply(xs_d, kp, deflate=1, defl_nderiv=LD, defl_kmax=KD)
@@ -124,12 +130,8 @@ def test_derivative_generalised_deflation(lqlib):
         print("deflated derivative (%d Jordan blocks, solves at depth %d): parity at k=%d deriv %.3g sign %.3g "
               "(oracle self-sensitivity %.3g, ratio %.2f); at k=%d deriv error vs exact %.3g (undeflated %.3g)"
               % (LD, KD, kp, pd, ps, sens, max(pd, ps) / sens, k, ed, ed0))
-        assert pd < max(1e-10, GEN_DEFL_FACTOR * sens) and ps < max(1e-10, GEN_DEFL_FACTOR * sens)
+        assert pd < max(1e-11, FP64_SENS_FACTOR * sens) and ps < max(1e-11, FP64_SENS_FACTOR * sens)
         assert ed < 0.1 * ed0
-
-
-# Parity bound of the generalised deflation, in units of the oracle's rounding sensitivity.
-GEN_DEFL_FACTOR = 30
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-10)])

@@ -9,7 +9,7 @@ import synthetic as syn
 from oracle import dirac as od
 from oracle import overlap as oo
 from oracle import tsl as ot
-from tests.helpers import oracle_ops, relerr
+from tests.helpers import FP64_SENS_FACTOR, oracle_ops, relerr
 
 pytestmark = pytest.mark.gpu
 MU = 0.3
@@ -49,7 +49,7 @@ def test_overlap_same_depth_parity(lqlib, kind):
         for _ in range(3):
             py, pdy = run(xv * (1 + 1e-16 * rng.standard_normal(xv.shape)))
             sens = max(sens, relerr(py, ry), relerr(pdy, rdy))
-        tol = max(1e-11, 30 * sens)
+        tol = max(1e-11, FP64_SENS_FACTOR * sens)
         ey, edy = relerr(y[s], ry), relerr(dy[s], rdy)
         # the sign-only call runs the plain process (A, not B): against the oracle's plain TSL
         r0 = xv + g5 @ ot.tsl_sign(A, Ah, xv, k)[0]
@@ -61,7 +61,7 @@ def test_overlap_same_depth_parity(lqlib, kind):
         print("overlap k=%d dir %d: D x %.3g, dD x %.3g (sensitivity %.3g); sign-only D x %.3g (sensitivity %.3g)"
               % (k, kind, ey, edy, sens, e0, sens0))
         assert ey < tol and edy < tol
-        assert e0 < max(1e-11, 30 * sens0)
+        assert e0 < max(1e-11, FP64_SENS_FACTOR * sens0)
 
 
 @pytest.mark.parametrize("prec,tol", [(0, 1e-6), (1, 1e-5)])

@@ -7,7 +7,8 @@ import pytest
 import torch
 
 import synthetic as syn
-from tests.helpers import relerr
+from oracle import tsl as ot
+from tests.helpers import FP64_SENS_FACTOR, oracle_ops, relerr
 
 pytestmark = pytest.mark.gpu
 
@@ -67,3 +68,36 @@ def test_two_pass_on_full_basis_and_short_runs(lqlib):
     with pytest.raises(lq.LQError):
         lq.Context(DIMS, mu=MU).reserve(60, 2, False, adjoint=True, two_pass=True)
 
+
+@pytest.mark.parametrize("deriv", [False, True])
+def test_two_pass_fp64_matches_the_oracle(lqlib, deriv):
+    """The two-pass run (FP64, k = 100: the ring of 32 wraps three times) against the oracle's
+    one-pass process at the same depth, within FP64_SENS_FACTOR of the oracle's own rounding
+    sensitivity, like the one-pass parity tests."""
+    from paper_1611_00195_gb300 import lq
+    k, nsrc = 100, 2
+    U = syn.gauge_field(DIMS, 0.4, 3)
+    x = syn.gaussian_source(DIMS, 5, nsrc=nsrc)
+    c = _ctx(lq, 0, k, nsrc, True)
+    if deriv:
+        ys, yd, rep = c.sign_derivative_apply(torch.from_numpy(x).cuda(), k, two_pass=1)
+        got = [yd.cpu().numpy(), ys.cpu().numpy()]
+    else:
+        ys, rep = c.sign_apply(torch.from_numpy(x).cuda(), k, two_pass=1)
+        got = [ys.cpu().numpy()]
+    lat, A, Ah, E, Eh = oracle_ops(DIMS, U, MU)
+    rng = np.random.default_rng(99)
+
+    def run(v):
+        if deriv:
+            return list(ot.tsl_sign_derivative(A, Ah, E, Eh, v, k)[:2])
+        return [ot.tsl_sign(A, Ah, v, k)[0]]
+    for s in range(nsrc):
+        assert rep[s]["status"] == 0 and rep[s]["k_eff"] == k
+        ref = run(x[s].ravel())
+        xp = x[s].ravel() * (1 + 1e-16 * rng.standard_normal(x[s].size))
+        sens = max(relerr(p, q) for p, q in zip(run(xp), ref))
+        errs = [relerr(g[s], r) for g, r in zip(got, ref)]
+        print("two-pass FP64 vs oracle k=%d deriv %d source %d: %s (sensitivity %.3g, ratio %.2f)"
+              % (k, deriv, s, ["%.3g" % e for e in errs], sens, max(errs) / sens))
+        assert max(errs) < max(1e-11, FP64_SENS_FACTOR * sens)
