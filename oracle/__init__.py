@@ -15,6 +15,7 @@ Modules:
                  the Frechet derivative (Mathias block, Eq. (2.5); Sylvester route).
   tsl         -- the two-sided Lanczos approximation (Sec. 2) of sgn(A)x and, through
                  Eq. (2.6), of d_t sgn(A)x; the error estimate eps_A (Sec. 4).
+  nested      -- the nested (one level) two-sided Lanczos evaluation of sgn(T_k) e_1 (Sec. 4).
   free_field  -- closed forms for U = 1 in momentum space (pins dirac and sign).
   deflation   -- standard (Eq. (3.1)) and generalised (Eqs. (3.2)-(3.4)) deflation.
   adjoint     -- the bilinear S = Re<y|sgn H|x> and its gradient (fermionic force).
