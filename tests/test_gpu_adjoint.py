@@ -10,6 +10,7 @@ import torch
 import synthetic as syn
 from oracle import adjoint as oad
 from oracle import dirac as od
+from tests.helpers import ADJ_SENS_FACTOR
 
 pytestmark = pytest.mark.gpu
 

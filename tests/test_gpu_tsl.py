@@ -302,5 +302,5 @@ def test_packed_schedules_are_bitwise_schedule_3(lqlib, dims, kind):
     for v in (7, 8):
         assert np.array_equal(out[v][0], out[3][0]) and np.array_equal(out[v][1], out[3][1])
         for s in range(nsrc):
-            for a, b in zip(out[v][3][s], out[3][s]):
+            for a, b in zip(out[v][3][s], out[3][3][s]):
                 assert np.array_equal(a, b)
