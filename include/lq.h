@@ -219,31 +219,63 @@ int  lq_sign_derivative_apply(lq_ctx* ctx, const lq_direction* dir, const double
 int  lq_upload_deflation(lq_ctx* ctx, int l, const double* lambda, const double* R, const double* L,
                          void* stream);
 
+/* Eigensolver of lq_compute_deflation. */
+#define LQ_EIG_SHIFT_INVERT 0   /* implicitly restarted Arnoldi on H^{-1} (default)               */
+#define LQ_EIG_CHEBYSHEV    1   /* Chebyshev-filtered subspace iteration on H^2                    */
+
 /* Options of lq_compute_deflation. */
 typedef struct {
     int nev;          /* eigenpairs wanted: the nev eigenvalues of H(mu) closest to zero          */
-    int nsub;         /* subspace size (>= nev + 2; default min(nev + 12, 64))                   */
-    int degree;       /* Chebyshev filter degree in H^2 (default 40)                              */
-    int max_iter;     /* filtered subspace iterations (default 60)                                */
-    double tol;       /* stop when ||H r - lambda r|| <= tol * |H|_est for the nev pairs
-                         (default 1e-10; the stencil of the eigensolver is FP64 in both precisions) */
+    int nsub;         /* shift-and-invert: Arnoldi basis size m (nev + 4 <= m <= 63; default
+                         min(2 nev + 10, 63)).  Chebyshev: subspace size (nev + 2 <= nsub <= 64;
+                         default min(nev + 12, 64))                                              */
+    int degree;       /* Chebyshev filter degree in H^2 (default 40; unused by shift-and-invert)  */
+    int max_iter;     /* restarts (shift-and-invert, default 300) or filtered subspace iterations
+                         (Chebyshev, default 60)                                                   */
+    double tol;       /* stop when ||H r - lambda r|| <= tol * ||H||_est for the nev pairs
+                         (default 1e-10; the eigensolver's FP64 stencil runs in both precisions)  */
+    int method;       /* LQ_EIG_SHIFT_INVERT (default, 0) or LQ_EIG_CHEBYSHEV                      */
+    int inner_max;    /* shift-and-invert: iteration cap of each FP32 inner solve (0: 20000)      */
 } lq_eig_opts;
+
+/* Statistics of the last lq_compute_deflation of a context (lq_eig_stats_read). */
+typedef struct {
+    int method;              /* the eigensolver that ran                                          */
+    int restarts;            /* Arnoldi restarts (shift-and-invert)                                */
+    long long solves;        /* operator inverse applications, both processes together            */
+    long long inner_iterations; /* FP32 CGNR iterations over all solves                           */
+    long long refinements;   /* FP64 defect-correction steps over all solves                       */
+    double norm_estimate;    /* ||H||_est, the scale of the reported residuals                     */
+    double max_residual;     /* largest returned residual                                           */
+    double pair_mismatch;    /* largest |lambda_i - conj(lambda'_j)| / |lambda_i| of the pairing of
+                                right and left eigenvalues                                          */
+    double seconds;          /* device time of the call                                             */
+} lq_eig_stats;
 
 /* Compute and install the deflation space of Sec. 3 with the library's own eigensolver (the
  * paper uses ARPACK's Arnoldi): the nev right eigenpairs of H(mu) closest to zero and the
  * matching left eigenvectors (from H(mu)^dag = H(-mu)), biorthonormalised so that
- * <Lk_i|R_j> = delta_ij.  Method: Chebyshev-filtered subspace iteration on H^2 (the wanted
- * eigenvalues are the smallest of H^2; the filter damps [a^2, b^2] with b^2 from a power
- * iteration and a^2 the largest Ritz value of the current subspace), each step closed by a
- * Rayleigh-Ritz projection (lq_dense_eig).  X0: nsub start fields (host or device, spinor layout
- * double[nsub][V][4][3][2]; random numbers are the caller's).  lambda, resid: host outputs
- * double[nev][2] and double[nev] (may be NULL); resid is the larger of the right and left
- * relative residuals.  The operator applications run in FP64 whatever the context's precision
- * (a mixed-precision context converts its FP64 copy of the links for the call): the generalised
- * deflation of the derivative needs eigenpairs accurate to FP64 rounding.  Allocates its own
- * temporary workspace (a set-up call).  Synchronises. */
+ * <Lk_i|R_j> = delta_ij.  Methods (eo->method):
+ *   LQ_EIG_SHIFT_INVERT: ARPACK's method, the implicitly restarted Arnoldi process with exact
+ *     shifts, on OP = H^{-1} (the wanted eigenvalues are the largest of OP, which polynomial
+ *     methods cannot isolate when the spectrum surrounds zero) and on (H^dag)^{-1} for the left
+ *     vectors, both in lockstep.  Each OP application is an FP64 solve: defect correction whose
+ *     corrections are FP32 CGNR solves (conjugate gradients on H^dag H).  X0: two start fields
+ *     (right, left).
+ *   LQ_EIG_CHEBYSHEV: Chebyshev-filtered subspace iteration on H^2 with Rayleigh-Ritz
+ *     (lq_dense_eig); converges only when the wanted eigenvalues are not surrounded by the rest
+ *     of the spectrum.  X0: nsub start fields.
+ * X0: host or device, spinor layout double[.][V][4][3][2] (random numbers are the caller's).
+ * lambda, resid: host outputs double[nev][2] and double[nev] (may be NULL); resid is the larger of
+ * the right and left residuals ||H r - lambda r|| / ||H||_est.  The FP64 operator applications run
+ * in FP64 whatever the context's precision (a mixed-precision context converts its FP64 copy of
+ * the links for the call): the generalised deflation of the derivative needs eigenpairs accurate
+ * to FP64 rounding.  Allocates its own temporary workspace (a set-up call).  Synchronises. */
 int  lq_compute_deflation(lq_ctx* ctx, const lq_eig_opts* eo, const double* X0, double* lambda,
                           double* resid, void* stream);
+
+/* Statistics of the context's last lq_compute_deflation (no device work). */
+int  lq_eig_stats_read(const lq_ctx* ctx, lq_eig_stats* out);
 
 /* The massless overlap operator at finite density, Eq. (1.1) with lattice spacing 1:
  *   y = D_ov x = x + gamma5 sgn(H(mu)) x,   dy = d D_ov x = gamma5 d_t sgn(H(mu)) x,

@@ -1172,6 +1172,346 @@ int eig_subspace(lq_ctx* c, const lq_eig_opts* eo, const double* X0, int dagger,
     return LQ_OK;
 }
 
+// ---- shift-and-invert eigensolver ---------------------------------------------------------------
+// The l eigenpairs of H(mu) nearest zero (Sec. 3; the paper computes them with ARPACK's Arnoldi
+// method) as the largest-modulus eigenvalues 1/lambda of OP = H^{-1}: ARPACK's implicitly restarted
+// Arnoldi method with exact shifts (Sorensen, SIAM J. Matrix Anal. Appl. 13 (1992) 357; Lehoucq &
+// Sorensen, ibid. 17 (1996) 789) on OP, and on (H^dag)^{-1} = H(-mu)^{-1} for the left eigenvectors.
+// The two processes run in lockstep so that their inner solves share every launch: system 0 holds
+// the right process (A_0 = H), system 1 the left one (A_1 = H^dag).  Each OP application is an
+// FP64 solve by defect correction around FP32 CGNR (lq_eig.cu).
+
+struct SiWork {
+    lq_ctx* c = nullptr;
+    cudaStream_t st = nullptr;
+    size_t V = 0, ne = 0, nv = 0;
+    const void* links32 = nullptr;
+    const void* links64 = nullptr;
+    float4 *x = nullptr, *r = nullptr, *p = nullptr, *q = nullptr, *z = nullptr;   // [2][ne] each
+    double* scal = nullptr;                      // [2][kCgNs]
+    double* part = nullptr;
+    int* counters = nullptr;
+    double* res64 = nullptr;                     // [2][nv]
+    double* tmp64 = nullptr;                     // [2][nv]
+    double* nrm = nullptr;                       // [2]
+    long long iters = 0, solves = 0, refinements = 0;
+    int inner_max = 20000;
+};
+
+// out_s = A_s in_s, or A_s^dag in_s with adjoint (FP32 internal layout, both systems in one launch:
+// side 0 of the stencil applies H, side 1 applies H^dag).
+int si_apply32(SiWork& w, const float4* in, float4* out, bool adjoint) {
+    lq_ctx* c = w.c;
+    HopArgs a = base_hop(c);
+    a.U = w.links32;
+    a.Up = nullptr; a.Y = nullptr; a.Yp = nullptr;
+    a.nsrc = 1; a.nsides = 2; a.side0 = 0;
+    set_side(a, 0, c, 0, 0);
+    set_side(a, 1, c, 1, 0);
+    a.in[0] = adjoint ? in + w.ne : in;           // fed to H: system 0 (A_0 = H), or system 1 (A_1^dag = H)
+    a.out[0] = adjoint ? out + w.ne : out;
+    a.in[1] = adjoint ? in : in + w.ne;           // fed to H^dag
+    a.out[1] = adjoint ? out : out + w.ne;
+    a.src_stride_in[0] = a.src_stride_in[1] = w.ne;
+    a.src_stride_out[0] = a.src_stride_out[1] = w.ne;
+    LQ_CUDA(c, launch_hop(LQ_MIXED, a, 1, 0, false, w.st));
+    c->launches += 1;
+    return LQ_OK;
+}
+
+// The same in FP64 on boundary-layout fields [2][nv].
+int si_apply64(SiWork& w, const double* in, double* out) {
+    for (int s = 0; s < 2; ++s) {
+        int r = apply_H_batch(w.c, in + (size_t)s * w.nv, out + (size_t)s * w.nv, 1, s, w.st, LQ_FP64, w.links64);
+        if (r) return r;
+    }
+    return LQ_OK;
+}
+
+// CGNR on A_s e_s = rhs_s (FP32, rhs in w.z, solution in w.x) until |r_s| <= tol |rhs_s|.
+int si_cgnr(SiWork& w, double tol) {
+    lq_ctx* c = w.c;
+    cudaStream_t st = w.st;
+    const size_t bytes = sizeof(float4) * 2 * w.ne;
+    LQ_CUDA(c, cudaMemsetAsync(w.x, 0, bytes, st));
+    LQ_CUDA(c, cudaMemcpyAsync(w.r, w.z, bytes, cudaMemcpyDeviceToDevice, st));
+    LQ_CUDA(c, cudaMemsetAsync(w.scal, 0, sizeof(double) * 2 * kCgNs, st));
+    CgArgs a;
+    a.ne = w.ne; a.nb = 2; a.it = 0;
+    a.x = w.x; a.r = w.r; a.p = w.p; a.q = w.q; a.z = w.z;
+    a.scal = w.scal; a.part = w.part; a.counters = w.counters;
+    LQ_CUDA(c, launch_cg_norm(a, w.r, CG_BB, st));
+    int r;
+    if ((r = si_apply32(w, w.r, w.z, true))) return r;                // z = A^dag r
+    LQ_CUDA(c, launch_cg_norm(a, w.z, CG_G0, st));
+    LQ_CUDA(c, cudaMemcpyAsync(w.p, w.z, bytes, cudaMemcpyDeviceToDevice, st));
+    c->launches += 2;
+    double h[2 * kCgNs];
+    int it = 0;
+    for (; it < w.inner_max; ++it) {
+        a.it = it;
+        if ((r = si_apply32(w, w.p, w.q, false))) return r;          // q = A p
+        LQ_CUDA(c, launch_cg_norm(a, w.q, CG_QQ, st));
+        LQ_CUDA(c, launch_cg_xr(a, st));                            // x += alpha p, r -= alpha q
+        if ((r = si_apply32(w, w.r, w.z, true))) return r;          // z = A^dag r
+        LQ_CUDA(c, launch_cg_norm(a, w.z, CG_G0 + ((it + 1) & 1), st));
+        LQ_CUDA(c, launch_cg_p(a, st));                             // p = z + beta p
+        c->launches += 4;
+        if ((it + 1) % 16 == 0 || it + 1 == w.inner_max) {
+            LQ_CUDA(c, cudaMemcpyAsync(h, w.scal, sizeof(h), cudaMemcpyDeviceToHost, st));
+            LQ_CUDA(c, cudaStreamSynchronize(st));
+            bool all = true;
+            for (int s = 0; s < 2; ++s) {
+                double* hs = h + s * kCgNs;
+                if (hs[CG_DONE] != 0.0) continue;
+                if (!std::isfinite(hs[CG_RR])) return set_err(c, LQ_ERR_NONFINITE, "non-finite residual in an inner solve");
+                if (hs[CG_RR] <= tol * tol * hs[CG_BB]) {
+                    const double one = 1.0;
+                    LQ_CUDA(c, cudaMemcpyAsync(w.scal + s * kCgNs + CG_DONE, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+                    LQ_CUDA(c, cudaStreamSynchronize(st));
+                } else {
+                    all = false;
+                }
+            }
+            if (all) { ++it; break; }
+        }
+    }
+    w.iters += it;
+    return LQ_OK;
+}
+
+// x_s = A_s^{-1} b_s to relative residual tol (FP64, boundary layout [2][nv]): defect correction,
+// each correction an FP32 CGNR solve of the current residual to 1e-5.
+int si_solve(SiWork& w, const double* b, double* xout, double tol) {
+    lq_ctx* c = w.c;
+    cudaStream_t st = w.st;
+    const size_t n2 = 2 * w.nv;
+    LQ_CUDA(c, cudaMemsetAsync(xout, 0, sizeof(double) * n2, st));
+    LQ_CUDA(c, cudaMemcpyAsync(w.res64, b, sizeof(double) * n2, cudaMemcpyDeviceToDevice, st));
+    double bn[2], rn[2];
+    LQ_CUDA(c, launch_norm2(b, nullptr, 0.0, w.V * 12, 2, w.nrm, st));
+    LQ_CUDA(c, cudaMemcpyAsync(bn, w.nrm, sizeof(bn), cudaMemcpyDeviceToHost, st));
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    int r;
+    for (int outer = 0;; ++outer) {
+        if (outer > 0) {
+            if ((r = si_apply64(w, xout, w.tmp64))) return r;           // res = b - A x
+            LQ_CUDA(c, launch_axpby3(w.res64, 1.0, b, -1.0, w.tmp64, 0.0, nullptr, n2, st));
+        }
+        LQ_CUDA(c, launch_norm2(w.res64, nullptr, 0.0, w.V * 12, 2, w.nrm, st));
+        LQ_CUDA(c, cudaMemcpyAsync(rn, w.nrm, sizeof(rn), cudaMemcpyDeviceToHost, st));
+        LQ_CUDA(c, cudaStreamSynchronize(st));
+        c->launches += 2;
+        bool done = true;
+        for (int s = 0; s < 2; ++s) {
+            if (!std::isfinite(rn[s])) return set_err(c, LQ_ERR_NONFINITE, "non-finite residual in a shifted solve");
+            if (rn[s] > tol * tol * bn[s]) done = false;
+        }
+        if (done) break;
+        if (outer >= 12) return set_err(c, LQ_ERR_NOT_CONVERGED, "inner solve of the eigensolver did not converge");
+        // converged systems get a zero right-hand side (their CG then stops at once)
+        for (int s = 0; s < 2; ++s)
+            if (rn[s] <= tol * tol * bn[s]) LQ_CUDA(c, cudaMemsetAsync(w.res64 + (size_t)s * w.nv, 0, sizeof(double) * w.nv, st));
+        LQ_CUDA(c, launch_to_internal(LQ_MIXED, w.res64, w.z, w.V, 2, st));
+        if ((r = si_cgnr(w, 1e-5))) return r;
+        LQ_CUDA(c, launch_to_boundary(LQ_MIXED, w.x, w.tmp64, w.V, 2, st));
+        LQ_CUDA(c, launch_axpby3(xout, 1.0, xout, 1.0, w.tmp64, 0.0, nullptr, n2, st));
+        c->launches += 3;
+        ++w.refinements;
+    }
+    ++w.solves;
+    return LQ_OK;
+}
+
+// One implicitly shifted QR step of the m x m upper Hessenberg H (row-major) with shift mu, by
+// Givens rotations; Q <- Q G_0^H G_1^H ... (Golub & Van Loan, "Matrix Computations", Sec. 7.5).
+void hess_qr_step(int m, std::vector<cplx>& H, std::vector<cplx>& Q, cplx mu) {
+    for (int i = 0; i < m; ++i) H[i * m + i] -= mu;
+    std::vector<double> cc(m, 1.0);
+    std::vector<cplx> sn(m, 0.0);
+    for (int i = 0; i + 1 < m; ++i) {               // R = G_{m-2} ... G_0 (H - mu)
+        const cplx a = H[i * m + i], b = H[(i + 1) * m + i];
+        const double aa = std::abs(a), ab = std::abs(b), rr = std::hypot(aa, ab);
+        double c_ = 1.0;
+        cplx s_ = 0.0;
+        if (rr > 0.0) {
+            if (aa == 0.0) { c_ = 0.0; s_ = std::conj(b) / ab; }
+            else { c_ = aa / rr; s_ = (a / aa) * std::conj(b) / rr; }
+        }
+        cc[i] = c_; sn[i] = s_;
+        for (int j = 0; j < m; ++j) {
+            const cplx x = H[i * m + j], y = H[(i + 1) * m + j];
+            H[i * m + j] = c_ * x + s_ * y;
+            H[(i + 1) * m + j] = -std::conj(s_) * x + c_ * y;
+        }
+    }
+    for (int i = 0; i + 1 < m; ++i) {               // R Q: columns times G_i^H
+        const double c_ = cc[i];
+        const cplx s_ = sn[i];
+        for (int r = 0; r < m; ++r) {
+            const cplx u = H[r * m + i], v = H[r * m + i + 1];
+            H[r * m + i] = c_ * u + std::conj(s_) * v;
+            H[r * m + i + 1] = -s_ * u + c_ * v;
+            const cplx qu = Q[r * m + i], qv = Q[r * m + i + 1];
+            Q[r * m + i] = c_ * qu + std::conj(s_) * qv;
+            Q[r * m + i + 1] = -s_ * qu + c_ * qv;
+        }
+    }
+    for (int i = 0; i < m; ++i) H[i * m + i] += mu;
+}
+
+// Ritz values of the m x m leading block of Hm ((m + 1) x m, row-major), sorted by decreasing
+// modulus, with unit eigenvectors Y (columns, in the same order) and their residual estimates
+// |h_{m+1,m}| |e_m^T y| / |theta|.
+int ritz(int m, const std::vector<cplx>& Hm, std::vector<cplx>& th, std::vector<cplx>& Y, std::vector<double>& est) {
+    std::vector<cplx> A(m * m), w(m), Vr(m * m);
+    for (int i = 0; i < m; ++i) for (int j = 0; j < m; ++j) A[i * m + j] = Hm[i * m + j];
+    if (dense_eig(m, A.data(), w.data(), Vr.data()) != LQ_OK) return LQ_ERR_NEWTON;
+    std::vector<int> ord(m);
+    std::iota(ord.begin(), ord.end(), 0);
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return std::abs(w[a]) > std::abs(w[b]); });
+    th.assign(m, 0.0); Y.assign(m * m, 0.0); est.assign(m, 0.0);
+    const double f = std::abs(Hm[m * m + (m - 1)]);
+    for (int b = 0; b < m; ++b) {
+        double nn = 0.0;
+        for (int a = 0; a < m; ++a) nn += std::norm(Vr[a * m + ord[b]]);
+        nn = std::sqrt(nn);
+        for (int a = 0; a < m; ++a) Y[a * m + b] = Vr[a * m + ord[b]] / nn;
+        th[b] = w[ord[b]];
+        est[b] = f * std::abs(Y[(m - 1) * m + b]) / std::max(std::abs(th[b]), 1e-300);
+    }
+    return LQ_OK;
+}
+
+struct SiResult {
+    std::vector<cplx> lam[2];       // eigenvalues of A_0 = H and of A_1 = H^dag
+    std::vector<double> res[2];     // true residuals ||A z - lambda z|| / ||H|| (unit z)
+    int restarts = 0;
+};
+
+// The implicitly restarted Arnoldi process on OP_s = A_s^{-1} for both systems.  Vb: [2][m + 1][nv]
+// basis, Zs: [2][kk + 1][nv] scratch, Z: [2][nev][nv] output Ritz vectors; X0: two start fields.
+int eig_shift_invert(SiWork& w, const lq_eig_opts& eo, const double* X0, double* Vb, double* Zs, double* Z,
+                     double hn, SiResult& out) {
+    lq_ctx* c = w.c;
+    cudaStream_t st = w.st;
+    const int m = eo.nsub, nev = eo.nev;
+    const int kk = std::min(m - 2, nev + std::max(2, (m - nev) / 2));   // kept at a restart
+    const size_t nv = w.nv;
+    const double tol_in = std::max(1e-13, 0.1 * eo.tol);
+    auto Vs = [&](int s, int j) { return Vb + ((size_t)s * (m + 1) + j) * nv; };
+    std::vector<cplx> Hm[2];
+    for (int s = 0; s < 2; ++s) Hm[s].assign((size_t)(m + 1) * m, 0.0);
+    double* rhs = Zs + (size_t)2 * (kk + 1) * nv;     // [2][nv]
+    double* sol = rhs + 2 * nv;                        // [2][nv]
+    int r;
+    // start vectors, normalised
+    for (int s = 0; s < 2; ++s) {
+        std::vector<double2> nn;
+        if ((r = bdots_host(c, X0 + (size_t)s * nv, 1, X0 + (size_t)s * nv, 1, nn, st))) return r;
+        if (!(nn[0].x > 0.0)) return set_err(c, LQ_ERR_ARG, "zero start vector for the eigensolver");
+        std::vector<double2> sc(1, make_double2(1.0 / std::sqrt(nn[0].x), 0.0));
+        if ((r = bcombine_host(c, Vs(s, 0), nullptr, 1, X0 + (size_t)s * nv, 1, sc, st))) return r;
+    }
+    int j0 = 0;
+    std::vector<cplx> th[2], Y[2];
+    std::vector<double> est[2];
+    for (int restart = 0;; ++restart) {
+        // Arnoldi steps j0 .. m-1
+        for (int j = j0; j < m; ++j) {
+            for (int s = 0; s < 2; ++s)
+                LQ_CUDA(c, cudaMemcpyAsync(rhs + (size_t)s * nv, Vs(s, j), sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+            if ((r = si_solve(w, rhs, sol, tol_in))) return r;
+            for (int s = 0; s < 2; ++s) {
+                double* wv = sol + (size_t)s * nv;
+                for (int pass = 0; pass < 2; ++pass) {             // classical Gram-Schmidt, twice
+                    std::vector<double2> h;
+                    if ((r = bdots_host(c, Vs(s, 0), j + 1, wv, 1, h, st))) return r;
+                    std::vector<double2> co(j + 1);
+                    for (int i = 0; i <= j; ++i) {
+                        Hm[s][(size_t)i * m + j] += cplx(h[i].x, h[i].y);
+                        co[i] = make_double2(-h[i].x, -h[i].y);
+                    }
+                    if ((r = bcombine_host(c, wv, wv, 1, Vs(s, 0), j + 1, co, st))) return r;
+                }
+                std::vector<double2> nn;
+                if ((r = bdots_host(c, wv, 1, wv, 1, nn, st))) return r;
+                const double beta = std::sqrt(std::max(nn[0].x, 0.0));
+                if (!(beta > 0.0) || !std::isfinite(beta)) return set_err(c, LQ_ERR_BREAKDOWN, "Arnoldi breakdown in the eigensolver");
+                Hm[s][(size_t)(j + 1) * m + j] = beta;
+                std::vector<double2> sc(1, make_double2(1.0 / beta, 0.0));
+                if ((r = bcombine_host(c, Vs(s, j + 1), nullptr, 1, wv, 1, sc, st))) return r;
+            }
+        }
+        // convergence of the nev wanted Ritz pairs of both processes.  With OP z = theta z + f and
+        // |f| = est |theta|: ||H z - z / theta|| = ||H f|| / |theta| <= ||H|| est, so est bounds the
+        // residual relative to ||H|| that the call reports
+        bool conv = true;
+        for (int s = 0; s < 2; ++s) {
+            if (ritz(m, Hm[s], th[s], Y[s], est[s]) != LQ_OK) return set_err(c, LQ_ERR_NEWTON, "Hessenberg eigensolver failed");
+            for (int i = 0; i < nev; ++i) conv = conv && est[s][i] <= 0.5 * eo.tol;
+        }
+        out.restarts = restart;
+        if (conv || restart >= eo.max_iter) break;
+        // restart: exact shifts = the m - kk unwanted Ritz values; keep kk vectors
+        for (int s = 0; s < 2; ++s) {
+            std::vector<cplx> H((size_t)m * m), Q((size_t)m * m, 0.0);
+            for (int i = 0; i < m; ++i) for (int jj = 0; jj < m; ++jj) H[i * m + jj] = Hm[s][(size_t)i * m + jj];
+            for (int i = 0; i < m; ++i) Q[i * m + i] = 1.0;
+            for (int i = kk; i < m; ++i) hess_qr_step(m, H, Q, th[s][i]);
+            const cplx bk = H[(size_t)kk * m + (kk - 1)];
+            const cplx sg = Q[(size_t)(m - 1) * m + (kk - 1)];
+            const cplx fm = Hm[s][(size_t)m * m + (m - 1)];
+            // Zs_b = sum_a V_a Q[a][b] (b < kk);  Zs_kk = bk V Q[:, kk] + fm sg v_{m+1}
+            std::vector<double2> co((size_t)(kk + 1) * (m + 1), make_double2(0.0, 0.0));
+            for (int b = 0; b < kk; ++b)
+                for (int a = 0; a < m; ++a) co[(size_t)b * (m + 1) + a] = make_double2(Q[a * m + b].real(), Q[a * m + b].imag());
+            for (int a = 0; a < m; ++a) {
+                const cplx v = bk * Q[a * m + kk];
+                co[(size_t)kk * (m + 1) + a] = make_double2(v.real(), v.imag());
+            }
+            const cplx tail = fm * sg;
+            co[(size_t)kk * (m + 1) + m] = make_double2(tail.real(), tail.imag());
+            double* Zb = Zs + (size_t)s * (kk + 1) * nv;
+            if ((r = bcombine_host(c, Zb, nullptr, kk + 1, Vs(s, 0), m + 1, co, st))) return r;
+            std::vector<double2> nn;
+            if ((r = bdots_host(c, Zb + (size_t)kk * nv, 1, Zb + (size_t)kk * nv, 1, nn, st))) return r;
+            const double fn = std::sqrt(std::max(nn[0].x, 0.0));
+            if (!(fn > 0.0) || !std::isfinite(fn)) return set_err(c, LQ_ERR_BREAKDOWN, "invariant subspace at a restart of the eigensolver");
+            LQ_CUDA(c, cudaMemcpyAsync(Vs(s, 0), Zb, sizeof(double) * nv * kk, cudaMemcpyDeviceToDevice, st));
+            std::vector<double2> sc(1, make_double2(1.0 / fn, 0.0));
+            if ((r = bcombine_host(c, Vs(s, kk), nullptr, 1, Zb + (size_t)kk * nv, 1, sc, st))) return r;
+            std::fill(Hm[s].begin(), Hm[s].end(), cplx(0.0));
+            for (int i = 0; i < kk; ++i) for (int jj = 0; jj < kk; ++jj) Hm[s][(size_t)i * m + jj] = H[i * m + jj];
+            Hm[s][(size_t)kk * m + (kk - 1)] = fn;
+        }
+        j0 = kk;
+    }
+    // Ritz vectors z = V y of the nev wanted pairs, lambda = 1 / theta, and their true residuals
+    for (int s = 0; s < 2; ++s) {
+        std::vector<double2> co((size_t)nev * m);
+        for (int b = 0; b < nev; ++b)
+            for (int a = 0; a < m; ++a) co[(size_t)b * m + a] = make_double2(Y[s][a * m + b].real(), Y[s][a * m + b].imag());
+        double* Zo = Z + (size_t)s * nev * nv;
+        if ((r = bcombine_host(c, Zo, nullptr, nev, Vs(s, 0), m, co, st))) return r;
+        out.lam[s].resize(nev);
+        for (int i = 0; i < nev; ++i) out.lam[s][i] = 1.0 / th[s][i];
+        double* HZ = Zs;                                   // nev <= kk + 1 vectors of scratch
+        if ((r = apply_H_batch(c, Zo, HZ, nev, s, st, LQ_FP64, w.links64))) return r;
+        std::vector<double2> cr((size_t)nev * nev, make_double2(0.0, 0.0));
+        for (int i = 0; i < nev; ++i) cr[(size_t)i * nev + i] = make_double2(-out.lam[s][i].real(), -out.lam[s][i].imag());
+        if ((r = bcombine_host(c, HZ, HZ, nev, Zo, nev, cr, st))) return r;
+        std::vector<double2> rr, zz;
+        out.res[s].assign(nev, 0.0);
+        for (int i = 0; i < nev; ++i) {
+            if ((r = bdots_host(c, HZ + (size_t)i * nv, 1, HZ + (size_t)i * nv, 1, rr, st))) return r;
+            if ((r = bdots_host(c, Zo + (size_t)i * nv, 1, Zo + (size_t)i * nv, 1, zz, st))) return r;
+            out.res[s][i] = std::sqrt(rr[0].x / zz[0].x) / hn;
+        }
+    }
+    return LQ_OK;
+}
+
 }  // namespace
 
 // ---------------------------------------------------------------------------------------------
@@ -1901,49 +2241,127 @@ int lq_upload_deflation(lq_ctx* c, int l, const double* lambda, const double* R,
 int lq_compute_deflation(lq_ctx* c, const lq_eig_opts* eo_in, const double* X0, double* lambda, double* resid, void* stream) {
     if (!c || !eo_in || !X0) return set_err(c, LQ_ERR_ARG, "null argument");
     lq_eig_opts eo = *eo_in;
-    if (eo.nsub <= 0) eo.nsub = std::min(eo.nev + 12, 64);
+    const bool si = eo.method == LQ_EIG_SHIFT_INVERT;
+    if (eo.method != LQ_EIG_SHIFT_INVERT && eo.method != LQ_EIG_CHEBYSHEV) return set_err(c, LQ_ERR_ARG, "unknown eigensolver method");
+    if (eo.nsub <= 0) eo.nsub = si ? std::min(2 * eo.nev + 10, 63) : std::min(eo.nev + 12, 64);
     if (eo.degree <= 0) eo.degree = 40;
-    if (eo.max_iter <= 0) eo.max_iter = 60;
+    if (eo.max_iter <= 0) eo.max_iter = si ? 300 : 60;
     if (!(eo.tol > 0.0)) eo.tol = 1e-10;
-    if (eo.nev < 1 || eo.nsub < eo.nev + 2 || eo.nsub > 64) return set_err(c, LQ_ERR_ARG, "need 1 <= nev and nev + 2 <= nsub <= 64");
+    if (si) {
+        if (eo.nev < 1 || eo.nsub < eo.nev + 4 || eo.nsub > 63) return set_err(c, LQ_ERR_ARG, "need 1 <= nev and nev + 4 <= nsub <= 63");
+    } else if (eo.nev < 1 || eo.nsub < eo.nev + 2 || eo.nsub > 64) {
+        return set_err(c, LQ_ERR_ARG, "need 1 <= nev and nev + 2 <= nsub <= 64");
+    }
     int r = check_ready(c, 1, 0);
     if (r) return r;
-    if ((size_t)eo.nsub * eo.nsub > (size_t)std::max(2 * c->nsrc, 64) * std::max(2 * c->nsrc, 64))
+    if ((size_t)(eo.nsub + 1) * (eo.nsub + 1) > (size_t)std::max(2 * c->nsrc, 64) * std::max(2 * c->nsrc, 64))
         return set_err(c, LQ_ERR_ARG, "nsub too large for the reserved reduction scratch");
     cudaStream_t st = (cudaStream_t)stream;
     const size_t nv = nvec(c);
     const int m = eo.nsub, nev = eo.nev;
-    double* W = nullptr;      // X, Y0, Y1, H1, H2 | ZR, ZL | X0 copy
-    if (cudaMalloc(&W, sizeof(double) * nv * m * 8) != cudaSuccess) { cudaGetLastError(); return set_err(c, LQ_ERR_OOM, "eigensolver workspace"); }
-    double* ZR = W + (size_t)5 * m * nv;
-    double* ZL = ZR + (size_t)m * nv;
-    double* X0d = ZL + (size_t)m * nv;
-    // the eigensolver's stencil runs in FP64: a mixed-precision context gets a temporary FP64 copy
-    // of the links in the internal layout
+    c->eig_stats = lq_eig_stats();
+    cudaEvent_t t0 = nullptr, t1 = nullptr;
+    if (cudaEventCreate(&t0) == cudaSuccess && cudaEventCreate(&t1) == cudaSuccess) cudaEventRecord(t0, st);
+    else cudaGetLastError();
+    // workspace (a set-up call): Chebyshev: X, Y0, Y1, H1, H2 | ZR, ZL | X0 copy (m fields each);
+    // shift-and-invert: basis [2][m+1] | restart scratch [2][kk+1] + [4] | Ritz vectors [2][nev] |
+    // residuals [4] | start fields [2] | the FP32 CG vectors and scalars
+    const int kk_max = m;   // bound on the vectors kept at a restart
+    const size_t doubles = si ? nv * ((size_t)2 * (m + 1) + 2 * (kk_max + 1) + 4 + 2 * nev + 4 + 2) : nv * (size_t)m * 8;
+    const size_t cg_bytes = si ? sizeof(float4) * 5 * 2 * (size_t)c->V * 6 + sizeof(double) * (2 * kCgNs + cg_partial_doubles(2) + 2) + sizeof(int) * 8 : 0;
+    char* W = nullptr;
+    if (cudaMalloc(&W, sizeof(double) * doubles + cg_bytes + 256) != cudaSuccess) { cudaGetLastError(); return set_err(c, LQ_ERR_OOM, "eigensolver workspace"); }
+    // the eigensolver's FP64 stencil: a mixed-precision context gets a temporary FP64 copy of the
+    // links; its FP32 stencil (shift-and-invert inner solves): an FP64 context gets an FP32 copy
     void* U64 = nullptr;
+    void* U32 = nullptr;
+    auto fail = [&](int code) { cudaFree(W); if (U64) cudaFree(U64); if (U32) cudaFree(U32); if (t0) cudaEventDestroy(t0); if (t1) cudaEventDestroy(t1); return code; };
     if (c->prec != LQ_FP64) {
-        if (cudaMalloc(&U64, sizeof(double2) * c->V * 36) != cudaSuccess) { cudaGetLastError(); cudaFree(W); return set_err(c, LQ_ERR_OOM, "eigensolver links"); }
+        if (cudaMalloc(&U64, sizeof(double2) * c->V * 36) != cudaSuccess) { cudaGetLastError(); U64 = nullptr; return fail(set_err(c, LQ_ERR_OOM, "eigensolver links")); }
         cudaError_t e = launch_links_internal(LQ_FP64, c->Ub, U64, c->V, st);
-        if (e != cudaSuccess) { cudaFree(U64); cudaFree(W); return set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e)); }
+        if (e != cudaSuccess) return fail(set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e)));
+    } else if (si) {
+        if (cudaMalloc(&U32, sizeof(float2) * c->V * 36) != cudaSuccess) { cudaGetLastError(); U32 = nullptr; return fail(set_err(c, LQ_ERR_OOM, "eigensolver links")); }
+        cudaError_t e = launch_links_internal(LQ_MIXED, c->Ub, U32, c->V, st);
+        if (e != cudaSuccess) return fail(set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e)));
     }
     const void* links64 = U64 ? U64 : c->U;
-    auto fail = [&](int code) { cudaFree(W); if (U64) cudaFree(U64); return code; };
-    if ((r = stage_in(c, X0d, X0, nv * m, st))) return fail(r);
+    const void* links32 = U32 ? U32 : c->U;
+    double* Wd = reinterpret_cast<double*>(W);
     std::vector<cplx> thR, thL;
     std::vector<double> resR, resL;
-    if ((r = eig_subspace(c, &eo, X0d, 0, W, thR, resR, ZR, st, links64))) return fail(r);
-    if ((r = eig_subspace(c, &eo, X0d, 1, W, thL, resL, ZL, st, links64))) return fail(r);
-    // pair right eigenvalue lambda_i with the left Ritz value conj(theta_j) closest to it
+    double* ZR = nullptr;
+    double* ZL = nullptr;
+    int ncand = m;       // left candidates for the pairing
+    if (!si) {
+        ZR = Wd + (size_t)5 * m * nv;
+        ZL = ZR + (size_t)m * nv;
+        double* X0d = ZL + (size_t)m * nv;
+        if ((r = stage_in(c, X0d, X0, nv * m, st))) return fail(r);
+        if ((r = eig_subspace(c, &eo, X0d, 0, Wd, thR, resR, ZR, st, links64))) return fail(r);
+        if ((r = eig_subspace(c, &eo, X0d, 1, Wd, thL, resL, ZL, st, links64))) return fail(r);
+    } else {
+        double* Vb = Wd;
+        double* Zs = Vb + (size_t)2 * (m + 1) * nv;
+        double* Z = Zs + ((size_t)2 * (kk_max + 1) + 4) * nv;
+        double* R4 = Z + (size_t)2 * nev * nv;
+        double* X0d = R4 + (size_t)4 * nv;
+        char* g = reinterpret_cast<char*>(X0d + 2 * nv);
+        SiWork w;
+        w.c = c; w.st = st; w.V = c->V; w.ne = (size_t)6 * c->V; w.nv = nv;
+        w.links32 = links32; w.links64 = links64;
+        float4* f = reinterpret_cast<float4*>(g);
+        w.x = f; w.r = f + 2 * w.ne; w.p = f + 4 * w.ne; w.q = f + 6 * w.ne; w.z = f + 8 * w.ne;
+        double* dd = reinterpret_cast<double*>(f + 10 * w.ne);
+        w.scal = dd; w.part = dd + 2 * kCgNs; w.nrm = w.part + cg_partial_doubles(2);
+        w.counters = reinterpret_cast<int*>(w.nrm + 2);
+        w.res64 = R4; w.tmp64 = R4 + 2 * nv;
+        if (eo.inner_max > 0) w.inner_max = eo.inner_max;
+        LQ_CUDA(c, cudaMemsetAsync(w.counters, 0, sizeof(int) * 8, st));
+        if ((r = stage_in(c, X0d, X0, nv * 2, st))) return fail(r);
+        // ||H|| estimate (power iteration with H^dag H on the first start field): the residual scale
+        double hn = 0.0;
+        {
+            double* y = R4;
+            double* t = R4 + nv;
+            LQ_CUDA(c, cudaMemcpyAsync(y, X0d, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+            for (int it = 0; it < 12; ++it) {
+                std::vector<double2> n0, n1;
+                if ((r = bdots_host(c, y, 1, y, 1, n0, st))) return fail(r);
+                if ((r = apply_H_batch(c, y, t, 1, 0, st, LQ_FP64, links64))) return fail(r);
+                if ((r = apply_H_batch(c, t, y, 1, 1, st, LQ_FP64, links64))) return fail(r);
+                if ((r = bdots_host(c, y, 1, y, 1, n1, st))) return fail(r);
+                hn = std::sqrt(std::sqrt(n1[0].x / n0[0].x));
+                std::vector<double2> sc(1, make_double2(1.0 / std::sqrt(n1[0].x), 0.0));
+                if ((r = bcombine_host(c, t, nullptr, 1, y, 1, sc, st))) return fail(r);
+                LQ_CUDA(c, cudaMemcpyAsync(y, t, sizeof(double) * nv, cudaMemcpyDeviceToDevice, st));
+            }
+            hn *= 1.05;
+        }
+        SiResult res;
+        if ((r = eig_shift_invert(w, eo, X0d, Vb, Zs, Z, hn, res))) return fail(r);
+        thR = res.lam[0]; thL = res.lam[1];
+        resR = res.res[0]; resL = res.res[1];
+        ZR = Z; ZL = Z + (size_t)nev * nv;
+        ncand = nev;
+        c->eig_stats.restarts = res.restarts;
+        c->eig_stats.solves = w.solves;
+        c->eig_stats.inner_iterations = w.iters;
+        c->eig_stats.refinements = w.refinements;
+        c->eig_stats.norm_estimate = hn;
+    }
+    // pair right eigenvalue lambda_i with the left eigenvalue conj(theta_j) closest to it
     std::vector<int> pick(nev, -1);
-    std::vector<char> used(m, 0);
+    std::vector<char> used(ncand, 0);
     for (int i = 0; i < nev; ++i) {
         double best = 1e300;
-        for (int j = 0; j < m; ++j) {
+        for (int j = 0; j < ncand; ++j) {
             if (used[j]) continue;
             const double d = std::abs(thR[i] - std::conj(thL[j]));
             if (d < best) { best = d; pick[i] = j; }
         }
         used[pick[i]] = 1;
+        c->eig_stats.pair_mismatch = std::max(c->eig_stats.pair_mismatch, best / std::max(std::abs(thR[i]), 1e-300));
     }
     // install: defl_V = R (first nev right Ritz vectors), defl_W = the paired left vectors
     if (nev > c->defl_cap) {
@@ -1977,9 +2395,22 @@ int lq_compute_deflation(lq_ctx* c, const lq_eig_opts* eo_in, const double* X0, 
     c->defl_dlam.assign(nev, make_double2(0.0, 0.0));
     c->defl_l = nev;
     if (lambda) for (int i = 0; i < nev; ++i) { lambda[2 * i] = thR[i].real(); lambda[2 * i + 1] = thR[i].imag(); }
+    for (int i = 0; i < nev; ++i) c->eig_stats.max_residual = std::max(c->eig_stats.max_residual, std::max(resR[i], resL[pick[i]]));
     if (resid) for (int i = 0; i < nev; ++i) resid[i] = std::max(resR[i], resL[pick[i]]);
-    cudaFree(W);
-    if (U64) cudaFree(U64);
+    if (t0 && t1) {
+        cudaEventRecord(t1, st);
+        cudaEventSynchronize(t1);
+        float ms = 0.f;
+        if (cudaEventElapsedTime(&ms, t0, t1) == cudaSuccess) c->eig_stats.seconds = ms * 1e-3;
+        else cudaGetLastError();
+    }
+    c->eig_stats.method = eo.method;
+    return fail(LQ_OK);
+}
+
+int lq_eig_stats_read(const lq_ctx* c, lq_eig_stats* out) {
+    if (!c || !out) return LQ_ERR_ARG;
+    *out = c->eig_stats;
     return LQ_OK;
 }
 

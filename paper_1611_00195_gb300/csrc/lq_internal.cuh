@@ -252,6 +252,7 @@ struct lq_ctx {
     size_t gen_scr_doubles = 0;
     double2* defl_shift = nullptr;   // [nsrc] resolvent shifts
     double defl_resid = 0.0;         // largest relative residual of the last shifted solves
+    lq_eig_stats eig_stats{};        // statistics of the last lq_compute_deflation
 
     // stencil autotuning: chosen variant per (batch size, nf, emode) of the Lanczos step
     struct Tuned { int nsrc, nf, emode, variant; };

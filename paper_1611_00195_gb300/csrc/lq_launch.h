@@ -99,6 +99,23 @@ struct RecArgs {
 
 
 cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st);
+// CGNR inner solves of the shift-and-invert eigensolver (lq_eig.cu): nb systems of ne float4
+// elements each (internal FP32 layout), FP64 scalars per system in scal[sys * kCgNs + slot].
+enum { CG_G0 = 0, CG_G1 = 1, CG_QQ = 2, CG_RR = 3, CG_BB = 4, CG_DONE = 5 };
+constexpr int kCgNs = 8;
+struct CgArgs {
+    size_t ne;             // float4 elements per system
+    int nb;                // systems
+    int it;                // iteration (selects the slot of g in the two-slot rotation)
+    float4* x; float4* r; float4* p; const float4* q; const float4* z;   // [nb][ne]
+    double* scal;          // [nb][kCgNs]
+    double* part;          // cg_partial_doubles(nb)
+    int* counters;         // [nb][3], zero
+};
+size_t cg_partial_doubles(int nsys);
+cudaError_t launch_cg_norm(const CgArgs& a, const float4* v, int slot, cudaStream_t st);   // |v_s|^2 -> slot
+cudaError_t launch_cg_xr(const CgArgs& a, cudaStream_t st);     // x += alpha p, r -= alpha q, |r|^2
+cudaError_t launch_cg_p(const CgArgs& a, cudaStream_t st);      // p = z + beta p
 // packed-FP32 block stencil (lq_hop_x2.cu): schedule 7, or 8 with the neighbour prefetch
 cudaError_t launch_hop_x2(const HopArgs& a, int emode, bool dot, bool prefetch, cudaStream_t st);
 cudaError_t launch_links_packed(const void* L, void* P, size_t V, cudaStream_t st);   // float2 -> (ux, ux, -uy, uy)

@@ -33,13 +33,14 @@ ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_C
 LQ_FP64, LQ_MIXED = 0, 1
 LQ_DIR_MU, LQ_DIR_SU3, LQ_DIR_U1 = 0, 1, 2
 LQ_PROJ_AUTO, LQ_PROJ_NEWTON, LQ_PROJ_QUAD = 0, 1, 2
+LQ_EIG_SHIFT_INVERT, LQ_EIG_CHEBYSHEV = 0, 1
 
 EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_upload_gauge", "lq_set_mu",
             "lq_reserve", "lq_apply_H", "lq_set_direction", "lq_apply_block", "lq_sign_apply",
             "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
             "lq_profile_read", "lq_newton_sign_noalloc", "lq_error_estimate",
             "lq_upload_deflation", "lq_deflation_derivatives", "lq_sign_bilinear_grad",
-            "lq_dense_eig", "lq_compute_deflation", "lq_overlap_apply", "lq_batch_apply", "lq_overlap_solve",
+            "lq_dense_eig", "lq_compute_deflation", "lq_eig_stats_read", "lq_overlap_apply", "lq_batch_apply", "lq_overlap_solve",
             "lq_axial_current"]
 
 
@@ -79,7 +80,17 @@ class Profile(ctypes.Structure):
 
 class EigOpts(ctypes.Structure):
     _fields_ = [("nev", ctypes.c_int), ("nsub", ctypes.c_int), ("degree", ctypes.c_int), ("max_iter", ctypes.c_int),
-                ("tol", ctypes.c_double)]
+                ("tol", ctypes.c_double), ("method", ctypes.c_int), ("inner_max", ctypes.c_int)]
+
+
+class EigStats(ctypes.Structure):
+    _fields_ = [("method", ctypes.c_int), ("restarts", ctypes.c_int), ("solves", ctypes.c_longlong),
+                ("inner_iterations", ctypes.c_longlong), ("refinements", ctypes.c_longlong),
+                ("norm_estimate", ctypes.c_double), ("max_residual", ctypes.c_double),
+                ("pair_mismatch", ctypes.c_double), ("seconds", ctypes.c_double)]
+
+    def as_dict(self):
+        return {f: getattr(self, f) for f, _ in self._fields_}
 
 
 class Direction(ctypes.Structure):
@@ -138,6 +149,7 @@ def lib():
         L.lq_sign_bilinear_grad.argtypes = [P, P, P, ctypes.POINTER(Opts), P, P, P, P]
         L.lq_dense_eig.argtypes = [I, P, P, P]
         L.lq_compute_deflation.argtypes = [P, ctypes.POINTER(EigOpts), P, P, P, P]
+        L.lq_eig_stats_read.argtypes = [P, ctypes.POINTER(EigStats)]
         L.lq_newton_sign_noalloc.argtypes = [P, P, I, I, I, D, ctypes.POINTER(I), P]
         L.lq_batch_apply.argtypes = [ctypes.POINTER(BatchItem), I, P]
         L.lq_overlap_solve.argtypes = [P, P, P, I, D, D, I, ctypes.POINTER(Opts), ctypes.POINTER(SolveReport), P]
@@ -470,16 +482,26 @@ class Context:
         self._defl_keep = (lam, R, L)
         self._check(self._L.lq_upload_deflation(self._h, int(lam.shape[0]), _ptr(lam), _ptr(R), _ptr(L), _stream(R)))
 
-    def compute_deflation(self, nev, X0, nsub=0, degree=0, max_iter=0, tol=0.0):
+    def compute_deflation(self, nev, X0, nsub=0, degree=0, max_iter=0, tol=0.0, method=LQ_EIG_SHIFT_INVERT, inner_max=0):
         """Install the nev eigenpairs of H(mu) closest to zero as the deflation space, from the
-        library's eigensolver started at X0 [nsub][V][4][3]; returns (lambda [nev], residuals [nev])."""
+        library's eigensolver (method LQ_EIG_SHIFT_INVERT: start fields X0[0] (right) and X0[1]
+        (left), basis size nsub; LQ_EIG_CHEBYSHEV: subspace X0 [nsub][V][4][3]); returns
+        (lambda [nev], residuals [nev]).  eig_stats() gives the run's statistics."""
         X0 = _as_c128(X0)
-        eo = EigOpts(int(nev), int(nsub or X0.shape[0]), int(degree), int(max_iter), float(tol))
+        if method == LQ_EIG_CHEBYSHEV and not nsub:
+            nsub = X0.shape[0]
+        eo = EigOpts(int(nev), int(nsub), int(degree), int(max_iter), float(tol), int(method), int(inner_max))
         lam = np.zeros(nev, np.complex128)
         res = np.zeros(nev, np.float64)
         self._check(self._L.lq_compute_deflation(self._h, ctypes.byref(eo), _ptr(X0), _ptr(lam), _ptr(res), _stream(X0)))
         self._defl_keep = (lam,)
         return lam, res
+
+    def eig_stats(self):
+        """Statistics of the last compute_deflation (restarts, solves, inner iterations, seconds ...)."""
+        s = EigStats()
+        self._check(self._L.lq_eig_stats_read(self._h, ctypes.byref(s)))
+        return s.as_dict()
 
     def deflation_derivatives(self, k, kind=LQ_DIR_MU, field=None, **kw):
         """(dlambda [l], dR [l][V][4][3], dL kets [l][V][4][3]) along the direction (host arrays)."""

@@ -134,12 +134,14 @@ def test_derivative_generalised_deflation(lqlib):
         assert ed < 0.1 * ed0
 
 
+@pytest.mark.parametrize("method", [0, 1])
 @pytest.mark.parametrize("prec,tol", [(0, 1e-10), (1, 1e-10)])
-def test_compute_deflation_eigensolver(lqlib, prec, tol):
-    """The library's eigensolver (Chebyshev-filtered subspace iteration on H^2 with Rayleigh-Ritz)
-    finds the eigenvalues of H(mu) closest to zero that the oracle's dense eig gives, and the
-    installed space deflates the sign like the oracle's eigenpairs do.  Its stencil is FP64 in
-    both precisions, so both reach the FP64 tolerance."""
+def test_compute_deflation_eigensolver(lqlib, prec, tol, method):
+    """The library's eigensolvers (0: implicitly restarted Arnoldi on H^{-1}; 1: Chebyshev-filtered
+    subspace iteration on H^2 with Rayleigh-Ritz) find the eigenvalues of H(mu) closest to zero
+    that the oracle's dense eig gives, and the installed space deflates the sign like the
+    oracle's eigenpairs do.  Their FP64 stencil runs in both precisions, so both reach the FP64
+    tolerance."""
     from paper_1611_00195_gb300 import lq
     dims, nev, nsub, k = (4, 2, 2, 2), 8, 16, 60
     lat = od.Lattice(dims)
@@ -152,9 +154,9 @@ def test_compute_deflation_eigensolver(lqlib, prec, tol):
     c.upload_gauge(torch.from_numpy(U).cuda())
     c.reserve(k, 8, True)
     X0 = syn.gaussian_source(dims, 41, nsrc=nsub)
-    lam, res = c.compute_deflation(nev, torch.from_numpy(X0).cuda(), nsub=nsub, tol=tol)
-    print("eigensolver prec %d: residuals max %.3g; eigenvalue error max %.3g"
-          % (prec, res.max(), max(np.min(np.abs(lam_all[:nev] - z)) for z in lam)))
+    lam, res = c.compute_deflation(nev, torch.from_numpy(X0).cuda(), nsub=nsub, tol=tol, method=method)
+    print("eigensolver %d prec %d: residuals max %.3g; eigenvalue error max %.3g; %s"
+          % (method, prec, res.max(), max(np.min(np.abs(lam_all[:nev] - z)) for z in lam), c.eig_stats()))
     assert res.max() <= tol
     for z in lam:
         assert np.min(np.abs(lam_all[:nev] - z)) < 20 * tol * np.abs(lam_all).max()
@@ -182,3 +184,41 @@ def test_compute_deflation_eigensolver(lqlib, prec, tol):
         e2 = relerr(y2.cpu().numpy(), y64.cpu().numpy())
         print("mixed deflated sign vs FP64: computed space %.3g, dense eigenpairs %.3g" % (e1, e2))
         assert e1 < 3 * e2 + 1e-9
+
+
+@pytest.mark.parametrize("prec", [0, 1])
+def test_shift_invert_where_the_spectrum_surrounds_zero(lqlib, prec):
+    """4x4x2x2 at mu = 0.6: the ten eigenvalues of H(mu) nearest zero lie at every phase around
+    the origin (|lambda| 0.59-0.61, a 3.5% gap to the eleventh), the situation of the 14x14^3
+    benchmark field, where no polynomial in H or H^2 can favour them.  The shift-and-invert
+    Arnoldi process finds exactly them, to the FP64 tolerance, with biorthonormal left vectors."""
+    from paper_1611_00195_gb300 import lq
+    dims, mu, nev, tol = (4, 4, 2, 2), 0.6, 10, 1e-10
+    lat = od.Lattice(dims)
+    U = syn.gauge_field(dims, 0.4, 3)
+    A = od.dense_H(lat, U, mu)
+    lam_all = np.linalg.eigvals(A)
+    lam_all = lam_all[np.argsort(np.abs(lam_all))]
+    assert np.abs(lam_all[nev]) > 1.03 * np.abs(lam_all[nev - 1])
+    c = lq.Context(dims, mu=mu, precision=prec)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(40, 4, True)
+    X0 = syn.gaussian_source(dims, 41, nsrc=2)
+    lam, res = c.compute_deflation(nev, torch.from_numpy(X0).cuda(), nsub=30, tol=tol)
+    st = c.eig_stats()
+    err = max(np.min(np.abs(lam_all[:nev] - z)) for z in lam)
+    print("shift-invert prec %d: residual max %.3g, eigenvalue error max %.3g, %s" % (prec, res.max(), err, st))
+    assert res.max() <= tol
+    assert err < 1e-9 * np.abs(lam_all[0])
+    assert len(set(int(np.argmin(np.abs(lam_all[:nev] - z))) for z in lam)) == nev      # each one once
+    assert st["method"] == 0 and st["solves"] > 0 and st["pair_mismatch"] < 1e-8
+    # the installed right/left vectors: eigenvectors of H and H^dag, biorthonormal
+    x = torch.from_numpy(syn.gaussian_source(dims, 5, nsrc=2)).cuda()
+    y1, _ = c.sign_apply(x, 30, deflate=1)
+    lo, R, L, _ = odf.eigenpairs(A, nev)
+    c.upload_deflation(lo, torch.from_numpy(np.ascontiguousarray(R.T.reshape(nev, lat.V, 4, 3))).cuda(),
+                       torch.from_numpy(np.ascontiguousarray(L.conj().reshape(nev, lat.V, 4, 3))).cuda())
+    y2, _ = c.sign_apply(x, 30, deflate=1)
+    e = relerr(y1.cpu().numpy(), y2.cpu().numpy())
+    print("deflated sign, computed vs dense eigenpairs: %.3g" % e)
+    assert e < (1e-8 if prec == 0 else 1e-5)
