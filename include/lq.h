@@ -121,27 +121,40 @@ typedef struct {
                               while lq_profile_enable times kernels, for two-pass runs and for
                               the adjoint.  Results differ from the unsplit run by FP32
                               rounding only (each half has its own reduction grids)           */
+    int nested_m;          /* inner Krylov size of LQ_PROJ_NESTED and of that rung of LQ_PROJ_AUTO
+                              (default 100, the paper's; capped by k and the reserved kmax)   */
 } lq_opts;
 
 /* Projected step sgn(T_k) e_1 (Sec. 2):
  *  LQ_PROJ_NEWTON  scaled Newton iteration on the dense k x k matrix (FP64, O(k^3));
  *  LQ_PROJ_QUAD    midpoint quadrature of sgn(T) = (2/pi) T int_0^inf (t^2 + T^2)^{-1} dt
  *                  with t = c tan(theta): 2N complex tridiagonal solves (FP64, O(N k));
+ *  LQ_PROJ_NESTED  the nested two-sided Lanczos process of Sec. 4 (one level of nesting): an
+ *                  inner process of opts.nested_m steps from e_1 on M = T/c + c T^{-1} (a
+ *                  function of T with the same sign), c = sqrt(|lambda|_min |lambda|_max)
+ *                  estimated as for the quadrature, then the scaled Newton iteration on the
+ *                  inner nested_m x nested_m tridiagonal; accepted per source only if the
+ *                  involution residual of a second pass from the result is <= proj_tol
+ *                  (O(m k) sequential work per source plus an m x m Newton);
  *  LQ_PROJ_AUTO    the quadrature, accepted per source only if its involution residual
  *                  ||Q(T) Q(T) e_1 - e_1|| <= proj_tol; a failing source is retried once
- *                  with 512 nodes, and only what still fails goes to Newton.             */
+ *                  with 512 nodes, then by the nested process, and only what still fails
+ *                  goes to Newton on the k x k matrix.                                   */
 #define LQ_PROJ_AUTO    0
 #define LQ_PROJ_NEWTON  1
 #define LQ_PROJ_QUAD    2
+#define LQ_PROJ_NESTED  3
 
 typedef struct {
     int k_eff;             /* dimension of T actually built (< kmax after a breakdown)        */
     int newton_iters;      /* Newton iterations taken on sgn(T_k) (0 if not used)             */
     int status;            /* LQ_OK, LQ_ERR_BREAKDOWN, LQ_ERR_NEWTON or LQ_ERR_NONFINITE      */
-    int projected;         /* solver that produced sgn(T_k) e_1: LQ_PROJ_NEWTON or LQ_PROJ_QUAD */
+    int projected;         /* solver that produced sgn(T_k) e_1: LQ_PROJ_NEWTON, LQ_PROJ_QUAD or
+                              LQ_PROJ_NESTED                                                  */
     double newton_change;  /* last relative Frobenius change of the Newton iterate            */
     double x_norm;         /* |x| of the source                                               */
-    double proj_check;     /* involution residual of the quadrature (0 if not attempted)       */
+    double proj_check;     /* involution residual of the quadrature or of the nested process
+                              that produced the result (0 if neither was attempted)            */
     int hop_variant;       /* stencil schedule used (see lq_opts.hop_variant)                  */
     int reserved;
 } lq_report;
@@ -431,6 +444,19 @@ int  lq_dense_eig(int n, const double* A, double* w, double* V);
  * Synchronises `stream`. */
 int  lq_newton_sign(lq_ctx* ctx, const double* X, double* S, int k, int nb,
                     int max_iter, double tol, int* iters, void* stream);
+
+/* sgn(T) e_1 of nb complex tridiagonal k x k matrices by the nested two-sided Lanczos process of
+ * LQ_PROJ_NESTED (Sec. 4): m inner steps on M = T/c + c T^{-1} from e_1, the inner projected sign
+ * by the scaled Newton iteration, and the involution residual of a second pass.
+ * alpha: diagonal double[nb][k][2]; beta: super-diagonal double[nb][k-1][2]; delta: real
+ * sub-diagonal double[nb][k-1] (the layout of lq_tsl_coefficients); scale: double[nb], the c of
+ * each matrix, or NULL for the library's estimate of sqrt(|lambda|_min |lambda|_max); host or
+ * device.  out: double[nb][k][2] (host or device); check: host double[nb] (may be NULL).
+ * Needs a workspace reserved with kmax >= k, nsrc >= nb and kmax >= m; overwrites the projected
+ * coefficients of the context's last solve (lq_tsl_coefficients).  Returns LQ_ERR_NEWTON if an
+ * inner Newton iteration did not converge.  Synchronises. */
+int  lq_nested_sign(lq_ctx* ctx, const double* alpha, const double* beta, const double* delta,
+                    const double* scale, int k, int nb, int m, double* out, double* check, void* stream);
 
 /* Allocation-free variant of lq_newton_sign, for callers that cannot allocate device
  * memory: for example a process whose device memory is handed in full to a pool allocator

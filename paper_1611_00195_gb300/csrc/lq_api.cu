@@ -255,6 +255,8 @@ void free_workspace(lq_ctx* c) {
                    (void**)&c->nx_X, (void**)&c->nx_Y, (void**)&c->nx_F, (void**)&c->nx_perm, (void**)&c->nx_scal,
                    (void**)&c->nx_partials, (void**)&c->nx_counters, (void**)&c->proj_c, (void**)&c->quad_q,
                    (void**)&c->quad_work, (void**)&c->quad_c, (void**)&c->quad_check, (void**)&c->quad_nodes, (void**)&c->quad_part, (void**)&c->proj_sel,
+                   (void**)&c->nest_state, (void**)&c->nest_alpha, (void**)&c->nest_beta, (void**)&c->nest_delta, (void**)&c->nest_s,
+                   (void**)&c->nest_q, (void**)&c->nest_norm, (void**)&c->nest_check, (void**)&c->nest_c,
                    &c->lbasis, (void**)&c->uscale, (void**)&c->adj_coef, &c->adj_nu, &c->adj_om,
                    (void**)&c->adj_force, (void**)&c->adj_dmu, (void**)&c->gen_scr, (void**)&c->solve_ws};
     for (void** p : ps) { dfree(*p); *p = nullptr; }
@@ -297,6 +299,54 @@ int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* vari
     const int bestv = (int)(std::min_element(best.begin(), best.end()) - best.begin());
     c->tuned.push_back({h.nsrc, nf, emode, bestv});
     *variant = bestv;
+    return LQ_OK;
+}
+
+// The nested two-sided Lanczos projected sign (lq_nested.cu, Sec. 4) for the sources with
+// sel[s] != 0: sgn(T) e_1 into out [nb][kmax] from the context's coefficient arrays (k_eff from
+// `state`, or kfix for every source when state is null), with scales cscale [nb] (device); the
+// involution residual of the second pass into check (host; +inf where an inner Newton iteration
+// failed).  Pass 1 starts at e_1, pass 2 at the result of pass 1.
+int nested_run(lq_ctx* c, const TslState* state, int kfix, int nb, int m, const double* cscale, const std::vector<int>& sel,
+               double2* out, std::vector<double>& check, int newton_max_iter, double newton_tol, cudaStream_t st) {
+    NestArgs na;
+    std::memset(&na, 0, sizeof(na));
+    na.nb = nb; na.kmax = c->kmax; na.kfix = kfix; na.m = m; na.state = state;
+    na.alpha = c->alpha; na.beta = c->beta; na.delta = c->delta; na.cscale = cscale;
+    na.work = c->quad_work; na.work_stride = (size_t)4 * c->kmax * 2 * kQuadRetryMaxNodes;
+    if (nest_work_entries(c->kmax, m) > na.work_stride) return set_err(c, LQ_ERR_ARG, "nested inner size too large for the workspace");
+    na.istate = c->nest_state; na.ialpha = c->nest_alpha; na.ibeta = c->nest_beta; na.idelta = c->nest_delta;
+    na.snorm = c->nest_norm; na.sel = c->proj_sel;
+    LQ_CUDA(c, cudaMemcpyAsync(c->proj_sel, sel.data(), sizeof(int) * nb, cudaMemcpyHostToDevice, st));
+    LQ_CUDA(c, nest_factor(na, st));
+    c->launches += 1;
+    std::vector<int> bad(nb, 0);
+    std::vector<double> scal;
+    const double one = 1.0;
+    for (int pass = 0; pass < 2; ++pass) {
+        na.start = pass ? out : nullptr;
+        cudaEvent_t e = prof_begin(c, st);
+        LQ_CUDA(c, nest_lanczos(na, st));
+        prof_end(c, PC_NEWTON, e, st, 0);
+        NewtonArgs nw = newton_args(c, m, nb, newton_max_iter, newton_tol);
+        nw.state = c->nest_state; nw.alpha = c->nest_alpha; nw.beta = c->nest_beta; nw.delta = c->nest_delta;
+        LQ_CUDA(c, newton_init_tridiag(nw, st));
+        for (int s = 0; s < nb; ++s)
+            if (!sel[s]) LQ_CUDA(c, cudaMemcpyAsync(c->nx_scal + (size_t)s * 16 + NS_DONE, &one, sizeof(double), cudaMemcpyHostToDevice, st));
+        c->launches += 2;
+        int r = run_newton(c, nw, st, scal);
+        if (r) return r;
+        for (int s = 0; s < nb; ++s) if (sel[s] && scal[(size_t)s * 16 + NS_STATUS] != 0.0) bad[s] = 1;
+        LQ_CUDA(c, newton_first_column(nw, c->nest_s, c->kmax, st, c->proj_sel));
+        LQ_CUDA(c, nest_combine(na, c->nest_s, pass ? c->nest_q : out, st));
+        c->launches += 2;
+    }
+    LQ_CUDA(c, nest_check(na, c->nest_q, c->nest_check, st));
+    c->launches += 1;
+    check.assign(nb, 0.0);
+    LQ_CUDA(c, cudaMemcpyAsync(check.data(), c->nest_check, sizeof(double) * nb, cudaMemcpyDeviceToHost, st));
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    for (int s = 0; s < nb; ++s) if (bad[s]) check[s] = INFINITY;
     return LQ_OK;
 }
 
@@ -492,7 +542,7 @@ struct TslRun {
             q.s = c->proj_c; q.check = c->quad_check;
             LQ_CUDA(c, proj_resolvent(q, shifts, st));
             c->launches += 1;
-            for (int s = 0; s < nsrc; ++s) used[s] = 3;
+            for (int s = 0; s < nsrc; ++s) used[s] = -1;   // not a reported solver
             return LQ_OK;
         }
         if (o->projected == LQ_PROJ_NEWTON) return LQ_OK;
@@ -501,9 +551,35 @@ struct TslRun {
         qa.alpha = c->alpha; qa.beta = c->beta; qa.delta = c->delta; qa.c = c->quad_c; qa.work = c->quad_work;
         qa.s = c->proj_c; qa.q = c->quad_q; qa.check = c->quad_check; qa.nodes = c->quad_nodes;
         qa.nth_max = 2 * kQuadRetryMaxNodes; qa.part = c->quad_part; qa.part_blocks = 2 * kQuadRetryMaxNodes / kQuadBlk;
+        if (o->projected == LQ_PROJ_NESTED) {      // the scales c only; the nested passes need host decisions
+            LQ_CUDA(c, quad_scale(qa, st));
+            c->launches += 1;
+            return LQ_OK;
+        }
         nodes.assign(nsrc, o->quad_nodes);
         quad_attempt = 0;
         return quad_pass(st);
+    }
+
+    // The nested rung for the sources with sel[s] != 0; accepted ones leave sel and report the
+    // nested solver and its residual.  Returns whether any source is left.
+    int nested_rung(std::vector<int>& sel, cudaStream_t st, bool* left) {
+        *left = false;
+        bool any = false;
+        for (int s = 0; s < nsrc; ++s) any = any || sel[s];
+        if (!any) return LQ_OK;
+        const int m = std::max(1, std::min({o->nested_m > 0 ? o->nested_m : 100, k, c->kmax}));
+        std::vector<double> chk;
+        int r = nested_run(c, c->state, k, nsrc, m, c->quad_c, sel, c->proj_c, chk, o->newton_max_iter, o->newton_tol, st);
+        if (r) return r;
+        for (int s = 0; s < nsrc; ++s) {
+            if (!sel[s]) continue;
+            used[s] = LQ_PROJ_NESTED;
+            check[s] = chk[s];
+            if (std::isfinite(chk[s]) && chk[s] <= o->proj_tol) sel[s] = 0;
+            else *left = true;
+        }
+        return LQ_OK;
     }
 
     // LQ_PROJ_QUAD: one pass with opts.quad_nodes.  LQ_PROJ_AUTO: a source whose involution
@@ -535,11 +611,22 @@ struct TslRun {
             need_newton = !ok && o->projected == LQ_PROJ_AUTO;
             for (int s = 0; s < nsrc; ++s) used[s] = LQ_PROJ_QUAD;
         }
+        std::vector<int> sel(nsrc, 1);
+        if (o->projected == LQ_PROJ_AUTO && need_newton) {
+            // the nested rung for what the quadrature left, Newton for what it leaves
+            for (int s = 0; s < nsrc; ++s) sel[s] = !(std::isfinite(check[s]) && check[s] <= o->proj_tol);
+            bool left = false;
+            int r = nested_rung(sel, st, &left);
+            if (r) return r;
+            need_newton = left;
+        } else if (o->projected == LQ_PROJ_NESTED && fn == FN_SIGN) {
+            bool left = false;
+            int r = nested_rung(sel, st, &left);
+            if (r) return r;
+            need_newton = false;
+        }
         if (need_newton) {
-            // Newton for every source (LQ_PROJ_NEWTON) or only for those whose quadrature failed
-            std::vector<int> sel(nsrc, 1);
-            if (o->projected == LQ_PROJ_AUTO)
-                for (int s = 0; s < nsrc; ++s) sel[s] = !(std::isfinite(check[s]) && check[s] <= o->proj_tol);
+            // Newton for every source (LQ_PROJ_NEWTON) or only for those the other rungs left
             NewtonArgs na = newton_args(c, k, nsrc, o->newton_max_iter, o->newton_tol);
             LQ_CUDA(c, newton_init_tridiag(na, st));
             c->launches += 1;
@@ -584,7 +671,8 @@ struct TslRun {
             R.proj_check = check[s];   // involution residual of the quadrature when it was attempted
             const int ts = hs[s].status;
             int ns = (int)scal[(size_t)s * 16 + NS_STATUS];
-            if (used[s] == LQ_PROJ_QUAD && !(std::isfinite(check[s]) && check[s] <= o->proj_tol)) ns = LQ_ERR_NEWTON;
+            if ((used[s] == LQ_PROJ_QUAD || used[s] == LQ_PROJ_NESTED) && !(std::isfinite(check[s]) && check[s] <= o->proj_tol))
+                ns = LQ_ERR_NEWTON;
             R.status = ts < 0 ? ts : (ns != 0 ? ns : LQ_OK);
         }
         return LQ_OK;
@@ -829,7 +917,8 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->newton_max_iter < 1 || !(o->newton_tol > 0.0) || !(o->breakdown_tol >= 0.0)) return set_err(c, LQ_ERR_ARG, "invalid Newton / breakdown options");
     if (o->deflate != 0 && !allow_deflate) return set_err(c, LQ_ERR_ARG, "deflation is not available in this entry point");
     if (o->deflate != 0 && c->defl_l <= 0) return set_err(c, LQ_ERR_NOT_READY, "deflate = 1 but no deflation space uploaded");
-    if (o->projected < LQ_PROJ_AUTO || o->projected > LQ_PROJ_QUAD) return set_err(c, LQ_ERR_ARG, "unknown projected-sign solver");
+    if (o->projected < LQ_PROJ_AUTO || o->projected > LQ_PROJ_NESTED) return set_err(c, LQ_ERR_ARG, "unknown projected-sign solver");
+    if (o->nested_m < 0) return set_err(c, LQ_ERR_ARG, "nested_m must be >= 0");
     if (o->projected != LQ_PROJ_NEWTON && (o->quad_nodes < 1 || o->quad_nodes > kQuadMaxNodes || !(o->proj_tol > 0.0)))
         return set_err(c, LQ_ERR_ARG, "quad_nodes must be in [1, 128] and proj_tol > 0");
     if (o->hop_variant < -1 || o->hop_variant >= kHopSchedules)
@@ -1533,6 +1622,7 @@ void lq_default_opts(lq_opts* o) {
     o->two_pass = 0;
     o->graph = -1;
     o->split = -1;
+    o->nested_m = 100;
 }
 
 int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
@@ -1663,6 +1753,15 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     if ((r = dalloc(c, &c->quad_nodes, (size_t)nsrc))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->quad_part, (size_t)nsrc * (2 * kQuadRetryMaxNodes / kQuadBlk) * kmax))) { free_workspace(c); return r; }
     if ((r = dalloc(c, &c->proj_sel, (size_t)nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nest_state, (size_t)nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nest_alpha, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nest_beta, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nest_delta, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nest_s, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nest_q, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nest_norm, (size_t)nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nest_check, (size_t)nsrc))) { free_workspace(c); return r; }
+    if ((r = dalloc(c, &c->nest_c, (size_t)nsrc))) { free_workspace(c); return r; }
     {
         const int m = std::max(2 * nsrc, 64);   // dots among up to m x m vectors
         c->gen_scr_doubles = bdots_partial_doubles(m * m) + (size_t)2 * m * m;
@@ -1684,6 +1783,7 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     LQ_CUDA(c, cudaMemset(c->nx_counters, 0, sizeof(int) * 3 * nsrc));
     LQ_CUDA(c, cudaMemset(c->nx_scal, 0, sizeof(double) * 16 * nsrc));
     LQ_CUDA(c, cudaMemset(c->state, 0, sizeof(TslState) * nsrc));
+    LQ_CUDA(c, cudaMemset(c->nest_state, 0, sizeof(TslState) * nsrc));
     c->kmax = kmax;
     c->nsrc = nsrc;
     c->block = block;
@@ -2637,6 +2737,57 @@ int lq_newton_sign(lq_ctx* c, const double* X, double* S, int k, int nb, int max
         if (scal[(size_t)b * 16 + NS_STATUS] != 0.0) bad = 1;
     }
     return bad ? set_err(c, LQ_ERR_NEWTON, "Newton iteration did not converge for at least one matrix") : LQ_OK;
+}
+
+int lq_nested_sign(lq_ctx* c, const double* alpha, const double* beta, const double* delta, const double* scale, int k, int nb,
+                   int m, double* out, double* check, void* stream) {
+    if (!c || !alpha || (k > 1 && (!beta || !delta)) || !out) return set_err(c, LQ_ERR_ARG, "null argument");
+    if (!c->nest_state) return set_err(c, LQ_ERR_NOT_READY, "workspace not reserved (lq_reserve)");
+    if (k < 1 || k > c->kmax || nb < 1 || nb > c->nsrc || m < 1 || m > c->kmax)
+        return set_err(c, LQ_ERR_ARG, "k, nb or m outside the reserved workspace");
+    cudaStream_t st = (cudaStream_t)stream;
+    // the coefficients go to the context's rows (stride kmax); rows beyond k are not read
+    for (int b = 0; b < nb; ++b) {
+        const size_t o = (size_t)b * c->kmax;
+        auto kind = [](const void* p) { return is_device_ptr(p) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice; };
+        LQ_CUDA(c, cudaMemcpyAsync(c->alpha + o, alpha + (size_t)b * k * 2, sizeof(double2) * k, kind(alpha), st));
+        if (k > 1) {
+            LQ_CUDA(c, cudaMemcpyAsync(c->beta + o, beta + (size_t)b * (k - 1) * 2, sizeof(double2) * (k - 1), kind(beta), st));
+            LQ_CUDA(c, cudaMemcpyAsync(c->delta + o, delta + (size_t)b * (k - 1), sizeof(double) * (k - 1), kind(delta), st));
+        }
+    }
+    if (scale) {
+        LQ_CUDA(c, cudaMemcpyAsync(c->nest_c, scale, sizeof(double) * nb, is_device_ptr(scale) ? cudaMemcpyDeviceToDevice : cudaMemcpyHostToDevice, st));
+    } else {
+        // the quadrature's estimate, from per-source states of dimension k
+        std::vector<TslState> hs(nb);
+        std::memset(hs.data(), 0, sizeof(TslState) * nb);
+        for (auto& s : hs) s.k_eff = k;
+        LQ_CUDA(c, cudaMemcpyAsync(c->state, hs.data(), sizeof(TslState) * nb, cudaMemcpyHostToDevice, st));
+        QuadArgs qa;
+        std::memset(&qa, 0, sizeof(qa));
+        qa.k = k; qa.nb = nb; qa.kmax = c->kmax; qa.state = c->state;
+        qa.alpha = c->alpha; qa.beta = c->beta; qa.delta = c->delta; qa.c = c->nest_c; qa.work = c->quad_work;
+        qa.nth_max = 2 * kQuadRetryMaxNodes;
+        LQ_CUDA(c, quad_scale(qa, st));
+        LQ_CUDA(c, cudaStreamSynchronize(st));   // hs is host memory
+    }
+    std::vector<int> sel(nb, 1);
+    std::vector<double> chk;
+    int r = nested_run(c, nullptr, k, nb, m, c->nest_c, sel, c->proj_c, chk, 50, 1e-13, st);
+    if (r) return r;
+    for (int b = 0; b < nb; ++b) {
+        const size_t o = (size_t)b * c->kmax;
+        LQ_CUDA(c, cudaMemcpyAsync(out + (size_t)b * k * 2, c->proj_c + o, sizeof(double2) * k,
+                                   is_device_ptr(out) ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, st));
+    }
+    LQ_CUDA(c, cudaStreamSynchronize(st));
+    bool bad = false;
+    for (int b = 0; b < nb; ++b) {
+        if (check) check[b] = chk[b];
+        bad = bad || !std::isfinite(chk[b]);
+    }
+    return bad ? set_err(c, LQ_ERR_NEWTON, "an inner Newton iteration of the nested process did not converge") : LQ_OK;
 }
 
 }  // extern "C"

@@ -225,6 +225,16 @@ struct lq_ctx {
     int* quad_nodes = nullptr;       // [nsrc] nodes of the current quadrature pass per source
     double2* quad_part = nullptr;    // [nsrc][2 * 512 / 32][kmax] block row sums of the quadrature
     int* proj_sel = nullptr;         // [nsrc] sources finished by the Newton fallback
+    // nested projected sign: inner state and coefficients, its first columns and results
+    lq::TslState* nest_state = nullptr;   // [nsrc]
+    double2* nest_alpha = nullptr;        // [nsrc][kmax]
+    double2* nest_beta = nullptr;         // [nsrc][kmax]
+    double* nest_delta = nullptr;         // [nsrc][kmax]
+    double2* nest_s = nullptr;            // [nsrc][kmax] inner sgn(T') e_1
+    double2* nest_q = nullptr;            // [nsrc][kmax] second-pass result
+    double* nest_norm = nullptr;          // [nsrc]
+    double* nest_check = nullptr;         // [nsrc]
+    double* nest_c = nullptr;             // [nsrc] staged scales (lq_nested_sign)
     size_t partial_blocks = 0;       // capacity per source of the TSL partials
     size_t nx_partial_blocks = 0;
 

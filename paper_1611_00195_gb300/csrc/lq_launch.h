@@ -210,6 +210,29 @@ struct AdjArgs {
 cudaError_t launch_adjoint(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,
                            size_t lbasis_vec_stride, int k, cudaStream_t st);
 
+// Nested two-sided Lanczos projected sign (lq_nested.cu)
+struct NestArgs {
+    int nb;                // sources
+    int kmax;              // row stride of every per-source array
+    int kfix;              // k when state is null
+    int m;                 // inner steps
+    const TslState* state; // outer k_eff per source, or null
+    const double2* alpha; const double2* beta; const double* delta;   // outer T (stride kmax)
+    const double* cscale;  // [nb] c of M = T/c + c T^{-1}
+    double2* work;         // per source nest_work_entries(kmax, m) complex entries
+    size_t work_stride;
+    const double2* start;  // [nb][kmax] start vector, or null for e_1
+    TslState* istate;      // [nb] inner: k_eff, status
+    double2* ialpha; double2* ibeta; double* idelta;   // [nb][kmax] inner coefficients
+    double* snorm;         // [nb] |start|
+    const int* sel;        // [nb] sources to process, or null for all
+};
+size_t nest_work_entries(int kmax, int m);
+cudaError_t nest_factor(const NestArgs& a, cudaStream_t st);
+cudaError_t nest_lanczos(const NestArgs& a, cudaStream_t st);
+cudaError_t nest_combine(const NestArgs& a, const double2* sp, double2* out, cudaStream_t st);
+cudaError_t nest_check(const NestArgs& a, const double2* q, double* check, cudaStream_t st);
+
 // Quadrature projected sign (lq_newton.cu)
 struct QuadArgs {
     int k;                 // padded dimension
@@ -234,6 +257,7 @@ constexpr int kQuadFinish = 256;          // threads of the summing kernel
 // sgn(T) e_1 and the involution check for the sources with a.nodes[src] > 0 (at most max_nodes;
 // contour scales recomputed when `scale`).  a.work needs 2 * max_nodes columns (nth_max).
 cudaError_t quad_sign_e1(const QuadArgs& a, int max_nodes, bool scale, cudaStream_t st);
+cudaError_t quad_scale(const QuadArgs& a, cudaStream_t st);   // contour scales c only
 // c = (sigma_src - T)^{-1} e_1 into a.s (per-source complex shifts, device array)
 cudaError_t proj_resolvent(const QuadArgs& a, const double2* shifts, cudaStream_t st);
 cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st, const int* sel = nullptr);

@@ -563,6 +563,11 @@ cudaError_t quad_sign_e1(const QuadArgs& a, int max_nodes, bool scale, cudaStrea
     return cudaGetLastError();
 }
 
+cudaError_t quad_scale(const QuadArgs& a, cudaStream_t st) {
+    k_quad_scale<<<a.nb, 32, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
 cudaError_t newton_first_column(const NewtonArgs& a, double2* out, int ldo, cudaStream_t st, const int* sel) {
     k_nt_first_column<<<dim3((unsigned)((a.k + 127) / 128), (unsigned)a.nb), 128, 0, st>>>(a, out, ldo, sel);
     return cudaGetLastError();

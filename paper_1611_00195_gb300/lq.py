@@ -32,13 +32,13 @@ ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_C
           -10: "LQ_ERR_NOT_CONVERGED"}
 LQ_FP64, LQ_MIXED = 0, 1
 LQ_DIR_MU, LQ_DIR_SU3, LQ_DIR_U1 = 0, 1, 2
-LQ_PROJ_AUTO, LQ_PROJ_NEWTON, LQ_PROJ_QUAD = 0, 1, 2
+LQ_PROJ_AUTO, LQ_PROJ_NEWTON, LQ_PROJ_QUAD, LQ_PROJ_NESTED = 0, 1, 2, 3
 LQ_EIG_SHIFT_INVERT, LQ_EIG_CHEBYSHEV = 0, 1
 
 EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_upload_gauge", "lq_set_mu",
             "lq_reserve", "lq_apply_H", "lq_set_direction", "lq_apply_block", "lq_sign_apply",
             "lq_sign_derivative_apply", "lq_tsl_coefficients", "lq_newton_sign", "lq_profile_enable",
-            "lq_profile_read", "lq_newton_sign_noalloc", "lq_error_estimate",
+            "lq_profile_read", "lq_newton_sign_noalloc", "lq_nested_sign", "lq_error_estimate",
             "lq_upload_deflation", "lq_deflation_derivatives", "lq_sign_bilinear_grad",
             "lq_dense_eig", "lq_compute_deflation", "lq_eig_stats_read", "lq_overlap_apply", "lq_batch_apply", "lq_overlap_solve",
             "lq_axial_current"]
@@ -55,7 +55,7 @@ class Opts(ctypes.Structure):
                 ("newton_tol", ctypes.c_double), ("deflate", ctypes.c_int), ("projected", ctypes.c_int),
                 ("quad_nodes", ctypes.c_int), ("proj_tol", ctypes.c_double), ("hop_variant", ctypes.c_int),
                 ("defl_kmax", ctypes.c_int), ("defl_nderiv", ctypes.c_int), ("two_pass", ctypes.c_int),
-                ("graph", ctypes.c_int), ("split", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("split", ctypes.c_int), ("nested_m", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -143,6 +143,7 @@ def lib():
         L.lq_profile_enable.argtypes = [P, I]
         L.lq_profile_read.argtypes = [P, ctypes.POINTER(Profile)]
         L.lq_newton_sign.argtypes = [P, P, P, I, I, I, D, ctypes.POINTER(I), P]
+        L.lq_nested_sign.argtypes = [P, P, P, P, P, I, I, I, P, P, P]
         L.lq_error_estimate.argtypes = [P, ctypes.POINTER(Direction), P, I, ctypes.POINTER(Opts), P, P]
         L.lq_upload_deflation.argtypes = [P, I, P, P, P, P]
         L.lq_deflation_derivatives.argtypes = [P, ctypes.POINTER(Direction), ctypes.POINTER(Opts), P, P, P, P]
@@ -374,7 +375,8 @@ class Context:
 
     @staticmethod
     def opts(k, breakdown_tol=1e-14, newton_max_iter=50, newton_tol=1e-13, projected=LQ_PROJ_AUTO, quad_nodes=64,
-             proj_tol=1e-11, hop_variant=-1, deflate=0, defl_kmax=0, defl_nderiv=0, two_pass=0, graph=-1, split=-1):
+             proj_tol=1e-11, hop_variant=-1, deflate=0, defl_kmax=0, defl_nderiv=0, two_pass=0, graph=-1, split=-1,
+             nested_m=100):
         o = Opts()
         lib().lq_default_opts(ctypes.byref(o))
         o.kmax = int(k)
@@ -391,6 +393,7 @@ class Context:
         o.two_pass = int(two_pass)
         o.graph = int(graph)
         o.split = int(split)
+        o.nested_m = int(nested_m)
         return o
 
     def sign_apply(self, x, k, out=None, **kw):
@@ -543,6 +546,20 @@ class Context:
                                              _stream(x))
         self._check(code)
         return eps
+
+    def nested_sign(self, alpha, beta, delta, m, scale=None):
+        """sgn(T) e_1 of tridiagonal T (alpha [nb][k] diagonal, beta [nb][k-1] super, delta
+        [nb][k-1] real sub-diagonal) by the nested two-sided Lanczos process (inner size m, scale c
+        per matrix or the library's estimate); returns (s [nb][k], involution residual [nb])."""
+        alpha, beta = _as_c128(alpha), _as_c128(beta)
+        delta = _as_f64(delta)
+        nb, k = alpha.shape[0], alpha.shape[1]
+        out = _empty_like(alpha)
+        chk = np.zeros(nb, np.float64)
+        sc = None if scale is None else _as_f64(scale)
+        self._check(self._L.lq_nested_sign(self._h, _ptr(alpha), _ptr(beta), _ptr(delta), _ptr(sc), int(k), int(nb), int(m),
+                                           _ptr(out), _ptr(chk), _stream(alpha)))
+        return out, chk
 
     def newton_sign(self, X, max_iter=50, tol=1e-13):
         """Batched dense sign of complex k x k matrices X [nb][k][k] (CUDA tensor)."""
