@@ -56,6 +56,12 @@ extern "C" {
 #define LQ_FP64   0   /* stencil, vectors, dots, scalars and Newton all in FP64                */
 #define LQ_MIXED  1   /* FP32 links, spinors and stencil (FP32 accumulation); FP64 compensated
                          dots, FP64 Lanczos coefficients, FP64 Newton, FP64 recombination      */
+#define LQ_MIXED_BF16 2 /* as LQ_MIXED with the links stored in BF16 (real and imaginary parts,
+                         4 bytes per complex entry).  The uploaded links are rounded once, FP64
+                         -> FP32 (nearest) -> BF16 (nearest even), and every operator of the
+                         context (stencil, derivative directions, adjoint force, eigensolver)
+                         uses the rounded links: H(mu) of the rounded gauge field.  Stencil
+                         schedules 6-8 are not available (schedule 3 runs instead)          */
 
 /* ---- derivative directions (d_t of Eq. (2.5)) --------------------------------------- */
 #define LQ_DIR_MU   0   /* d/dmu: field unused                                               */
@@ -72,7 +78,7 @@ typedef struct {
     double r;              /* Wilson parameter; only r = 1 is supported (spin projectors)     */
     double mu;             /* chemical potential                                              */
     int t_antiperiodic;    /* 1: antiperiodic in time (default), 0: periodic                  */
-    int precision;         /* LQ_FP64 or LQ_MIXED                                             */
+    int precision;         /* LQ_FP64, LQ_MIXED or LQ_MIXED_BF16                              */
 } lq_lattice_desc;
 
 typedef struct {

@@ -145,6 +145,7 @@ HopArgs base_hop(const lq_ctx* c) {
     a.diag = 4.0 * c->desc.r + c->desc.m_w;
     a.diag_f = (float)a.diag;
     a.U = c->U;
+    a.link_bf16 = c->link_bf16 ? 1 : 0;
     a.Y = c->Y;
     a.Up = c->Up;
     a.Yp = c->Yp;
@@ -271,7 +272,7 @@ void free_workspace(lq_ctx* c) {
 // coefficients), so the tuning leaves no trace in the results.
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
-    const int nvar = (c->prec == LQ_FP64) ? 2 : kHopSchedules;
+    const int nvar = (c->prec == LQ_FP64) ? 2 : (c->link_bf16 ? 6 : kHopSchedules);   // BF16 links: 0-5
     for (const auto& t : c->tuned)
         if (t.nsrc == h.nsrc && t.nf == nf && t.emode == emode) { *variant = t.variant; return LQ_OK; }
     h.j = 0;
@@ -450,6 +451,7 @@ struct TslRun {
             int v = (nf == 2) ? o->hop_variant : 0;
             if (c->prec == LQ_FP64 && v > 1) v = 0;
             if (v == 6 && !tile_ok(h.dims)) v = 3;
+            if (c->link_bf16 && v >= 6) v = 3;
             h.variant = v;
         } else {
             h.in[0] = bvec(0);
@@ -1123,6 +1125,7 @@ int apply_H_batch(lq_ctx* c, const double* in, double* out, int count, int dagge
         LQ_CUDA(c, launch_to_internal(prec, in + (size_t)b0 * nv, c->rout, c->V, nb, st));
         HopArgs a = base_hop(c);
         a.U = links;
+        a.link_bf16 = (links == c->U && c->link_bf16) ? 1 : 0;
         a.nsrc = nb;
         a.nsides = 1;
         a.side0 = 0;
@@ -1292,7 +1295,8 @@ struct SiWork {
 int si_apply32(SiWork& w, const float4* in, float4* out, bool adjoint) {
     lq_ctx* c = w.c;
     HopArgs a = base_hop(c);
-    a.U = w.links32;
+    a.U = w.links32;             // always FP32 entries (a BF16 context gets an FP32 copy)
+    a.link_bf16 = 0;
     a.Up = nullptr; a.Y = nullptr; a.Yp = nullptr;
     a.nsrc = 1; a.nsides = 2; a.side0 = 0;
     set_side(a, 0, c, 0, 0);
@@ -1630,7 +1634,7 @@ int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
     *out = nullptr;
     if (d->nt < 1 || d->nx < 1 || d->ny < 1 || d->nz < 1) return LQ_ERR_ARG;
     if (d->r != 1.0) return LQ_ERR_ARG;
-    if (d->precision != LQ_FP64 && d->precision != LQ_MIXED) return LQ_ERR_ARG;
+    if (d->precision != LQ_FP64 && d->precision != LQ_MIXED && d->precision != LQ_MIXED_BF16) return LQ_ERR_ARG;
     if (!std::isfinite(d->mu) || !std::isfinite(d->m_w)) return LQ_ERR_ARG;
     const double vol = (double)d->nt * d->nx * d->ny * d->nz;
     if (vol * 12.0 > 4.0e9) return LQ_ERR_ARG;
@@ -1639,7 +1643,8 @@ int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
     c->desc = *d;
     c->dims[0] = d->nx; c->dims[1] = d->ny; c->dims[2] = d->nz; c->dims[3] = d->nt;
     c->V = (size_t)d->nt * d->nx * d->ny * d->nz;
-    c->prec = d->precision;
+    c->prec = d->precision == LQ_FP64 ? LQ_FP64 : LQ_MIXED;
+    c->link_bf16 = d->precision == LQ_MIXED_BF16;
     cudaGetDevice(&c->device);
     *out = c;
     return LQ_OK;
@@ -1669,16 +1674,22 @@ int lq_upload_gauge(lq_ctx* c, const double* U, void* stream) {
     const size_t n = c->V * 4 * 9 * 2;
     if (!c->Ub) { int r = dalloc(c, &c->Ub, n); if (r) return r; }
     if (!c->U) {
-        size_t cb = (c->prec == LQ_FP64 ? sizeof(double2) : sizeof(float2)) * c->V * 36;
+        // FP64: double2, FP32: float2, BF16: two bfloat16 (4 bytes) per complex entry
+        size_t cb = (c->prec == LQ_FP64 ? sizeof(double2) : (c->link_bf16 ? (size_t)4 : sizeof(float2))) * c->V * 36;
         void* p = nullptr;
         if (cudaMalloc(&p, cb) != cudaSuccess) { cudaGetLastError(); return set_err(c, LQ_ERR_OOM, "gauge allocation failed"); }
         c->U = p;
     }
     int r = stage_in(c, c->Ub, U, n, st);
     if (r) return r;
-    LQ_CUDA(c, launch_links_internal(c->prec, c->Ub, c->U, c->V, st));
+    if (c->link_bf16) {
+        // round the FP64 copy to the stored BF16 values: every operator of the context uses them
+        LQ_CUDA(c, launch_links_bf16(c->Ub, c->U, c->V, st));
+    } else {
+        LQ_CUDA(c, launch_links_internal(c->prec, c->Ub, c->U, c->V, st));
+    }
     c->launches += 1;
-    if (c->prec != LQ_FP64) {   // the packed stencil's copy of the FP32 links
+    if (c->prec != LQ_FP64 && !c->link_bf16) {   // the packed stencil's copy of the FP32 links
         if (!c->Up && cudaMalloc(&c->Up, sizeof(float4) * c->V * 36) != cudaSuccess) {
             cudaGetLastError();
             c->Up = nullptr;
@@ -1688,6 +1699,7 @@ int lq_upload_gauge(lq_ctx* c, const double* U, void* stream) {
         c->launches += 1;
     }
     c->gauge_ready = true;
+    ++c->defl_version;
     if (c->dir_kind == LQ_DIR_SU3 || c->dir_kind == LQ_DIR_U1) c->dir_kind = -1;   // Y is stale
     return LQ_OK;
 }
@@ -1699,6 +1711,7 @@ int lq_set_mu(lq_ctx* c, double mu) {
 }
 
 int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
+    if (c) c->defl_prep_ok = false;
     if (!c || kmax < 1 || nsrc < 1 || (flags & ~(LQ_RESERVE_BLOCK | LQ_RESERVE_ADJOINT | LQ_RESERVE_TWO_PASS | LQ_RESERVE_SOLVE)))
         return set_err(c, LQ_ERR_ARG, "invalid reserve arguments");
     if ((flags & LQ_RESERVE_TWO_PASS) && (flags & LQ_RESERVE_ADJOINT))
@@ -1933,8 +1946,21 @@ int sign_derivative_core(lq_ctx* c, const lq_direction* dir, const double* x, in
         // generalised deflation, Eqs. (3.2)-(3.4), for psi = (0, x):
         //   Pbar psi = (-sum_i [R_i <dLk_i|x> + dR_i <Lk_i|x>],  x - sum_i R_i <Lk_i|x>)
         //   exact    = ( sum_i sgn_i [R_i <dLk_i|x> + dR_i <Lk_i|x>],  sum_i sgn_i R_i <Lk_i|x>)
-        if ((r = prepare_deflation_derivative(c, o, st))) return r;
         const int ld = nderiv_of(c, o);   // Jordan blocks used (coefficients of the other pairs stay 0)
+        const int kd = o->defl_kmax > 0 ? o->defl_kmax : c->kmax;
+        const bool cached = c->dir_kind == LQ_DIR_MU && c->defl_prep_ok && c->defl_prep_version == c->defl_version &&
+                            c->defl_prep_mu == c->desc.mu && c->defl_prep_ld == ld && c->defl_prep_kd == kd;
+        if (!cached) {
+            c->defl_prep_ok = false;
+            if ((r = prepare_deflation_derivative(c, o, st))) return r;
+            if (c->dir_kind == LQ_DIR_MU) {
+                c->defl_prep_ok = true;
+                c->defl_prep_version = c->defl_version;
+                c->defl_prep_mu = c->desc.mu;
+                c->defl_prep_ld = ld;
+                c->defl_prep_kd = kd;
+            }
+        }
         std::vector<double2> cd;   // [2l][nsrc]: <Lk_i|x>, then <dLk_i|x>
         if ((r = bdots_host(c, c->defl_W, 2 * l, c->io, nsrc, cd, st))) return r;
         double* xt = c->io + 3 * reg;
@@ -2309,6 +2335,7 @@ int lq_profile_read(lq_ctx* c, lq_profile* o) {
 }
 
 int lq_upload_deflation(lq_ctx* c, int l, const double* lambda, const double* R, const double* L, void* stream) {
+    if (c) { ++c->defl_version; c->defl_prep_ok = false; }
     if (!c || l < 0) return set_err(c, LQ_ERR_ARG, "invalid deflation arguments");
     if (l == 0) { c->defl_l = 0; return LQ_OK; }
     if (!lambda || !R || !L) return set_err(c, LQ_ERR_ARG, "null deflation data");
@@ -2339,6 +2366,7 @@ int lq_upload_deflation(lq_ctx* c, int l, const double* lambda, const double* R,
 }
 
 int lq_compute_deflation(lq_ctx* c, const lq_eig_opts* eo_in, const double* X0, double* lambda, double* resid, void* stream) {
+    if (c) { ++c->defl_version; c->defl_prep_ok = false; }
     if (!c || !eo_in || !X0) return set_err(c, LQ_ERR_ARG, "null argument");
     lq_eig_opts eo = *eo_in;
     const bool si = eo.method == LQ_EIG_SHIFT_INVERT;
@@ -2380,7 +2408,8 @@ int lq_compute_deflation(lq_ctx* c, const lq_eig_opts* eo_in, const double* X0, 
         if (cudaMalloc(&U64, sizeof(double2) * c->V * 36) != cudaSuccess) { cudaGetLastError(); U64 = nullptr; return fail(set_err(c, LQ_ERR_OOM, "eigensolver links")); }
         cudaError_t e = launch_links_internal(LQ_FP64, c->Ub, U64, c->V, st);
         if (e != cudaSuccess) return fail(set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e)));
-    } else if (si) {
+    }
+    if (si && (c->prec == LQ_FP64 || c->link_bf16)) {   // FP32 links for the inner solves
         if (cudaMalloc(&U32, sizeof(float2) * c->V * 36) != cudaSuccess) { cudaGetLastError(); U32 = nullptr; return fail(set_err(c, LQ_ERR_OOM, "eigensolver links")); }
         cudaError_t e = launch_links_internal(LQ_MIXED, c->Ub, U32, c->V, st);
         if (e != cudaSuccess) return fail(set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e)));
@@ -2516,6 +2545,7 @@ int lq_eig_stats_read(const lq_ctx* c, lq_eig_stats* out) {
 
 int lq_deflation_derivatives(lq_ctx* c, const lq_direction* dir, const lq_opts* o, double* dlambda, double* dR,
                              double* dL, void* stream) {
+    if (c) c->defl_prep_ok = false;   // the derivatives below are along its own direction
     if (!c || !dir) return set_err(c, LQ_ERR_ARG, "null argument");
     if (c->defl_l <= 0) return set_err(c, LQ_ERR_NOT_READY, "no deflation space uploaded");
     int r = check_ready(c, 1, 1);

@@ -177,7 +177,8 @@ struct lq_ctx {
     lq_lattice_desc desc;
     int dims[4];           // nx, ny, nz, nt (direction order x, y, z, t)
     size_t V = 0;
-    int prec = LQ_FP64;
+    int prec = LQ_FP64;              // LQ_FP64 or LQ_MIXED (the arithmetic of every kernel)
+    bool link_bf16 = false;          // LQ_MIXED_BF16: the stencil's links stored in BF16
     int device = 0;
     std::string err;
 
@@ -262,6 +263,13 @@ struct lq_ctx {
     size_t gen_scr_doubles = 0;
     double2* defl_shift = nullptr;   // [nsrc] resolvent shifts
     double defl_resid = 0.0;         // largest relative residual of the last shifted solves
+    // the eigenvector derivatives of the generalised deflation along d/dmu are kept until the
+    // space, the links, mu, the Jordan blocks or the shifted-solve depth change
+    long long defl_version = 0;      // bumped by every change of the space or the links
+    bool defl_prep_ok = false;
+    long long defl_prep_version = -1;
+    double defl_prep_mu = 0.0;
+    int defl_prep_ld = 0, defl_prep_kd = 0, defl_prep_prec = 0;
     lq_eig_stats eig_stats{};        // statistics of the last lq_compute_deflation
 
     // stencil autotuning: chosen variant per (batch size, nf, emode) of the Lanczos step

@@ -28,9 +28,8 @@ __device__ __forceinline__ void do_hop(const HopArgs& a, int side, size_t V, siz
     constexpr bool DAG = SP > 0;   // backward hop uses the adjoint link at x - nu
     const R fa = fac_a<R>(a, side, NU, SP < 0) * bsign;
     const R fe = fac_e<R>(a, side, NU, SP < 0) * bsign;
-    const C* __restrict__ Lu = reinterpret_cast<const C*>(a.U);
     C u[9];
-    load_link(Lu, V, NU, lsite, u);
+    load_gauge(a, V, NU, lsite, u);
     C psi[12], h0[6], g[6];
     load_spinor(in0, V, nb, psi);
     project<C, NU, SP>(psi, h0);
@@ -197,7 +196,7 @@ __device__ __forceinline__ void role_hop(const HopArgs& a, int side, bool with_e
     const R fa = fac_a<R>(a, side, NU, SP < 0) * bsign;
     const bool ehop = with_e && (EMODE == 2 || (EMODE == 1 && NU == 3));
     C u[9], psi[12], h[6], g[6];
-    load_link(reinterpret_cast<const C*>(a.U), V, NU, lsite, u);
+    load_gauge(a, V, NU, lsite, u);
     load_spinor(fa_in, V, nb, psi);
     project<C, NU, SP>(psi, h);
     hscale(h, fa);
@@ -1014,6 +1013,24 @@ __global__ void k_links_internal(const double2* __restrict__ U, typename Tr<R>::
     }
 }
 
+// BF16 link storage: the FP64 boundary links are rounded in place (FP64 -> FP32 nearest -> BF16
+// nearest even -> exact back to FP64), so that every FP64 user of them sees the stored values;
+// the internal copy holds the BF16 pairs.
+__global__ void k_links_bf16(double2* __restrict__ U, __nv_bfloat162* __restrict__ L, size_t V) {
+    const size_t s = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    const int nu = blockIdx.y;
+    if (s >= V) return;
+#pragma unroll
+    for (int e = 0; e < 9; ++e) {
+        double2* p = U + ((size_t)nu * V + s) * 9 + e;
+        const double2 z = *p;
+        const __nv_bfloat162 b = __floats2bfloat162_rn((float)z.x, (float)z.y);
+        const float2 r = __bfloat1622float2(b);
+        *p = make_double2((double)r.x, (double)r.y);
+        L[((size_t)nu * 9 + e) * V + s] = b;
+    }
+}
+
 // dU/dt = i Omega U with Omega = sum_a w^a lambda_a / 2 (su(3)) or theta * 1 (U(1)).
 // U (FP64 boundary copy), w: [4][V][8] or [4][V]; output Y internal.
 template <typename R>
@@ -1118,6 +1135,11 @@ static cudaError_t launch_tiled_t(const HopArgs& a, int emode, bool dot, cudaStr
 //   8: as 7 with the next hop's neighbour spinors prefetched into shared memory
 cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st) {
     const bool lanczos_block = nf == 2 && a.nsides == 2 && a.side0 == 0;
+    if (a.link_bf16 && a.variant >= 6) {     // schedules 6-8 read FP32 links: BF16 links run 3
+        HopArgs b = a;
+        b.variant = 3;
+        return launch_hop(prec, b, nf, emode, dot, st);
+    }
     if (lanczos_block && prec != LQ_FP64 && (a.variant == 7 || a.variant == 8))
         return launch_hop_x2(a, emode, dot, a.variant == 8, st);
     if (lanczos_block && prec != LQ_FP64 && a.variant == 6) {
@@ -1195,6 +1217,12 @@ cudaError_t launch_to_boundary(int prec, const void* f, double* x, size_t V, int
     dim3 grid((unsigned)((V + 127) / 128), (unsigned)nfields);
     if (prec == LQ_FP64) k_to_boundary<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(f), reinterpret_cast<double2*>(x), V, nfields);
     else k_to_boundary<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float4*>(f), reinterpret_cast<double2*>(x), V, nfields);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_links_bf16(double* U, void* L, size_t V, cudaStream_t st) {
+    dim3 grid((unsigned)((V + 127) / 128), 4);
+    k_links_bf16<<<grid, 128, 0, st>>>(reinterpret_cast<double2*>(U), reinterpret_cast<__nv_bfloat162*>(L), V);
     return cudaGetLastError();
 }
 

@@ -30,6 +30,7 @@ struct HopArgs {
     float diag_f;
     const void* U;         // links (internal)
     const void* Y;         // dU/dt (internal), EMODE 2
+    int link_bf16;         // FP32 kernels: U holds __nv_bfloat162 entries instead of float2
     const void* Up;        // FP32 links pre-broadcast as float4 (ux, ux, -uy, uy) (schedules 7, 8)
     const void* Yp;        // the same for dU/dt
     const void* in[2];     // per side: NF consecutive fields of source 0
@@ -127,6 +128,9 @@ cudaError_t launch_recombine(int prec, int nf, const RecArgs& a, cudaStream_t st
 cudaError_t launch_to_internal(int prec, const double* x, void* f, size_t V, int nfields, cudaStream_t st);
 cudaError_t launch_to_boundary(int prec, const void* f, double* x, size_t V, int nfields, cudaStream_t st);
 cudaError_t launch_links_internal(int prec, const double* U, void* L, size_t V, cudaStream_t st);
+// BF16 link storage: round the boundary-layout FP64 links in place (FP64 -> FP32 -> BF16, nearest
+// even) and write the internal BF16 copy [4][9][V] of __nv_bfloat162
+cudaError_t launch_links_bf16(double* U, void* L, size_t V, cudaStream_t st);
 cudaError_t launch_direction(int prec, const double* U, const double* w, int kind, void* Y, size_t V, cudaStream_t st);
 unsigned update_grid(size_t nelem, int nsrc, size_t cap);
 // Deflation vector algebra on FP64 boundary-layout vectors (lq_deflate.cu).  Sizes and strides

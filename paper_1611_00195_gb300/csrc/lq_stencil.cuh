@@ -2,6 +2,8 @@
 // accumulators for the inner products, block / grid reductions, and the spin-colour algebra of
 // one Wilson hop (projection to half spinors, SU(3) multiply, reconstruction).
 #pragma once
+#include <cuda_bf16.h>
+
 #include "lq_internal.cuh"
 #include "lq_launch.h"
 
@@ -231,6 +233,19 @@ template <typename C>
 __device__ __forceinline__ void load_link(const C* __restrict__ L, size_t V, int nu, size_t s, C (&u)[9]) {
 #pragma unroll
     for (int e = 0; e < 9; ++e) u[e] = __ldg(L + ((size_t)nu * 9 + e) * V + s);
+}
+// The gauge links of the operator: FP32 or FP64 entries, or BF16 pairs widened to FP32.
+__device__ __forceinline__ void load_gauge(const HopArgs& a, size_t V, int nu, size_t s, double2 (&u)[9]) {
+    load_link(reinterpret_cast<const double2*>(a.U), V, nu, s, u);
+}
+__device__ __forceinline__ void load_gauge(const HopArgs& a, size_t V, int nu, size_t s, float2 (&u)[9]) {
+    if (a.link_bf16) {
+        const __nv_bfloat162* L = reinterpret_cast<const __nv_bfloat162*>(a.U);
+#pragma unroll
+        for (int e = 0; e < 9; ++e) u[e] = __bfloat1622float2(__ldg(L + ((size_t)nu * 9 + e) * V + s));
+    } else {
+        load_link(reinterpret_cast<const float2*>(a.U), V, nu, s, u);
+    }
 }
 
 template <typename C>

@@ -20,6 +20,19 @@ FP32_DEEP_SENS_FACTOR = 60.0
 ADJ_SENS_FACTOR = 18.0
 
 
+def round_bf16(a):
+    """Complex FP64 array -> the values of its BF16 storage: each real part rounded to FP32
+    (nearest), then to BF16 (8-bit significand, nearest even on the FP32 bit pattern), back to
+    FP64 exactly.  An input transformation for the BF16-link tests (no method arithmetic)."""
+    a = np.asarray(a, dtype=np.complex128)
+
+    def r(x):
+        b = np.ascontiguousarray(x, dtype=np.float64).astype(np.float32).view(np.uint32).astype(np.uint64)
+        b = (b + 0x7FFF + ((b >> 16) & 1)) & 0xFFFF0000
+        return b.astype(np.uint32).view(np.float32).astype(np.float64)
+    return r(a.real) + 1j * r(a.imag)
+
+
 def relerr(a, b):
     a = np.asarray(a).ravel()
     b = np.asarray(b).ravel()
