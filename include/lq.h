@@ -114,7 +114,9 @@ typedef struct {
                               the second reruns the (deterministic) process and recombines
                               windows of 16 vectors as they appear; twice the operator work.
                               Required for kmax beyond the ring of a LQ_RESERVE_TWO_PASS
-                              workspace; not available to lq_sign_bilinear_grad (default 0) */
+                              workspace.  lq_sign_bilinear_grad (without deflation) keeps rings
+                              of the right and the left basis and accumulates the pair vectors
+                              of the force window by window in its second pass (default 0)  */
     int graph;             /* -1 / 1: the Krylov loop (2k - 1 launches) is captured once per
                               configuration into a CUDA graph and replayed (default -1); 0:
                               plain launches.  Off while lq_profile_enable times kernels.  The
@@ -191,7 +193,8 @@ int  lq_set_mu(lq_ctx* ctx, double mu);
  * LQ_RESERVE_BLOCK for the derivative path (2n-dimensional block vectors of Eq. (2.6)),
  * LQ_RESERVE_ADJOINT for lq_sign_bilinear_grad (stored left basis, nsrc >= 2); 0 for the sign
  * path only.  LQ_RESERVE_TWO_PASS keeps a ring of 32 basis vectors per source instead of kmax
- * (runs deeper than 32 then need lq_opts.two_pass = 1; not with LQ_RESERVE_ADJOINT).  No later
+ * (runs deeper than 32 then need lq_opts.two_pass = 1; with LQ_RESERVE_ADJOINT the stored left
+ * basis becomes a ring of 32 as well).  No later
  * solve call allocates device memory.  LQ_ERR_OOM on failure. */
 #define LQ_RESERVE_BLOCK    1
 #define LQ_RESERVE_ADJOINT  2
@@ -413,7 +416,11 @@ int  lq_profile_read(lq_ctx* ctx, lq_profile* out);
  * exactly (divided differences of sgn at the eigenvalues), the two mixed blocks through
  * (sgn z - sgn lambda_j) / (z - lambda_j) of the two Lanczos runs, and the rest by the Krylov route
  * on the deflated sources Pbar x, Pbar^H y; S is deflated by Eq. (3.1).  This needs
- * 2 quad_nodes + 3 l <= 256.  x, y: one field each (host or device); S, dS_dmu: host double*; force:
+ * 2 quad_nodes + 3 l <= 256.  With opts->two_pass = 1 (no deflation; workspace reserved with
+ * LQ_RESERVE_ADJOINT | LQ_RESERVE_TWO_PASS) both processes run twice with rings of 32 right and
+ * left basis vectors: the first pass gives T_1, T_2 and the projected sign, the second reruns them
+ * and accumulates the 2N pair vectors of the contraction window by window (O(n) memory, twice
+ * the operator work).  x, y: one field each (host or device); S, dS_dmu: host double*; force:
  * double[4][V][8] (host or device, may be NULL).  Needs lq_reserve(kmax, nsrc >= 2,
  * LQ_RESERVE_ADJOINT).  Synchronises `stream`. */
 int  lq_sign_bilinear_grad(lq_ctx* ctx, const double* x, const double* y, const lq_opts* opts,

@@ -260,6 +260,61 @@ __global__ void __launch_bounds__(128) k_recomb_multi(const typename Tr<R>::Chun
     }
 }
 
+// The same over a window [j0, j1) of Krylov indices whose vectors sit in ring slots j % ring
+// (the second pass of a two-pass run), added to out (accumulate) or written.  FP64 accumulation
+// within the window for both precisions; the window sums are added in FP64 (FP32 fields are
+// widened, added, and rounded once per window).
+template <typename R>
+__global__ void __launch_bounds__(128) k_recomb_window(const typename Tr<R>::Chunk* __restrict__ basis, size_t vec_stride,
+                                                       int j0, int j1, int ring, const double2* __restrict__ coef, int kmax,
+                                                       int nq, typename Tr<R>::Chunk* __restrict__ out, size_t F, int accumulate) {
+    using Chunk = typename Tr<R>::Chunk;
+    __shared__ double2 sc[kQB * kTwoPassRing];
+    const int q0 = blockIdx.y * kQB;
+    const int w = j1 - j0;
+    for (int i = threadIdx.x; i < kQB * w; i += blockDim.x) {
+        const int qq = i / w, j = i % w;
+        sc[i] = (q0 + qq < nq) ? coef[(size_t)(q0 + qq) * kmax + j0 + j] : make_double2(0.0, 0.0);
+    }
+    __syncthreads();
+    const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (e >= F) return;
+    constexpr int PC = Tr<R>::kPerChunk;     // complex numbers per chunk
+    double2 acc[kQB][PC];
+#pragma unroll
+    for (int qq = 0; qq < kQB; ++qq)
+#pragma unroll
+        for (int p = 0; p < PC; ++p) acc[qq][p] = make_double2(0.0, 0.0);
+    for (int j = 0; j < w; ++j) {
+        const int slot = ring > 0 ? (j0 + j) % ring : j0 + j;
+        const Chunk v = basis[(size_t)slot * vec_stride + e];
+        double2 vv[PC];
+        if constexpr (PC == 1) vv[0] = make_double2((double)reinterpret_cast<const double2&>(v).x, (double)reinterpret_cast<const double2&>(v).y);
+        else { const float4 f = reinterpret_cast<const float4&>(v); vv[0] = make_double2(f.x, f.y); vv[1] = make_double2(f.z, f.w); }
+#pragma unroll
+        for (int qq = 0; qq < kQB; ++qq)
+#pragma unroll
+            for (int p = 0; p < PC; ++p) acc[qq][p] = cfma(sc[qq * w + j], vv[p], acc[qq][p]);
+    }
+#pragma unroll
+    for (int qq = 0; qq < kQB; ++qq) {
+        if (q0 + qq >= nq) continue;
+        Chunk* o = out + (size_t)(q0 + qq) * F + e;
+        if constexpr (PC == 1) {
+            double2 r = acc[qq][0];
+            if (accumulate) { const double2 t = *reinterpret_cast<const double2*>(o); r.x += t.x; r.y += t.y; }
+            *reinterpret_cast<double2*>(o) = r;
+        } else {
+            double2 r0 = acc[qq][0], r1 = acc[qq][1];
+            if (accumulate) {
+                const float4 t = *reinterpret_cast<const float4*>(o);
+                r0.x += t.x; r0.y += t.y; r1.x += t.z; r1.y += t.w;
+            }
+            *reinterpret_cast<float4*>(o) = make_float4((float)r0.x, (float)r0.y, (float)r1.x, (float)r1.y);
+        }
+    }
+}
+
 // Spinor loads in FP64 from either internal precision.
 __device__ __forceinline__ void load_d(const double2* f, size_t V, size_t s, double2 (&o)[12]) { load_spinor(f, V, s, o); }
 __device__ __forceinline__ void load_d(const float4* f, size_t V, size_t s, double2 (&o)[12]) {
@@ -411,6 +466,37 @@ __global__ void __launch_bounds__(128) k_force(AdjArgs a) {
         __syncthreads();
     }
     if (threadIdx.x == 0) a.dmu_part[blockIdx.x] = red[0];
+}
+
+cudaError_t launch_adj_pairs(const AdjArgs& a, cudaStream_t st) {
+    k_adj_pairs<<<1, 2 * a.npairs, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_window(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,
+                              size_t lbasis_vec_stride, int j0, int j1, int ring, cudaStream_t st) {
+    if (j1 - j0 > kTwoPassRing || j1 <= j0) return cudaErrorInvalidValue;
+    const size_t F = (prec == LQ_FP64) ? field_elems<double>(a.V) : field_elems<float>(a.V);
+    dim3 grid((unsigned)((F + 127) / 128), (unsigned)((a.npairs + kQB - 1) / kQB));
+    const int acc = j0 > 0 ? 1 : 0;
+    if (prec == LQ_FP64) {
+        k_recomb_window<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(basis), basis_vec_stride, j0, j1, ring,
+                                                      a.cnu, a.kmax, a.npairs, reinterpret_cast<double2*>(a.nu), F, acc);
+        k_recomb_window<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(lbasis), lbasis_vec_stride, j0, j1, ring,
+                                                      a.com, a.kmax, a.npairs, reinterpret_cast<double2*>(a.om), F, acc);
+    } else {
+        k_recomb_window<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float4*>(basis), basis_vec_stride, j0, j1, ring,
+                                                     a.cnu, a.kmax, a.npairs, reinterpret_cast<float4*>(a.nu), F, acc);
+        k_recomb_window<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float4*>(lbasis), lbasis_vec_stride, j0, j1, ring,
+                                                     a.com, a.kmax, a.npairs, reinterpret_cast<float4*>(a.om), F, acc);
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_adj_force(int prec, const AdjArgs& a, cudaStream_t st) {
+    if (prec == LQ_FP64) k_force<double><<<(unsigned)((a.V + 127) / 128), 128, 0, st>>>(a);
+    else k_force<float><<<(unsigned)((a.V + 127) / 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,

@@ -6,6 +6,7 @@
 #include <cstdio>
 #include <complex>
 #include <cstring>
+#include <functional>
 #include <mutex>
 #include <numeric>
 #include <new>
@@ -383,6 +384,9 @@ struct TslRun {
     std::vector<double> scal, check;
     std::vector<int> used, nodes;
     int quad_attempt = -1;   // quadrature passes enqueued so far - 1; -1: no quadrature
+    // second pass of a two-pass run: called after each window [j0, j1) is recombined, while its
+    // right and left vectors are still in the rings (the adjoint accumulates its pair vectors)
+    std::function<int(int, int, cudaStream_t)> on_window;
 
     void* bvec(int j) const {
         return reinterpret_cast<char*>(c->basis) + ((size_t)s0 * sb + (size_t)(ring ? j % ring : j) * vstride) * cb;
@@ -414,7 +418,7 @@ struct TslRun {
         // of kTwoPassWindow vectors into y while they are still in the ring.
         two = o->two_pass != 0 && k > 1;
         ring = two ? std::min(slots, kTwoPassRing) : 0;
-        sst = (size_t)c->kmax * F;                   // per source: stored left basis (NF = 1)
+        sst = (size_t)slots * F;                     // per source: stored left basis (NF = 1), ring or full
 
         // per-source arrays from source s0 on (a source group of a split run); the group's
         // last-block counters are a block of 3 nsrc from 3 s0 on
@@ -502,6 +506,7 @@ struct TslRun {
             // vh_0 .. vh_j are in the ring and the update below overwrites slot j + 1
             if (windows && (j + 1 - j0 == kTwoPassWindow || j == k - 1)) {
                 int rr = recombine(j0, j + 1, ls);
+                if (!rr && on_window) rr = on_window(j0, j + 1, ls);
                 if (rr) return rr;
                 j0 = j + 1;
             }
@@ -509,7 +514,10 @@ struct TslRun {
                 u.j = j;
                 u.v_cur = bvec(j); u.v_prev = bvec(j > 0 ? j - 1 : j); u.v_next = bvec(j + 1);
                 u.w_cur = lvec(j); u.w_prev = lvec(j > 0 ? j - 1 : j); u.w_next = lvec(j + 1);
-                if (store_left) { u.w_store = reinterpret_cast<char*>(c->lbasis) + (size_t)(j + 1) * F * cb; u.src_stride_store = sst; }
+                if (store_left) {
+                    u.w_store = reinterpret_cast<char*>(c->lbasis) + (size_t)(ring ? (j + 1) % ring : j + 1) * F * cb;
+                    u.src_stride_store = sst;
+                }
                 cudaEvent_t eu = prof_begin(c, ls);
                 LQ_CUDA(c, launch_update(c->prec, u, ls));
                 prof_end(c, PC_UPDATE, eu, ls);
@@ -1714,8 +1722,6 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     if (c) c->defl_prep_ok = false;
     if (!c || kmax < 1 || nsrc < 1 || (flags & ~(LQ_RESERVE_BLOCK | LQ_RESERVE_ADJOINT | LQ_RESERVE_TWO_PASS | LQ_RESERVE_SOLVE)))
         return set_err(c, LQ_ERR_ARG, "invalid reserve arguments");
-    if ((flags & LQ_RESERVE_TWO_PASS) && (flags & LQ_RESERVE_ADJOINT))
-        return set_err(c, LQ_ERR_ARG, "the adjoint keeps the whole left basis: no two-pass reserve");
     free_workspace(c);
     const int block = (flags & LQ_RESERVE_BLOCK) ? 1 : 0;
     const int nf = block ? 2 : 1;
@@ -1783,7 +1789,7 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     if ((flags & LQ_RESERVE_SOLVE) && (r = dalloc(c, &c->solve_ws, (size_t)9 * nsrc * c->V * 24))) { free_workspace(c); return r; }
     if (flags & LQ_RESERVE_ADJOINT) {
         const int np = 2 * kQuadMaxNodes;
-        if ((r = alloc_fields(&c->lbasis, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+        if ((r = alloc_fields(&c->lbasis, (size_t)nsrc * (ring ? ring : kmax)))) { free_workspace(c); return r; }
         if ((r = dalloc(c, &c->uscale, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
         if ((r = dalloc(c, &c->adj_coef, (size_t)2 * np * kmax))) { free_workspace(c); return r; }
         if ((r = alloc_fields(&c->adj_nu, (size_t)np))) { free_workspace(c); return r; }
@@ -2567,8 +2573,9 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
     if (!c->adjoint) return set_err(c, LQ_ERR_NOT_READY, "workspace reserved without LQ_RESERVE_ADJOINT");
     int r = check_ready(c, 2, 0);
     if (r || (r = check_opts(c, o, true))) return r;
-    if (o->two_pass) return set_err(c, LQ_ERR_ARG, "the adjoint keeps the whole left basis: two_pass is not available");
     const int l = o->deflate ? c->defl_l : 0;
+    const bool two = o->two_pass != 0 && o->kmax > 1;
+    if (two && l > 0) return set_err(c, LQ_ERR_ARG, "the two-pass adjoint runs without deflation");
     if (l > 0 && 2 * o->quad_nodes + 3 * l > 2 * kQuadMaxNodes)
         return set_err(c, LQ_ERR_ARG, "deflated adjoint: 2 quad_nodes + 3 l must not exceed " + std::to_string(2 * kQuadMaxNodes));
     cudaStream_t st = (cudaStream_t)stream;
@@ -2594,7 +2601,65 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
     lq_opts so = *o;
     if (so.projected == LQ_PROJ_NEWTON) so.projected = LQ_PROJ_AUTO;   // the adjoint uses the quadrature
     std::vector<lq_report> rep(2);
-    if ((r = run_tsl(c, 1, 0, 2, &so, rep.data(), io1, nullptr, st, io0, nullptr, FN_SIGN, nullptr, true))) return r;
+    const size_t F = fe(c);
+    // right basis of source 0 (x) and stored left basis of source 1 (y): full, or rings of a
+    // two-pass workspace
+    const size_t lslots = (size_t)(c->ring > 0 ? c->ring : c->kmax);
+    const void* lb1 = reinterpret_cast<const char*>(c->lbasis) + lslots * F * chunk_bytes(c);
+    double cscale = 1.0;
+    AdjArgs a;
+    auto make_adj = [&]() {
+        std::memset(&a, 0, sizeof(a));
+        a.npairs = 2 * o->quad_nodes;
+        a.kmax = c->kmax;
+        a.nth_max = 2 * kQuadMaxNodes;
+        a.c = cscale;
+        a.state = c->state;
+        a.alpha = c->alpha; a.beta = c->beta; a.delta = c->delta;
+        a.scale = c->scale; a.uscale = c->uscale;
+        a.work = c->quad_work;
+        a.cnu = c->adj_coef;
+        a.com = c->adj_coef + (size_t)2 * kQuadMaxNodes * c->kmax;
+        a.nu = c->adj_nu; a.om = c->adj_om;
+        a.V = c->V;
+        for (int i = 0; i < 4; ++i) a.dims[i] = c->dims[i];
+        a.strides[0] = 1;
+        a.strides[1] = (size_t)c->dims[0];
+        a.strides[2] = (size_t)c->dims[0] * c->dims[1];
+        a.strides[3] = (size_t)c->dims[0] * c->dims[1] * c->dims[2];
+        a.apbc = c->desc.t_antiperiodic ? 1 : 0;
+        a.efwd = std::exp(c->desc.mu);
+        a.ebwd = std::exp(-c->desc.mu);
+        a.Ub = reinterpret_cast<const double2*>(c->Ub);
+        a.force = c->adj_force;
+        a.dmu_part = c->adj_dmu;
+    };
+    if (!two) {
+        if ((r = run_tsl(c, 1, 0, 2, &so, rep.data(), io1, nullptr, st, io0, nullptr, FN_SIGN, nullptr, true))) return r;
+        LQ_CUDA(c, cudaMemcpy(&cscale, c->quad_c, sizeof(double), cudaMemcpyDeviceToHost));
+        make_adj();
+    } else {
+        // two-pass adjoint: the first pass (rings only) yields T_1, T_2 and the projected sign; the
+        // pair coefficients follow from them; the second pass reruns both processes and, window by
+        // window, recombines sgn(H) x' and accumulates the 2N pair vectors from the rings
+        so.two_pass = 1;
+        TslRun t;
+        t.c = c; t.nf = 1; t.emode = 0; t.nsrc = 2; t.o = &so; t.rep = rep.data();
+        t.y0 = io1; t.y1 = nullptr; t.fn = FN_SIGN; t.store_left = true;
+        if ((r = t.setup(st, io0, nullptr)) || (r = t.lanczos(false, st))) return r;
+        if ((r = t.proj_enqueue(st)) || (r = t.proj_complete(st))) return r;
+        LQ_CUDA(c, cudaMemcpy(&cscale, c->quad_c, sizeof(double), cudaMemcpyDeviceToHost));
+        make_adj();
+        LQ_CUDA(c, launch_adj_pairs(a, st));
+        c->launches += 1;
+        const int ring = t.ring;
+        t.on_window = [&](int j0, int j1, cudaStream_t ls) -> int {
+            cudaError_t e = launch_adj_window(c->prec, a, c->basis, F, lb1, F, j0, j1, ring, ls);
+            c->launches += 2;
+            return e == cudaSuccess ? LQ_OK : set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e));
+        };
+        if ((r = t.finish_enqueue(st)) || (r = t.finish_complete(st))) return r;
+    }
     for (int s = 0; s < 2; ++s)
         if (rep[s].status != LQ_OK) return set_err(c, rep[s].status, "Lanczos process failed for the bilinear");
     // S = Re <y | sgn(H) x'> (+ Re sum_j sgn(lambda_j) c_j d_j with deflation)
@@ -2605,36 +2670,7 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
         const cplx cj(cx[j].x, cx[j].y), dj(ry[j].x, -ry[j].y);
         Sdefl += sgn_re(c->defl_lam[j]) * (cj * dj).real();
     }
-    // gradient from 2N quadrature pairs
-    double cscale = 1.0;
-    LQ_CUDA(c, cudaMemcpy(&cscale, c->quad_c, sizeof(double), cudaMemcpyDeviceToHost));
     const int k = o->kmax;
-    AdjArgs a;
-    std::memset(&a, 0, sizeof(a));
-    a.npairs = 2 * o->quad_nodes;
-    a.kmax = c->kmax;
-    a.nth_max = 2 * kQuadMaxNodes;
-    a.c = cscale;
-    a.state = c->state;
-    a.alpha = c->alpha; a.beta = c->beta; a.delta = c->delta;
-    a.scale = c->scale; a.uscale = c->uscale;
-    a.work = c->quad_work;
-    a.cnu = c->adj_coef;
-    a.com = c->adj_coef + (size_t)2 * kQuadMaxNodes * c->kmax;
-    a.nu = c->adj_nu; a.om = c->adj_om;
-    a.V = c->V;
-    for (int i = 0; i < 4; ++i) a.dims[i] = c->dims[i];
-    a.strides[0] = 1;
-    a.strides[1] = (size_t)c->dims[0];
-    a.strides[2] = (size_t)c->dims[0] * c->dims[1];
-    a.strides[3] = (size_t)c->dims[0] * c->dims[1] * c->dims[2];
-    a.apbc = c->desc.t_antiperiodic ? 1 : 0;
-    a.efwd = std::exp(c->desc.mu);
-    a.ebwd = std::exp(-c->desc.mu);
-    a.Ub = reinterpret_cast<const double2*>(c->Ub);
-    a.force = c->adj_force;
-    a.dmu_part = c->adj_dmu;
-    const size_t F = fe(c);
     if (l > 0) {
         // the 3 l deflation pairs after the 2N Krylov pairs, from the four-block split of G by the
         // spectral projectors (lq_adjoint.cu, k_defl_coef): (R_i, b_i) with b_i = sum_j conj(F_ij c_i
@@ -2673,10 +2709,13 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
         a.dcx = dsmall + l;
         a.ddy = dsmall + 2 * l;
     }
-    // right basis of source 0 (x) and stored left basis of source 1 (y)
-    const void* lb1 = reinterpret_cast<const char*>(c->lbasis) + (size_t)c->kmax * F * chunk_bytes(c);
-    LQ_CUDA(c, launch_adjoint(c->prec, a, c->basis, F, lb1, F, std::max(k, 1), st));
-    c->launches += 4;
+    if (!two) {
+        LQ_CUDA(c, launch_adjoint(c->prec, a, c->basis, F, lb1, F, std::max(k, 1), st));
+        c->launches += 4;
+    } else {
+        LQ_CUDA(c, launch_adj_force(c->prec, a, st));
+        c->launches += 1;
+    }
     const size_t nblk = (c->V + 127) / 128;
     std::vector<double> dmu(nblk);
     LQ_CUDA(c, cudaMemcpyAsync(dmu.data(), c->adj_dmu, sizeof(double) * nblk, cudaMemcpyDeviceToHost, st));

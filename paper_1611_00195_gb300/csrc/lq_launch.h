@@ -213,6 +213,12 @@ struct AdjArgs {
 };
 cudaError_t launch_adjoint(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,
                            size_t lbasis_vec_stride, int k, cudaStream_t st);
+// the same in three parts for a two-pass run: the pair coefficients (after the first pass), the
+// pair vectors accumulated over a window [j0, j1) of ring slots (second pass), the contraction
+cudaError_t launch_adj_pairs(const AdjArgs& a, cudaStream_t st);
+cudaError_t launch_adj_window(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,
+                              size_t lbasis_vec_stride, int j0, int j1, int ring, cudaStream_t st);
+cudaError_t launch_adj_force(int prec, const AdjArgs& a, cudaStream_t st);
 
 // Nested two-sided Lanczos projected sign (lq_nested.cu)
 struct NestArgs {

@@ -254,3 +254,41 @@ def test_deflated_force_converges(lqlib, prec):
           % (prec, k, eF, eF0, abs(S - Sd) / abs(Sd), abs(dmu - dmud) / abs(dmud)))
     tol = 1e-6 if prec == 0 else 1e-3
     assert eF < tol and abs(S - Sd) < tol * abs(Sd) and abs(dmu - dmud) < tol * abs(dmud)
+
+
+@pytest.mark.parametrize("prec,tol", [(0, 1e-11), (1, 2e-6)])
+def test_two_pass_adjoint(lqlib, prec, tol):
+    """The adjoint with O(n) memory (lq_opts.two_pass on a workspace reserved with
+    LQ_RESERVE_ADJOINT | LQ_RESERVE_TWO_PASS): rings of 32 right and left basis vectors per
+    source; the second pass accumulates the 2N pair vectors of the force window by window.  The
+    processes are the same, so S, the force and dS/dmu equal the one-pass run up to the order of
+    the recombination sums (k = 100 wraps the rings three times; 4x4x2x6).  The FP64 two-pass
+    force is also checked against the oracle's Krylov route at the same depth."""
+    from paper_1611_00195_gb300 import lq
+    dims, k = (4, 4, 2, 6), 100
+    lat = od.Lattice(dims)
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = torch.from_numpy(syn.gaussian_source(dims, 5)).cuda()
+    y = torch.from_numpy(syn.gaussian_source(dims, 6)).cuda()
+    c1 = _ctx(lq, dims, U, k, prec)
+    c2 = lq.Context(dims, mu=MU, precision=prec)
+    c2.upload_gauge(torch.from_numpy(U).cuda())
+    c2.reserve(k, 2, block=False, adjoint=True, two_pass=True)
+    S1, F1, m1 = c1.bilinear_grad(x, y, k)
+    S2, F2, m2 = c2.bilinear_grad(x, y, k, two_pass=1)
+    F1, F2 = F1.cpu().numpy(), F2.cpu().numpy()
+    eF = np.linalg.norm(F2 - F1) / np.linalg.norm(F1)
+    print("two-pass adjoint prec %d: S %.3g F %.3g dmu %.3g against one pass"
+          % (prec, abs(S2 - S1) / abs(S1), eF, abs(m2 - m1) / abs(m1)))
+    assert eF < tol and abs(S2 - S1) < tol * abs(S1) and abs(m2 - m1) < tol * abs(m1)
+    with pytest.raises(lq.LQError):
+        c2.bilinear_grad(x, y, k)                     # deeper than the ring without two_pass
+    if prec == 0:
+        So, Fo, mo = oad.grad_tsl(lat, U, x.cpu().numpy(), y.cpu().numpy(), MU, k)
+        rng = np.random.default_rng(1)
+        xp = x.cpu().numpy() * (1 + 1e-16 * rng.standard_normal(x.shape))
+        Sp, Fp, mp = oad.grad_tsl(lat, U, xp, y.cpu().numpy(), MU, k)
+        sens = np.linalg.norm(Fp - Fo) / np.linalg.norm(Fo)
+        e = np.linalg.norm(F2 - Fo) / np.linalg.norm(Fo)
+        print("two-pass adjoint FP64 vs oracle: F %.3g (sensitivity %.3g)" % (e, sens))
+        assert e < max(1e-10, ADJ_SENS_FACTOR * sens)
