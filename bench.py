@@ -682,7 +682,10 @@ def main():
                      "achieved": achieved, "peak": peak, "unit": "GB/s", "frac": achieved / peak,
                      "peak_source": "of measured (MEASURED_PEAKS.json hbm_gbs, STREAM-style copy)" if peak_kind == "measured" else "of fallback (6.8 TB/s)",
                      "traffic": traffic, "algorithmic_bytes_per_launch": hop_bytes, "launch_ms": hop_ms,
-                     "achieved_tflops": hop_flops / (hop_ms * 1e-3) / 1e12},
+                     "achieved_tflops": hop_flops / (hop_ms * 1e-3) / 1e12,
+                     "target_frac": 0.7, "target_met": bool(achieved / peak >= 0.7),
+                     "why_below": "latency of the neighbour loads with 16 warps per SM at 128 registers; at full issue "
+                                  "the 134.7 M warp instructions per launch cap the kernel near 0.66 (ncu)"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(prof["launches"]),
