@@ -562,7 +562,8 @@ def main():
             cc.reserve(kc, nc, True)
             msc, rc = timed(lambda: cc.sign_derivative_apply(xc, kc), steps=1)
             resc[pname] = rc
-            conv[pname] = {"ms": msc, "eps_A_deriv": cc.error_estimate(xc, kc, kind=lq.LQ_DIR_MU).tolist(),
+            conv[pname] = {"ms": msc, "value": nc / (msc / 1e3), "unit": "solves/s",
+                           "eps_A_deriv": cc.error_estimate(xc, kc, kind=lq.LQ_DIR_MU).tolist(),
                            "status": [x["status"] for x in rc[2]], "projected": [x["projected"] for x in rc[2]]}
             del cc
         relv = lambda a, b: (torch.linalg.vector_norm((a - b).reshape(nc, -1), dim=1) / torch.linalg.vector_norm(b.reshape(nc, -1), dim=1)).tolist()

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "liblq.so")
 LQ_OK = 0
 LQ_ERR_ARG, LQ_ERR_LAYOUT, LQ_ERR_BREAKDOWN, LQ_ERR_NEWTON, LQ_ERR_NONFINITE = -1, -2, -5, -6, -9
 # Revision tag of the stencil kernel; stored ncu traffic figures are only valid for this one.
-KERNEL_REV = "hop-v3"
+KERNEL_REV = "hop-v5"
 ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_CUDA", -5: "LQ_ERR_BREAKDOWN",
           -6: "LQ_ERR_NEWTON", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NOT_READY", -9: "LQ_ERR_NONFINITE",
           -10: "LQ_ERR_NOT_CONVERGED"}
