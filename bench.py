@@ -290,7 +290,8 @@ def run_reference(args, ws, rank):
 HOP_KERNELS = {0: "k_hop<float,2,1,true,1>", 1: "k_hop_roles<float,1,true,32,1>", 2: "k_hop<float,2,1,true,5>",
                3: "k_hop<float,2,1,true,4>", 4: "k_hop_roles<float,1,true,64,2>", 5: "k_hop_roles<float,1,true,32,5>",
                6: "k_hop_tiled<1,true>", 7: "k_hop_x2<1,true,false> (packed FP32 pairs)",
-               8: "k_hop_x2<1,true,true> (packed FP32 pairs, prefetched neighbours)"}
+               8: "k_hop_x2<1,true,true> (packed FP32 pairs, prefetched neighbours)",
+               9: "k_hop<float,2,1,true,4,true> (both sides of 64 sites per block)"}
 # DRAM bytes (read + write) per launch of the block stencil from one ncu capture of that kernel
 # revision and schedule on the same per-launch shape (14x14^3, 16 sources, both sides; the
 # Krylov depth does not change a launch).  Source: profiles/k_hop_block_stencil_14x14c3_b16.md.

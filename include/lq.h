@@ -100,9 +100,10 @@ typedef struct {
                               blocks per SM, 6 = shared-memory tiles of whole x rows x 2x2x2
                               (needs even y, z, t extents; else 3), 7 = as 3 in packed FP32
                               pair arithmetic (identical results), 8 = as 7 with the next
-                              hop's neighbour spinors prefetched into shared memory.  2-8 are
-                              FP32 only (FP64 runs 0); lq_report.hop_variant gives the
-                              schedule that ran                                               */
+                              hop's neighbour spinors prefetched into shared memory, 9 = as 3
+                              with both sides of 64 sites in one block (the second load of a
+                              link hits L1).  2-9 are FP32 only (FP64 runs 0);
+                              lq_report.hop_variant gives the schedule that ran               */
     int defl_kmax;         /* depth of the shifted solves for the eigenvector derivatives of the
                               generalised deflation (0 = the reserved kmax)                    */
     int defl_nderiv;       /* Jordan blocks of the derivative deflation: the first defl_nderiv

@@ -273,7 +273,9 @@ void free_workspace(lq_ctx* c) {
 // coefficients), so the tuning leaves no trace in the results.
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
-    const int nvar = (c->prec == LQ_FP64) ? 2 : (c->link_bf16 ? 6 : kHopSchedules);   // BF16 links: 0-5
+    const int nvar = (c->prec == LQ_FP64) ? 2 : kHopSchedules;
+    // candidates: FP64 0-1; FP32 all; BF16 links without 6-8 (they read FP32 links)
+    auto candidate = [&](int v) { return !(v == 6 && !tile_ok(h.dims)) && !(c->link_bf16 && v >= 6 && v <= 8); };
     for (const auto& t : c->tuned)
         if (t.nsrc == h.nsrc && t.nf == nf && t.emode == emode) { *variant = t.variant; return LQ_OK; }
     h.j = 0;
@@ -284,7 +286,7 @@ int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* vari
     std::vector<float> best(nvar, 1e30f);
     for (int round = 0; round < 2; ++round)
         for (int v = 0; v < nvar; ++v) {
-            if (v == 6 && !tile_ok(h.dims)) continue;
+            if (!candidate(v)) continue;
             h.variant = v;
             LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));   // warm-up
             LQ_CUDA(c, cudaEventRecord(e0, st));
@@ -455,7 +457,7 @@ struct TslRun {
             int v = (nf == 2) ? o->hop_variant : 0;
             if (c->prec == LQ_FP64 && v > 1) v = 0;
             if (v == 6 && !tile_ok(h.dims)) v = 3;
-            if (c->link_bf16 && v >= 6) v = 3;
+            if (c->link_bf16 && v >= 6 && v <= 8) v = 3;
             h.variant = v;
         } else {
             h.in[0] = bvec(0);

@@ -102,19 +102,22 @@ __device__ __forceinline__ void do_dir(const HopArgs& a, int side, size_t V, siz
 }
 
 
-template <typename R, int NF, int EMODE, bool DOT, int MINB>
+template <typename R, int NF, int EMODE, bool DOT, int MINB, bool PAIR = false>
 __global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
     using C = typename Tr<R>::C;
     using Chunk = typename Tr<R>::Chunk;
     __shared__ CSum smem[32 * 2];
     // grid (site blocks, sides, sources): the two sides of one source run close together in
-    // launch order, so that the right side's alpha dot finds the left vectors in L2
-    const int side = blockIdx.y + a.side0;
+    // launch order, so that the right side's alpha dot finds the left vectors in L2.  PAIR
+    // (schedule 9): a block holds both sides of kHopThreads / 2 sites instead, warps 0-1 the right
+    // and 2-3 the left side, so that the second load of each link hits L1
+    constexpr int kHalf = kHopThreads / 2;
+    const int side = PAIR ? (int)(threadIdx.x / kHalf) : (int)blockIdx.y + a.side0;
     const unsigned bx = blockIdx.x;
     const int src = blockIdx.z;
     if (a.state != nullptr && a.state[src].status != 0) return;   // source finished / failed
     const size_t V = a.V;
-    const size_t s = (size_t)bx * blockDim.x + threadIdx.x;
+    const size_t s = PAIR ? (size_t)bx * kHalf + threadIdx.x % kHalf : (size_t)bx * blockDim.x + threadIdx.x;
     const bool active = s < V;
     const Chunk* in0 = reinterpret_cast<const Chunk*>(a.in[side]) + (size_t)src * a.src_stride_in[side];
     const Chunk* in1 = in0 + field_elems<R>(V);
@@ -161,7 +164,7 @@ __global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
             }
         }
     }
-    if (DOT && side == 0) {
+    if (DOT && (PAIR || side == 0)) {   // (block-uniform; with PAIR the left warps add zeros)
         const int nbx = (int)gridDim.x;
         CSum tot[2];
         block_total<R, 2>(d, tot, smem);
@@ -1133,9 +1136,10 @@ static cudaError_t launch_tiled_t(const HopArgs& a, int emode, bool dot, cudaStr
 //      schedule 3 otherwise)
 //   7: as 3 with packed FP32 pair arithmetic (lq_hop_x2.cu; identical results)
 //   8: as 7 with the next hop's neighbour spinors prefetched into shared memory
+//   9: as 3 with both sides of 64 sites in a block (the second load of a link hits L1)
 cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st) {
     const bool lanczos_block = nf == 2 && a.nsides == 2 && a.side0 == 0;
-    if (a.link_bf16 && a.variant >= 6) {     // schedules 6-8 read FP32 links: BF16 links run 3
+    if (a.link_bf16 && a.variant >= 6 && a.variant <= 8) {     // schedules 6-8 read FP32 links: BF16 links run 3
         HopArgs b = a;
         b.variant = 3;
         return launch_hop(prec, b, nf, emode, dot, st);
@@ -1151,6 +1155,15 @@ cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, 
                                : launch_roles_t<float, kRoleSites, 1>(a, emode, dot, st);
     if (lanczos_block && prec != LQ_FP64 && a.variant == 2) return launch_hop_t<float, 5>(a, nf, emode, dot, st);
     if (lanczos_block && prec != LQ_FP64 && a.variant == 3) return launch_hop_t<float, 4>(a, nf, emode, dot, st);
+    if (lanczos_block && prec != LQ_FP64 && a.variant == 9) {
+        const dim3 grid((unsigned)((a.V + kHopThreads / 2 - 1) / (kHopThreads / 2)), 1, (unsigned)a.nsrc);
+#define LQ_HOP_P(EM, D) k_hop<float, 2, EM, D, 4, true><<<grid, kHopThreads, 0, st>>>(a)
+        if (emode == 0) { if (dot) LQ_HOP_P(0, true); else LQ_HOP_P(0, false); }
+        else if (emode == 1) { if (dot) LQ_HOP_P(1, true); else LQ_HOP_P(1, false); }
+        else { if (dot) LQ_HOP_P(2, true); else LQ_HOP_P(2, false); }
+#undef LQ_HOP_P
+        return cudaGetLastError();
+    }
     if (lanczos_block && prec != LQ_FP64 && a.variant == 4) return launch_roles_t<float, 2 * kRoleSites, 2>(a, emode, dot, st);
     if (lanczos_block && prec != LQ_FP64 && a.variant == 5) return launch_roles_t<float, kRoleSites, 5>(a, emode, dot, st);
     return prec == LQ_FP64 ? launch_hop_t<double, 1>(a, nf, emode, dot, st) : launch_hop_t<float, 1>(a, nf, emode, dot, st);
@@ -1159,6 +1172,7 @@ cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, 
 size_t hop_blocks(const HopArgs& a, int nf) {
     if (nf == 2 && a.nsides == 2 && a.side0 == 0 && (a.variant == 1 || a.variant == 5)) return (a.V + kRoleSites - 1) / kRoleSites;
     if (nf == 2 && a.nsides == 2 && a.side0 == 0 && a.variant == 4) return (a.V + 2 * kRoleSites - 1) / (2 * kRoleSites);
+    if (nf == 2 && a.nsides == 2 && a.side0 == 0 && a.variant == 9) return (a.V + kHopThreads / 2 - 1) / (kHopThreads / 2);
     return (a.V + kHopThreads - 1) / kHopThreads;
 }
 

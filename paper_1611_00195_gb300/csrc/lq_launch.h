@@ -120,7 +120,7 @@ cudaError_t launch_cg_p(const CgArgs& a, cudaStream_t st);      // p = z + beta 
 // packed-FP32 block stencil (lq_hop_x2.cu): schedule 7, or 8 with the neighbour prefetch
 cudaError_t launch_hop_x2(const HopArgs& a, int emode, bool dot, bool prefetch, cudaStream_t st);
 cudaError_t launch_links_packed(const void* L, void* P, size_t V, cudaStream_t st);   // float2 -> (ux, ux, -uy, uy)
-constexpr int kHopSchedules = 9;     // FP32 block-stencil schedules 0..8 (FP64: 0, 1)
+constexpr int kHopSchedules = 10;    // FP32 block-stencil schedules 0..9 (FP64: 0, 1)
 bool tile_ok(const int (&dims)[4]);   // schedule 6 (shared-memory tiles) covers this lattice
 cudaError_t launch_update(int prec, const UpdArgs& a, cudaStream_t st);
 cudaError_t launch_tsl_init(int prec, int nf, const InitArgs& a, cudaStream_t st);

@@ -60,7 +60,7 @@ def test_bf16_derivative_solve(lqlib, kind):
         return lambda v: (lambda y: y * (1 + 6e-8 * (rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape))
                                          / np.sqrt(2)))(op(v))
     for s in range(2):
-        assert rep[s]["status"] == 0 and rep[s]["hop_variant"] <= 5
+        assert rep[s]["status"] == 0 and rep[s]["hop_variant"] not in (6, 7, 8)
         rd, rs, _ = ot.tsl_sign_derivative(A, Ah, E, Eh, x[s], k)
         sens = 0.0
         for _ in range(2):

@@ -111,7 +111,7 @@ def test_sign_derivative_fp64_parity(lqlib, dims, k, nsrc, kind, variant):
         assert ed < _parity_tol(sens)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8])
+@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
 @pytest.mark.parametrize("kind", [0, 1])
 def test_sign_derivative_mixed_schedules(lqlib, variant, kind):
     """Every FP32 stencil schedule of the block TSL step (lq_opts.hop_variant) against the FP64
