@@ -465,6 +465,17 @@ def main():
                              "basis_gb": basis_gb(32), "basis_gb_one_pass": basis_gb(k),
                              "rel_diff_vs_one_pass": {"sign": relmax(ys, ys_ref), "deriv": relmax(yd, yd_ref)}}
         ctx.reserve(k, nsrc, True)
+        # the nested two-sided Lanczos projected sign (Sec. 4, inner size 100) on the same 16
+        # processes: involution residuals and the projected step's time, against the quadrature
+        ctx.profile_enable(True)
+        _, _, rn = ctx.sign_derivative_apply(xd, k, out=(ys, yd), projected=lq.LQ_PROJ_NESTED, nested_m=100, graph=0)
+        pn = ctx.profile()
+        ctx.profile_enable(False)
+        extra["nested_projected_sign"] = {"inner_m": 100, "ms_projected_step": pn["newton_ms"],
+                                          "involution_residual_max": max(x["proj_check"] for x in rn),
+                                          "accepted": sum(1 for x in rn if x["status"] == 0 and x["projected"] == lq.LQ_PROJ_NESTED),
+                                          "sources": nsrc, "quadrature_ms_projected_step": prof["newton_ms"] / args.steps,
+                                          "rel_diff_vs_quadrature": {"sign": relmax(ys, ys_ref), "deriv": relmax(yd, yd_ref)}}
         # BF16 link storage on the same workload: H(mu) of the BF16-rounded field, FP32 otherwise
         cbf = lq.Context(DIMS, m_w=M_W, mu=MU, precision=lq.LQ_MIXED_BF16)
         cbf.upload_gauge(torch.from_numpy(U).to(dev))

@@ -93,7 +93,8 @@ typedef struct {
     int quad_nodes;        /* quadrature nodes N (default 64, at most 128)                      */
     double proj_tol;       /* accept the quadrature when ||Q(T)Q(T)e_1 - e_1|| <= proj_tol
                               (default 1e-11)                                                   */
-    int hop_variant;       /* stencil schedule: -1 = autotuned on first use (default), 0 = one
+    int hop_variant;       /* stencil schedule: -1 = autotuned on first use (default; the
+                              autotuner leaves out 7 and 8, measured slower), 0 = one
                               thread per (site, side), 1 = one thread per (site, output field),
                               2 / 3 = as 0 with at least 5 / 4 resident blocks per SM, 4 = as
                               1 with 64 sites per block, 5 = as 1 with at least 5 resident

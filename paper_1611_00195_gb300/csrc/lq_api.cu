@@ -274,8 +274,10 @@ void free_workspace(lq_ctx* c) {
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
     const int nvar = (c->prec == LQ_FP64) ? 2 : kHopSchedules;
-    // candidates: FP64 0-1; FP32 all; BF16 links without 6-8 (they read FP32 links)
-    auto candidate = [&](int v) { return !(v == 6 && !tile_ok(h.dims)) && !(c->link_bf16 && v >= 6 && v <= 8); };
+    // candidates: FP64 0-1; FP32 all but the packed schedules 7 and 8 (bitwise the same as 3 and
+    // measured slower on every lattice tried: they remain selectable through opts.hop_variant);
+    // BF16 links without 6 (it reads FP32 links)
+    auto candidate = [&](int v) { return !(v == 6 && (!tile_ok(h.dims) || c->link_bf16)) && v != 7 && v != 8; };
     for (const auto& t : c->tuned)
         if (t.nsrc == h.nsrc && t.nf == nf && t.emode == emode) { *variant = t.variant; return LQ_OK; }
     h.j = 0;
@@ -284,18 +286,20 @@ int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* vari
     LQ_CUDA(c, cudaEventCreate(&e0));
     LQ_CUDA(c, cudaEventCreate(&e1));
     std::vector<float> best(nvar, 1e30f);
-    for (int round = 0; round < 2; ++round)
+    // three rounds over the candidates, six timed launches each after a warm-up: the minimum
+    // over the rounds is robust to the noise of a shared machine
+    for (int round = 0; round < 3; ++round)
         for (int v = 0; v < nvar; ++v) {
             if (!candidate(v)) continue;
             h.variant = v;
             LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));   // warm-up
             LQ_CUDA(c, cudaEventRecord(e0, st));
-            for (int i = 0; i < 4; ++i) LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));
+            for (int i = 0; i < 6; ++i) LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, st));
             LQ_CUDA(c, cudaEventRecord(e1, st));
             LQ_CUDA(c, cudaEventSynchronize(e1));
             float ms = 0.f;
             LQ_CUDA(c, cudaEventElapsedTime(&ms, e0, e1));
-            c->launches += 5;
+            c->launches += 7;
             best[v] = std::min(best[v], ms);
         }
     cudaEventDestroy(e0);
