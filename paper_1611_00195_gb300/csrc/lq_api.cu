@@ -393,6 +393,9 @@ struct TslRun {
     // second pass of a two-pass run: called after each window [j0, j1) is recombined, while its
     // right and left vectors are still in the rings (the adjoint accumulates its pair vectors)
     std::function<int(int, int, cudaStream_t)> on_window;
+    // recorded on the loop's stream right after the first stencil launch (the split loop starts
+    // the other half's branch there, so that each half's update runs beside the other's stencil)
+    cudaEvent_t after_first_hop = nullptr;
 
     void* bvec(int j) const {
         return reinterpret_cast<char*>(c->basis) + ((size_t)s0 * sb + (size_t)(ring ? j % ring : j) * vstride) * cb;
@@ -476,6 +479,7 @@ struct TslRun {
         u.src_stride_io = sio; u.src_stride_basis = sb; u.src_stride_left = sl;
         u.state = state; u.partials = partials; u.partial_stride = c->partial_blocks; u.counters = counters;
         u.beta = c->beta + ks; u.delta = c->delta + ks; u.kmax = c->kmax;
+        u.bulk = o->update_variant != 0 ? 1 : 0;
 
         std::memset(&ra, 0, sizeof(ra));
         ra.V = c->V; ra.nsrc = nsrc; ra.basis = c->basis; ra.src_stride_basis = sb; ra.vec_stride = vstride;
@@ -509,6 +513,7 @@ struct TslRun {
             LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, ls));
             prof_end(c, PC_HOP, eh, ls);
             c->launches += 1;
+            if (j == 0 && after_first_hop) LQ_CUDA(c, cudaEventRecord(after_first_hop, ls));
             // vh_0 .. vh_j are in the ring and the update below overwrites slot j + 1
             if (windows && (j + 1 - j0 == kTwoPassWindow || j == k - 1)) {
                 int rr = recombine(j0, j + 1, ls);
@@ -738,7 +743,8 @@ int lanczos_graph(TslRun& t, cudaStream_t st) {
     for (auto& g : c->graphs) if (g.key == key) exec = g.exec;
     if (!exec) {
         if (!ensure_cap_stream(c)) return t.lanczos(false, st);
-        (void)update_grid(t.u.nelem, t.u.nsrc, t.u.partial_stride);   // its one-time device query, before capture
+        (void)update_grid(t.u.nelem, t.u.nsrc, t.u.partial_stride);   // one-time device queries, before capture
+        update_bulk_prepare();
         const long long launches0 = c->launches;
         cudaGraph_t g = nullptr;
         if (cudaStreamBeginCapture(c->cap_stream, cudaStreamCaptureModeThreadLocal) != cudaSuccess) {
@@ -770,11 +776,24 @@ int lanczos_graph(TslRun& t, cudaStream_t st) {
 int lanczos_split(TslRun (&g)[2], cudaStream_t st, bool graphed) {
     lq_ctx* c = g[0].c;
     const std::vector<cudaStream_t> br{c->cap_stream, c->cap_stream2};
+    // the second half's branch starts after the first half's first stencil: from then on each
+    // half's update (bandwidth-bound, few registers, high priority) runs beside the other half's
+    // stencil (latency-bound) instead of the two stencils and the two updates running together
+    cudaEvent_t stagger = nullptr;
+    LQ_CUDA(c, cudaEventCreateWithFlags(&stagger, cudaEventDisableTiming));
+    struct EvGuard { cudaEvent_t e; ~EvGuard() { if (e) cudaEventDestroy(e); } } guard{stagger};
+    g[0].after_first_hop = stagger;
+    auto branches = [&]() -> int {
+        int r = g[0].lanczos(false, br[0]);
+        cudaError_t e = cudaStreamWaitEvent(br[1], stagger, 0);
+        if (!r && e != cudaSuccess) r = set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e));
+        if (!r) r = g[1].lanczos(false, br[1]);
+        return r;
+    };
     auto plain = [&]() -> int {
         int r = fork_streams(c, st, br);
         if (r) return r;
-        r = g[0].lanczos(false, br[0]);
-        if (!r) r = g[1].lanczos(false, br[1]);
+        r = branches();
         const int rj = join_streams(c, br, st);
         return r ? r : rj;
     };
@@ -784,6 +803,7 @@ int lanczos_split(TslRun (&g)[2], cudaStream_t st, bool graphed) {
     for (auto& e : c->graphs) if (e.key == key) exec = e.exec;
     if (!exec) {
         for (auto& t : g) (void)update_grid(t.u.nelem, t.u.nsrc, t.u.partial_stride);   // device queries, before capture
+        update_bulk_prepare();
         const long long launches0 = c->launches;
         cudaEvent_t ev[2] = {nullptr, nullptr};   // fork, join
         bool ok = cudaEventCreateWithFlags(&ev[0], cudaEventDisableTiming) == cudaSuccess &&
@@ -793,9 +813,7 @@ int lanczos_split(TslRun (&g)[2], cudaStream_t st, bool graphed) {
             int rr = (cudaEventRecord(ev[0], br[0]) == cudaSuccess && cudaStreamWaitEvent(br[1], ev[0], 0) == cudaSuccess)
                          ? LQ_OK : LQ_ERR_CUDA;
             if (!rr) {
-                rr = g[0].lanczos(false, br[0]);
-                const int r1 = g[1].lanczos(false, br[1]);
-                rr = rr ? rr : r1;
+                rr = branches();
                 // join even after a failed launch, so that the capture ends on the origin stream
                 if (cudaEventRecord(ev[1], br[1]) != cudaSuccess || cudaStreamWaitEvent(br[0], ev[1], 0) != cudaSuccess)
                     rr = rr ? rr : LQ_ERR_CUDA;
@@ -843,6 +861,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
             g[i].s0 = i * (nsrc / 2);
             g[i].rep = nullptr;
             if ((r = g[i].setup(st, x_dev, x_top))) return r;
+            g[i].u.high_priority = 1;   // the update of one half takes SMs beside the other half's stencil
         }
         t.args_only = true;
         if ((r = t.setup(st, x_dev, x_top))) return r;
@@ -885,6 +904,7 @@ int batch_lanczos_graph(std::vector<TslRun>& runs, cudaStream_t st) {
     }
     if (!exec) {
         for (auto& t : runs) (void)update_grid(t.u.nelem, t.u.nsrc, t.u.partial_stride);   // device queries, before capture
+        update_bulk_prepare();
         std::vector<long long> launches0;
         for (auto& t : runs) launches0.push_back(t.c->launches);
         std::vector<cudaEvent_t> ev(n, nullptr);   // ev[0]: the fork; ev[i], i > 0: the join of member i
@@ -944,6 +964,7 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->two_pass != 0 && o->two_pass != 1) return set_err(c, LQ_ERR_ARG, "two_pass must be 0 or 1");
     if (o->graph < -1 || o->graph > 1) return set_err(c, LQ_ERR_ARG, "graph must be -1, 0 or 1");
     if (o->split < -1 || o->split > 1) return set_err(c, LQ_ERR_ARG, "split must be -1, 0 or 1");
+    if (o->update_variant < -1 || o->update_variant > 1) return set_err(c, LQ_ERR_ARG, "update_variant must be -1, 0 or 1");
     if (c->ring > 0 && !o->two_pass && o->kmax > c->ring)
         return set_err(c, LQ_ERR_ARG, "workspace reserved for two-pass runs: set opts.two_pass = 1 or kmax <= " + std::to_string(c->ring));
     return LQ_OK;
@@ -1640,6 +1661,7 @@ void lq_default_opts(lq_opts* o) {
     o->two_pass = 0;
     o->graph = -1;
     o->split = -1;
+    o->update_variant = -1;
     o->nested_m = 100;
 }
 

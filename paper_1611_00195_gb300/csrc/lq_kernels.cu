@@ -102,20 +102,12 @@ __device__ __forceinline__ void do_dir(const HopArgs& a, int side, size_t V, siz
 }
 
 
-template <typename R, int NF, int EMODE, bool DOT, int MINB, bool PAIR = false>
-__global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
+// One (site block, side, source) of the block stencil: one thread per site.
+template <typename R, int NF, int EMODE, bool DOT, bool PAIR>
+__device__ __forceinline__ void hop_block(const HopArgs& a, int side, int src, unsigned bx, CSum* smem) {
     using C = typename Tr<R>::C;
     using Chunk = typename Tr<R>::Chunk;
-    __shared__ CSum smem[32 * 2];
-    // grid (site blocks, sides, sources): the two sides of one source run close together in
-    // launch order, so that the right side's alpha dot finds the left vectors in L2.  PAIR
-    // (schedule 9): a block holds both sides of kHopThreads / 2 sites instead, warps 0-1 the right
-    // and 2-3 the left side, so that the second load of each link hits L1
     constexpr int kHalf = kHopThreads / 2;
-    const int side = PAIR ? (int)(threadIdx.x / kHalf) : (int)blockIdx.y + a.side0;
-    const unsigned bx = blockIdx.x;
-    const int src = blockIdx.z;
-    if (a.state != nullptr && a.state[src].status != 0) return;   // source finished / failed
     const size_t V = a.V;
     const size_t s = PAIR ? (size_t)bx * kHalf + threadIdx.x % kHalf : (size_t)bx * blockDim.x + threadIdx.x;
     const bool active = s < V;
@@ -176,6 +168,20 @@ __global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
             if (threadIdx.x == 0) tsl_alpha_step(a, src, res[0], res[1]);
         }
     }
+}
+
+// The block stencil.  Grid (site blocks, sides, sources): the two sides of one source run close
+// together in launch order, so that the right side's alpha dot finds the left vectors in L2.
+// PAIR (schedule 9): a block holds both sides of kHopThreads / 2 sites instead, warps 0-1 the
+// right and 2-3 the left side, so that the second load of each link hits L1.
+template <typename R, int NF, int EMODE, bool DOT, int MINB, bool PAIR = false>
+__global__ void __launch_bounds__(kHopThreads, MINB) k_hop(HopArgs a) {
+    __shared__ CSum smem[32 * 2];
+    constexpr int kHalf = kHopThreads / 2;
+    const int side = PAIR ? (int)(threadIdx.x / kHalf) : (int)blockIdx.y + a.side0;
+    const int src = blockIdx.z;
+    if (a.state != nullptr && a.state[src].status != 0) return;   // source finished / failed
+    hop_block<R, NF, EMODE, DOT, PAIR>(a, side, src, blockIdx.x, smem);
 }
 
 // ---------------------------------------------------------------------------------------
@@ -609,65 +615,6 @@ __global__ void __launch_bounds__(kTileThreadsMax) k_hop_tiled(HopArgs a) {
 // Update: new right/left vectors and the omega dot, |vh|^2, |wh|^2.
 // ---------------------------------------------------------------------------------------
 template <typename R>
-__device__ __forceinline__ typename Tr<R>::Chunk axpy3(typename Tr<R>::Chunk r, typename Tr<R>::Chunk v, typename Tr<R>::Chunk p,
-                                                      const typename Tr<R>::C (&c)[3], bool has_prev);
-
-template <>
-__device__ __forceinline__ double2 axpy3<double>(double2 r, double2 v, double2 p, const double2 (&c)[3], bool has_prev) {
-    double2 o = cmul(c[0], r);
-    o = cfma(c[1], v, o);
-    if (has_prev) o = cfma(c[2], p, o);
-    return o;
-}
-template <>
-__device__ __forceinline__ float4 axpy3<float>(float4 r, float4 v, float4 p, const float2 (&c)[3], bool has_prev) {
-    float2 o0 = cmul(c[0], make_float2(r.x, r.y));
-    float2 o1 = cmul(c[0], make_float2(r.z, r.w));
-    o0 = cfma(c[1], make_float2(v.x, v.y), o0);
-    o1 = cfma(c[1], make_float2(v.z, v.w), o1);
-    if (has_prev) {
-        o0 = cfma(c[2], make_float2(p.x, p.y), o0);
-        o1 = cfma(c[2], make_float2(p.z, p.w), o1);
-    }
-    return make_float4(o0.x, o0.y, o1.x, o1.y);
-}
-
-template <typename R>
-__device__ __forceinline__ void dot_chunk(DotAcc<R> (&d)[6], typename Tr<R>::Chunk w, typename Tr<R>::Chunk v);
-// omega = <w, v> compensated over the elements (it becomes delta_j and beta_j); the norms
-// |v|^2, |w|^2 only set the breakdown thresholds and are summed plainly
-template <>
-__device__ __forceinline__ void dot_chunk<double>(DotAcc<double> (&d)[6], double2 w, double2 v) {
-    add_cdot(d[0], d[1], w, v);
-    d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y);
-    d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y);
-}
-template <>
-__device__ __forceinline__ void dot_chunk<float>(DotAcc<float> (&d)[6], float4 w, float4 v) {
-    d[0].add_prod(w.x, v.x); d[0].add_prod(w.y, v.y); d[0].add_prod(w.z, v.z); d[0].add_prod(w.w, v.w);
-    d[1].add_prod(w.x, v.y); d[1].add_prod(-w.y, v.x); d[1].add_prod(w.z, v.w); d[1].add_prod(-w.w, v.z);
-    d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y); d[2].add_plain(v.z, v.z); d[2].add_plain(v.w, v.w);
-    d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y); d[3].add_plain(w.z, w.z); d[3].add_plain(w.w, w.w);
-}
-// |B vh_j|^2 (d[4]) and |B^dag wh_j|^2 (d[5]): the scale against which an invariant subspace is
-// detected (plain sums, thresholds only)
-__device__ __forceinline__ void norm_chunk(DotAcc<double> (&d)[6], double2 r, double2 l) {
-    d[4].add_plain(r.x, r.x); d[4].add_plain(r.y, r.y);
-    d[5].add_plain(l.x, l.x); d[5].add_plain(l.y, l.y);
-}
-__device__ __forceinline__ void norm_chunk(DotAcc<float> (&d)[6], float4 r, float4 l) {
-    d[4].add_plain(r.x, r.x); d[4].add_plain(r.y, r.y); d[4].add_plain(r.z, r.z); d[4].add_plain(r.w, r.w);
-    d[5].add_plain(l.x, l.x); d[5].add_plain(l.y, l.y); d[5].add_plain(l.z, l.z); d[5].add_plain(l.w, l.w);
-}
-
-// An invariant subspace: the new vector has cancelled to this fraction of |B v_j| (right) or
-// |B^dag w_j| (left), a few hundred times the rounding level of the vectors' precision.  A
-// regular step of these processes keeps the ratio of order one.
-template <typename R> __host__ __device__ constexpr double invariant_tol();
-template <> __host__ __device__ constexpr double invariant_tol<double>() { return 1e-10; }
-template <> __host__ __device__ constexpr double invariant_tol<float>() { return 1e-5; }
-
-template <typename R>
 __global__ void __launch_bounds__(kUpdThreads, 3) k_update(UpdArgs a) {
     using C = typename Tr<R>::C;
     using Chunk = typename Tr<R>::Chunk;
@@ -732,33 +679,7 @@ __global__ void __launch_bounds__(kUpdThreads, 3) k_update(UpdArgs a) {
     if (last_block(a.counters + a.nsrc + src, gridDim.x)) {
         double res[6];
         reduce_partials<6>(a.partials + (size_t)src * a.partial_stride * 12, gridDim.x, res, smem);
-        if (threadIdx.x == 0) {
-            // omega = <wh_{j+1}, vh_{j+1}>; delta_j = sqrt|omega|; beta_j = omega / delta_j
-            const double om_re = res[0], om_im = res[1];
-            const double nv2 = res[2], nw2 = res[3];
-            const double om = hypot(om_re, om_im);
-            const int j = a.j;
-            if (!isfinite(om) || !isfinite(nv2) || !isfinite(nw2)) { st.status = LQ_ERR_NONFINITE; return; }
-            // |B v_j|^2 = |s_j|^2 |B vh_j|^2 and |B^dag w_j|^2 = |u_j|^2 |B^dag wh_j|^2 (cv[0] = s_j, cw[0] = u_j)
-            const double tol2 = invariant_tol<R>() * invariant_tol<R>();
-            const double rr = (st.cv[0].x * st.cv[0].x + st.cv[0].y * st.cv[0].y) * res[4];
-            const double ll = (st.cw[0].x * st.cw[0].x + st.cw[0].y * st.cw[0].y) * res[5];
-            // vh_{j+1} = s_j B vh_j - ... is in the units of B v_j already (likewise wh_{j+1})
-            if (nv2 <= tol2 * rr || nw2 <= tol2 * ll) { st.status = LQ_ERR_BREAKDOWN; return; }
-            if (om < st.breakdown_tol * sqrt(nv2) * sqrt(nw2) || om == 0.0) { st.status = LQ_ERR_BREAKDOWN; return; }
-            const double dl = sqrt(om);
-            const double2 be = make_double2(om_re / dl, om_im / dl);
-            a.delta[(size_t)src * a.kmax + j] = dl;
-            a.beta[(size_t)src * a.kmax + j] = be;
-            st.s_prev = st.s_cur;
-            st.u_prev = st.u_cur;
-            st.beta_prev = be;
-            st.delta_prev = dl;
-            st.s_cur = 1.0 / dl;
-            // u_{j+1} = 1 / conj(beta_j)
-            const double bn = be.x * be.x + be.y * be.y;
-            st.u_cur = make_double2(be.x / bn, be.y / bn);
-        }
+        if (threadIdx.x == 0) update_scalars<R>(a, src, res);
     }
 }
 
@@ -1194,6 +1115,7 @@ unsigned update_grid(size_t nelem, int nsrc, size_t cap) {
 }
 
 cudaError_t launch_update(int prec, const UpdArgs& a, cudaStream_t st) {
+    if (prec != LQ_FP64 && a.bulk && update_bulk_ready()) return launch_update_bulk(a, a.high_priority != 0, st);
     dim3 grid(update_grid(a.nelem, a.nsrc, a.partial_stride), (unsigned)a.nsrc);
     if (prec == LQ_FP64) k_update<double><<<grid, kUpdThreads, 0, st>>>(a);
     else k_update<float><<<grid, kUpdThreads, 0, st>>>(a);

@@ -291,6 +291,102 @@ __device__ __forceinline__ void finish(const C (&psi)[12], decltype(C::x) diag, 
     }
 }
 
+// ---------------------------------------------------------------------------------------
+// Update step of the Lanczos recurrences (Sec. 2): elementwise part and the scalar step that
+// the last block of a source takes once omega, |vh|^2, |wh|^2, |B vh|^2, |B^dag wh|^2 are summed.
+// ---------------------------------------------------------------------------------------
+template <typename R>
+__device__ __forceinline__ typename Tr<R>::Chunk axpy3(typename Tr<R>::Chunk r, typename Tr<R>::Chunk v, typename Tr<R>::Chunk p,
+                                                      const typename Tr<R>::C (&c)[3], bool has_prev);
+
+template <>
+__device__ __forceinline__ double2 axpy3<double>(double2 r, double2 v, double2 p, const double2 (&c)[3], bool has_prev) {
+    double2 o = cmul(c[0], r);
+    o = cfma(c[1], v, o);
+    if (has_prev) o = cfma(c[2], p, o);
+    return o;
+}
+template <>
+__device__ __forceinline__ float4 axpy3<float>(float4 r, float4 v, float4 p, const float2 (&c)[3], bool has_prev) {
+    float2 o0 = cmul(c[0], make_float2(r.x, r.y));
+    float2 o1 = cmul(c[0], make_float2(r.z, r.w));
+    o0 = cfma(c[1], make_float2(v.x, v.y), o0);
+    o1 = cfma(c[1], make_float2(v.z, v.w), o1);
+    if (has_prev) {
+        o0 = cfma(c[2], make_float2(p.x, p.y), o0);
+        o1 = cfma(c[2], make_float2(p.z, p.w), o1);
+    }
+    return make_float4(o0.x, o0.y, o1.x, o1.y);
+}
+
+template <typename R>
+__device__ __forceinline__ void dot_chunk(DotAcc<R> (&d)[6], typename Tr<R>::Chunk w, typename Tr<R>::Chunk v);
+// omega = <w, v> compensated over the elements (it becomes delta_j and beta_j); the norms
+// |v|^2, |w|^2 only set the breakdown thresholds and are summed plainly
+template <>
+__device__ __forceinline__ void dot_chunk<double>(DotAcc<double> (&d)[6], double2 w, double2 v) {
+    add_cdot(d[0], d[1], w, v);
+    d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y);
+    d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y);
+}
+template <>
+__device__ __forceinline__ void dot_chunk<float>(DotAcc<float> (&d)[6], float4 w, float4 v) {
+    d[0].add_prod(w.x, v.x); d[0].add_prod(w.y, v.y); d[0].add_prod(w.z, v.z); d[0].add_prod(w.w, v.w);
+    d[1].add_prod(w.x, v.y); d[1].add_prod(-w.y, v.x); d[1].add_prod(w.z, v.w); d[1].add_prod(-w.w, v.z);
+    d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y); d[2].add_plain(v.z, v.z); d[2].add_plain(v.w, v.w);
+    d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y); d[3].add_plain(w.z, w.z); d[3].add_plain(w.w, w.w);
+}
+// |B vh_j|^2 (d[4]) and |B^dag wh_j|^2 (d[5]): the scale against which an invariant subspace is
+// detected (plain sums, thresholds only)
+__device__ __forceinline__ void norm_chunk(DotAcc<double> (&d)[6], double2 r, double2 l) {
+    d[4].add_plain(r.x, r.x); d[4].add_plain(r.y, r.y);
+    d[5].add_plain(l.x, l.x); d[5].add_plain(l.y, l.y);
+}
+__device__ __forceinline__ void norm_chunk(DotAcc<float> (&d)[6], float4 r, float4 l) {
+    d[4].add_plain(r.x, r.x); d[4].add_plain(r.y, r.y); d[4].add_plain(r.z, r.z); d[4].add_plain(r.w, r.w);
+    d[5].add_plain(l.x, l.x); d[5].add_plain(l.y, l.y); d[5].add_plain(l.z, l.z); d[5].add_plain(l.w, l.w);
+}
+
+// An invariant subspace: the new vector has cancelled to this fraction of |B v_j| (right) or
+// |B^dag w_j| (left), a few hundred times the rounding level of the vectors' precision.  A
+// regular step of these processes keeps the ratio of order one.
+template <typename R> __host__ __device__ constexpr double invariant_tol();
+template <> __host__ __device__ constexpr double invariant_tol<double>() { return 1e-10; }
+template <> __host__ __device__ constexpr double invariant_tol<float>() { return 1e-5; }
+
+// The scalar step after omega_j = <wh_{j+1}, vh_{j+1}> (res[0], res[1]) and the norms res[2..5]:
+// breakdown and invariant-subspace tests, delta_j = sqrt|omega|, beta_j = omega / delta_j and the
+// scales of the next step.  One thread.
+template <typename R>
+__device__ inline void update_scalars(const UpdArgs& a, int src, const double (&res)[6]) {
+    TslState& st = a.state[src];
+    // omega = <wh_{j+1}, vh_{j+1}>; delta_j = sqrt|omega|; beta_j = omega / delta_j
+    const double om_re = res[0], om_im = res[1];
+    const double nv2 = res[2], nw2 = res[3];
+    const double om = hypot(om_re, om_im);
+    const int j = a.j;
+    if (!isfinite(om) || !isfinite(nv2) || !isfinite(nw2)) { st.status = LQ_ERR_NONFINITE; return; }
+    // |B v_j|^2 = |s_j|^2 |B vh_j|^2 and |B^dag w_j|^2 = |u_j|^2 |B^dag wh_j|^2 (cv[0] = s_j, cw[0] = u_j)
+    const double tol2 = invariant_tol<R>() * invariant_tol<R>();
+    const double rr = (st.cv[0].x * st.cv[0].x + st.cv[0].y * st.cv[0].y) * res[4];
+    const double ll = (st.cw[0].x * st.cw[0].x + st.cw[0].y * st.cw[0].y) * res[5];
+    // vh_{j+1} = s_j B vh_j - ... is in the units of B v_j already (likewise wh_{j+1})
+    if (nv2 <= tol2 * rr || nw2 <= tol2 * ll) { st.status = LQ_ERR_BREAKDOWN; return; }
+    if (om < st.breakdown_tol * sqrt(nv2) * sqrt(nw2) || om == 0.0) { st.status = LQ_ERR_BREAKDOWN; return; }
+    const double dl = sqrt(om);
+    const double2 be = make_double2(om_re / dl, om_im / dl);
+    a.delta[(size_t)src * a.kmax + j] = dl;
+    a.beta[(size_t)src * a.kmax + j] = be;
+    st.s_prev = st.s_cur;
+    st.u_prev = st.u_cur;
+    st.beta_prev = be;
+    st.delta_prev = dl;
+    st.s_cur = 1.0 / dl;
+    // u_{j+1} = 1 / conj(beta_j)
+    const double bn = be.x * be.x + be.y * be.y;
+    st.u_cur = make_double2(be.x / bn, be.y / bn);
+}
+
 // Lanczos scalar step after alpha_j: record alpha_j and prepare the update coefficients
 //   vh_{j+1} = s_j B vh_j - alpha_j s_j vh_j - beta_{j-1} s_{j-1} vh_{j-1}
 //   wh_{j+1} = u_j B^dag wh_j - conj(alpha_j) u_j wh_j - delta_{j-1} u_{j-1} wh_{j-1}

@@ -26,7 +26,7 @@ LIB_PATH = os.path.join(_HERE, "liblq.so")
 LQ_OK = 0
 LQ_ERR_ARG, LQ_ERR_LAYOUT, LQ_ERR_BREAKDOWN, LQ_ERR_NEWTON, LQ_ERR_NONFINITE = -1, -2, -5, -6, -9
 # Revision tag of the stencil kernel; stored ncu traffic figures are only valid for this one.
-KERNEL_REV = "hop-v5"
+KERNEL_REV = "hop-v7"
 ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_CUDA", -5: "LQ_ERR_BREAKDOWN",
           -6: "LQ_ERR_NEWTON", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NOT_READY", -9: "LQ_ERR_NONFINITE",
           -10: "LQ_ERR_NOT_CONVERGED"}
@@ -55,7 +55,8 @@ class Opts(ctypes.Structure):
                 ("newton_tol", ctypes.c_double), ("deflate", ctypes.c_int), ("projected", ctypes.c_int),
                 ("quad_nodes", ctypes.c_int), ("proj_tol", ctypes.c_double), ("hop_variant", ctypes.c_int),
                 ("defl_kmax", ctypes.c_int), ("defl_nderiv", ctypes.c_int), ("two_pass", ctypes.c_int),
-                ("graph", ctypes.c_int), ("split", ctypes.c_int), ("nested_m", ctypes.c_int)]
+                ("graph", ctypes.c_int), ("split", ctypes.c_int), ("nested_m", ctypes.c_int),
+                ("update_variant", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -376,7 +377,7 @@ class Context:
     @staticmethod
     def opts(k, breakdown_tol=1e-14, newton_max_iter=50, newton_tol=1e-13, projected=LQ_PROJ_AUTO, quad_nodes=64,
              proj_tol=1e-11, hop_variant=-1, deflate=0, defl_kmax=0, defl_nderiv=0, two_pass=0, graph=-1, split=-1,
-             nested_m=100):
+             nested_m=100, update_variant=-1):
         o = Opts()
         lib().lq_default_opts(ctypes.byref(o))
         o.kmax = int(k)
@@ -394,6 +395,7 @@ class Context:
         o.graph = int(graph)
         o.split = int(split)
         o.nested_m = int(nested_m)
+        o.update_variant = int(update_variant)
         return o
 
     def sign_apply(self, x, k, out=None, **kw):

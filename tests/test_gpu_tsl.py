@@ -111,7 +111,7 @@ def test_sign_derivative_fp64_parity(lqlib, dims, k, nsrc, kind, variant):
         assert ed < _parity_tol(sens)
 
 
-@pytest.mark.parametrize("variant", [0, 1, 2, 3, 4, 5, 6, 7, 8, 9])
+@pytest.mark.parametrize("variant", list(range(10)))
 @pytest.mark.parametrize("kind", [0, 1])
 def test_sign_derivative_mixed_schedules(lqlib, variant, kind):
     """Every FP32 stencil schedule of the block TSL step (lq_opts.hop_variant) against the FP64
@@ -277,8 +277,7 @@ def test_error_estimate_parity(lqlib, dims, k, deriv):
 @pytest.mark.parametrize("kind", [0, 1, 2])
 def test_packed_schedules_are_bitwise_schedule_3(lqlib, dims, kind):
     """Schedules 7 and 8 (packed FP32 pair arithmetic, the hop factor -1/2 taken out of the sum,
-    and for 8 the prefetched neighbours) perform the same roundings in the same order as schedule
-    3: every result, report and Lanczos coefficient must be bitwise identical, for the three
+    and for 8 the prefetched neighbours) perform the same roundings in the same order as schedule 3: every result, report and Lanczos coefficient must be bitwise identical, for the three
     derivative kinds (d/dmu, su(3) and U(1) link directions), on lattices whose site count leaves
     a ragged last block of the 128-site grid (V = 192, 384, 180)."""
     from paper_1611_00195_gb300 import lq
