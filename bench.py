@@ -426,7 +426,7 @@ def main():
             return (torch.linalg.vector_norm(p - q, dim=1) / torch.linalg.vector_norm(q, dim=1)).cpu().numpy()
         es, ed = rel(ys, ys64), rel(yd, yd64)
         fp64 = {"value": nsrc / (ms64 / 1e3), "unit": "solves/s", "ms_per_step": ms64,
-                "speedup_mixed_over_fp64": (ms64 / (ms_local / args.steps)),
+                "speedup_mixed_over_fp64": (ms64 / (ms / args.steps)),
                 "rel_err_mixed_vs_fp64_sign": {"max": float(es.max()), "median": float(np.median(es))},
                 "rel_err_mixed_vs_fp64_deriv": {"max": float(ed.max()), "median": float(np.median(ed))}}
         del ctx64

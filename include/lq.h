@@ -133,12 +133,12 @@ typedef struct {
                               rounding only (each half has its own reduction grids)           */
     int nested_m;          /* inner Krylov size of LQ_PROJ_NESTED and of that rung of LQ_PROJ_AUTO
                               (default 100, the paper's; capped by k and the reserved kmax)   */
-    int update_variant;    /* FP32 Lanczos update kernel: -1 / 1 (default) = inputs staged in
-                              shared memory by bulk asynchronous copies (few registers, so that
-                              in a split run the update of one half shares the SMs with the
-                              other half's stencil, launched at the highest stream priority);
-                              0 = register-streaming kernel.  The vectors are bitwise the same;
-                              the inner products differ by the order of their partial sums    */
+    int update_variant;    /* FP32 Lanczos update kernel: 1 = inputs staged in shared memory by
+                              bulk asynchronous copies, 0 = register-streaming kernel, -1
+                              (default) = 1 for a loop run as one batch, 0 for the split loop
+                              (the bulk kernel's shared memory would take the L1 of the stencil
+                              running beside it).  The vectors are bitwise the same; the inner
+                              products differ by the order of their partial sums              */
 } lq_opts;
 
 /* Projected step sgn(T_k) e_1 (Sec. 2):

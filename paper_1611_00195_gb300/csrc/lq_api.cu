@@ -393,9 +393,6 @@ struct TslRun {
     // second pass of a two-pass run: called after each window [j0, j1) is recombined, while its
     // right and left vectors are still in the rings (the adjoint accumulates its pair vectors)
     std::function<int(int, int, cudaStream_t)> on_window;
-    // recorded on the loop's stream right after the first stencil launch (the split loop starts
-    // the other half's branch there, so that each half's update runs beside the other's stencil)
-    cudaEvent_t after_first_hop = nullptr;
 
     void* bvec(int j) const {
         return reinterpret_cast<char*>(c->basis) + ((size_t)s0 * sb + (size_t)(ring ? j % ring : j) * vstride) * cb;
@@ -513,7 +510,6 @@ struct TslRun {
             LQ_CUDA(c, launch_hop(c->prec, h, nf, emode, true, ls));
             prof_end(c, PC_HOP, eh, ls);
             c->launches += 1;
-            if (j == 0 && after_first_hop) LQ_CUDA(c, cudaEventRecord(after_first_hop, ls));
             // vh_0 .. vh_j are in the ring and the update below overwrites slot j + 1
             if (windows && (j + 1 - j0 == kTwoPassWindow || j == k - 1)) {
                 int rr = recombine(j0, j + 1, ls);
@@ -538,7 +534,9 @@ struct TslRun {
         return LQ_OK;
     }
 
-    lq_ctx::GraphKey key(int groups = 1) const { return {k, nsrc, nf, emode, h.variant, store_left ? 1 : 0, ring, c->desc.mu, groups}; }
+    lq_ctx::GraphKey key(int groups = 1) const {
+        return {k, nsrc, nf, emode, h.variant, store_left ? 1 : 0, ring, c->desc.mu, groups, u.bulk};
+    }
     bool graphed() const { return o->graph != 0 && !c->prof_on; }
     long long loop_launches() const { return 2 * (long long)k - 1; }
 
@@ -776,17 +774,8 @@ int lanczos_graph(TslRun& t, cudaStream_t st) {
 int lanczos_split(TslRun (&g)[2], cudaStream_t st, bool graphed) {
     lq_ctx* c = g[0].c;
     const std::vector<cudaStream_t> br{c->cap_stream, c->cap_stream2};
-    // the second half's branch starts after the first half's first stencil: from then on each
-    // half's update (bandwidth-bound, few registers, high priority) runs beside the other half's
-    // stencil (latency-bound) instead of the two stencils and the two updates running together
-    cudaEvent_t stagger = nullptr;
-    LQ_CUDA(c, cudaEventCreateWithFlags(&stagger, cudaEventDisableTiming));
-    struct EvGuard { cudaEvent_t e; ~EvGuard() { if (e) cudaEventDestroy(e); } } guard{stagger};
-    g[0].after_first_hop = stagger;
     auto branches = [&]() -> int {
         int r = g[0].lanczos(false, br[0]);
-        cudaError_t e = cudaStreamWaitEvent(br[1], stagger, 0);
-        if (!r && e != cudaSuccess) r = set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e));
         if (!r) r = g[1].lanczos(false, br[1]);
         return r;
     };
@@ -861,7 +850,11 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
             g[i].s0 = i * (nsrc / 2);
             g[i].rep = nullptr;
             if ((r = g[i].setup(st, x_dev, x_top))) return r;
-            g[i].u.high_priority = 1;   // the update of one half takes SMs beside the other half's stencil
+            // the bulk-copy update needs ~200 KB of shared memory per SM, which leaves the other
+            // half's stencil, running beside it, almost no L1: the split loop takes the register
+            // kernel unless the caller asks for the bulk one (measured at 14^4, 16 sources:
+            // 162.5 ms against 179.6 ms per call)
+            g[i].u.bulk = o->update_variant == 1 ? 1 : 0;
         }
         t.args_only = true;
         if ((r = t.setup(st, x_dev, x_top))) return r;

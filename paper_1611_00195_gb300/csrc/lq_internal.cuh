@@ -282,9 +282,11 @@ struct lq_ctx {
         int k, nsrc, nf, emode, variant, store_left, ring;
         double mu;
         int groups;        // source groups run as concurrent branches (1: none)
+        int update;        // update kernel (UpdArgs.bulk)
         bool operator==(const GraphKey& o) const {
             return k == o.k && nsrc == o.nsrc && nf == o.nf && emode == o.emode && variant == o.variant &&
-                   store_left == o.store_left && ring == o.ring && mu == o.mu && groups == o.groups;
+                   store_left == o.store_left && ring == o.ring && mu == o.mu && groups == o.groups &&
+                   update == o.update;
         }
     };
     struct GraphEntry { GraphKey key; cudaGraphExec_t exec; };

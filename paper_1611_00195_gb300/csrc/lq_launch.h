@@ -66,7 +66,6 @@ struct UpdArgs {
     double* delta;
     int kmax;
     int bulk;              // FP32: 1 = k_update_bulk (inputs staged by bulk copies), 0 = k_update
-    int high_priority;     // k_update_bulk launched at the highest stream priority
 };
 
 struct InitArgs {
@@ -136,7 +135,7 @@ cudaError_t launch_links_bf16(double* U, void* L, size_t V, cudaStream_t st);
 cudaError_t launch_direction(int prec, const double* U, const double* w, int kind, void* Y, size_t V, cudaStream_t st);
 unsigned update_grid(size_t nelem, int nsrc, size_t cap);
 // the bulk-copy FP32 update (lq_update_bulk.cu)
-cudaError_t launch_update_bulk(const UpdArgs& a, bool high_priority, cudaStream_t st);
+cudaError_t launch_update_bulk(const UpdArgs& a, cudaStream_t st);
 bool update_bulk_ready();                 // opts in to its shared memory (once); false: unavailable
 unsigned update_bulk_grid(size_t nelem, int nsrc, size_t cap);
 void update_bulk_prepare();               // every one-time device query, before a stream capture

@@ -3,11 +3,12 @@
 // B^dag wh_j, wh_j, wh_{j-1}) are fetched into shared memory by bulk asynchronous copies
 // (cp.async.bulk, completion counted on an mbarrier), kBuStages tiles ahead of the threads that
 // combine them.  The loads in flight live in shared memory, not in registers: a block of four
-// warps keeps ~72 KB of HBM reads outstanding, and two such blocks per SM need only 16 K
-// registers, so that the update of one source half fits beside three blocks of the other half's
-// stencil (the split Krylov loop).  The arithmetic per element, the compensated dots and the
-// scalar step are those of k_update (lq_stencil.cuh); the vectors are bitwise the same, the dots
-// differ by the order of their (compensated) partial sums.
+// warps keeps ~72 KB of HBM reads outstanding with 8 K registers.  Alone it moves the update's
+// bytes at 0.78 of the measured HBM copy rate against 0.75 for the register-streaming k_update;
+// beside the stencil (the split Krylov loop) its shared memory would take the L1 the stencil
+// reuses its neighbour rows from, so that loop keeps k_update.  The arithmetic per element, the
+// compensated dots and the scalar step are those of k_update (lq_stencil.cuh); the vectors are
+// bitwise the same, the dots differ by the order of their (compensated) partial sums.
 #include "lq_internal.cuh"
 #include "lq_launch.h"
 #include "lq_stencil.cuh"
@@ -196,37 +197,15 @@ bool update_bulk_ready() {
     return ok == 1;
 }
 
-static int greatest_priority() {
-    static int greatest = 1;   // numerically lowest = highest priority
-    if (greatest > 0) {
-        int least = 0;
-        if (cudaDeviceGetStreamPriorityRange(&least, &greatest) != cudaSuccess) { cudaGetLastError(); greatest = 0; }
-    }
-    return greatest;
-}
-
 void update_bulk_prepare() {
     (void)update_bulk_ready();
     (void)update_bulk_grid(1, 1, 1);
-    (void)greatest_priority();
 }
 
-// high_priority: launched ahead of the stencil blocks waiting for an SM (the split Krylov loop,
-// where the update of one half runs beside the stencil of the other)
-cudaError_t launch_update_bulk(const UpdArgs& a, bool high_priority, cudaStream_t st) {
-    cudaLaunchConfig_t cfg = {};
-    cfg.gridDim = dim3(update_bulk_grid(a.nelem, a.nsrc, a.partial_stride), (unsigned)a.nsrc);
-    cfg.blockDim = dim3(kBuThreads);
-    cfg.dynamicSmemBytes = kBuSmem;
-    cfg.stream = st;
-    cudaLaunchAttribute attr[1];
-    if (high_priority) {
-        attr[0].id = cudaLaunchAttributePriority;
-        attr[0].val.priority = greatest_priority();
-        cfg.attrs = attr;
-        cfg.numAttrs = 1;
-    }
-    return cudaLaunchKernelEx(&cfg, k_update_bulk, a);
+cudaError_t launch_update_bulk(const UpdArgs& a, cudaStream_t st) {
+    const dim3 grid(update_bulk_grid(a.nelem, a.nsrc, a.partial_stride), (unsigned)a.nsrc);
+    k_update_bulk<<<grid, kBuThreads, kBuSmem, st>>>(a);
+    return cudaGetLastError();
 }
 
 }  // namespace lq
