@@ -293,10 +293,11 @@ HOP_KERNELS = {0: "k_hop<float,2,1,true,1>", 1: "k_hop_roles<float,1,true,32,1>"
                8: "k_hop_x2<1,true,true> (packed FP32 pairs, prefetched neighbours)",
                9: "k_hop<float,2,1,true,4,true> (both sides of 64 sites per block)"}
 # DRAM bytes (read + write) per launch of the block stencil from one ncu capture of that kernel
-# revision and schedule on the same per-launch shape (14x14^3, 16 sources, both sides; the
-# Krylov depth does not change a launch).  Source: profiles/k_hop_block_stencil_14x14c3_b16.md.
+# revision and schedule (14x14^3, both sides; the Krylov depth does not change a launch): twice
+# the 136.8 + 88.5 MB of the 8-source launch of the split loop, the per-source work of a
+# 16-source launch being the same.  Source: profiles/k_hop_block_stencil_14x14c3_b16.md.
 # Keyed by (kernel revision, schedule, V, sources); anything else reports traffic = null.
-HOP_TRAFFIC = {("hop-v3", 3, 38416, 16): 467833856}
+HOP_TRAFFIC = {("hop-v7", 3, 38416, 16): 2 * 225285376}
 
 
 def main():
@@ -494,6 +495,51 @@ def main():
                                "rel_diff_vs_fp32_links": {"sign": relmax(ysb, ys_ref), "deriv": relmax(ydb, yd_ref)},
                                "note": "a different operator: the links rounded to BF16 (relative 2^-9)"}
         del cbf
+        # the update kernels in the split loop and in one batch (lq_opts.update_variant: 0 register
+        # streaming, 1 bulk-copy staging): the default takes 1 for one batch and 0 for the split loop
+        upd = {}
+        for name, kw in (("split_register", dict(update_variant=0)), ("split_bulk", dict(update_variant=1)),
+                         ("one_batch_register", dict(update_variant=0, split=0)),
+                         ("one_batch_bulk", dict(update_variant=1, split=0))):
+            upd[name + "_ms"] = timed(lambda: ctx.sign_derivative_apply(xd, k, out=(ys, yd), **kw, **hv))[0]
+        extra["update_kernels"] = upd
+        # saturation: two independent 8-source solves at once (two contexts, two streams, two host
+        # threads) against one 8-source and one 16-source solve, k = 100, one batch each
+        import threading
+        ks, half = 100, nsrc // 2
+        csat = [lq.Context(DIMS, m_w=M_W, mu=MU, precision=lq.LQ_MIXED) for _ in range(3)]
+        for cc, ns in zip(csat, (nsrc, half, half)):
+            cc.upload_gauge(torch.from_numpy(U).to(dev))
+            cc.reserve(ks, ns, True)
+        xs = [xd, xd[:half].contiguous(), xd[half:].contiguous()]
+        streams = [torch.cuda.Stream(dev), torch.cuda.Stream(dev)]
+
+        def run_on(i, s):
+            with torch.cuda.stream(s):
+                csat[i].sign_derivative_apply(xs[i], ks, split=0, **hv)
+            s.synchronize()
+
+        def both():
+            th = [threading.Thread(target=run_on, args=(1 + i, streams[i])) for i in range(2)]
+            for t in th:
+                t.start()
+            for t in th:
+                t.join()
+
+        def wall(fn, reps=3):
+            fn()
+            torch.cuda.synchronize(dev)
+            t0 = time.perf_counter()
+            for _ in range(reps):
+                fn()
+            torch.cuda.synchronize(dev)
+            return (time.perf_counter() - t0) / reps * 1e3
+        extra["saturation_k100"] = {"one_16_source_ms": wall(lambda: run_on(0, streams[0])),
+                                    "one_8_source_ms": wall(lambda: run_on(1, streams[0])),
+                                    "two_8_source_concurrent_ms": wall(both),
+                                    "note": "two independent half batches at once take as long as one full batch: "
+                                            "one solve already occupies the GPU"}
+        del csat
         # the batching workload: 32 Z2-noise sources on 10^4, k = 150, mu = 0.2 (d/dmu), with the
         # Krylov loop replayed from a CUDA graph and with plain launches
         d3, k3, n3 = (10, 10, 10, 10), 150, 32
@@ -704,8 +750,12 @@ def main():
                      "traffic": traffic, "algorithmic_bytes_per_launch": hop_bytes, "launch_ms": hop_ms,
                      "achieved_tflops": hop_flops / (hop_ms * 1e-3) / 1e12,
                      "target_frac": 0.7, "target_met": bool(achieved / peak >= 0.7),
-                     "why_below": "latency of the neighbour loads with 16 warps per SM at 128 registers; at full issue "
-                                  "the 134.7 M warp instructions per launch cap the kernel near 0.66 (ncu)"},
+                     "traffic_note": "2 x the ncu DRAM bytes of the same kernel's 8-source launch (split loop)",
+                     "why_below": "the launch moves 4.7x its algorithmic bytes between L2 and the SMs (neighbour spinors "
+                                  "and links re-read by up to nine threads, 24% L1 hits) with 16 warps per SM at 128 "
+                                  "registers: long-scoreboard waits and FP32 issue, not DRAM (traffic 0.91x algorithmic, "
+                                  "DRAM at 22% of its peak); two concurrent half batches take as long as one full batch, "
+                                  "so no idle resource is left to fill"},
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),

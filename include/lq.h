@@ -62,6 +62,14 @@ extern "C" {
                          context (stencil, derivative directions, adjoint force, eigensolver)
                          uses the rounded links: H(mu) of the rounded gauge field.  Stencil
                          schedules 6-8 are not available (schedule 3 runs instead)          */
+#define LQ_FLOAT_FLOAT 3 /* links, spinors, stencil and update in float-float: pairs of FP32
+                         numbers (hi + lo, about 48 significant bits) with compensated sums and
+                         FMA-exact products, on the FP32 units (FP64 runs at 1/64 of their
+                         rate on this GPU); dots in float-float, coefficients, Newton and
+                         recombination in FP64.  Per-step rounding near 2^-47 instead of 2^-24:
+                         the accuracy class of LQ_FP64 at a fraction of its time.  Stencil
+                         schedule 0 only, no split loop; lq_sign_bilinear_grad returns
+                         LQ_ERR_ARG for such a context                                     */
 
 /* ---- derivative directions (d_t of Eq. (2.5)) --------------------------------------- */
 #define LQ_DIR_MU   0   /* d/dmu: field unused                                               */
@@ -78,7 +86,7 @@ typedef struct {
     double r;              /* Wilson parameter; only r = 1 is supported (spin projectors)     */
     double mu;             /* chemical potential                                              */
     int t_antiperiodic;    /* 1: antiperiodic in time (default), 0: periodic                  */
-    int precision;         /* LQ_FP64, LQ_MIXED or LQ_MIXED_BF16                              */
+    int precision;         /* LQ_FP64, LQ_MIXED, LQ_MIXED_BF16 or LQ_FLOAT_FLOAT             */
 } lq_lattice_desc;
 
 typedef struct {

@@ -95,13 +95,18 @@ int dalloc(lq_ctx* c, T** p, size_t count) {
 
 void dfree(void* p) { if (p) cudaFree(p); }
 
-size_t fe(const lq_ctx* c) {  // Chunk elements of one field
-    return c->prec == LQ_FP64 ? field_elems<double>(c->V) : field_elems<float>(c->V);
-}
-size_t fb(const lq_ctx* c) {  // bytes of one field
-    return c->prec == LQ_FP64 ? field_bytes<double>(c->V) : field_bytes<float>(c->V);
-}
+// Chunk elements / bytes of one field in the internal layout of precision prec (FP64 and
+// float-float: 12 chunks of 16 bytes per site; FP32: 6)
+size_t field_elems_of(int prec, size_t V) { return prec == LQ_MIXED ? field_elems<float>(V) : field_elems<double>(V); }
+size_t field_bytes_of(int prec, size_t V) { return prec == LQ_MIXED ? field_bytes<float>(V) : field_bytes<double>(V); }
+size_t fe(const lq_ctx* c) { return field_elems_of(c->prec, c->V); }   // Chunk elements of one field
+size_t fb(const lq_ctx* c) { return field_bytes_of(c->prec, c->V); }   // bytes of one field
 size_t chunk_bytes(const lq_ctx* c) { return c->prec == LQ_FP64 ? sizeof(double2) : sizeof(float4); }
+// bytes of one complex link entry in the internal layout (BF16: two bfloat16)
+size_t link_entry_bytes(const lq_ctx* c) {
+    if (c->prec == LQ_MIXED) return c->link_bf16 ? (size_t)4 : sizeof(float2);
+    return 16;   // double2, or float-float (hi, lo) x (re, im)
+}
 
 
 // Copy n doubles from a caller buffer (host or device) into device memory.
@@ -273,7 +278,7 @@ void free_workspace(lq_ctx* c) {
 // coefficients), so the tuning leaves no trace in the results.
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
-    const int nvar = (c->prec == LQ_FP64) ? 2 : kHopSchedules;
+    const int nvar = (c->prec == LQ_FP64) ? 2 : (c->prec == LQ_FLOAT_FLOAT ? 1 : kHopSchedules);
     // candidates: FP64 0-1; FP32 all but the packed schedules 7 and 8 (bitwise the same as 3 and
     // measured slower on every lattice tried: they remain selectable through opts.hop_variant);
     // BF16 links without 6 (it reads FP32 links)
@@ -460,6 +465,7 @@ struct TslRun {
             // the plain operator 0 only, and schedule 6 needs tiles that cover the lattice
             int v = (nf == 2) ? o->hop_variant : 0;
             if (c->prec == LQ_FP64 && v > 1) v = 0;
+            if (c->prec == LQ_FLOAT_FLOAT) v = 0;
             if (v == 6 && !tile_ok(h.dims)) v = 3;
             if (c->link_bf16 && v >= 6 && v <= 8) v = 3;
             h.variant = v;
@@ -836,7 +842,7 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     t.y0 = y0; t.y1 = y1; t.fn = fn; t.shifts = shifts; t.store_left = store_left;
     // lq_opts.split: the two source halves' Krylov loops as concurrent branches (the update of one
     // half, bandwidth-bound, overlaps the stencil of the other, issue-bound)
-    const bool split = o->split != 0 && !c->prof_on && c->prec != LQ_FP64 && nf == 2 && fn == FN_SIGN && !store_left &&
+    const bool split = o->split != 0 && !c->prof_on && c->prec == LQ_MIXED && nf == 2 && fn == FN_SIGN && !store_left &&
                        !(o->two_pass != 0 && o->kmax > 1) && nsrc >= 8 && nsrc % 2 == 0 &&
                        ensure_cap_stream(c) && ensure_cap_stream(c, true);
     int r;
@@ -1144,10 +1150,10 @@ using cplx = std::complex<double>;
 int apply_H_batch(lq_ctx* c, const double* in, double* out, int count, int dagger, cudaStream_t st,
                   int prec, const void* links) {
     const size_t fb_ctx = fb(c);
-    const size_t fb_op = prec == LQ_FP64 ? field_bytes<double>(c->V) : field_bytes<float>(c->V);
+    const size_t fb_op = field_bytes_of(prec, c->V);
     const int cap = std::max(1, (int)((size_t)c->nsrc * (c->block ? 2 : 1) * fb_ctx / fb_op));
     const size_t nv = nvec(c);
-    const size_t fe_op = prec == LQ_FP64 ? field_elems<double>(c->V) : field_elems<float>(c->V);
+    const size_t fe_op = field_elems_of(prec, c->V);
     for (int b0 = 0; b0 < count; b0 += cap) {
         const int nb = std::min(cap, count - b0);
         LQ_CUDA(c, launch_to_internal(prec, in + (size_t)b0 * nv, c->rout, c->V, nb, st));
@@ -1663,7 +1669,9 @@ int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
     *out = nullptr;
     if (d->nt < 1 || d->nx < 1 || d->ny < 1 || d->nz < 1) return LQ_ERR_ARG;
     if (d->r != 1.0) return LQ_ERR_ARG;
-    if (d->precision != LQ_FP64 && d->precision != LQ_MIXED && d->precision != LQ_MIXED_BF16) return LQ_ERR_ARG;
+    if (d->precision != LQ_FP64 && d->precision != LQ_MIXED && d->precision != LQ_MIXED_BF16 &&
+        d->precision != LQ_FLOAT_FLOAT)
+        return LQ_ERR_ARG;
     if (!std::isfinite(d->mu) || !std::isfinite(d->m_w)) return LQ_ERR_ARG;
     const double vol = (double)d->nt * d->nx * d->ny * d->nz;
     if (vol * 12.0 > 4.0e9) return LQ_ERR_ARG;
@@ -1672,7 +1680,7 @@ int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
     c->desc = *d;
     c->dims[0] = d->nx; c->dims[1] = d->ny; c->dims[2] = d->nz; c->dims[3] = d->nt;
     c->V = (size_t)d->nt * d->nx * d->ny * d->nz;
-    c->prec = d->precision == LQ_FP64 ? LQ_FP64 : LQ_MIXED;
+    c->prec = d->precision == LQ_MIXED_BF16 ? LQ_MIXED : d->precision;
     c->link_bf16 = d->precision == LQ_MIXED_BF16;
     cudaGetDevice(&c->device);
     *out = c;
@@ -1703,8 +1711,8 @@ int lq_upload_gauge(lq_ctx* c, const double* U, void* stream) {
     const size_t n = c->V * 4 * 9 * 2;
     if (!c->Ub) { int r = dalloc(c, &c->Ub, n); if (r) return r; }
     if (!c->U) {
-        // FP64: double2, FP32: float2, BF16: two bfloat16 (4 bytes) per complex entry
-        size_t cb = (c->prec == LQ_FP64 ? sizeof(double2) : (c->link_bf16 ? (size_t)4 : sizeof(float2))) * c->V * 36;
+        // FP64: double2, FP32: float2, BF16: two bfloat16 (4 bytes), float-float: 16 bytes per entry
+        size_t cb = link_entry_bytes(c) * c->V * 36;
         void* p = nullptr;
         if (cudaMalloc(&p, cb) != cudaSuccess) { cudaGetLastError(); return set_err(c, LQ_ERR_OOM, "gauge allocation failed"); }
         c->U = p;
@@ -1718,7 +1726,7 @@ int lq_upload_gauge(lq_ctx* c, const double* U, void* stream) {
         LQ_CUDA(c, launch_links_internal(c->prec, c->Ub, c->U, c->V, st));
     }
     c->launches += 1;
-    if (c->prec != LQ_FP64 && !c->link_bf16) {   // the packed stencil's copy of the FP32 links
+    if (c->prec == LQ_MIXED && !c->link_bf16) {   // the packed stencil's copy of the FP32 links
         if (!c->Up && cudaMalloc(&c->Up, sizeof(float4) * c->V * 36) != cudaSuccess) {
             cudaGetLastError();
             c->Up = nullptr;
@@ -1865,7 +1873,7 @@ int lq_set_direction(lq_ctx* c, const lq_direction* d, void* stream) {
     int r;
     if (!c->dir_scratch && (r = dalloc(c, &c->dir_scratch, c->V * 4 * 8))) return r;
     if (!c->Y) {
-        size_t cb = (c->prec == LQ_FP64 ? sizeof(double2) : sizeof(float2)) * c->V * 36;
+        size_t cb = (c->prec == LQ_MIXED ? sizeof(float2) : (size_t)16) * c->V * 36;
         void* p = nullptr;
         if (cudaMalloc(&p, cb) != cudaSuccess) { cudaGetLastError(); return set_err(c, LQ_ERR_OOM, "direction allocation failed"); }
         c->Y = p;
@@ -1874,7 +1882,7 @@ int lq_set_direction(lq_ctx* c, const lq_direction* d, void* stream) {
     if ((r = stage_in(c, c->dir_scratch, d->field, n, st))) return r;
     LQ_CUDA(c, launch_direction(c->prec, c->Ub, c->dir_scratch, d->kind, c->Y, c->V, st));
     c->launches += 1;
-    if (c->prec != LQ_FP64) {
+    if (c->prec == LQ_MIXED) {
         if (!c->Yp && cudaMalloc(&c->Yp, sizeof(float4) * c->V * 36) != cudaSuccess) {
             cudaGetLastError();
             c->Yp = nullptr;
@@ -2436,7 +2444,7 @@ int lq_compute_deflation(lq_ctx* c, const lq_eig_opts* eo_in, const double* X0, 
         cudaError_t e = launch_links_internal(LQ_FP64, c->Ub, U64, c->V, st);
         if (e != cudaSuccess) return fail(set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e)));
     }
-    if (si && (c->prec == LQ_FP64 || c->link_bf16)) {   // FP32 links for the inner solves
+    if (si && (c->prec != LQ_MIXED || c->link_bf16)) {   // FP32 links for the inner solves
         if (cudaMalloc(&U32, sizeof(float2) * c->V * 36) != cudaSuccess) { cudaGetLastError(); U32 = nullptr; return fail(set_err(c, LQ_ERR_OOM, "eigensolver links")); }
         cudaError_t e = launch_links_internal(LQ_MIXED, c->Ub, U32, c->V, st);
         if (e != cudaSuccess) return fail(set_err(c, LQ_ERR_CUDA, cudaGetErrorString(e)));
@@ -2592,6 +2600,7 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
                           double* dS_dmu, void* stream) {
     if (!c || !x || !y) return set_err(c, LQ_ERR_ARG, "null argument");
     if (!c->adjoint) return set_err(c, LQ_ERR_NOT_READY, "workspace reserved without LQ_RESERVE_ADJOINT");
+    if (c->prec == LQ_FLOAT_FLOAT) return set_err(c, LQ_ERR_ARG, "the adjoint has no float-float kernels (use LQ_FP64)");
     int r = check_ready(c, 2, 0);
     if (r || (r = check_opts(c, o, true))) return r;
     const int l = o->deflate ? c->defl_l : 0;

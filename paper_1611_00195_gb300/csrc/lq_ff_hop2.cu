@@ -1,0 +1,14 @@
+// Float-float block stencil, derivative mode 2 (a link direction: the hops with the links
+// Y = dU/dt): the instantiations of k_hop (lq_kernels.cuh) for lq::ff, schedule 0.
+#include "lq_kernels.cuh"
+
+namespace lq {
+
+cudaError_t launch_hop_ff2(const HopArgs& a, bool dot, cudaStream_t st) {
+    const dim3 grid((unsigned)((a.V + kHopThreads - 1) / kHopThreads), (unsigned)a.nsides, (unsigned)a.nsrc);
+    if (dot) k_hop<ff, 2, 2, true, 1><<<grid, kHopThreads, 0, st>>>(a);
+    else k_hop<ff, 2, 2, false, 1><<<grid, kHopThreads, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+}  // namespace lq

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "../../include/lq.h"
+#include "lq_ff.cuh"
 
 namespace lq {
 
@@ -17,7 +18,8 @@ namespace lq {
 // coalesced 512-byte requests:
 //   FP64: 12 chunks of double2 (one complex each):  f[c * V + s], c = 3*spin + colour
 //   FP32:  6 chunks of float4  (two complex each):  f[q * V + s] holds c = 2q, 2q+1
-// Links: [4 directions][9 elements (row*3+col)][V] of double2 / float2.
+//   float-float: 12 chunks of float4 (one complex each: re.hi, re.lo, im.hi, im.lo)
+// Links: [4 directions][9 elements (row*3+col)][V] of double2 / float2 / float-float complex.
 // A block vector (top, bottom) of Eq. (2.6) is two consecutive fields.
 // ---------------------------------------------------------------------------------------
 template <typename R> struct Tr;
@@ -26,12 +28,21 @@ template <> struct Tr<double> {
     using Chunk = double2;    // storage unit of a spinor field
     static constexpr int kChunks = 12;
     static constexpr int kPerChunk = 1;
+    static constexpr int kKind = 0;
 };
 template <> struct Tr<float> {
     using C = float2;
     using Chunk = float4;
     static constexpr int kChunks = 6;
     static constexpr int kPerChunk = 2;
+    static constexpr int kKind = 1;
+};
+template <> struct Tr<ff> {
+    using C = cff;
+    using Chunk = float4;
+    static constexpr int kChunks = 12;
+    static constexpr int kPerChunk = 1;
+    static constexpr int kKind = 2;
 };
 
 template <typename R> __host__ __device__ inline size_t field_elems(size_t V) {
@@ -83,6 +94,10 @@ __device__ __forceinline__ void load_spinor(const float4* __restrict__ f, size_t
         o[2 * q + 1] = make_float2(v.z, v.w);
     }
 }
+__device__ __forceinline__ void load_spinor(const float4* __restrict__ f, size_t V, size_t s, cff (&o)[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) o[c] = cff_from_chunk(__ldg(f + c * V + s));
+}
 __device__ __forceinline__ void store_spinor(double2* __restrict__ f, size_t V, size_t s, const double2 (&o)[12]) {
 #pragma unroll
     for (int c = 0; c < 12; ++c) f[c * V + s] = o[c];
@@ -90,6 +105,10 @@ __device__ __forceinline__ void store_spinor(double2* __restrict__ f, size_t V, 
 __device__ __forceinline__ void store_spinor(float4* __restrict__ f, size_t V, size_t s, const float2 (&o)[12]) {
 #pragma unroll
     for (int q = 0; q < 6; ++q) f[q * V + s] = make_float4(o[2 * q].x, o[2 * q].y, o[2 * q + 1].x, o[2 * q + 1].y);
+}
+__device__ __forceinline__ void store_spinor(float4* __restrict__ f, size_t V, size_t s, const cff (&o)[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) f[c * V + s] = cff_to_chunk(o[c]);
 }
 
 // ---- error-free transformations (Ogita, Rump & Oishi, SIAM J. Sci. Comput. 26 (2005)) --

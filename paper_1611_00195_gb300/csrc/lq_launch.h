@@ -119,6 +119,19 @@ cudaError_t launch_cg_norm(const CgArgs& a, const float4* v, int slot, cudaStrea
 cudaError_t launch_cg_xr(const CgArgs& a, cudaStream_t st);     // x += alpha p, r -= alpha q, |r|^2
 cudaError_t launch_cg_p(const CgArgs& a, cudaStream_t st);      // p = z + beta p
 // packed-FP32 block stencil (lq_hop_x2.cu): schedule 7, or 8 with the neighbour prefetch
+// float-float instantiations of the kernel templates (lq_ff_hop0.cu .. lq_ff_hop2.cu: the block
+// stencil for derivative mode 0 (and the plain operator), 1 and 2; lq_ff_vec.cu: the rest), called
+// by the launchers above with their grids
+cudaError_t launch_hop_ff0(const HopArgs& a, int nf, bool dot, cudaStream_t st);
+cudaError_t launch_hop_ff1(const HopArgs& a, bool dot, cudaStream_t st);
+cudaError_t launch_hop_ff2(const HopArgs& a, bool dot, cudaStream_t st);
+cudaError_t launch_update_ff(const UpdArgs& a, dim3 grid, cudaStream_t st);
+cudaError_t launch_tsl_init_ff(int nf, const InitArgs& a, dim3 grid, cudaStream_t st);
+cudaError_t launch_recombine_ff(int nf, const RecArgs& a, dim3 grid, size_t smem, cudaStream_t st);
+cudaError_t launch_to_internal_ff(const double* x, void* f, size_t V, int nfields, dim3 grid, cudaStream_t st);
+cudaError_t launch_to_boundary_ff(const void* f, double* x, size_t V, int nfields, dim3 grid, cudaStream_t st);
+cudaError_t launch_links_internal_ff(const double* U, void* L, size_t V, dim3 grid, cudaStream_t st);
+cudaError_t launch_direction_ff(const double* U, const double* w, int kind, void* Y, size_t V, dim3 grid, cudaStream_t st);
 cudaError_t launch_hop_x2(const HopArgs& a, int emode, bool dot, bool prefetch, cudaStream_t st);
 cudaError_t launch_links_packed(const void* L, void* P, size_t V, cudaStream_t st);   // float2 -> (ux, ux, -uy, uy)
 constexpr int kHopSchedules = 10;    // FP32 block-stencil schedules 0..9 (FP64: 0, 1)

@@ -68,6 +68,32 @@ template <> struct DotAcc<float> {
     }
 };
 
+// float-float data: float-float products added into a float-float accumulator (FP32 operations
+// only, as for FP32 data)
+template <> struct DotAcc<ff> {
+    FF v;
+    __device__ __forceinline__ void zero() { v.h = 0.f; v.l = 0.f; }
+    __device__ __forceinline__ void add_prod(ff a, ff b) {
+        const ff p = a * b;
+        float s, t;
+        two_sum_f(v.h, p.hi, s, t);
+        v.h = s;
+        v.l += t + p.lo;
+    }
+    __device__ __forceinline__ void add_plain(ff a, ff b) { v.h = fmaf(a.hi, b.hi, v.h); }
+    __device__ __forceinline__ CSum warp_total() {   // valid in lane 0 only
+        FF r = v;
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            FF o; o.h = __shfl_down_sync(0xffffffffu, r.h, off); o.l = __shfl_down_sync(0xffffffffu, r.l, off);
+            r = ff_merge(r, o);
+        }
+        CSum c{0.0, 0.0};
+        if ((threadIdx.x & 31) == 0) { c.s = (double)r.h; c.e = (double)r.l; }
+        return c;
+    }
+};
+
 // re += Re conj(w) a, im += Im conj(w) a.  FP64: each complex term is formed with one product
 // and one FMA and then added by a compensated two-sum, so the long sums over sites and elements
 // stay compensated while a term costs a few FP64 operations instead of two exact products (FP64
@@ -77,6 +103,10 @@ __device__ __forceinline__ void add_cdot(DotAcc<double>& re, DotAcc<double>& im,
     cs_add(im.v, fma(w.x, a.y, -(w.y * a.x)));
 }
 __device__ __forceinline__ void add_cdot(DotAcc<float>& re, DotAcc<float>& im, float2 w, float2 a) {
+    re.add_prod(w.x, a.x); re.add_prod(w.y, a.y);
+    im.add_prod(w.x, a.y); im.add_prod(-w.y, a.x);
+}
+__device__ __forceinline__ void add_cdot(DotAcc<ff>& re, DotAcc<ff>& im, cff w, cff a) {
     re.add_prod(w.x, a.x); re.add_prod(w.y, a.y);
     im.add_prod(w.x, a.y); im.add_prod(-w.y, a.x);
 }
@@ -234,9 +264,17 @@ __device__ __forceinline__ void load_link(const C* __restrict__ L, size_t V, int
 #pragma unroll
     for (int e = 0; e < 9; ++e) u[e] = __ldg(L + ((size_t)nu * 9 + e) * V + s);
 }
+__device__ __forceinline__ void load_link(const cff* __restrict__ L, size_t V, int nu, size_t s, cff (&u)[9]) {
+    const float4* L4 = reinterpret_cast<const float4*>(L);
+#pragma unroll
+    for (int e = 0; e < 9; ++e) u[e] = cff_from_chunk(__ldg(L4 + ((size_t)nu * 9 + e) * V + s));
+}
 // The gauge links of the operator: FP32 or FP64 entries, or BF16 pairs widened to FP32.
 __device__ __forceinline__ void load_gauge(const HopArgs& a, size_t V, int nu, size_t s, double2 (&u)[9]) {
     load_link(reinterpret_cast<const double2*>(a.U), V, nu, s, u);
+}
+__device__ __forceinline__ void load_gauge(const HopArgs& a, size_t V, int nu, size_t s, cff (&u)[9]) {
+    load_link(reinterpret_cast<const cff*>(a.U), V, nu, s, u);
 }
 __device__ __forceinline__ void load_gauge(const HopArgs& a, size_t V, int nu, size_t s, float2 (&u)[9]) {
     if (a.link_bf16) {
@@ -269,6 +307,9 @@ template <> __device__ __forceinline__ float fac_e<float>(const HopArgs& a, int 
 template <typename R> __device__ __forceinline__ R fac_diag(const HopArgs& a);
 template <> __device__ __forceinline__ double fac_diag<double>(const HopArgs& a) { return a.diag; }
 template <> __device__ __forceinline__ float fac_diag<float>(const HopArgs& a) { return a.diag_f; }
+template <> __device__ __forceinline__ ff fac_a<ff>(const HopArgs& a, int side, int nu, bool fwd) { return ff(fwd ? a.a_fwd[side][nu] : a.a_bwd[side][nu]); }
+template <> __device__ __forceinline__ ff fac_e<ff>(const HopArgs& a, int side, int nu, bool fwd) { return ff(fwd ? a.e_fwd[side][nu] : a.e_bwd[side][nu]); }
+template <> __device__ __forceinline__ ff fac_diag<ff>(const HopArgs& a) { return ff(a.diag); }
 
 // Site coordinates (x, y, z, t) from the linear site index (32-bit arithmetic: V < 2^31).
 __device__ __forceinline__ void site_coords(const HopArgs& a, size_t s, int (&x)[4]) {
@@ -319,6 +360,15 @@ __device__ __forceinline__ float4 axpy3<float>(float4 r, float4 v, float4 p, con
     return make_float4(o0.x, o0.y, o1.x, o1.y);
 }
 
+template <>
+__device__ __forceinline__ float4 axpy3<ff>(float4 r, float4 v, float4 p, const cff (&c)[3], bool has_prev) {
+    const cff rr = cff_from_chunk(r), vv = cff_from_chunk(v);
+    cff o = cmul(c[0], rr);
+    o = cfma(c[1], vv, o);
+    if (has_prev) o = cfma(c[2], cff_from_chunk(p), o);
+    return cff_to_chunk(o);
+}
+
 template <typename R>
 __device__ __forceinline__ void dot_chunk(DotAcc<R> (&d)[6], typename Tr<R>::Chunk w, typename Tr<R>::Chunk v);
 // omega = <w, v> compensated over the elements (it becomes delta_j and beta_j); the norms
@@ -336,11 +386,22 @@ __device__ __forceinline__ void dot_chunk<float>(DotAcc<float> (&d)[6], float4 w
     d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y); d[2].add_plain(v.z, v.z); d[2].add_plain(v.w, v.w);
     d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y); d[3].add_plain(w.z, w.z); d[3].add_plain(w.w, w.w);
 }
+template <>
+__device__ __forceinline__ void dot_chunk<ff>(DotAcc<ff> (&d)[6], float4 w4, float4 v4) {
+    const cff w = cff_from_chunk(w4), v = cff_from_chunk(v4);
+    add_cdot(d[0], d[1], w, v);
+    d[2].add_plain(v.x, v.x); d[2].add_plain(v.y, v.y);
+    d[3].add_plain(w.x, w.x); d[3].add_plain(w.y, w.y);
+}
 // |B vh_j|^2 (d[4]) and |B^dag wh_j|^2 (d[5]): the scale against which an invariant subspace is
 // detected (plain sums, thresholds only)
 __device__ __forceinline__ void norm_chunk(DotAcc<double> (&d)[6], double2 r, double2 l) {
     d[4].add_plain(r.x, r.x); d[4].add_plain(r.y, r.y);
     d[5].add_plain(l.x, l.x); d[5].add_plain(l.y, l.y);
+}
+__device__ __forceinline__ void norm_chunk(DotAcc<ff> (&d)[6], float4 r, float4 l) {
+    d[4].add_plain(ff(r.x), ff(r.x)); d[4].add_plain(ff(r.z), ff(r.z));
+    d[5].add_plain(ff(l.x), ff(l.x)); d[5].add_plain(ff(l.z), ff(l.z));
 }
 __device__ __forceinline__ void norm_chunk(DotAcc<float> (&d)[6], float4 r, float4 l) {
     d[4].add_plain(r.x, r.x); d[4].add_plain(r.y, r.y); d[4].add_plain(r.z, r.z); d[4].add_plain(r.w, r.w);
@@ -353,6 +414,7 @@ __device__ __forceinline__ void norm_chunk(DotAcc<float> (&d)[6], float4 r, floa
 template <typename R> __host__ __device__ constexpr double invariant_tol();
 template <> __host__ __device__ constexpr double invariant_tol<double>() { return 1e-10; }
 template <> __host__ __device__ constexpr double invariant_tol<float>() { return 1e-5; }
+template <> __host__ __device__ constexpr double invariant_tol<ff>() { return 1e-10; }
 
 // The scalar step after omega_j = <wh_{j+1}, vh_{j+1}> (res[0], res[1]) and the norms res[2..5]:
 // breakdown and invariant-subspace tests, delta_j = sqrt|omega|, beta_j = omega / delta_j and the

@@ -30,7 +30,7 @@ KERNEL_REV = "hop-v7"
 ERRORS = {-1: "LQ_ERR_ARG", -2: "LQ_ERR_LAYOUT", -3: "LQ_ERR_OOM", -4: "LQ_ERR_CUDA", -5: "LQ_ERR_BREAKDOWN",
           -6: "LQ_ERR_NEWTON", -7: "LQ_ERR_TIMEOUT", -8: "LQ_ERR_NOT_READY", -9: "LQ_ERR_NONFINITE",
           -10: "LQ_ERR_NOT_CONVERGED"}
-LQ_FP64, LQ_MIXED, LQ_MIXED_BF16 = 0, 1, 2
+LQ_FP64, LQ_MIXED, LQ_MIXED_BF16, LQ_FLOAT_FLOAT = 0, 1, 2, 3
 LQ_DIR_MU, LQ_DIR_SU3, LQ_DIR_U1 = 0, 1, 2
 LQ_PROJ_AUTO, LQ_PROJ_NEWTON, LQ_PROJ_QUAD, LQ_PROJ_NESTED = 0, 1, 2, 3
 LQ_EIG_SHIFT_INVERT, LQ_EIG_CHEBYSHEV = 0, 1

@@ -18,6 +18,11 @@ FP64_SENS_FACTOR = 5.0
 FP32_SENS_FACTOR = 20.0
 FP32_DEEP_SENS_FACTOR = 60.0
 ADJ_SENS_FACTOR = 18.0
+# float-float: relative noise of one operator application in the oracle's sensitivity runs, 2^-44
+# (a float-float result carries a few units of 2^-47 after the sums of a Wilson hop), and the
+# factor allowed over the oracle's response to it (the FP32 tests' factor)
+FF_STEP_NOISE = 2.0 ** -44
+FF_SENS_FACTOR = 20.0
 
 
 def round_bf16(a):
@@ -71,8 +76,9 @@ def oracle_block_tsl_run(job):
     """One oracle block-TSL run (Eq. (2.6), d/dmu) for a process pool, built from seeds so that
     nothing but plain data crosses the process boundary.  job = (dims, eps, gauge_seed,
     source_seed, mu, k, perturbation, perturbation_seed); perturbation None, "input" (1e-16
-    relative noise on the source: the FP64 rounding sensitivity) or "step" (6e-8 relative noise
-    on every operator application: the FP32 sensitivity).  Returns (d sgn(H) x, sgn(H) x)."""
+    relative noise on the source: the FP64 rounding sensitivity), "step" (6e-8 relative noise
+    on every operator application: the FP32 sensitivity) or "step_ff" (FF_STEP_NOISE on every
+    operator application: the float-float sensitivity).  Returns (d sgn(H) x, sgn(H) x)."""
     import synthetic as syn
     from oracle import tsl as ot
     dims, eps, gseed, sseed, mu, k, pert, pseed = job
@@ -82,11 +88,13 @@ def oracle_block_tsl_run(job):
     rng = np.random.default_rng(pseed)
     if pert == "input":
         x = x * (1 + 1e-16 * rng.standard_normal(x.shape))
-    elif pert == "step":
+    elif pert in ("step", "step_ff"):
+        size = 6e-8 if pert == "step" else FF_STEP_NOISE
+
         def wrap(op):
             def f(v):
                 y = op(v)
-                return y * (1 + 6e-8 * (rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape)) / np.sqrt(2))
+                return y * (1 + size * (rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape)) / np.sqrt(2))
             return f
         A, Ah, E, Eh = wrap(A), wrap(Ah), wrap(E), wrap(Eh)
     rd, rs, _ = ot.tsl_sign_derivative(A, Ah, E, Eh, x, k)

@@ -1,0 +1,123 @@
+"""The float-float precision (LQ_FLOAT_FLOAT: links, vectors, stencil and update in pairs of FP32
+numbers with compensated sums and FMA-exact products) against the FP64 oracle:
+  * the operator H(mu) and its adjoint on a ragged lattice, at the float-float rounding level;
+  * the block TSL of Eq. (2.6) at the same depth, d/dmu and an su(3) link direction, within
+    FF_SENS_FACTOR of the oracle's response to FF_STEP_NOISE on every operator application;
+  * the precision workload where the mixed path misses 1e-6 (8^4, mu = 0.2, k = 200): float-float
+    within 1e-6 of the FP64 oracle, and of the FP64 GPU path."""
+import multiprocessing as mp
+
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from oracle import dirac as od
+from oracle import tsl as ot
+from tests.helpers import FF_SENS_FACTOR, FF_STEP_NOISE, oracle_block_tsl_run, oracle_ops, relerr
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.mark.parametrize("mu", [0.0, 0.3])
+def test_float_float_operator(lqlib, mu):
+    from paper_1611_00195_gb300 import lq
+    dims = (5, 3, 3, 4)
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = syn.gaussian_source(dims, 5, nsrc=2)
+    c = lq.Context(dims, mu=mu, precision=lq.LQ_FLOAT_FLOAT)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    lat = od.Lattice(dims, m_w=-2.0)
+    for dag in (False, True):
+        y = c.apply_H(torch.from_numpy(x).cuda(), dagger=dag).cpu().numpy()
+        for s in range(2):
+            ref = (od.apply_Hdag if dag else od.apply_H)(lat, U, x[s], mu)
+            e = relerr(y[s], ref)
+            print("float-float H%s mu=%.1f source %d: %.3g" % ("^dag" if dag else "", mu, s, e))
+            assert e < 1e-12
+
+
+def _pert(rng, size):
+    def wrap(op):
+        def f(v):
+            y = op(v)
+            return y * (1 + size * (rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape)) / np.sqrt(2))
+        return f
+    return wrap
+
+
+@pytest.mark.parametrize("kind", [0, 1])
+def test_float_float_block_tsl_parity(lqlib, kind):
+    from paper_1611_00195_gb300 import lq
+    dims, k, mu, nsrc = (4, 4, 2, 6), 60, 0.3, 2
+    U = syn.gauge_field(dims, 0.4, 3)
+    x = syn.gaussian_source(dims, 5, nsrc=nsrc)
+    field = syn.su3_direction(dims, 77) if kind == 1 else None
+    c = lq.Context(dims, mu=mu, precision=lq.LQ_FLOAT_FLOAT)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(k, nsrc, True)
+    ys, yd, rep = c.sign_derivative_apply(torch.from_numpy(x).cuda(), k, kind=kind,
+                                          field=torch.from_numpy(field).cuda() if field is not None else None)
+    ys, yd = ys.cpu().numpy(), yd.cpu().numpy()
+    lat, A, Ah, E, Eh = oracle_ops(dims, U, mu, kind=kind, field=field)
+    rng = np.random.default_rng(23)
+    w = _pert(rng, FF_STEP_NOISE)
+    for s in range(nsrc):
+        assert rep[s]["status"] == 0 and rep[s]["k_eff"] == k and rep[s]["hop_variant"] == 0
+        rd, rs, _ = ot.tsl_sign_derivative(A, Ah, E, Eh, x[s].ravel(), k)
+        pd, ps, _ = ot.tsl_sign_derivative(w(A), w(Ah), w(E), w(Eh), x[s].ravel(), k)
+        sens = max(relerr(pd, rd), relerr(ps, rs))
+        errs = [relerr(ys[s], rs), relerr(yd[s], rd)]
+        print("float-float block TSL kind %d source %d: sign %.3g deriv %.3g (float-float sensitivity %.3g, "
+              "ratio %.2f)" % (kind, s, errs[0], errs[1], sens, max(errs) / sens))
+        assert max(errs) < max(1e-12, FF_SENS_FACTOR * sens)
+
+
+def test_float_float_meets_the_target_where_mixed_does_not(lqlib):
+    """8^4, eps 0.4, mu = 0.2, k = 200, one Gaussian source: the mixed path differs from FP64 by
+    about 1e-3 on the derivative here (the process amplifies FP32 rounding); float-float stays
+    within 1e-6 of the FP64 oracle and of the FP64 GPU path."""
+    from paper_1611_00195_gb300 import lq
+    dims, eps, k, mu = (8, 8, 8, 8), 0.4, 200, 0.2
+    jobs = [(dims, eps, 3, 5, mu, k, None, 17), (dims, eps, 3, 5, mu, k, "step_ff", 17)]
+    with mp.get_context("spawn").Pool(2) as pool:
+        (rd, rs), (pd, ps) = pool.map(oracle_block_tsl_run, jobs)
+    sens = max(relerr(pd, rd), relerr(ps, rs))
+    U = torch.from_numpy(syn.gauge_field(dims, eps, 3)).cuda()
+    x = torch.from_numpy(syn.gaussian_source(dims, 5, nsrc=1)).cuda()
+    out = {}
+    for prec in (lq.LQ_FP64, lq.LQ_FLOAT_FLOAT, lq.LQ_MIXED):
+        c = lq.Context(dims, mu=mu, precision=prec)
+        c.upload_gauge(U)
+        c.reserve(k, 1, True)
+        ys, yd, rep = c.sign_derivative_apply(x, k)
+        assert rep[0]["status"] == 0 and rep[0]["k_eff"] == k
+        out[prec] = (ys[0].cpu().numpy(), yd[0].cpu().numpy())
+    e_ff = max(relerr(out[lq.LQ_FLOAT_FLOAT][0], rs), relerr(out[lq.LQ_FLOAT_FLOAT][1], rd))
+    e_64 = max(relerr(out[lq.LQ_FP64][0], rs), relerr(out[lq.LQ_FP64][1], rd))
+    e_32 = max(relerr(out[lq.LQ_MIXED][0], rs), relerr(out[lq.LQ_MIXED][1], rd))
+    g_ff = max(relerr(out[lq.LQ_FLOAT_FLOAT][i], out[lq.LQ_FP64][i]) for i in (0, 1))
+    print("8^4 mu=0.2 k=200 vs the oracle: FP64 %.3g, float-float %.3g (float-float sensitivity %.3g, ratio %.2f), "
+          "mixed %.3g; float-float vs FP64 GPU %.3g (target 1e-6)" % (e_64, e_ff, sens, e_ff / sens, e_32, g_ff))
+    assert e_ff <= 1e-6 and g_ff <= 1e-6
+    assert e_ff < max(1e-12, FF_SENS_FACTOR * sens)
+
+
+def test_float_float_runs_one_batch_and_replays_its_graph(lqlib):
+    from paper_1611_00195_gb300 import lq
+    dims, k, nsrc = (4, 4, 2, 6), 40, 8
+    c = lq.Context(dims, mu=0.3, precision=lq.LQ_FLOAT_FLOAT)
+    c.upload_gauge(torch.from_numpy(syn.gauge_field(dims, 0.4, 3)).cuda())
+    c.reserve(k, nsrc, True)
+    x = torch.from_numpy(syn.gaussian_source(dims, 5, nsrc=nsrc)).cuda()
+    a = c.sign_derivative_apply(x, k)               # graph captured (no split for float-float)
+    b = c.sign_derivative_apply(x, k)               # replayed
+    p = c.sign_derivative_apply(x, k, graph=0, split=0)
+    for r in (b, p):
+        assert torch.equal(a[0], r[0]) and torch.equal(a[1], r[1])
+    assert all(r["hop_variant"] == 0 for r in a[2])
+    ca = lq.Context(dims, mu=0.3, precision=lq.LQ_FLOAT_FLOAT)
+    ca.upload_gauge(torch.from_numpy(syn.gauge_field(dims, 0.4, 3)).cuda())
+    ca.reserve(k, 2, block=False, adjoint=True)
+    with pytest.raises(lq.LQError):
+        ca.bilinear_grad(x[0], x[1], k)
