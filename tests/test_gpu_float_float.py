@@ -27,6 +27,7 @@ def test_float_float_operator(lqlib, mu):
     x = syn.gaussian_source(dims, 5, nsrc=2)
     c = lq.Context(dims, mu=mu, precision=lq.LQ_FLOAT_FLOAT)
     c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(4, 2, True)
     lat = od.Lattice(dims, m_w=-2.0)
     for dag in (False, True):
         y = c.apply_H(torch.from_numpy(x).cuda(), dagger=dag).cpu().numpy()
