@@ -431,6 +431,31 @@ def main():
                 "rel_err_mixed_vs_fp64_sign": {"max": float(es.max()), "median": float(np.median(es))},
                 "rel_err_mixed_vs_fp64_deriv": {"max": float(ed.max()), "median": float(np.median(ed))}}
         del ctx64
+        # the float-float path (LQ_FLOAT_FLOAT) on the same workload: FP64-class rounding on the
+        # FP32 units; its rate and its difference from the FP64 path
+        cff = lq.Context(DIMS, m_w=M_W, mu=MU, precision=lq.LQ_FLOAT_FLOAT)
+        cff.upload_gauge(torch.from_numpy(U).to(dev))
+        cff.reserve(k, nsrc, True)
+        ysf, ydf = torch.empty_like(xd), torch.empty_like(xd)
+        cff.sign_derivative_apply(xd, k, out=(ysf, ydf))
+        torch.cuda.synchronize(dev)
+        a.record(stream)
+        cff.sign_derivative_apply(xd, k, out=(ysf, ydf))
+        b.record(stream)
+        torch.cuda.synchronize(dev)
+        msf = a.elapsed_time(b)
+        cff.profile_enable(True)
+        cff.sign_derivative_apply(xd, k, out=(ysf, ydf))
+        pf = cff.profile()
+        cff.profile_enable(False)
+        fs, fd = rel(ysf, ys64), rel(ydf, yd64)
+        fp64["float_float"] = {"value": nsrc / (msf / 1e3), "unit": "solves/s", "ms_per_step": msf,
+                               "speedup_over_fp64": ms64 / msf,
+                               "stencil_ms_per_launch": pf["hop_ms"] / max(1, pf["hop_launches"]),
+                               "update_ms_per_launch": pf["update_ms"] / max(1, pf["update_launches"]),
+                               "rel_err_vs_fp64_sign": {"max": float(fs.max()), "median": float(np.median(fs))},
+                               "rel_err_vs_fp64_deriv": {"max": float(fd.max()), "median": float(np.median(fd))}}
+        del cff
 
     # the other workloads of the same configuration: an su(3) link direction (k as configured)
     # and k = 800 (d/dmu); two timed steps each after one warm-up, same clock and events
@@ -574,8 +599,8 @@ def main():
                                  "status": [[x["status"] for x in m_out[2]] for m_out in rb]}
         del members
         # the precision workload: 8^4, one Gaussian source, k = 200, mu in {0, 0.1, 0.2}; the
-        # plain FP64 GPU path against the mixed path (their relative difference per mu; the
-        # FP64 path's parity with the oracle is a GPU test)
+        # plain FP64 GPU path against the mixed and the float-float paths (their relative
+        # differences per mu; the parity of each with the oracle is a GPU test)
         d2, k2 = (8, 8, 8, 8), 200
         x2p = torch.from_numpy(syn.gaussian_source(d2, SOURCE_SEED, nsrc=1)).to(dev)
         U2 = torch.from_numpy(syn.gauge_field(d2, EPS, GAUGE_SEED)).to(dev)
@@ -583,7 +608,7 @@ def main():
         for mu2 in (0.0, 0.1, 0.2):
             row = {"mu": mu2}
             res2 = {}
-            for pname, pcode in (("fp64", lq.LQ_FP64), ("mixed", lq.LQ_MIXED)):
+            for pname, pcode in (("fp64", lq.LQ_FP64), ("mixed", lq.LQ_MIXED), ("float_float", lq.LQ_FLOAT_FLOAT)):
                 c2 = lq.Context(d2, m_w=M_W, mu=mu2, precision=pcode)
                 c2.upload_gauge(U2)
                 c2.reserve(k2, 1, True)
@@ -594,6 +619,8 @@ def main():
             rel = lambda a, b: float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
             row["mixed_vs_fp64_rel_diff"] = {"sign": rel(res2["mixed"][0], res2["fp64"][0]),
                                              "deriv": rel(res2["mixed"][1], res2["fp64"][1])}
+            row["float_float_vs_fp64_rel_diff"] = {"sign": rel(res2["float_float"][0], res2["fp64"][0]),
+                                                   "deriv": rel(res2["float_float"][1], res2["fp64"][1])}
             prec_rows.append(row)
         extra["precision_8x8c3"] = {"k": k2, "source": "1 Gaussian", "eps": EPS, "per_mu": prec_rows}
         # the differentiation workload: 12x12^3, k = 300, mu = 0.3, S = Re <y|sgn(H)|x> with the
@@ -615,13 +642,13 @@ def main():
             del c5
         force["mixed_vs_fp64_rel_diff"] = float(torch.linalg.vector_norm(F5["mixed"] - F5["fp64"]) / torch.linalg.vector_norm(F5["fp64"]))
         extra["force_12x12c3"] = force
-        # accuracy at a converged depth on this workload: 2 sources, k = 2400, FP64 and mixed, with
-        # eps_A of the derivative (Sec. 4) for each path and their relative difference
+        # accuracy at a converged depth on this workload: 2 sources, k = 2400, FP64, float-float and
+        # mixed, with eps_A of the derivative (Sec. 4) for each path and their differences from FP64
         kc, nc = 2400, 2
         xc = xd[:nc].contiguous()
         conv = {"k": kc, "sources": nc}
         resc = {}
-        for pname, pcode in (("fp64", lq.LQ_FP64), ("mixed", lq.LQ_MIXED)):
+        for pname, pcode in (("fp64", lq.LQ_FP64), ("float_float", lq.LQ_FLOAT_FLOAT), ("mixed", lq.LQ_MIXED)):
             cc = lq.Context(DIMS, m_w=M_W, mu=MU, precision=pcode)
             cc.upload_gauge(torch.from_numpy(U).to(dev))
             cc.reserve(kc, nc, True)
@@ -633,6 +660,8 @@ def main():
             del cc
         relv = lambda a, b: (torch.linalg.vector_norm((a - b).reshape(nc, -1), dim=1) / torch.linalg.vector_norm(b.reshape(nc, -1), dim=1)).tolist()
         conv["mixed_vs_fp64_rel_diff"] = {"sign": relv(resc["mixed"][0], resc["fp64"][0]), "deriv": relv(resc["mixed"][1], resc["fp64"][1])}
+        conv["float_float_vs_fp64_rel_diff"] = {"sign": relv(resc["float_float"][0], resc["fp64"][0]),
+                                                "deriv": relv(resc["float_float"][1], resc["fp64"][1])}
         extra["converged_depth_accuracy"] = conv
         # the axial-current workload on the paper's lattice shape for it: 6x18^3, mu = 0.04, the
         # massless overlap operator, 8 Z2 noise vectors, the current through all z links (a U(1)

@@ -4,6 +4,8 @@
 #pragma once
 #include <cuda_bf16.h>
 
+#include <type_traits>
+
 #include "lq_internal.cuh"
 #include "lq_launch.h"
 
@@ -225,9 +227,36 @@ __device__ __forceinline__ void project(const C (&p)[12], C (&h)[6]) {
     }
 }
 
+// Float-float accumulator step a += s b (s = +-1) without renormalising: TwoSum of the high
+// parts, the rest into the low part.  The accumulators of a site's output spinor take eight such
+// steps per component and are renormalised once, in finish(), by its float-float FMA.
+template <bool NEG>
+__device__ __forceinline__ void ff_acc_add(ff& a, ff b) {
+    float s, t;
+    two_sum_f(a.hi, NEG ? -b.hi : b.hi, s, t);
+    a.hi = s;
+    a.lo += t + (NEG ? -b.lo : b.lo);
+}
+
 // acc += (g, s B^dag g)
 template <typename C, int NU, int SP>
 __device__ __forceinline__ void reconstruct_add(const C (&g)[6], C (&acc)[12]) {
+    if constexpr (std::is_same_v<C, cff>) {
+#pragma unroll
+        for (int col = 0; col < 3; ++col) {
+            const cff g0 = g[col], g1 = g[3 + col];
+            cff l0, l1;   // B^dag g
+            if (NU == 0) { l0 = cmul_i(g1); l1 = cmul_i(g0); }
+            else if (NU == 1) { l0 = g1; l1 = cmk<cff>(-g0.x, -g0.y); }
+            else if (NU == 2) { l0 = cmul_i(g0); l1 = cmul_mi(g1); }
+            else { l0 = g0; l1 = g1; }
+            ff_acc_add<false>(acc[col].x, g0.x); ff_acc_add<false>(acc[col].y, g0.y);
+            ff_acc_add<false>(acc[3 + col].x, g1.x); ff_acc_add<false>(acc[3 + col].y, g1.y);
+            ff_acc_add<(SP < 0)>(acc[6 + col].x, l0.x); ff_acc_add<(SP < 0)>(acc[6 + col].y, l0.y);
+            ff_acc_add<(SP < 0)>(acc[9 + col].x, l1.x); ff_acc_add<(SP < 0)>(acc[9 + col].y, l1.y);
+        }
+        return;
+    }
 #pragma unroll
     for (int col = 0; col < 3; ++col) {
         C g0 = g[col], g1 = g[3 + col];
@@ -243,8 +272,51 @@ __device__ __forceinline__ void reconstruct_add(const C (&g)[6], C (&acc)[12]) {
     }
 }
 
+// Float-float accumulation of a sum of products without renormalising after every term: the
+// high parts of the exact products (one product and one FMA each) are added by TwoSum into s,
+// everything of order u |term| (the products' errors, the cross terms hi * lo, the TwoSum
+// errors) into e in FP32; one TwoSum of (s, e) at the end.  Twelve FP32 operations per real
+// product instead of about twenty-six for a float-float multiply followed by an add.
+struct FFSum {
+    float s, e;
+};
+template <bool NEG>
+__device__ __forceinline__ void ffsum_add_prod(FFSum& a, ff x, ff y) {
+    float p = x.hi * y.hi;
+    float pe = fmaf(x.hi, y.hi, -p);
+    pe = fmaf(x.hi, y.lo, pe);
+    pe = fmaf(x.lo, y.hi, pe);
+    if (NEG) { p = -p; pe = -pe; }
+    float s, t;
+    two_sum_f(a.s, p, s, t);
+    a.s = s;
+    a.e += t + pe;
+}
+
 template <typename C, bool DAG>
 __device__ __forceinline__ void su3_mul(const C (&u)[9], const C (&h)[6], C (&g)[6]) {
+    if constexpr (std::is_same_v<C, cff>) {
+        // float-float: each output component as one FFSum over its six real products
+#pragma unroll
+        for (int sc = 0; sc < 2; ++sc)
+#pragma unroll
+            for (int row = 0; row < 3; ++row) {
+                FFSum re{0.f, 0.f}, im{0.f, 0.f};
+#pragma unroll
+                for (int col = 0; col < 3; ++col) {
+                    const cff uu = DAG ? u[col * 3 + row] : u[row * 3 + col];
+                    const cff hh = h[sc * 3 + col];
+                    // U h: (ux hx - uy hy, ux hy + uy hx);  U^dag h: (ux hx + uy hy, ux hy - uy hx)
+                    ffsum_add_prod<false>(re, uu.x, hh.x);
+                    ffsum_add_prod<!DAG>(re, uu.y, hh.y);
+                    ffsum_add_prod<false>(im, uu.x, hh.y);
+                    ffsum_add_prod<DAG>(im, uu.y, hh.x);
+                }
+                g[sc * 3 + row].x = ff_two_sum(re.s, re.e);
+                g[sc * 3 + row].y = ff_two_sum(im.s, im.e);
+            }
+        return;
+    }
 #pragma unroll
     for (int sc = 0; sc < 2; ++sc)
 #pragma unroll
