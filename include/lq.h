@@ -68,8 +68,9 @@ extern "C" {
                          rate on this GPU); dots in float-float, coefficients, Newton and
                          recombination in FP64.  Per-step rounding near 2^-47 instead of 2^-24:
                          the accuracy class of LQ_FP64 at a fraction of its time.  Stencil
-                         schedule 0 only, no split loop; lq_sign_bilinear_grad returns
-                         LQ_ERR_ARG for such a context                                     */
+                         schedules 0 (one thread per site and side), 1 and 2 (one thread per
+                         site and output field, at least 3 / 4 blocks per SM); no split
+                         loop; lq_sign_bilinear_grad returns LQ_ERR_ARG for such a context */
 
 /* ---- derivative directions (d_t of Eq. (2.5)) --------------------------------------- */
 #define LQ_DIR_MU   0   /* d/dmu: field unused                                               */

@@ -278,7 +278,7 @@ void free_workspace(lq_ctx* c) {
 // coefficients), so the tuning leaves no trace in the results.
 int tune_hop(lq_ctx* c, HopArgs h, int nf, int emode, cudaStream_t st, int* variant) {
     if (nf != 2) { *variant = 0; return LQ_OK; }
-    const int nvar = (c->prec == LQ_FP64) ? 2 : (c->prec == LQ_FLOAT_FLOAT ? 1 : kHopSchedules);
+    const int nvar = c->prec == LQ_FP64 ? 2 : (c->prec == LQ_FLOAT_FLOAT ? 3 : kHopSchedules);
     // candidates: FP64 0-1; FP32 all but the packed schedules 7 and 8 (bitwise the same as 3 and
     // measured slower on every lattice tried: they remain selectable through opts.hop_variant);
     // BF16 links without 6 (it reads FP32 links)
@@ -465,7 +465,7 @@ struct TslRun {
             // the plain operator 0 only, and schedule 6 needs tiles that cover the lattice
             int v = (nf == 2) ? o->hop_variant : 0;
             if (c->prec == LQ_FP64 && v > 1) v = 0;
-            if (c->prec == LQ_FLOAT_FLOAT) v = 0;
+            if (c->prec == LQ_FLOAT_FLOAT && v > 2) v = 0;
             if (v == 6 && !tile_ok(h.dims)) v = 3;
             if (c->link_bf16 && v >= 6 && v <= 8) v = 3;
             h.variant = v;

@@ -17,122 +17,6 @@
 namespace lq {
 
 // ---------------------------------------------------------------------------------------
-// Role-split block stencil: one thread per (site, output field, source).  The four outputs
-// of a site for the block operator of Eq. (2.5) are
-//   role 0: A t + E b      role 1: A b          (right side, operator A = H(mu))
-//   role 2: A^dag p        role 3: A^dag q + E^dag p   (left side, A^dag = H(-mu))
-// A block holds RS sites x 4 roles (RS / 32 warps per role), so the four roles read the
-// same links and neighbour sites and share them in L1.  The alpha dot is accumulated by the
-// right-side roles: conj(p(x)) . (A t + E b)(x) + conj(q(x)) . (A b)(x).
-// ---------------------------------------------------------------------------------------
-constexpr int kRoleSites = 32;
-
-template <typename R, int EMODE, int NU, int SP>
-__device__ __forceinline__ void role_hop(const HopArgs& a, int side, bool with_e, size_t V, size_t nb, size_t lsite, R bsign,
-                                         const typename Tr<R>::Chunk* __restrict__ fa_in,
-                                         const typename Tr<R>::Chunk* __restrict__ fe_in,
-                                         typename Tr<R>::C (&acc)[12]) {
-    using C = typename Tr<R>::C;
-    constexpr bool DAG = SP > 0;
-    const R fa = fac_a<R>(a, side, NU, SP < 0) * bsign;
-    const bool ehop = with_e && (EMODE == 2 || (EMODE == 1 && NU == 3));
-    C u[9], psi[12], h[6], g[6];
-    load_gauge(a, V, NU, lsite, u);
-    load_spinor(fa_in, V, nb, psi);
-    project<C, NU, SP>(psi, h);
-    hscale(h, fa);
-    if (ehop) {
-        const R fe = fac_e<R>(a, side, NU, SP < 0) * bsign;
-        C he[6];
-        load_spinor(fe_in, V, nb, psi);
-        project<C, NU, SP>(psi, he);
-        if (EMODE == 1) {
-            haxpy(h, fe, he);                 // same link: combine before the multiply
-        } else {
-            C y[9];
-            load_link(reinterpret_cast<const C*>(a.Y), V, NU, lsite, y);
-            hscale(he, fe);
-            su3_mul<C, DAG>(y, he, g);
-            reconstruct_add<C, NU, SP>(g, acc);
-        }
-    }
-    su3_mul<C, DAG>(u, h, g);
-    reconstruct_add<C, NU, SP>(g, acc);
-}
-
-template <typename R, int EMODE, int NU>
-__device__ __forceinline__ void role_dir(const HopArgs& a, int side, bool with_e, size_t V, size_t s, const int (&x)[4],
-                                         const typename Tr<R>::Chunk* fa_in, const typename Tr<R>::Chunk* fe_in,
-                                         typename Tr<R>::C (&acc)[12]) {
-    const int ext = a.dims[NU];
-    const size_t stride = a.strides[NU];
-    const size_t sf = (x[NU] == ext - 1) ? s - (size_t)(ext - 1) * stride : s + stride;
-    const R bf = (NU == 3 && a.apbc && x[NU] == ext - 1) ? (R)-1 : (R)1;
-    role_hop<R, EMODE, NU, -1>(a, side, with_e, V, sf, s, bf, fa_in, fe_in, acc);
-    const size_t sb = (x[NU] == 0) ? s + (size_t)(ext - 1) * stride : s - stride;
-    const R bb = (NU == 3 && a.apbc && x[NU] == 0) ? (R)-1 : (R)1;
-    role_hop<R, EMODE, NU, +1>(a, side, with_e, V, sb, sb, bb, fa_in, fe_in, acc);
-}
-
-template <typename R, int EMODE, bool DOT, int RS, int MINB>
-__global__ void __launch_bounds__(4 * RS, MINB) k_hop_roles(HopArgs a) {
-    using C = typename Tr<R>::C;
-    using Chunk = typename Tr<R>::Chunk;
-    __shared__ CSum smem[32 * 2];
-    const int src = blockIdx.y;
-    if (a.state != nullptr && a.state[src].status != 0) return;
-    const int role = threadIdx.x / RS;                // warp-uniform
-    const int side = role >> 1;                       // 0 right, 1 left
-    const int fld = role & 1;                         // output field within the side
-    const size_t V = a.V;
-    const size_t s = (size_t)blockIdx.x * RS + (threadIdx.x % RS);
-    const bool active = s < V;
-    const size_t F = field_elems<R>(V);
-    const Chunk* in0 = reinterpret_cast<const Chunk*>(a.in[side]) + (size_t)src * a.src_stride_in[side];
-    Chunk* out = reinterpret_cast<Chunk*>(a.out[side]) + (size_t)src * a.src_stride_out[side] + (size_t)fld * F;
-    // operator input and derivative input of this role
-    const Chunk* fa_in = in0 + (size_t)fld * F;
-    const bool with_e = (EMODE != 0) && ((side == 0 && fld == 0) || (side == 1 && fld == 1));
-    const Chunk* fe_in = (side == 0) ? in0 + F : in0;   // right: E acts on the bottom; left: E^dag on the top
-    DotAcc<R> d[2];
-    d[0].zero(); d[1].zero();
-    if (active) {
-        C acc[12];
-#pragma unroll
-        for (int c = 0; c < 12; ++c) acc[c] = cmk<C>(0, 0);
-        int x[4];
-        site_coords(a, s, x);
-        role_dir<R, EMODE, 0>(a, side, with_e, V, s, x, fa_in, fe_in, acc);
-        role_dir<R, EMODE, 1>(a, side, with_e, V, s, x, fa_in, fe_in, acc);
-        role_dir<R, EMODE, 2>(a, side, with_e, V, s, x, fa_in, fe_in, acc);
-        role_dir<R, EMODE, 3>(a, side, with_e, V, s, x, fa_in, fe_in, acc);
-        C psi[12];
-        load_spinor(fa_in, V, s, psi);
-        finish(psi, fac_diag<R>(a), acc);
-        store_spinor(out, V, s, acc);
-        if (DOT && side == 0) {
-            const Chunk* w = reinterpret_cast<const Chunk*>(a.in[1]) + (size_t)src * a.src_stride_in[1] + (size_t)fld * F;
-            load_spinor(w, V, s, psi);
-#pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                add_cdot(d[0], d[1], psi[c], acc[c]);
-            }
-        }
-    }
-    if (DOT) {
-        CSum tot[2];
-        block_total<R, 2>(d, tot, smem);
-        double* part = a.partials + ((size_t)src * a.partial_stride + blockIdx.x) * 4;
-        if (threadIdx.x == 0) { part[0] = tot[0].s; part[1] = tot[0].e; part[2] = tot[1].s; part[3] = tot[1].e; }
-        if (last_block(a.counters + src, gridDim.x)) {
-            double res[2];
-            reduce_partials<2>(a.partials + (size_t)src * a.partial_stride * 4, gridDim.x, res, smem);
-            if (threadIdx.x == 0) tsl_alpha_step(a, src, res[0], res[1]);
-        }
-    }
-}
-
-// ---------------------------------------------------------------------------------------
 // Shared-memory tiled block stencil (schedule 6, FP32).  A block takes a tile of whole x rows,
 // kTileY x kTileZ x kTileT in (y, z, t), for one side of one source.  It copies into shared
 // memory, each site once and with all loads in flight together: the links of the tile (forward
@@ -553,7 +437,9 @@ static cudaError_t launch_tiled_t(const HopArgs& a, int emode, bool dot, cudaStr
 //   8: as 7 with the next hop's neighbour spinors prefetched into shared memory
 //   9: as 3 with both sides of 64 sites in a block (the second load of a link hits L1)
 cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, cudaStream_t st) {
-    if (prec == LQ_FLOAT_FLOAT) {   // schedule 0 only
+    if (prec == LQ_FLOAT_FLOAT) {   // schedules 0, 1 and 2
+        if (nf == 2 && a.nsides == 2 && a.side0 == 0 && (a.variant == 1 || a.variant == 2))
+            return emode == 0 ? launch_roles_ff0(a, dot, st) : emode == 1 ? launch_roles_ff1(a, dot, st) : launch_roles_ff2(a, dot, st);
         if (nf == 1 || emode == 0) return launch_hop_ff0(a, nf, dot, st);
         return emode == 1 ? launch_hop_ff1(a, dot, st) : launch_hop_ff2(a, dot, st);
     }

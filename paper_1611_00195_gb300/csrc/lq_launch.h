@@ -125,6 +125,9 @@ cudaError_t launch_cg_p(const CgArgs& a, cudaStream_t st);      // p = z + beta 
 cudaError_t launch_hop_ff0(const HopArgs& a, int nf, bool dot, cudaStream_t st);
 cudaError_t launch_hop_ff1(const HopArgs& a, bool dot, cudaStream_t st);
 cudaError_t launch_hop_ff2(const HopArgs& a, bool dot, cudaStream_t st);
+cudaError_t launch_roles_ff0(const HopArgs& a, bool dot, cudaStream_t st);   // schedule 1, block operator
+cudaError_t launch_roles_ff1(const HopArgs& a, bool dot, cudaStream_t st);
+cudaError_t launch_roles_ff2(const HopArgs& a, bool dot, cudaStream_t st);
 cudaError_t launch_update_ff(const UpdArgs& a, dim3 grid, cudaStream_t st);
 cudaError_t launch_tsl_init_ff(int nf, const InitArgs& a, dim3 grid, cudaStream_t st);
 cudaError_t launch_recombine_ff(int nf, const RecArgs& a, dim3 grid, size_t smem, cudaStream_t st);

@@ -47,8 +47,9 @@ def _pert(rng, size):
     return wrap
 
 
+@pytest.mark.parametrize("variant", [0, 1, 2])
 @pytest.mark.parametrize("kind", [0, 1])
-def test_float_float_block_tsl_parity(lqlib, kind):
+def test_float_float_block_tsl_parity(lqlib, kind, variant):
     from paper_1611_00195_gb300 import lq
     dims, k, mu, nsrc = (4, 4, 2, 6), 60, 0.3, 2
     U = syn.gauge_field(dims, 0.4, 3)
@@ -57,20 +58,20 @@ def test_float_float_block_tsl_parity(lqlib, kind):
     c = lq.Context(dims, mu=mu, precision=lq.LQ_FLOAT_FLOAT)
     c.upload_gauge(torch.from_numpy(U).cuda())
     c.reserve(k, nsrc, True)
-    ys, yd, rep = c.sign_derivative_apply(torch.from_numpy(x).cuda(), k, kind=kind,
+    ys, yd, rep = c.sign_derivative_apply(torch.from_numpy(x).cuda(), k, kind=kind, hop_variant=variant,
                                           field=torch.from_numpy(field).cuda() if field is not None else None)
     ys, yd = ys.cpu().numpy(), yd.cpu().numpy()
     lat, A, Ah, E, Eh = oracle_ops(dims, U, mu, kind=kind, field=field)
     rng = np.random.default_rng(23)
     w = _pert(rng, FF_STEP_NOISE)
     for s in range(nsrc):
-        assert rep[s]["status"] == 0 and rep[s]["k_eff"] == k and rep[s]["hop_variant"] == 0
+        assert rep[s]["status"] == 0 and rep[s]["k_eff"] == k and rep[s]["hop_variant"] == variant
         rd, rs, _ = ot.tsl_sign_derivative(A, Ah, E, Eh, x[s].ravel(), k)
         pd, ps, _ = ot.tsl_sign_derivative(w(A), w(Ah), w(E), w(Eh), x[s].ravel(), k)
         sens = max(relerr(pd, rd), relerr(ps, rs))
         errs = [relerr(ys[s], rs), relerr(yd[s], rd)]
-        print("float-float block TSL kind %d source %d: sign %.3g deriv %.3g (float-float sensitivity %.3g, "
-              "ratio %.2f)" % (kind, s, errs[0], errs[1], sens, max(errs) / sens))
+        print("float-float block TSL kind %d schedule %d source %d: sign %.3g deriv %.3g (float-float "
+              "sensitivity %.3g, ratio %.2f)" % (kind, variant, s, errs[0], errs[1], sens, max(errs) / sens))
         assert max(errs) < max(1e-12, FF_SENS_FACTOR * sens)
 
 
@@ -116,7 +117,7 @@ def test_float_float_runs_one_batch_and_replays_its_graph(lqlib):
     p = c.sign_derivative_apply(x, k, graph=0, split=0)
     for r in (b, p):
         assert torch.equal(a[0], r[0]) and torch.equal(a[1], r[1])
-    assert all(r["hop_variant"] == 0 for r in a[2])
+    assert all(r["hop_variant"] in (0, 1, 2) for r in a[2])   # the autotuner's choice
     ca = lq.Context(dims, mu=0.3, precision=lq.LQ_FLOAT_FLOAT)
     ca.upload_gauge(torch.from_numpy(syn.gauge_field(dims, 0.4, 3)).cuda())
     ca.reserve(k, 2, block=False, adjoint=True)
