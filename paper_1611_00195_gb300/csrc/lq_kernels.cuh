@@ -338,8 +338,8 @@ __global__ void __launch_bounds__(kUpdThreads) k_tsl_init(InitArgs a) {
 // ---------------------------------------------------------------------------------------
 // Recombination y = |x| sum_j c_j s_j vh_j for each field, written in the boundary layout.
 // c = sgn(T_k) e_1 (from the Newton iteration or the quadrature), one row per source.
-// FP64 and float-float bases: FP64 accumulation.  FP32 basis: groups of four terms in FP32, the
-// group sums in float-float (see the kernel).
+// FP64 basis: FP64 accumulation.  Float-float basis: unnormalised float-float sums of exact
+// products.  FP32 basis: groups of four terms in FP32, the group sums in float-float.
 // ---------------------------------------------------------------------------------------
 template <typename R, int NF>
 __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
@@ -357,7 +357,7 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
         double2 c = a.coef[(size_t)src * a.kmax + j];
         double sc = a.scale[(size_t)src * a.kmax + j] * xn;
         double2 cs = make_double2(c.x * sc, c.y * sc);
-        if (Tr<R>::kKind != 1) coef[j - j0] = cs;
+        if (Tr<R>::kKind == 0) coef[j - j0] = cs;
         else {
             // split once per block: no FP64 arithmetic is left in the k-loop below
             const float hx = (float)cs.x, hy = (float)cs.y;
@@ -376,8 +376,33 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
     }
     auto slot = [&](int j) -> size_t { return (size_t)(a.ring > 0 ? j % a.ring : j); };
     const Chunk* base = reinterpret_cast<const Chunk*>(a.basis) + (size_t)src * a.src_stride_basis + (size_t)f * field_elems<R>(V);
-    if (Tr<R>::kKind != 1) {
-        // FP64 accumulation; a float-float basis entry converts to FP64 exactly
+    if constexpr (Tr<R>::kKind == 2) {
+        // float-float basis: each component an unnormalised float-float sum of the exact
+        // products with the float-float coefficient (FP32 operations only), converted at the end
+        FFSum ar[12], ai[12];
+#pragma unroll
+        for (int c = 0; c < 12; ++c) { ar[c] = FFSum{0.f, 0.f}; ai[c] = FFSum{0.f, 0.f}; }
+        for (int j = j0; j < j1; ++j) {
+            const float4* vj = reinterpret_cast<const float4*>(base + slot(j) * a.vec_stride);
+            const float4 cf = reinterpret_cast<const float4*>(coef)[j - j0];
+            const ff cr(cf.x, cf.z), ci(cf.y, cf.w);
+#pragma unroll
+            for (int c = 0; c < 12; ++c) {
+                const float4 q = __ldg(vj + (size_t)c * V + s);
+                const ff vr(q.x, q.y), vi(q.z, q.w);
+                ffsum_add_prod<false>(ar[c], cr, vr);
+                ffsum_add_prod<true>(ar[c], ci, vi);
+                ffsum_add_prod<false>(ai[c], cr, vi);
+                ffsum_add_prod<false>(ai[c], ci, vr);
+            }
+        }
+#pragma unroll
+        for (int c = 0; c < 12; ++c) {
+            const double2 w = make_double2((double)ar[c].s + (double)ar[c].e, (double)ai[c].s + (double)ai[c].e);
+            y[c] = a.accumulate ? cadd(y[c], w) : w;
+        }
+    } else if (Tr<R>::kKind == 0) {
+        // FP64 accumulation
         double2 acc[12];
 #pragma unroll
         for (int c = 0; c < 12; ++c) acc[c] = make_double2(0.0, 0.0);
@@ -385,15 +410,7 @@ __global__ void __launch_bounds__(kRecThreads) k_recombine(RecArgs a) {
             const Chunk* vj = base + slot(j) * a.vec_stride;
             const double2 cj = coef[j - j0];
 #pragma unroll
-            for (int c = 0; c < 12; ++c) {
-                double2 e;
-                if constexpr (Tr<R>::kKind == 0) e = __ldg(reinterpret_cast<const double2*>(vj) + (size_t)c * V + s);
-                else {
-                    const float4 q = __ldg(reinterpret_cast<const float4*>(vj) + (size_t)c * V + s);
-                    e = make_double2((double)q.x + (double)q.y, (double)q.z + (double)q.w);
-                }
-                acc[c] = cfma(cj, e, acc[c]);
-            }
+            for (int c = 0; c < 12; ++c) acc[c] = cfma(cj, __ldg(reinterpret_cast<const double2*>(vj) + (size_t)c * V + s), acc[c]);
         }
 #pragma unroll
         for (int c = 0; c < 12; ++c) y[c] = a.accumulate ? cadd(y[c], acc[c]) : acc[c];

@@ -186,7 +186,7 @@ def test_compute_deflation_eigensolver(lqlib, prec, tol, method):
         assert e1 < 3 * e2 + 1e-9
 
 
-@pytest.mark.parametrize("prec", [0, 1])
+@pytest.mark.parametrize("prec", [0, 1, 3])
 def test_shift_invert_where_the_spectrum_surrounds_zero(lqlib, prec):
     """4x4x2x2 at mu = 0.6: the ten eigenvalues of H(mu) nearest zero lie at every phase around
     the origin (|lambda| 0.59-0.61, a 3.5% gap to the eleventh), the situation of the 14x14^3
@@ -221,4 +221,4 @@ def test_shift_invert_where_the_spectrum_surrounds_zero(lqlib, prec):
     y2, _ = c.sign_apply(x, 30, deflate=1)
     e = relerr(y1.cpu().numpy(), y2.cpu().numpy())
     print("deflated sign, computed vs dense eigenpairs: %.3g" % e)
-    assert e < (1e-8 if prec == 0 else 1e-5)
+    assert e < (1e-5 if prec == 1 else 1e-8)   # float-float (3) is held to the FP64 bound
