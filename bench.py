@@ -632,7 +632,7 @@ def main():
         y5 = torch.from_numpy(syn.gaussian_source(d5, SOURCE_SEED + 1)).to(dev)
         force = {"k": k5, "mu": MU, "outputs": "S, dS/domega [4][V][8], dS/dmu"}
         F5 = {}
-        for pname, pcode in (("mixed", lq.LQ_MIXED), ("fp64", lq.LQ_FP64)):
+        for pname, pcode in (("mixed", lq.LQ_MIXED), ("fp64", lq.LQ_FP64), ("float_float", lq.LQ_FLOAT_FLOAT)):
             c5 = lq.Context(d5, m_w=M_W, mu=MU, precision=pcode)
             c5.upload_gauge(U5)
             c5.reserve(k5, 2, block=False, adjoint=True)
@@ -641,6 +641,7 @@ def main():
             force[pname] = {"value": 1 / (ms5 / 1e3), "unit": "forces/s", "ms": ms5}
             del c5
         force["mixed_vs_fp64_rel_diff"] = float(torch.linalg.vector_norm(F5["mixed"] - F5["fp64"]) / torch.linalg.vector_norm(F5["fp64"]))
+        force["float_float_vs_fp64_rel_diff"] = float(torch.linalg.vector_norm(F5["float_float"] - F5["fp64"]) / torch.linalg.vector_norm(F5["fp64"]))
         extra["force_12x12c3"] = force
         # accuracy at a converged depth on this workload: 2 sources, k = 2400, FP64, float-float and
         # mixed, with eps_A of the derivative (Sec. 4) for each path and their differences from FP64

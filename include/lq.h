@@ -70,7 +70,8 @@ extern "C" {
                          the accuracy class of LQ_FP64 at a fraction of its time.  Stencil
                          schedules 0 (one thread per site and side), 1 and 2 (one thread per
                          site and output field, at least 3 / 4 blocks per SM); no split
-                         loop; lq_sign_bilinear_grad returns LQ_ERR_ARG for such a context */
+                         loop.  The adjoint's pair vectors are recombined in FP64 and stored
+                         in float-float; the force contraction runs in FP64              */
 
 /* ---- derivative directions (d_t of Eq. (2.5)) --------------------------------------- */
 #define LQ_DIR_MU   0   /* d/dmu: field unused                                               */

@@ -215,19 +215,36 @@ __global__ void __launch_bounds__(128) k_recomb_multi(const typename Tr<R>::Chun
                                                       int k, const double2* __restrict__ coef, int kmax, int nq,
                                                       typename Tr<R>::Chunk* __restrict__ out, size_t F) {
     using Chunk = typename Tr<R>::Chunk;
-    extern __shared__ double2 sc[];    // [kQB][k] (FP64), or float2 [kQB][k] for FP32 bases
+    extern __shared__ double2 sc[];    // [kQB][k] (FP64 and float-float bases), or float2 [kQB][k] for FP32 ones
     float2* scf = reinterpret_cast<float2*>(sc);
     const int q0 = blockIdx.y * kQB;
     for (int i = threadIdx.x; i < kQB * k; i += blockDim.x) {
         const int qq = i / k, j = i % k;
         const double2 cv = (q0 + qq < nq) ? coef[(size_t)(q0 + qq) * kmax + j] : make_double2(0.0, 0.0);
-        if (sizeof(R) == 8) sc[i] = cv;
+        if (Tr<R>::kKind != 1) sc[i] = cv;
         else scf[i] = make_float2((float)cv.x, (float)cv.y);
     }
     __syncthreads();
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= F) return;
-    if (sizeof(R) == 8) {
+    if constexpr (Tr<R>::kKind == 2) {
+        // float-float basis: FP64 accumulation of the exactly widened entries, stored as float-float
+        double2 acc[kQB];
+#pragma unroll
+        for (int qq = 0; qq < kQB; ++qq) acc[qq] = make_double2(0.0, 0.0);
+        for (int j = 0; j < k; ++j) {
+            const float4 q = reinterpret_cast<const float4*>(basis)[(size_t)j * vec_stride + e];
+            const double2 v = make_double2((double)q.x + (double)q.y, (double)q.z + (double)q.w);
+#pragma unroll
+            for (int qq = 0; qq < kQB; ++qq) acc[qq] = cfma(sc[qq * k + j], v, acc[qq]);
+        }
+#pragma unroll
+        for (int qq = 0; qq < kQB; ++qq)
+            if (q0 + qq < nq) {
+                const ff re(acc[qq].x), im(acc[qq].y);
+                reinterpret_cast<float4*>(out)[(size_t)(q0 + qq) * F + e] = make_float4(re.hi, re.lo, im.hi, im.lo);
+            }
+    } else if (Tr<R>::kKind == 0) {
         double2 acc[kQB];
 #pragma unroll
         for (int qq = 0; qq < kQB; ++qq) acc[qq] = make_double2(0.0, 0.0);
@@ -289,8 +306,14 @@ __global__ void __launch_bounds__(128) k_recomb_window(const typename Tr<R>::Chu
         const int slot = ring > 0 ? (j0 + j) % ring : j0 + j;
         const Chunk v = basis[(size_t)slot * vec_stride + e];
         double2 vv[PC];
-        if constexpr (PC == 1) vv[0] = make_double2((double)reinterpret_cast<const double2&>(v).x, (double)reinterpret_cast<const double2&>(v).y);
-        else { const float4 f = reinterpret_cast<const float4&>(v); vv[0] = make_double2(f.x, f.y); vv[1] = make_double2(f.z, f.w); }
+        if constexpr (Tr<R>::kKind == 2) {
+            const float4 f = reinterpret_cast<const float4&>(v);
+            vv[0] = make_double2((double)f.x + (double)f.y, (double)f.z + (double)f.w);
+        } else if constexpr (PC == 1) {
+            vv[0] = make_double2((double)reinterpret_cast<const double2&>(v).x, (double)reinterpret_cast<const double2&>(v).y);
+        } else {
+            const float4 f = reinterpret_cast<const float4&>(v); vv[0] = make_double2(f.x, f.y); vv[1] = make_double2(f.z, f.w);
+        }
 #pragma unroll
         for (int qq = 0; qq < kQB; ++qq)
 #pragma unroll
@@ -300,7 +323,15 @@ __global__ void __launch_bounds__(128) k_recomb_window(const typename Tr<R>::Chu
     for (int qq = 0; qq < kQB; ++qq) {
         if (q0 + qq >= nq) continue;
         Chunk* o = out + (size_t)(q0 + qq) * F + e;
-        if constexpr (PC == 1) {
+        if constexpr (Tr<R>::kKind == 2) {
+            double2 r = acc[qq][0];
+            if (accumulate) {
+                const float4 t = *reinterpret_cast<const float4*>(o);
+                r.x += (double)t.x + (double)t.y; r.y += (double)t.z + (double)t.w;
+            }
+            const ff re(r.x), im(r.y);
+            *reinterpret_cast<float4*>(o) = make_float4(re.hi, re.lo, im.hi, im.lo);
+        } else if constexpr (PC == 1) {
             double2 r = acc[qq][0];
             if (accumulate) { const double2 t = *reinterpret_cast<const double2*>(o); r.x += t.x; r.y += t.y; }
             *reinterpret_cast<double2*>(o) = r;
@@ -322,6 +353,19 @@ __device__ __forceinline__ void load_d(const float4* f, size_t V, size_t s, doub
     load_spinor(f, V, s, t);
 #pragma unroll
     for (int c = 0; c < 12; ++c) o[c] = make_double2((double)t[c].x, (double)t[c].y);
+}
+// float-float fields (one complex per float4 chunk), widened exactly
+__device__ __forceinline__ void load_d_ff(const float4* f, size_t V, size_t s, double2 (&o)[12]) {
+#pragma unroll
+    for (int c = 0; c < 12; ++c) {
+        const float4 q = __ldg(f + (size_t)c * V + s);
+        o[c] = make_double2((double)q.x + (double)q.y, (double)q.z + (double)q.w);
+    }
+}
+template <typename R, typename Chunk>
+__device__ __forceinline__ void load_dk(const Chunk* f, size_t V, size_t s, double2 (&o)[12]) {
+    if constexpr (Tr<R>::kKind == 2) load_d_ff(f, V, s, o);
+    else load_d(f, V, s, o);
 }
 
 // (gamma5 (1 + SP gamma_NU) psi) in the chiral basis: (h, SP B^dag h) with the lower half negated.
@@ -383,13 +427,13 @@ __device__ __forceinline__ void force_dir(const AdjArgs& a, size_t s, const int 
     for (int q = 0; q < np; ++q) {
         double2 w[12], v[12], g[12];
         // forward hop: conj(omega(x)) . gamma5 (1 - gamma) nu(x + nu)
-        load_d(om + (size_t)q * F, V, s, w);
-        load_d(nu + (size_t)q * F, V, sp, v);
+        load_dk<R>(om + (size_t)q * F, V, s, w);
+        load_dk<R>(nu + (size_t)q * F, V, sp, v);
         g5_proj<NU, -1>(v, g);
         outer_acc(w, g, Pf);
         // backward hop: conj(omega(x + nu)) . gamma5 (1 + gamma) nu(x)
-        load_d(om + (size_t)q * F, V, sp, w);
-        load_d(nu + (size_t)q * F, V, s, v);
+        load_dk<R>(om + (size_t)q * F, V, sp, w);
+        load_dk<R>(nu + (size_t)q * F, V, s, v);
         g5_proj<NU, +1>(v, g);
         outer_acc(w, g, Pb);
     }
@@ -473,76 +517,74 @@ cudaError_t launch_adj_pairs(const AdjArgs& a, cudaStream_t st) {
     return cudaGetLastError();
 }
 
-cudaError_t launch_adj_window(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,
-                              size_t lbasis_vec_stride, int j0, int j1, int ring, cudaStream_t st) {
-    if (j1 - j0 > kTwoPassRing || j1 <= j0) return cudaErrorInvalidValue;
-    const size_t F = (prec == LQ_FP64) ? field_elems<double>(a.V) : field_elems<float>(a.V);
-    dim3 grid((unsigned)((F + 127) / 128), (unsigned)((a.npairs + kQB - 1) / kQB));
+namespace {
+// element counts of a field and the kernels' chunk type per precision
+size_t adj_field_elems(int prec, size_t V) { return prec == LQ_MIXED ? field_elems<float>(V) : field_elems<double>(V); }
+
+template <typename R>
+cudaError_t adj_window_t(const AdjArgs& a, const void* basis, size_t bstride, const void* lbasis, size_t lstride, int j0,
+                         int j1, int ring, size_t F, cudaStream_t st) {
+    using Chunk = typename Tr<R>::Chunk;
+    const dim3 grid((unsigned)((F + 127) / 128), (unsigned)((a.npairs + kQB - 1) / kQB));
     const int acc = j0 > 0 ? 1 : 0;
-    if (prec == LQ_FP64) {
-        k_recomb_window<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(basis), basis_vec_stride, j0, j1, ring,
-                                                      a.cnu, a.kmax, a.npairs, reinterpret_cast<double2*>(a.nu), F, acc);
-        k_recomb_window<double><<<grid, 128, 0, st>>>(reinterpret_cast<const double2*>(lbasis), lbasis_vec_stride, j0, j1, ring,
-                                                      a.com, a.kmax, a.npairs, reinterpret_cast<double2*>(a.om), F, acc);
-    } else {
-        k_recomb_window<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float4*>(basis), basis_vec_stride, j0, j1, ring,
-                                                     a.cnu, a.kmax, a.npairs, reinterpret_cast<float4*>(a.nu), F, acc);
-        k_recomb_window<float><<<grid, 128, 0, st>>>(reinterpret_cast<const float4*>(lbasis), lbasis_vec_stride, j0, j1, ring,
-                                                     a.com, a.kmax, a.npairs, reinterpret_cast<float4*>(a.om), F, acc);
-    }
+    k_recomb_window<R><<<grid, 128, 0, st>>>(reinterpret_cast<const Chunk*>(basis), bstride, j0, j1, ring, a.cnu, a.kmax,
+                                             a.npairs, reinterpret_cast<Chunk*>(a.nu), F, acc);
+    k_recomb_window<R><<<grid, 128, 0, st>>>(reinterpret_cast<const Chunk*>(lbasis), lstride, j0, j1, ring, a.com, a.kmax,
+                                             a.npairs, reinterpret_cast<Chunk*>(a.om), F, acc);
     return cudaGetLastError();
 }
 
+template <typename R>
+cudaError_t adjoint_t(const AdjArgs& a, const void* basis, size_t bstride, const void* lbasis, size_t lstride, int k,
+                      size_t F, cudaStream_t st) {
+    using Chunk = typename Tr<R>::Chunk;
+    const dim3 grid((unsigned)((F + 127) / 128), (unsigned)((a.npairs + kQB - 1) / kQB));
+    const size_t sm = (size_t)kQB * k * sizeof(double2);
+    cudaFuncSetAttribute(k_recomb_multi<R>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
+    k_recomb_multi<R><<<grid, 128, sm, st>>>(reinterpret_cast<const Chunk*>(basis), bstride, k, a.cnu, a.kmax, a.npairs,
+                                             reinterpret_cast<Chunk*>(a.nu), F);
+    k_recomb_multi<R><<<grid, 128, sm, st>>>(reinterpret_cast<const Chunk*>(lbasis), lstride, k, a.com, a.kmax, a.npairs,
+                                             reinterpret_cast<Chunk*>(a.om), F);
+    if (a.ndefl > 0) {
+        const int nq = a.npairs, nd = a.ndefl;
+        const dim3 gd((unsigned)((F + 127) / 128), (unsigned)((nd + kQB - 1) / kQB));
+        k_defl_coef<<<1, 2 * nd, 0, st>>>(a);
+        k_recomb_multi<R><<<gd, 128, sm, st>>>(reinterpret_cast<const Chunk*>(basis), bstride, k,
+                                               a.cnu + (size_t)(nq + 2 * nd) * a.kmax, a.kmax, nd,
+                                               reinterpret_cast<Chunk*>(a.nu) + (size_t)(nq + 2 * nd) * F, F);
+        k_recomb_multi<R><<<gd, 128, sm, st>>>(reinterpret_cast<const Chunk*>(lbasis), lstride, k,
+                                               a.com + (size_t)(nq + nd) * a.kmax, a.kmax, nd,
+                                               reinterpret_cast<Chunk*>(a.om) + (size_t)(nq + nd) * F, F);
+    }
+    k_force<R><<<(unsigned)((a.V + 127) / 128), 128, 0, st>>>(a);
+    return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t launch_adj_window(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,
+                              size_t lbasis_vec_stride, int j0, int j1, int ring, cudaStream_t st) {
+    if (j1 - j0 > kTwoPassRing || j1 <= j0) return cudaErrorInvalidValue;
+    const size_t F = adj_field_elems(prec, a.V);
+    if (prec == LQ_FP64) return adj_window_t<double>(a, basis, basis_vec_stride, lbasis, lbasis_vec_stride, j0, j1, ring, F, st);
+    if (prec == LQ_FLOAT_FLOAT) return adj_window_t<ff>(a, basis, basis_vec_stride, lbasis, lbasis_vec_stride, j0, j1, ring, F, st);
+    return adj_window_t<float>(a, basis, basis_vec_stride, lbasis, lbasis_vec_stride, j0, j1, ring, F, st);
+}
+
 cudaError_t launch_adj_force(int prec, const AdjArgs& a, cudaStream_t st) {
-    if (prec == LQ_FP64) k_force<double><<<(unsigned)((a.V + 127) / 128), 128, 0, st>>>(a);
-    else k_force<float><<<(unsigned)((a.V + 127) / 128), 128, 0, st>>>(a);
+    const unsigned g = (unsigned)((a.V + 127) / 128);
+    if (prec == LQ_FP64) k_force<double><<<g, 128, 0, st>>>(a);
+    else if (prec == LQ_FLOAT_FLOAT) k_force<ff><<<g, 128, 0, st>>>(a);
+    else k_force<float><<<g, 128, 0, st>>>(a);
     return cudaGetLastError();
 }
 
 cudaError_t launch_adjoint(int prec, const AdjArgs& a, const void* basis, size_t basis_vec_stride, const void* lbasis,
                            size_t lbasis_vec_stride, int k, cudaStream_t st) {
     k_adj_pairs<<<1, 2 * a.npairs, 0, st>>>(a);
-    const size_t F = (prec == LQ_FP64) ? field_elems<double>(a.V) : field_elems<float>(a.V);
-    dim3 grid((unsigned)((F + 127) / 128), (unsigned)((a.npairs + kQB - 1) / kQB));
-    const size_t sm = (size_t)kQB * k * sizeof(double2);
-    if (prec == LQ_FP64) {
-        cudaFuncSetAttribute(k_recomb_multi<double>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_recomb_multi<double><<<grid, 128, sm, st>>>(reinterpret_cast<const double2*>(basis), basis_vec_stride, k, a.cnu, a.kmax,
-                                                     a.npairs, reinterpret_cast<double2*>(a.nu), F);
-        k_recomb_multi<double><<<grid, 128, sm, st>>>(reinterpret_cast<const double2*>(lbasis), lbasis_vec_stride, k, a.com, a.kmax,
-                                                     a.npairs, reinterpret_cast<double2*>(a.om), F);
-        if (a.ndefl > 0) {
-            const int nq = a.npairs, nd = a.ndefl;
-            dim3 gd((unsigned)((F + 127) / 128), (unsigned)((nd + kQB - 1) / kQB));
-            k_defl_coef<<<1, 2 * nd, 0, st>>>(a);
-            k_recomb_multi<double><<<gd, 128, sm, st>>>(reinterpret_cast<const double2*>(basis), basis_vec_stride, k,
-                                                       a.cnu + (size_t)(nq + 2 * nd) * a.kmax, a.kmax, nd,
-                                                       reinterpret_cast<double2*>(a.nu) + (size_t)(nq + 2 * nd) * F, F);
-            k_recomb_multi<double><<<gd, 128, sm, st>>>(reinterpret_cast<const double2*>(lbasis), lbasis_vec_stride, k,
-                                                       a.com + (size_t)(nq + nd) * a.kmax, a.kmax, nd,
-                                                       reinterpret_cast<double2*>(a.om) + (size_t)(nq + nd) * F, F);
-        }
-        k_force<double><<<(unsigned)((a.V + 127) / 128), 128, 0, st>>>(a);
-    } else {
-        cudaFuncSetAttribute(k_recomb_multi<float>, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)sm);
-        k_recomb_multi<float><<<grid, 128, sm, st>>>(reinterpret_cast<const float4*>(basis), basis_vec_stride, k, a.cnu, a.kmax,
-                                                    a.npairs, reinterpret_cast<float4*>(a.nu), F);
-        k_recomb_multi<float><<<grid, 128, sm, st>>>(reinterpret_cast<const float4*>(lbasis), lbasis_vec_stride, k, a.com, a.kmax,
-                                                    a.npairs, reinterpret_cast<float4*>(a.om), F);
-        if (a.ndefl > 0) {
-            const int nq = a.npairs, nd = a.ndefl;
-            dim3 gd((unsigned)((F + 127) / 128), (unsigned)((nd + kQB - 1) / kQB));
-            k_defl_coef<<<1, 2 * nd, 0, st>>>(a);
-            k_recomb_multi<float><<<gd, 128, sm, st>>>(reinterpret_cast<const float4*>(basis), basis_vec_stride, k,
-                                                      a.cnu + (size_t)(nq + 2 * nd) * a.kmax, a.kmax, nd,
-                                                      reinterpret_cast<float4*>(a.nu) + (size_t)(nq + 2 * nd) * F, F);
-            k_recomb_multi<float><<<gd, 128, sm, st>>>(reinterpret_cast<const float4*>(lbasis), lbasis_vec_stride, k,
-                                                      a.com + (size_t)(nq + nd) * a.kmax, a.kmax, nd,
-                                                      reinterpret_cast<float4*>(a.om) + (size_t)(nq + nd) * F, F);
-        }
-        k_force<float><<<(unsigned)((a.V + 127) / 128), 128, 0, st>>>(a);
-    }
-    return cudaGetLastError();
+    const size_t F = adj_field_elems(prec, a.V);
+    if (prec == LQ_FP64) return adjoint_t<double>(a, basis, basis_vec_stride, lbasis, lbasis_vec_stride, k, F, st);
+    if (prec == LQ_FLOAT_FLOAT) return adjoint_t<ff>(a, basis, basis_vec_stride, lbasis, lbasis_vec_stride, k, F, st);
+    return adjoint_t<float>(a, basis, basis_vec_stride, lbasis, lbasis_vec_stride, k, F, st);
 }
 
 }  // namespace lq

@@ -2600,7 +2600,6 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
                           double* dS_dmu, void* stream) {
     if (!c || !x || !y) return set_err(c, LQ_ERR_ARG, "null argument");
     if (!c->adjoint) return set_err(c, LQ_ERR_NOT_READY, "workspace reserved without LQ_RESERVE_ADJOINT");
-    if (c->prec == LQ_FLOAT_FLOAT) return set_err(c, LQ_ERR_ARG, "the adjoint has no float-float kernels (use LQ_FP64)");
     int r = check_ready(c, 2, 0);
     if (r || (r = check_opts(c, o, true))) return r;
     const int l = o->deflate ? c->defl_l : 0;

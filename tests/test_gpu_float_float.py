@@ -4,7 +4,8 @@ numbers with compensated sums and FMA-exact products) against the FP64 oracle:
   * the block TSL of Eq. (2.6) at the same depth, d/dmu and an su(3) link direction, within
     FF_SENS_FACTOR of the oracle's response to FF_STEP_NOISE on every operator application;
   * the precision workload where the mixed path misses 1e-6 (8^4, mu = 0.2, k = 200): float-float
-    within 1e-6 of the FP64 oracle, and of the FP64 GPU path."""
+    within 1e-6 of the FP64 oracle, and of the FP64 GPU path;
+  * the adjoint (force) against the oracle at the same depth and the dense route when converged."""
 import multiprocessing as mp
 
 import numpy as np
@@ -118,8 +119,42 @@ def test_float_float_runs_one_batch_and_replays_its_graph(lqlib):
     for r in (b, p):
         assert torch.equal(a[0], r[0]) and torch.equal(a[1], r[1])
     assert all(r["hop_variant"] in (0, 1, 2) for r in a[2])   # the autotuner's choice
-    ca = lq.Context(dims, mu=0.3, precision=lq.LQ_FLOAT_FLOAT)
-    ca.upload_gauge(torch.from_numpy(syn.gauge_field(dims, 0.4, 3)).cuda())
-    ca.reserve(k, 2, block=False, adjoint=True)
-    with pytest.raises(lq.LQError):
-        ca.bilinear_grad(x[0], x[1], k)
+
+
+def test_float_float_force(lqlib):
+    """The adjoint (fermionic force, S = Re <y| sgn(H) |x>) in float-float: at the same depth
+    against the oracle's Krylov route, bounded by ADJ_SENS_FACTOR times the oracle's response to
+    1e-16 input noise scaled by 64 (the float-float unit roundoff 2^-47 against FP64's 2^-53);
+    at a converged depth on 2^4 against the dense trace-identity route to the FP64 test's 1e-6."""
+    from paper_1611_00195_gb300 import lq
+    from oracle import adjoint as oad
+    from tests.helpers import ADJ_SENS_FACTOR
+    mu = 0.3
+    for dims, k, dense in (((4, 2, 2, 2), 80, False), ((2, 2, 2, 2), 150, True)):
+        lat = od.Lattice(dims)
+        U = syn.gauge_field(dims, 0.3 if dense else 0.4, 3)
+        x = syn.gaussian_source(dims, 5)
+        y = syn.gaussian_source(dims, 6)
+        c = lq.Context(dims, mu=mu, precision=lq.LQ_FLOAT_FLOAT)
+        c.upload_gauge(torch.from_numpy(U).cuda())
+        c.reserve(k, 2, block=False, adjoint=True)
+        S, F, dmu = c.bilinear_grad(torch.from_numpy(x).cuda(), torch.from_numpy(y).cuda(), k)
+        F = F.cpu().numpy()
+        if dense:
+            Sd, Fd, dmud = oad.grad_dense(lat, U, x, y, mu)
+            eF = np.linalg.norm(F - Fd) / np.linalg.norm(Fd)
+            print("float-float force vs dense k=%d: S %.3g F %.3g dmu %.3g" % (k, abs(S - Sd) / abs(Sd), eF, abs(dmu - dmud) / abs(dmud)))
+            assert eF < 1e-6 and abs(S - Sd) < 1e-8 * abs(Sd)
+            continue
+        So, Fo, dmuo = oad.grad_tsl(lat, U, x, y, mu, k)
+        rng = np.random.default_rng(1)
+        sens = 0.0
+        for xp, yp in ((x * (1 + 1e-16 * rng.standard_normal(x.shape)), y), (x, y * (1 + 1e-16 * rng.standard_normal(y.shape)))):
+            Fp = oad.grad_tsl(lat, U, xp, yp, mu, k)[1]
+            sens = max(sens, np.linalg.norm(Fp - Fo) / np.linalg.norm(Fo))
+        eF = np.linalg.norm(F - Fo) / np.linalg.norm(Fo)
+        tol = max(1e-10, ADJ_SENS_FACTOR * 64 * sens)
+        print("float-float force parity %s k=%d: S %.3g F %.3g dmu %.3g (64 x oracle sensitivity %.3g, ratio %.2f)"
+              % (dims, k, abs(S - So) / abs(So), eF, abs(dmu - dmuo) / abs(dmuo), 64 * sens, eF / (64 * sens)))
+        assert eF < tol
+        assert abs(S - So) < tol * abs(So) and abs(dmu - dmuo) < tol * max(abs(dmuo), 1e-3)
