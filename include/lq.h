@@ -113,7 +113,9 @@ typedef struct {
                               pair arithmetic (identical results), 8 = as 7 with the next
                               hop's neighbour spinors prefetched into shared memory, 9 = as 3
                               with both sides of 64 sites in one block (the second load of a
-                              link hits L1).  2-9 are FP32 only (FP64 runs 0);
+                              link hits L1).  2-9 are FP32 only (FP64 runs 0, 1; float-float
+                              0, 1 and 2, where 1 / 2 are the one-thread-per-output-field
+                              kernel at 3 / 4 blocks per SM, any other value runs 0);
                               lq_report.hop_variant gives the schedule that ran               */
     int defl_kmax;         /* depth of the shifted solves for the eigenvector derivatives of the
                               generalised deflation (0 = the reserved kmax)                    */
