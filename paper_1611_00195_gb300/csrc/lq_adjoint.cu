@@ -12,6 +12,7 @@
 // omega_q = W_2 conj(b_q): 2N vector pairs, contracted link by link.
 #include "lq_internal.cuh"
 #include "lq_launch.h"
+#include "lq_stencil.cuh"
 
 namespace lq {
 
@@ -221,27 +222,39 @@ __global__ void __launch_bounds__(128) k_recomb_multi(const typename Tr<R>::Chun
     for (int i = threadIdx.x; i < kQB * k; i += blockDim.x) {
         const int qq = i / k, j = i % k;
         const double2 cv = (q0 + qq < nq) ? coef[(size_t)(q0 + qq) * kmax + j] : make_double2(0.0, 0.0);
-        if (Tr<R>::kKind != 1) sc[i] = cv;
-        else scf[i] = make_float2((float)cv.x, (float)cv.y);
+        if (Tr<R>::kKind == 0) sc[i] = cv;
+        else if (Tr<R>::kKind == 2) {   // float-float coefficient (re.hi, re.lo, im.hi, im.lo)
+            const ff re(cv.x), im(cv.y);
+            reinterpret_cast<float4*>(sc)[i] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        } else scf[i] = make_float2((float)cv.x, (float)cv.y);
     }
     __syncthreads();
     const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
     if (e >= F) return;
     if constexpr (Tr<R>::kKind == 2) {
-        // float-float basis: FP64 accumulation of the exactly widened entries, stored as float-float
-        double2 acc[kQB];
+        // float-float basis: unnormalised float-float sums of the exact products (FP32 operations
+        // only), renormalised once and stored as float-float
+        FFSum ar[kQB], ai[kQB];
 #pragma unroll
-        for (int qq = 0; qq < kQB; ++qq) acc[qq] = make_double2(0.0, 0.0);
+        for (int qq = 0; qq < kQB; ++qq) { ar[qq] = FFSum{0.f, 0.f}; ai[qq] = FFSum{0.f, 0.f}; }
+        const float4* scq = reinterpret_cast<const float4*>(sc);
         for (int j = 0; j < k; ++j) {
             const float4 q = reinterpret_cast<const float4*>(basis)[(size_t)j * vec_stride + e];
-            const double2 v = make_double2((double)q.x + (double)q.y, (double)q.z + (double)q.w);
+            const ff vr(q.x, q.y), vi(q.z, q.w);
 #pragma unroll
-            for (int qq = 0; qq < kQB; ++qq) acc[qq] = cfma(sc[qq * k + j], v, acc[qq]);
+            for (int qq = 0; qq < kQB; ++qq) {
+                const float4 cf = scq[qq * k + j];
+                const ff cr(cf.x, cf.y), ci(cf.z, cf.w);
+                ffsum_add_prod<false>(ar[qq], cr, vr);
+                ffsum_add_prod<true>(ar[qq], ci, vi);
+                ffsum_add_prod<false>(ai[qq], cr, vi);
+                ffsum_add_prod<false>(ai[qq], ci, vr);
+            }
         }
 #pragma unroll
         for (int qq = 0; qq < kQB; ++qq)
             if (q0 + qq < nq) {
-                const ff re(acc[qq].x), im(acc[qq].y);
+                const ff re = ff_two_sum(ar[qq].s, ar[qq].e), im = ff_two_sum(ai[qq].s, ai[qq].e);
                 reinterpret_cast<float4*>(out)[(size_t)(q0 + qq) * F + e] = make_float4(re.hi, re.lo, im.hi, im.lo);
             }
     } else if (Tr<R>::kKind == 0) {
