@@ -474,13 +474,6 @@ cudaError_t launch_hop(int prec, const HopArgs& a, int nf, int emode, bool dot, 
     return prec == LQ_FP64 ? launch_hop_t<double, 1>(a, nf, emode, dot, st) : launch_hop_t<float, 1>(a, nf, emode, dot, st);
 }
 
-size_t hop_blocks(const HopArgs& a, int nf) {
-    if (nf == 2 && a.nsides == 2 && a.side0 == 0 && (a.variant == 1 || a.variant == 5)) return (a.V + kRoleSites - 1) / kRoleSites;
-    if (nf == 2 && a.nsides == 2 && a.side0 == 0 && a.variant == 4) return (a.V + 2 * kRoleSites - 1) / (2 * kRoleSites);
-    if (nf == 2 && a.nsides == 2 && a.side0 == 0 && a.variant == 9) return (a.V + kHopThreads / 2 - 1) / (kHopThreads / 2);
-    return (a.V + kHopThreads - 1) / kHopThreads;
-}
-
 // Blocks per source of the grid-stride update: enough for exactly one resident wave over all
 // sources (no partial last wave), at most one per 256 chunks and at most `cap` (the partials).
 unsigned update_grid(size_t nelem, int nsrc, size_t cap) {

@@ -176,7 +176,6 @@ cudaError_t launch_scomb(double* Z, const double* X0, const double* X1, const do
                          size_t n, int nsrc, cudaStream_t st);
 // out = cx x + cs gamma5 s over nsites boundary-layout sites (x may be null)
 cudaError_t launch_g5axpy(double* out, const double* x, double cx, const double* s, double cs, size_t nsites, cudaStream_t st);
-size_t hop_blocks(const HopArgs& a, int nf);
 
 // Newton sign iteration (lq_newton.cu)
 struct NewtonArgs {
