@@ -166,7 +166,7 @@ typedef struct {
  *                  (O(m k) sequential work per source plus an m x m Newton);
  *  LQ_PROJ_AUTO    the quadrature, accepted per source only if its involution residual
  *                  ||Q(T) Q(T) e_1 - e_1|| <= proj_tol; a failing source is retried once
- *                  with 512 nodes, then by the nested process, and only what still fails
+ *                  with 2048 nodes, then by the nested process, and only what still fails
  *                  goes to Newton on the k x k matrix.                                   */
 #define LQ_PROJ_AUTO    0
 #define LQ_PROJ_NEWTON  1

@@ -243,7 +243,7 @@ struct lq_ctx {
     double* quad_c = nullptr;        // [nsrc]
     double* quad_check = nullptr;    // [nsrc]
     int* quad_nodes = nullptr;       // [nsrc] nodes of the current quadrature pass per source
-    double2* quad_part = nullptr;    // [nsrc][2 * 512 / 32][kmax] block row sums of the quadrature
+    double2* quad_part = nullptr;    // [nsrc][2 * kQuadRetryMaxNodes / 32][kmax] block row sums of the quadrature
     int* proj_sel = nullptr;         // [nsrc] sources finished by the Newton fallback
     // nested projected sign: inner state and coefficients, its first columns and results
     lq::TslState* nest_state = nullptr;   // [nsrc]

@@ -282,7 +282,7 @@ struct QuadArgs {
     double* check;         // [nb] ||q - e_1||
 };
 constexpr int kQuadMaxNodes = 128;        // opts.quad_nodes and the adjoint's rank-one terms
-constexpr int kQuadRetryMaxNodes = 512;   // LQ_PROJ_AUTO doubles a failing source's nodes up to this
+constexpr int kQuadRetryMaxNodes = 2048;  // LQ_PROJ_AUTO retries a failing source once with this many nodes
 constexpr int kQuadBlk = 32;              // shifted solves per block of the sign quadrature
 constexpr int kQuadFinish = 256;          // threads of the summing kernel
 // sgn(T) e_1 and the involution check for the sources with a.nodes[src] > 0 (at most max_nodes;
