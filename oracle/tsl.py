@@ -24,14 +24,27 @@ invariant subspace (the paper is silent on both): |vh| <= invariant_tol |A v_j| 
 |wh| <= invariant_tol |A^H w_j|, where the recurrence has cancelled to rounding.  On an
 invariant right subspace A V_j = V_j T_j holds exactly, so f(A)x = |x| V_j f(T_j) e_1 is
 then the exact result (a free-field plane wave stops at k_eff = 2).
+
+Re-biorthogonalisation (not in the paper; the remedy for the loss of biorthogonality in finite
+precision): with period p, the three-term step that makes v_{j+1}, w_{j+1} (j = 1, 2, ...) is
+followed, when j or j - 1 is divisible by p, by a projection of the new pair against all j
+earlier pairs before omega is formed,
+    vh <- vh - V_j (W_j^H vh),   wh <- wh - W_j (V_j^H wh),
+with V_j = [v_1 .. v_j], W_j = [w_1 .. w_j] (W_j^H V_j = 1).  T keeps its three-term entries.
+Two consecutive pairs are corrected because the recurrence forms each new pair from the last
+two: a lone corrected pair next to an uncorrected one hands the lost biorthogonality straight
+to the following vectors (the rule of periodic reorthogonalisation in the symmetric Lanczos
+method, Grcar 1981; Simon, Math. Comp. 42 (1984) 115).  p = 1 corrects every pair.
 """
 import numpy as np
 
 from .sign import sign_schur
 
 
-def tsl(apply_A, apply_Ah, v1, w1, k, breakdown_tol=1e-14, rebiorth=False, invariant_tol=1e-10):
-    """Run k steps; returns dict(T, V [k_eff][n], W [k_eff][n], k_eff, alpha, beta, delta)."""
+def tsl(apply_A, apply_Ah, v1, w1, k, breakdown_tol=1e-14, rebiorth=0, invariant_tol=1e-10):
+    """Run k steps; returns dict(T, V [k_eff][n], W [k_eff][n], k_eff, alpha, beta, delta).
+    rebiorth: 0 (off) or the period p of the re-biorthogonalisation (True is p = 1)."""
+    period = int(rebiorth)
     V = [np.asarray(v1, dtype=complex)]
     W = [np.asarray(w1, dtype=complex)]
     alpha, beta, delta = [], [], []
@@ -48,7 +61,7 @@ def tsl(apply_A, apply_Ah, v1, w1, k, breakdown_tol=1e-14, rebiorth=False, invar
         if j > 0:
             vh = vh - beta[j - 1] * V[j - 1]
             wh = wh - np.conj(delta[j - 1]) * W[j - 1]
-        if rebiorth:
+        if period > 0 and ((j + 1) % period == 0 or (j > 0 and j % period == 0)):
             Vm, Wm = np.array(V), np.array(W)
             vh = vh - Vm.T @ (Wm.conj() @ vh)
             wh = wh - Wm.T @ (Vm.conj() @ wh)
