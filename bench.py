@@ -497,6 +497,24 @@ def main():
         extra["two_pass"] = {"value": nsrc / (ms_tp / 1e3), "unit": "solves/s", "ms_per_step": ms_tp, "k": k,
                              "basis_gb": basis_gb(32), "basis_gb_one_pass": basis_gb(k),
                              "rel_diff_vs_one_pass": {"sign": relmax(ys, ys_ref), "deriv": relmax(yd, yd_ref)}}
+        # periodic re-biorthogonalisation (two consecutive pairs per period projected against all
+        # earlier pairs; the whole left basis is kept): its cost, and whether it moves the FP32
+        # answer towards FP64 on this field
+        ctx.reserve(k, nsrc, True, rebiorth=True)
+        extra["rebiorth"] = {"k": k, "left_basis_gb": basis_gb(k), "per_period": {},
+                             "note": "the projection's rounding grows with the condition |v_i||w_i| of the pairs; "
+                                     "between corrections a long period lets the bases drift beyond repair"}
+        for p in (1, 10):
+            ms_rb, r = timed(lambda: ctx.sign_derivative_apply(xd, k, out=(ys, yd), rebiorth=p, **hv), steps=1)
+            row = {"value": nsrc / (ms_rb / 1e3), "unit": "solves/s", "ms_per_step": ms_rb,
+                   "status": sorted(set(x["status"] for x in r[2])),
+                   "rel_diff_vs_plain": {"sign": relmax(ys, ys_ref), "deriv": relmax(yd, yd_ref)},
+                   "eps_A_deriv": ctx.error_estimate(xd[:2].contiguous(), k, kind=lq.LQ_DIR_MU, rebiorth=p).tolist()}
+            if fp64 is not None:
+                row["rel_diff_vs_fp64"] = {"sign": relmax(ys, ys64), "deriv": relmax(yd, yd64)}
+            extra["rebiorth"]["per_period"][str(p)] = row
+        if fp64 is not None:
+            extra["rebiorth"]["plain_rel_diff_vs_fp64"] = {"sign": relmax(ys_ref, ys64), "deriv": relmax(yd_ref, yd64)}
         ctx.reserve(k, nsrc, True)
         # the nested two-sided Lanczos projected sign (Sec. 4, inner size 100) on the same 16
         # processes: involution residuals and the projected step's time, against the quadrature

@@ -151,6 +151,24 @@ typedef struct {
                               (the bulk kernel's shared memory would take the L1 of the stencil
                               running beside it).  The vectors are bitwise the same; the inner
                               products differ by the order of their partial sums              */
+    int rebiorth;          /* 0 (default): plain three-term recurrences.  p > 0: the new pair
+                              (vh, wh) of step j (v_{j+1}, counting from v_0) is made
+                              biorthogonal to all earlier pairs when j + 1 or j (j > 0) is a
+                              multiple of p, vh -= sum_i v_i <w_i, vh>, wh -= sum_i w_i <v_i,
+                              wh>, before omega and the next beta, delta are formed (two
+                              consecutive pairs per period: the recurrence builds each pair
+                              from the last two); T keeps its three-term entries.  Costs
+                              O(j n) bytes per corrected step (p = 1: every step, O(k^2 n) per
+                              solve).  The projection's own rounding is amplified by the
+                              condition |v_i| |w_i| of the pairs (FP32 data: float-float sums,
+                              one rounding per stored element), so on strongly non-normal
+                              kernels it can add more error than it removes: on the Wilson
+                              kernel at 14^4, mu = 0.3, k = 400 it moves even float-float
+                              results by 0.1.  It restores exactness where the bases stay
+                              well conditioned.  Sign and derivative solves only (not the
+                              adjoint, two-pass runs or lq_batch_apply); needs a workspace
+                              reserved with LQ_RESERVE_REBIORTH (LQ_ERR_NOT_READY otherwise).
+                              Runs with it do not split into source halves                    */
 } lq_opts;
 
 /* Projected step sgn(T_k) e_1 (Sec. 2):
@@ -221,6 +239,9 @@ int  lq_set_mu(lq_ctx* ctx, double mu);
 #define LQ_RESERVE_TWO_PASS 4
 #define LQ_RESERVE_SOLVE    8   /* nine more FP64 fields per source for lq_overlap_solve and
                                    lq_axial_current */
+#define LQ_RESERVE_REBIORTH 16  /* the whole left basis (kmax vectors per source, NF fields each)
+                                   and the dot scratch for lq_opts.rebiorth; LQ_ERR_ARG together
+                                   with a two-pass ring (LQ_RESERVE_TWO_PASS and kmax > 32) */
 int  lq_reserve(lq_ctx* ctx, int kmax, int nsrc, int flags);
 
 /* y = H(mu) x (dagger = 0) or y = H(mu)^dag x = H(-mu) x (dagger = 1) for nsrc fields

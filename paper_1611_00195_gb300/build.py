@@ -13,7 +13,7 @@ ROOT = os.path.dirname(PKG)
 CSRC = os.path.join(PKG, "csrc")
 BUILD = os.path.join(ROOT, "_build")
 LIB = os.path.join(PKG, "liblq.so")
-SOURCES = ["lq_kernels.cu", "lq_ff_hop0.cu", "lq_ff_hop1.cu", "lq_ff_hop2.cu", "lq_ff_vec.cu", "lq_update_bulk.cu", "lq_hop_x2.cu", "lq_eig.cu", "lq_nested.cu", "lq_newton.cu", "lq_deflate.cu", "lq_adjoint.cu", "lq_dense.cu", "lq_api.cu"]
+SOURCES = ["lq_kernels.cu", "lq_ff_hop0.cu", "lq_ff_hop1.cu", "lq_ff_hop2.cu", "lq_ff_vec.cu", "lq_update_bulk.cu", "lq_rebiorth.cu", "lq_hop_x2.cu", "lq_eig.cu", "lq_nested.cu", "lq_newton.cu", "lq_deflate.cu", "lq_adjoint.cu", "lq_dense.cu", "lq_api.cu"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 FLAGS = ["-O3", "-std=c++17", "-lineinfo", "-Xcompiler", "-fPIC", "-Xcompiler", "-O2"]
 

@@ -265,10 +265,13 @@ void free_workspace(lq_ctx* c) {
                    (void**)&c->nest_state, (void**)&c->nest_alpha, (void**)&c->nest_beta, (void**)&c->nest_delta, (void**)&c->nest_s,
                    (void**)&c->nest_q, (void**)&c->nest_norm, (void**)&c->nest_check, (void**)&c->nest_c,
                    &c->lbasis, (void**)&c->uscale, (void**)&c->adj_coef, &c->adj_nu, &c->adj_om,
-                   (void**)&c->adj_force, (void**)&c->adj_dmu, (void**)&c->gen_scr, (void**)&c->solve_ws};
+                   (void**)&c->adj_force, (void**)&c->adj_dmu, (void**)&c->gen_scr, (void**)&c->solve_ws,
+                   (void**)&c->rb_part, (void**)&c->rb_coef, (void**)&c->rb_coef_f};
     for (void** p : ps) { dfree(*p); *p = nullptr; }
     c->kmax = c->nsrc = c->block = c->ring = 0;
+    c->lbasis_nf = 0;
     c->adjoint = false;
+    c->rebiorth = false;
 }
 
 // Choose the stencil schedule for the Lanczos step: time each variant on the caller's data with
@@ -372,6 +375,12 @@ int nested_run(lq_ctx* c, const TslState* state, int kfix, int nb, int m, const 
 // and the recombination with the reports (enqueued, then completed).
 enum { FN_SIGN = 0, FN_RESOLVENT = 1 };
 
+// lq_opts.rebiorth = p: the pair made by the update of step j (v_{j+1}, w_{j+1}, counting from
+// v_0) is re-biorthogonalised when j + 1 or j is a multiple of p (j > 0): two consecutive pairs
+// per period, since the recurrence forms each new pair from the last two and a lone corrected
+// pair would hand the lost biorthogonality straight to the next one
+inline bool rb_corrects(int p, int j) { return p > 0 && ((j + 1) % p == 0 || (j > 0 && j % p == 0)); }
+
 struct TslRun {
     lq_ctx* c = nullptr;
     int nf = 1, emode = 0, nsrc = 0, fn = FN_SIGN;
@@ -386,6 +395,8 @@ struct TslRun {
 
     int k = 0, ring = 0;
     bool two = false;
+    int rb = 0;                // re-biorthogonalisation period (0: none)
+    bool keep_left = false;    // the left vectors are stored in c->lbasis (adjoint or re-biorthogonalisation)
     size_t F = 0, vstride = 0, sst = 0, cb = 0, sb = 0, sl = 0, sio = 0;
     InitArgs ia;
     HopArgs h;
@@ -429,7 +440,11 @@ struct TslRun {
         // of kTwoPassWindow vectors into y while they are still in the ring.
         two = o->two_pass != 0 && k > 1;
         ring = two ? std::min(slots, kTwoPassRing) : 0;
-        sst = (size_t)slots * F;                     // per source: stored left basis (NF = 1), ring or full
+        // lq_opts.rebiorth: the new pair is re-biorthogonalised every rb steps against the whole
+        // right basis and the stored left basis (sign and derivative solves; not the adjoint)
+        rb = (o->rebiorth > 0 && fn == FN_SIGN && !store_left && !two) ? o->rebiorth : 0;
+        keep_left = store_left || rb > 0;
+        sst = (size_t)slots * vstride;               // per source: stored left basis, ring or full
 
         // per-source arrays from source s0 on (a source group of a split run); the group's
         // last-block counters are a block of 3 nsrc from 3 s0 on
@@ -444,7 +459,7 @@ struct TslRun {
         ia.src_stride_basis = sb; ia.src_stride_left = sl; ia.state = state;
         ia.partials = partials; ia.partial_stride = c->partial_blocks; ia.counters = counters;
         ia.breakdown_tol = o->breakdown_tol;
-        if (store_left) { ia.w1_store = c->lbasis; ia.src_stride_store = sst; }
+        if (keep_left) { ia.w1_store = reinterpret_cast<char*>(c->lbasis) + (size_t)s0 * sst * cb; ia.src_stride_store = sst; }
         int r = args_only ? LQ_OK : init(st);
         if (r) return r;
 
@@ -454,7 +469,7 @@ struct TslRun {
         set_side(h, 1, c, 1, emode);
         h.state = state; h.partials = partials; h.partial_stride = c->partial_blocks; h.counters = counters;
         h.alpha = c->alpha + ks; h.scale = c->scale + ks; h.kmax = c->kmax; h.kmax_run = k;
-        h.uscale = store_left ? c->uscale : nullptr;
+        h.uscale = keep_left ? c->uscale + ks : nullptr;
         h.src_stride_in[0] = sb; h.src_stride_in[1] = sl;
         h.src_stride_out[0] = sio; h.src_stride_out[1] = sio;
         h.out[0] = ofs(c->rout, sio); h.out[1] = ofs(c->lout, sio);
@@ -483,6 +498,7 @@ struct TslRun {
         u.state = state; u.partials = partials; u.partial_stride = c->partial_blocks; u.counters = counters;
         u.beta = c->beta + ks; u.delta = c->delta + ks; u.kmax = c->kmax;
         u.bulk = o->update_variant != 0 ? 1 : 0;
+        if (keep_left) u.src_stride_store = sst;
 
         std::memset(&ra, 0, sizeof(ra));
         ra.V = c->V; ra.nsrc = nsrc; ra.basis = c->basis; ra.src_stride_basis = sb; ra.vec_stride = vstride;
@@ -527,24 +543,47 @@ struct TslRun {
                 u.j = j;
                 u.v_cur = bvec(j); u.v_prev = bvec(j > 0 ? j - 1 : j); u.v_next = bvec(j + 1);
                 u.w_cur = lvec(j); u.w_prev = lvec(j > 0 ? j - 1 : j); u.w_next = lvec(j + 1);
-                if (store_left) {
-                    u.w_store = reinterpret_cast<char*>(c->lbasis) + (size_t)(ring ? (j + 1) % ring : j + 1) * F * cb;
-                    u.src_stride_store = sst;
-                }
+                if (keep_left)
+                    u.w_store = reinterpret_cast<char*>(c->lbasis) + ((size_t)s0 * sst + (size_t)(ring ? (j + 1) % ring : j + 1) * vstride) * cb;
+                const bool rb_step = rb_corrects(rb, j);
+                u.defer = rb_step ? 1 : 0;
                 cudaEvent_t eu = prof_begin(c, ls);
                 LQ_CUDA(c, launch_update(c->prec, u, ls));
                 prof_end(c, PC_UPDATE, eu, ls);
                 c->launches += 1;
+                if (rb_step) {
+                    RbArgs b;
+                    std::memset(&b, 0, sizeof(b));
+                    b.u = u;
+                    b.m = j + 1;
+                    b.vbasis = bvec(0);
+                    b.wbasis = reinterpret_cast<char*>(c->lbasis) + (size_t)s0 * sst * cb;
+                    b.vec_stride = vstride;
+                    b.scale = c->scale + (size_t)s0 * c->kmax;
+                    b.uscale = c->uscale + (size_t)s0 * c->kmax;
+                    b.dot_blocks = rb_dot_blocks(vstride);
+                    b.part = c->rb_part + (size_t)s0 * c->kmax * b.dot_blocks * 8;
+                    b.coef = c->rb_coef + (size_t)s0 * 2 * c->kmax;
+                    b.coef_f = c->rb_coef_f + (size_t)s0 * 2 * c->kmax;
+                    cudaEvent_t eb = prof_begin(c, ls);
+                    LQ_CUDA(c, launch_rebiorth(c->prec, b, ls));
+                    prof_end(c, PC_UPDATE, eb, ls);
+                    c->launches += 3;
+                }
             }
         }
         return LQ_OK;
     }
 
     lq_ctx::GraphKey key(int groups = 1) const {
-        return {k, nsrc, nf, emode, h.variant, store_left ? 1 : 0, ring, c->desc.mu, groups, u.bulk};
+        return {k, nsrc, nf, emode, h.variant, store_left ? 1 : 0, ring, c->desc.mu, groups, u.bulk, rb};
     }
     bool graphed() const { return o->graph != 0 && !c->prof_on; }
-    long long loop_launches() const { return 2 * (long long)k - 1; }
+    long long loop_launches() const {
+        long long n = 2 * (long long)k - 1;
+        for (int j = 0; j + 1 < k; ++j) n += rb_corrects(rb, j) ? 3 : 0;
+        return n;
+    }
 
     int quad_pass(cudaStream_t st) {
         LQ_CUDA(c, cudaMemcpyAsync(c->quad_nodes, nodes.data(), sizeof(int) * nsrc, cudaMemcpyHostToDevice, st));
@@ -842,8 +881,11 @@ int run_tsl(lq_ctx* c, int nf, int emode, int nsrc, const lq_opts* o, lq_report*
     t.y0 = y0; t.y1 = y1; t.fn = fn; t.shifts = shifts; t.store_left = store_left;
     // lq_opts.split: the two source halves' Krylov loops as concurrent branches (the update of one
     // half, bandwidth-bound, overlaps the stencil of the other, issue-bound)
+    if (o->rebiorth > 0 && fn == FN_SIGN && !store_left && !(c->rebiorth && c->lbasis_nf >= nf))
+        return set_err(c, LQ_ERR_NOT_READY, "opts.rebiorth needs a workspace reserved with LQ_RESERVE_REBIORTH"
+                                            " (with LQ_RESERVE_BLOCK for the derivative)");
     const bool split = o->split != 0 && !c->prof_on && c->prec == LQ_MIXED && nf == 2 && fn == FN_SIGN && !store_left &&
-                       !(o->two_pass != 0 && o->kmax > 1) && nsrc >= 8 && nsrc % 2 == 0 &&
+                       !(o->two_pass != 0 && o->kmax > 1) && o->rebiorth <= 0 && nsrc >= 8 && nsrc % 2 == 0 &&
                        ensure_cap_stream(c) && ensure_cap_stream(c, true);
     int r;
     if (!split) {
@@ -964,6 +1006,8 @@ int check_opts(lq_ctx* c, const lq_opts* o, bool allow_deflate = false) {
     if (o->graph < -1 || o->graph > 1) return set_err(c, LQ_ERR_ARG, "graph must be -1, 0 or 1");
     if (o->split < -1 || o->split > 1) return set_err(c, LQ_ERR_ARG, "split must be -1, 0 or 1");
     if (o->update_variant < -1 || o->update_variant > 1) return set_err(c, LQ_ERR_ARG, "update_variant must be -1, 0 or 1");
+    if (o->rebiorth < 0) return set_err(c, LQ_ERR_ARG, "rebiorth must be >= 0");
+    if (o->rebiorth > 0 && o->two_pass) return set_err(c, LQ_ERR_ARG, "re-biorthogonalisation needs the whole bases: not with two_pass");
     if (c->ring > 0 && !o->two_pass && o->kmax > c->ring)
         return set_err(c, LQ_ERR_ARG, "workspace reserved for two-pass runs: set opts.two_pass = 1 or kmax <= " + std::to_string(c->ring));
     return LQ_OK;
@@ -1662,6 +1706,7 @@ void lq_default_opts(lq_opts* o) {
     o->split = -1;
     o->update_variant = -1;
     o->nested_m = 100;
+    o->rebiorth = 0;
 }
 
 int lq_create(const lq_lattice_desc* d, lq_ctx** out) {
@@ -1749,7 +1794,8 @@ int lq_set_mu(lq_ctx* c, double mu) {
 
 int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     if (c) c->defl_prep_ok = false;
-    if (!c || kmax < 1 || nsrc < 1 || (flags & ~(LQ_RESERVE_BLOCK | LQ_RESERVE_ADJOINT | LQ_RESERVE_TWO_PASS | LQ_RESERVE_SOLVE)))
+    if (!c || kmax < 1 || nsrc < 1 ||
+        (flags & ~(LQ_RESERVE_BLOCK | LQ_RESERVE_ADJOINT | LQ_RESERVE_TWO_PASS | LQ_RESERVE_SOLVE | LQ_RESERVE_REBIORTH)))
         return set_err(c, LQ_ERR_ARG, "invalid reserve arguments");
     free_workspace(c);
     const int block = (flags & LQ_RESERVE_BLOCK) ? 1 : 0;
@@ -1767,6 +1813,8 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
     };
     // the Krylov basis: kmax vectors per source, or a ring of kTwoPassRing for two-pass runs
     const int ring = ((flags & LQ_RESERVE_TWO_PASS) && kmax > kTwoPassRing) ? kTwoPassRing : 0;
+    const bool rbw = (flags & LQ_RESERVE_REBIORTH) != 0;
+    if (rbw && ring) return set_err(c, LQ_ERR_ARG, "LQ_RESERVE_REBIORTH needs the whole basis: not with a two-pass ring");
     if ((r = alloc_fields(&c->basis, (size_t)nsrc * (ring ? ring : kmax) * nf))) { free_workspace(c); return r; }
     if ((r = alloc_fields(&c->left, (size_t)nsrc * 3 * nf))) { free_workspace(c); return r; }
     if ((r = alloc_fields(&c->rout, (size_t)nsrc * nf))) { free_workspace(c); return r; }
@@ -1816,10 +1864,21 @@ int lq_reserve(lq_ctx* c, int kmax, int nsrc, int flags) {
         if ((r = dalloc(c, &c->gen_scr, c->gen_scr_doubles))) { free_workspace(c); return r; }
     }
     if ((flags & LQ_RESERVE_SOLVE) && (r = dalloc(c, &c->solve_ws, (size_t)9 * nsrc * c->V * 24))) { free_workspace(c); return r; }
+    if ((flags & LQ_RESERVE_ADJOINT) || rbw) {
+        // stored left basis: one field per vector for the adjoint, NF for the re-biorthogonalisation
+        c->lbasis_nf = rbw ? nf : 1;
+        if ((r = alloc_fields(&c->lbasis, (size_t)nsrc * (ring ? ring : kmax) * c->lbasis_nf))) { free_workspace(c); return r; }
+        if ((r = dalloc(c, &c->uscale, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
+    }
+    if (rbw) {
+        const size_t nelem = (size_t)nf * fe(c);
+        if ((r = dalloc(c, &c->rb_part, (size_t)nsrc * kmax * rb_dot_blocks(nelem) * 8))) { free_workspace(c); return r; }
+        if ((r = dalloc(c, &c->rb_coef, (size_t)nsrc * 2 * kmax))) { free_workspace(c); return r; }
+        if ((r = dalloc(c, &c->rb_coef_f, (size_t)nsrc * 2 * kmax))) { free_workspace(c); return r; }
+        c->rebiorth = true;
+    }
     if (flags & LQ_RESERVE_ADJOINT) {
         const int np = 2 * kQuadMaxNodes;
-        if ((r = alloc_fields(&c->lbasis, (size_t)nsrc * (ring ? ring : kmax)))) { free_workspace(c); return r; }
-        if ((r = dalloc(c, &c->uscale, (size_t)nsrc * kmax))) { free_workspace(c); return r; }
         if ((r = dalloc(c, &c->adj_coef, (size_t)2 * np * kmax))) { free_workspace(c); return r; }
         if ((r = alloc_fields(&c->adj_nu, (size_t)np))) { free_workspace(c); return r; }
         if ((r = alloc_fields(&c->adj_om, (size_t)np))) { free_workspace(c); return r; }
@@ -2249,6 +2308,7 @@ int lq_batch_apply(const lq_batch_item* items, int n, void* stream) {
         int r = check_ready(c, it.nsrc, it.dir ? 1 : 0);
         if (r || (r = check_opts(c, it.opts))) return r;
         if (it.opts->two_pass) return set_err(c, LQ_ERR_ARG, "two-pass runs are not batched");
+        if (it.opts->rebiorth > 0) return set_err(c, LQ_ERR_ARG, "re-biorthogonalised runs are not batched");
         if (!ensure_cap_stream(c)) return set_err(c, LQ_ERR_CUDA, "cannot create the member's stream");
     }
     cudaStream_t st = (cudaStream_t)stream;
@@ -2602,6 +2662,7 @@ int lq_sign_bilinear_grad(lq_ctx* c, const double* x, const double* y, const lq_
     if (!c->adjoint) return set_err(c, LQ_ERR_NOT_READY, "workspace reserved without LQ_RESERVE_ADJOINT");
     int r = check_ready(c, 2, 0);
     if (r || (r = check_opts(c, o, true))) return r;
+    if (o->rebiorth > 0) return set_err(c, LQ_ERR_ARG, "re-biorthogonalisation is not available for the adjoint");
     const int l = o->deflate ? c->defl_l : 0;
     const bool two = o->two_pass != 0 && o->kmax > 1;
     if (two && l > 0) return set_err(c, LQ_ERR_ARG, "the two-pass adjoint runs without deflation");

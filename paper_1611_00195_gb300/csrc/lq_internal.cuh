@@ -184,6 +184,8 @@ struct TslState {
     double2 cv[3];                     // update coefficients (right) for the current step
     double2 cw[3];                     // update coefficients (left)
     double breakdown_tol;
+    double rb_nr, rb_nl;               // |B vh_j|^2, |B^dag wh_j|^2 of an update whose scalar step
+                                       // waits for the re-biorthogonalisation
 };
 
 // Per-source slices of the projected tridiagonal T_k: alpha[k], beta[k], delta[k], scale[k]
@@ -259,8 +261,14 @@ struct lq_ctx {
     size_t nx_partial_blocks = 0;
 
     // adjoint workspace (lq_reserve flag LQ_RESERVE_ADJOINT)
-    void* lbasis = nullptr;          // [nsrc][kmax] left Lanczos vectors (NF = 1)
+    void* lbasis = nullptr;          // [nsrc][kmax][lbasis_nf] left Lanczos vectors
+    int lbasis_nf = 0;               // fields per stored left vector: 1 (adjoint), NF (re-biorthogonalisation)
     double2* uscale = nullptr;       // [nsrc][kmax] left scales
+    // re-biorthogonalisation workspace (lq_reserve flag LQ_RESERVE_REBIORTH)
+    double* rb_part = nullptr;       // [nsrc][kmax][rb_dot_blocks][8]
+    double2* rb_coef = nullptr;      // [nsrc][2][kmax]
+    float4* rb_coef_f = nullptr;     // [nsrc][2][kmax]
+    bool rebiorth = false;
     double2* adj_coef = nullptr;     // [2][2 * kQuadMaxNodes][kmax]
     void* adj_nu = nullptr;          // [2 * kQuadMaxNodes] fields
     void* adj_om = nullptr;          // [2 * kQuadMaxNodes] fields
@@ -302,10 +310,11 @@ struct lq_ctx {
         double mu;
         int groups;        // source groups run as concurrent branches (1: none)
         int update;        // update kernel (UpdArgs.bulk)
+        int rebiorth;      // re-biorthogonalisation period (0: none)
         bool operator==(const GraphKey& o) const {
             return k == o.k && nsrc == o.nsrc && nf == o.nf && emode == o.emode && variant == o.variant &&
                    store_left == o.store_left && ring == o.ring && mu == o.mu && groups == o.groups &&
-                   update == o.update;
+                   update == o.update && rebiorth == o.rebiorth;
         }
     };
     struct GraphEntry { GraphKey key; cudaGraphExec_t exec; };

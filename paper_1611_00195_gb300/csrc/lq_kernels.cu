@@ -492,7 +492,7 @@ unsigned update_grid(size_t nelem, int nsrc, size_t cap) {
 }
 
 cudaError_t launch_update(int prec, const UpdArgs& a, cudaStream_t st) {
-    if (prec == LQ_MIXED && a.bulk && update_bulk_ready()) return launch_update_bulk(a, st);
+    if (prec == LQ_MIXED && a.bulk && !a.defer && update_bulk_ready()) return launch_update_bulk(a, st);
     dim3 grid(update_grid(a.nelem, a.nsrc, a.partial_stride), (unsigned)a.nsrc);
     if (prec == LQ_FP64) k_update<double><<<grid, kUpdThreads, 0, st>>>(a);
     else if (prec == LQ_FLOAT_FLOAT) return launch_update_ff(a, grid, st);

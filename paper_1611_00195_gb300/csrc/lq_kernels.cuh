@@ -246,7 +246,10 @@ __global__ void __launch_bounds__(kUpdThreads, 3) k_update(UpdArgs a) {
     if (last_block(a.counters + a.nsrc + src, gridDim.x)) {
         double res[6];
         reduce_partials<6>(a.partials + (size_t)src * a.partial_stride * 12, gridDim.x, res, smem);
-        if (threadIdx.x == 0) update_scalars<R>(a, src, res);
+        if (threadIdx.x == 0) {
+            if (a.defer) { st.rb_nr = res[4]; st.rb_nl = res[5]; }
+            else update_scalars<R>(a, src, res);
+        }
     }
 }
 

@@ -66,6 +66,8 @@ struct UpdArgs {
     double* delta;
     int kmax;
     int bulk;              // FP32: 1 = k_update_bulk (inputs staged by bulk copies), 0 = k_update
+    int defer;             // 1: keep the norm terms in the state and leave the scalar step to the
+                           // re-biorthogonalisation that follows (k_update only)
 };
 
 struct InitArgs {
@@ -155,6 +157,30 @@ cudaError_t launch_update_bulk(const UpdArgs& a, cudaStream_t st);
 bool update_bulk_ready();                 // opts in to its shared memory (once); false: unavailable
 unsigned update_bulk_grid(size_t nelem, int nsrc, size_t cap);
 void update_bulk_prepare();               // every one-time device query, before a stream capture
+// Periodic re-biorthogonalisation of the new Lanczos pair (lq_rebiorth.cu): the pair written by
+// an update with defer = 1 is projected against the m earlier pairs, then omega and the scalar
+// step are formed from the corrected pair.  Needs the whole right basis and the stored left
+// basis (a full left basis: LQ_RESERVE_REBIORTH).
+constexpr int kRbThreads = 256;
+constexpr int kRbPerThread = 4;           // chunks of each new vector a dot thread holds
+inline unsigned rb_dot_blocks(size_t nelem) {
+    const size_t per = (size_t)kRbThreads * kRbPerThread;
+    return (unsigned)(nelem == 0 ? 1 : (nelem + per - 1) / per);
+}
+struct RbArgs {
+    UpdArgs u;             // the update of this step: new pair slots, state, scalars, partials
+    int m;                 // earlier pairs: j + 1
+    const void* vbasis;    // right basis vh_0 ..: per source u.src_stride_basis (Chunk units)
+    const void* wbasis;    // stored left basis wh_0 ..: per source u.src_stride_store
+    size_t vec_stride;     // Chunk elements per basis vector
+    const double* scale;   // s_i [src][kmax]
+    const double2* uscale; // u_i [src][kmax]
+    double* part;          // [src][kmax][dot_blocks][8] block sums of the dots
+    unsigned dot_blocks;   // rb_dot_blocks(u.nelem)
+    double2* coef;         // [src][2][kmax]: c_i (right), d_i (left)
+    float4* coef_f;        // the same split into float-float (re.hi, re.lo, im.hi, im.lo)
+};
+cudaError_t launch_rebiorth(int prec, const RbArgs& a, cudaStream_t st);
 // Deflation vector algebra on FP64 boundary-layout vectors (lq_deflate.cu).  Sizes and strides
 // are in doubles (2 per complex number).
 cudaError_t launch_bdots(const double* X, size_t xs, int nx, const double* Y, size_t ys, int ny, size_t n,

@@ -56,7 +56,7 @@ class Opts(ctypes.Structure):
                 ("quad_nodes", ctypes.c_int), ("proj_tol", ctypes.c_double), ("hop_variant", ctypes.c_int),
                 ("defl_kmax", ctypes.c_int), ("defl_nderiv", ctypes.c_int), ("two_pass", ctypes.c_int),
                 ("graph", ctypes.c_int), ("split", ctypes.c_int), ("nested_m", ctypes.c_int),
-                ("update_variant", ctypes.c_int)]
+                ("update_variant", ctypes.c_int), ("rebiorth", ctypes.c_int)]
 
 
 class Report(ctypes.Structure):
@@ -342,8 +342,9 @@ class Context:
         self._check(self._L.lq_set_mu(self._h, float(mu)))
         self.mu = float(mu)
 
-    def reserve(self, kmax, nsrc, block=True, adjoint=False, two_pass=False, solve=False):
-        flags = (1 if block else 0) | (2 if adjoint else 0) | (4 if two_pass else 0) | (8 if solve else 0)
+    def reserve(self, kmax, nsrc, block=True, adjoint=False, two_pass=False, solve=False, rebiorth=False):
+        flags = ((1 if block else 0) | (2 if adjoint else 0) | (4 if two_pass else 0) | (8 if solve else 0)
+                 | (16 if rebiorth else 0))
         self._check(self._L.lq_reserve(self._h, int(kmax), int(nsrc), int(flags)))
 
     def _direction(self, kind, field):
@@ -377,7 +378,7 @@ class Context:
     @staticmethod
     def opts(k, breakdown_tol=1e-14, newton_max_iter=50, newton_tol=1e-13, projected=LQ_PROJ_AUTO, quad_nodes=64,
              proj_tol=1e-11, hop_variant=-1, deflate=0, defl_kmax=0, defl_nderiv=0, two_pass=0, graph=-1, split=-1,
-             nested_m=100, update_variant=-1):
+             nested_m=100, update_variant=-1, rebiorth=0):
         o = Opts()
         lib().lq_default_opts(ctypes.byref(o))
         o.kmax = int(k)
@@ -396,6 +397,7 @@ class Context:
         o.split = int(split)
         o.nested_m = int(nested_m)
         o.update_variant = int(update_variant)
+        o.rebiorth = int(rebiorth)
         return o
 
     def sign_apply(self, x, k, out=None, **kw):

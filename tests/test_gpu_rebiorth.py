@@ -1,0 +1,167 @@
+"""GPU parity of the periodic re-biorthogonalisation of the two-sided Lanczos process
+(lq_opts.rebiorth = p: two consecutive pairs per period projected against all earlier pairs;
+Sec. 2's process with the correction the oracle states):
+  * exactness at k = n on 4x2^3 (n = 384, a complete Krylov space): FP64 and float-float with
+    p = 1 and p = 10 return the exact sgn(H) x of the oracle's dense ordered-Schur sign, which the
+    plain process misses by about 2e-7;
+  * same-depth parity with the oracle's corrected process (4x2^3, k = 60, p = 6): the sign in FP64
+    and the derivative of Eq. (2.6) in FP64, FP32 and float-float, each within its precision's
+    factor of the oracle's own rounding sensitivity, and the early T entries to 1e-12 in FP64;
+  * the corrected Krylov loop replayed from its CUDA graph equals plain launches bitwise;
+  * argument errors, with the context usable afterwards."""
+import numpy as np
+import pytest
+import torch
+
+import synthetic as syn
+from oracle import dirac as od
+from oracle import sign as osg
+from oracle import tsl as ot
+from tests.helpers import (FF_SENS_FACTOR, FF_STEP_NOISE, FP32_SENS_FACTOR, FP64_SENS_FACTOR, oracle_ops,
+                           relerr)
+
+pytestmark = pytest.mark.gpu
+DIMS, EPS, GSEED, SSEED, MU = (4, 2, 2, 2), 0.4, 3, 5, 0.3
+
+
+def _ctx(lq, prec, k, nsrc, block, rebiorth=True):
+    U = syn.gauge_field(DIMS, EPS, GSEED)
+    c = lq.Context(DIMS, mu=MU, precision=prec)
+    c.upload_gauge(torch.from_numpy(U).cuda())
+    c.reserve(k, nsrc, block, rebiorth=rebiorth)
+    return c, U
+
+
+def _noisy(ops, size, seed):
+    """The oracle's operators with relative noise of the given size on every application."""
+    rng = np.random.default_rng(seed)
+
+    def wrap(op):
+        def f(v):
+            y = op(v)
+            return y * (1 + size * (rng.standard_normal(y.shape) + 1j * rng.standard_normal(y.shape)) / np.sqrt(2))
+        return f
+    return [wrap(op) for op in ops]
+
+
+@pytest.mark.parametrize("prec_name", ["LQ_FP64", "LQ_FLOAT_FLOAT"])
+def test_rebiorth_exact_at_full_dimension(lqlib, prec_name):
+    from paper_1611_00195_gb300 import lq
+    prec = getattr(lq, prec_name)
+    lat = od.Lattice(DIMS)
+    k = lat.n
+    c, U = _ctx(lq, prec, k, 1, False)
+    x = syn.gaussian_source(DIMS, SSEED, nsrc=1)
+    exact = osg.sign_schur(od.dense_H(lat, U, MU)) @ x[0].ravel()
+    xt = torch.from_numpy(x).cuda()
+    # the projected sign by the Newton iteration (to 1e-13), not the quadrature accepted at 1e-11
+    y0, rep0 = c.sign_apply(xt, k, projected=lq.LQ_PROJ_NEWTON)
+    e0 = relerr(y0[0].cpu().numpy(), exact)
+    for p in (1, 10):
+        y, rep = c.sign_apply(xt, k, rebiorth=p, projected=lq.LQ_PROJ_NEWTON)
+        e = relerr(y[0].cpu().numpy(), exact)
+        print("%s 4x2^3 k = n = %d: rebiorth %d err %.3g (plain %.3g, status %d)" % (prec_name, k, p, e, e0, rep0[0]["status"]))
+        assert rep[0]["status"] == 0 and rep[0]["k_eff"] == k
+        assert e < 1e-11
+
+
+def _oracle_deriv(x, k, p, pert=None, seed=0):
+    lat, A, Ah, E, Eh = oracle_ops(DIMS, syn.gauge_field(DIMS, EPS, GSEED), MU)
+    if pert == "input":
+        rng = np.random.default_rng(seed)
+        x = x * (1 + 1e-16 * rng.standard_normal(x.shape))
+    elif pert is not None:
+        A, Ah, E, Eh = _noisy((A, Ah, E, Eh), pert, seed)
+    rd, rs, r = ot.tsl_sign_derivative(A, Ah, E, Eh, x, k, rebiorth=p)
+    return rd, rs, r
+
+
+@pytest.mark.parametrize("prec_name", ["LQ_FP64", "LQ_MIXED", "LQ_FLOAT_FLOAT"])
+def test_rebiorth_derivative_parity(lqlib, prec_name):
+    from paper_1611_00195_gb300 import lq
+    prec = getattr(lq, prec_name)
+    k, p, nsrc = 60, 6, 2
+    c, U = _ctx(lq, prec, k, nsrc, True)
+    x = syn.gaussian_source(DIMS, SSEED, nsrc=nsrc)
+    ys, yd, rep = c.sign_derivative_apply(torch.from_numpy(x).cuda(), k, rebiorth=p)
+    ys, yd = ys.cpu().numpy(), yd.cpu().numpy()
+    pert, factor, floor = {"LQ_FP64": ("input", FP64_SENS_FACTOR, 1e-11),
+                           "LQ_MIXED": (6e-8, FP32_SENS_FACTOR, 1e-6),
+                           "LQ_FLOAT_FLOAT": (FF_STEP_NOISE, FF_SENS_FACTOR, 1e-12)}[prec_name]
+    for s in range(nsrc):
+        xs = x[s].ravel()
+        rd, rs, r = _oracle_deriv(xs, k, p)
+        pd, ps, _ = _oracle_deriv(xs, k, p, pert, seed=11 + s)
+        sens = max(relerr(pd, rd), relerr(ps, rs))
+        errs = [relerr(ys[s], rs), relerr(yd[s], rd)]
+        print("%s rebiorth %d k=%d source %d: sign %.3g deriv %.3g (sensitivity %.3g, ratio %.2f)"
+              % (prec_name, p, k, s, errs[0], errs[1], sens, max(errs) / sens))
+        assert rep[s]["status"] == 0 and rep[s]["k_eff"] == k
+        assert max(errs) < max(floor, factor * sens)
+
+
+def test_rebiorth_sign_fp64_parity_and_coefficients(lqlib):
+    from paper_1611_00195_gb300 import lq
+    k, p, nsrc = 60, 6, 2
+    c, U = _ctx(lq, lq.LQ_FP64, k, nsrc, False)
+    x = syn.gaussian_source(DIMS, SSEED, nsrc=nsrc)
+    y, rep = c.sign_apply(torch.from_numpy(x).cuda(), k, rebiorth=p)
+    y = y.cpu().numpy()
+    lat, A, Ah, E, Eh = oracle_ops(DIMS, U, MU)
+    for s in range(nsrc):
+        ref, r = ot.tsl_sign(A, Ah, x[s].ravel(), k, rebiorth=p)
+        al, be, de = c.tsl_coefficients(s, k)
+        m = 12   # steps 5, 6 and 11, 12 are corrected
+        assert np.abs(al[:m] - r["alpha"][:m]).max() < 1e-12 * np.abs(r["alpha"][:m]).max()
+        assert np.abs(de[:m - 1] - r["delta"][:m - 1]).max() < 1e-12 * np.abs(r["delta"][:m - 1]).max()
+        assert np.abs(be[:m - 1] - r["beta"][:m - 1]).max() < 1e-12 * np.abs(r["beta"][:m - 1]).max()
+        rng = np.random.default_rng(99)
+        xp = x[s].ravel() * (1 + 1e-16 * rng.standard_normal(x[s].size))
+        sens = relerr(ot.tsl_sign(A, Ah, xp, k, rebiorth=p)[0], ref)
+        err = relerr(y[s], ref)
+        print("FP64 sign rebiorth %d k=%d source %d: err %.3g (sensitivity %.3g)" % (p, k, s, err, sens))
+        assert rep[s]["status"] == 0
+        assert err < max(1e-11, FP64_SENS_FACTOR * sens)
+
+
+def test_rebiorth_graph_equals_plain_launches(lqlib):
+    from paper_1611_00195_gb300 import lq
+    k, nsrc = 40, 2
+    c, U = _ctx(lq, lq.LQ_MIXED, k, nsrc, True)
+    x = torch.from_numpy(syn.gaussian_source(DIMS, SSEED, nsrc=nsrc)).cuda()
+    a = c.sign_derivative_apply(x, k, rebiorth=5, graph=1)
+    b = c.sign_derivative_apply(x, k, rebiorth=5, graph=0)
+    d = c.sign_derivative_apply(x, k, rebiorth=0, graph=1)
+    assert torch.equal(a[0], b[0]) and torch.equal(a[1], b[1])
+    assert not torch.equal(a[1], d[1])       # the corrections do change the process
+
+
+def test_rebiorth_argument_errors(lqlib):
+    from paper_1611_00195_gb300 import lq
+    k = 20
+    x = torch.from_numpy(syn.gaussian_source(DIMS, SSEED, nsrc=2)).cuda()
+    c, U = _ctx(lq, lq.LQ_FP64, k, 2, False, rebiorth=False)
+    with pytest.raises(lq.LQError) as e:
+        c.sign_apply(x, k, rebiorth=3)          # workspace without the left basis
+    assert e.value.code == -8
+    c, U = _ctx(lq, lq.LQ_FP64, k, 2, False)
+    with pytest.raises(lq.LQError) as e:
+        c.sign_apply(x, k, rebiorth=-1)
+    assert e.value.code == -1
+    with pytest.raises(lq.LQError) as e:
+        c.sign_apply(x, k, rebiorth=3, two_pass=1)
+    assert e.value.code == -1
+    with pytest.raises(lq.LQError) as e:
+        lq.batch_apply([dict(ctx=c, x=x, k=k, kind=None, rebiorth=3)])
+    assert e.value.code == -1
+    y, rep = c.sign_apply(x, k, rebiorth=3)     # still usable
+    assert rep[0]["status"] == 0
+    with pytest.raises(lq.LQError) as e:
+        c.reserve(64, 1, False, two_pass=True, rebiorth=True)
+    assert e.value.code == -1
+    ca = lq.Context(DIMS, mu=MU, precision=lq.LQ_FP64)
+    ca.upload_gauge(torch.from_numpy(U).cuda())
+    ca.reserve(k, 2, False, adjoint=True, rebiorth=True)
+    with pytest.raises(lq.LQError) as e:
+        ca.bilinear_grad(x[0], x[1], k, rebiorth=3)
+    assert e.value.code == -1
