@@ -62,7 +62,9 @@ def test_rebiorth_exact_at_full_dimension(lqlib, prec_name):
         e = relerr(y[0].cpu().numpy(), exact)
         print("%s 4x2^3 k = n = %d: rebiorth %d err %.3g (plain %.3g, status %d)" % (prec_name, k, p, e, e0, rep0[0]["status"]))
         assert rep[0]["status"] == 0 and rep[0]["k_eff"] == k
-        assert e < 1e-11
+        # measured on the GB300: 2.0-2.1e-13 (FP64) and 4.1-4.8e-12 (float-float); the oracle's own
+        # process reaches 1.3e-13 / 3.1e-13 in FP64 (p = 1 / 10)
+        assert e < (1e-12 if prec == lq.LQ_FP64 else 1.5e-11)
 
 
 def _oracle_deriv(x, k, p, pert=None, seed=0):
