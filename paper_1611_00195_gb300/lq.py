@@ -34,6 +34,7 @@ LQ_FP64, LQ_MIXED, LQ_MIXED_BF16, LQ_FLOAT_FLOAT = 0, 1, 2, 3
 LQ_DIR_MU, LQ_DIR_SU3, LQ_DIR_U1 = 0, 1, 2
 LQ_PROJ_AUTO, LQ_PROJ_NEWTON, LQ_PROJ_QUAD, LQ_PROJ_NESTED = 0, 1, 2, 3
 LQ_EIG_SHIFT_INVERT, LQ_EIG_CHEBYSHEV = 0, 1
+LQ_RESERVE_BLOCK, LQ_RESERVE_ADJOINT, LQ_RESERVE_TWO_PASS, LQ_RESERVE_SOLVE, LQ_RESERVE_REBIORTH = 1, 2, 4, 8, 16
 
 EXPORTED = ["lq_default_opts", "lq_create", "lq_destroy", "lq_last_error", "lq_upload_gauge", "lq_set_mu",
             "lq_reserve", "lq_apply_H", "lq_set_direction", "lq_apply_block", "lq_sign_apply",
@@ -343,8 +344,9 @@ class Context:
         self.mu = float(mu)
 
     def reserve(self, kmax, nsrc, block=True, adjoint=False, two_pass=False, solve=False, rebiorth=False):
-        flags = ((1 if block else 0) | (2 if adjoint else 0) | (4 if two_pass else 0) | (8 if solve else 0)
-                 | (16 if rebiorth else 0))
+        flags = ((LQ_RESERVE_BLOCK if block else 0) | (LQ_RESERVE_ADJOINT if adjoint else 0)
+                 | (LQ_RESERVE_TWO_PASS if two_pass else 0) | (LQ_RESERVE_SOLVE if solve else 0)
+                 | (LQ_RESERVE_REBIORTH if rebiorth else 0))
         self._check(self._L.lq_reserve(self._h, int(kmax), int(nsrc), int(flags)))
 
     def _direction(self, kind, field):

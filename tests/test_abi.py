@@ -46,6 +46,43 @@ def test_binding_registers_every_declared_symbol(built_lib):
         assert getattr(L, name).argtypes is not None, name
 
 
+def _header_struct(name):
+    """Field names, in order, of `typedef struct { ... } name;` in include/lq.h."""
+    src = open(os.path.join(ROOT, "include", "lq.h")).read()
+    src = re.sub(r"/\*.*?\*/", "", src, flags=re.S)
+    body = re.search(r"typedef struct \{([^}]*)\}\s*%s;" % name, src).group(1)
+    names = []
+    for decl in body.split(";"):
+        decl = decl.strip()
+        if decl:
+            parts = decl.split(None, 1)[1] if not decl.startswith("const") else decl.split(None, 2)[2]
+            names += [d.strip().lstrip("*").strip() for d in parts.split(",")]
+    return names
+
+
+@pytest.mark.parametrize("struct,cls", [("lq_opts", "Opts"), ("lq_lattice_desc", "LatticeDesc"), ("lq_report", "Report")])
+def test_binding_structs_mirror_the_header(struct, cls):
+    from paper_1611_00195_gb300 import lq
+    assert [f for f, _ in getattr(lq, cls)._fields_] == _header_struct(struct)
+
+
+def test_default_opts_and_reserve_flags(built_lib):
+    """lq_default_opts (host only) writes every field of the binding's mirror of lq_opts, and the
+    binding's reserve flags are the header's."""
+    from paper_1611_00195_gb300 import lq
+    o = lq.Opts()
+    ctypes.memset(ctypes.byref(o), 0x7f, ctypes.sizeof(o))
+    lq.lib().lq_default_opts(ctypes.byref(o))
+    want = dict(kmax=0, breakdown_tol=1e-14, newton_max_iter=50, newton_tol=1e-13, deflate=0, projected=0, quad_nodes=64,
+                proj_tol=1e-11, hop_variant=-1, defl_kmax=0, defl_nderiv=0, two_pass=0, graph=-1, split=-1, nested_m=100,
+                update_variant=-1, rebiorth=0)
+    assert {f: getattr(o, f) for f, _ in o._fields_} == want
+    src = open(os.path.join(ROOT, "include", "lq.h")).read()
+    for name in ("BLOCK", "ADJOINT", "TWO_PASS", "SOLVE", "REBIORTH"):
+        m = re.search(r"#define LQ_RESERVE_%s\s+(\d+)" % name, src)
+        assert int(m.group(1)) == getattr(lq, "LQ_RESERVE_" + name), name
+
+
 def test_create_rejects_bad_descriptors_without_gpu(built_lib):
     """lq_create validates on the host and allocates nothing on the device."""
     from paper_1611_00195_gb300 import lq
