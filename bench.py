@@ -155,6 +155,22 @@ def cpu_baseline(iters, k, workers=None):
     return P / per_solve, P, desc
 
 
+def solve_level(V, nsrc, k, ms_step, peak):
+    """Solve-level effective bandwidth of one step of nsrc derivative solves at depth k: the
+    algorithmic bytes of every kernel of the step over the step's time.  FP32 block vectors, 96 B
+    per site and field: k stencil launches (4 fields in and 4 out per source, the links once), k - 1
+    updates (12 fields read and 4 written per source), the recombination (the k block vectors of
+    the basis read once) and the two FP64 outputs (192 B per site each)."""
+    f = 96 * V
+    parts = {"stencil": k * (8 * f * nsrc + 288 * V),
+             "update": (k - 1) * 16 * f * nsrc,
+             "recombination": k * 2 * f * nsrc + 2 * 192 * V * nsrc}
+    total = sum(parts.values())
+    gbs = total / (ms_step * 1e-3) / 1e9
+    return {"bytes_per_step": total, "bytes_by_kernel": parts, "achieved": gbs, "unit": "GB/s",
+            "frac": gbs / peak, "note": "algorithmic bytes of the whole step over its time (value's timing)"}
+
+
 # ------------------------------------------------------------------------------------------
 # GPU clocks sampled during the timed region
 # ------------------------------------------------------------------------------------------
@@ -804,6 +820,7 @@ def main():
                                   "registers: long-scoreboard waits and FP32 issue, not DRAM (traffic 0.91x algorithmic, "
                                   "DRAM at 22% of its peak); two concurrent half batches take as long as one full batch, "
                                   "so no idle resource is left to fill"},
+        "solve_level": solve_level(V, nsrc, k, ms / args.steps, peak),
         "cpu_baseline": cpu,
         "e2e": e2e,
         "gpu_launches": int(launches),
