@@ -13,9 +13,14 @@ Printed (one JSON line, rank 0):
   e2e        the same through the C ABI with pinned HOST buffers (copies inside the region)
   roofline   the stencil kernel (dominant): algorithmic bytes per launch / event-timed launch
              duration against the measured HBM copy bandwidth
+  solve_level  every kernel's algorithmic bytes per step over the step's time
   cpu_baseline  the FP64 CPU oracle on a bounded sample of the same workload, one process per
              host core (each on its own source)
   fp64_path  the plain FP64 GPU path on the same workload, and the mixed-vs-FP64 error
+             (float-float path inside it)
+  other_workloads  su(3) direction, k = 800, two-pass, re-biorthogonalisation, nested projected
+             sign, BF16 links, the batching and ragged workloads, the precision and
+             differentiation workloads, the converged depth and the axial current
 
 `--impl reference` times the CPU oracle alone (rank 0) on the same workload and metric.
 """
